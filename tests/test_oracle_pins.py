@@ -1,0 +1,331 @@
+"""Pins of the FP64 scalar-CSR oracle against what the paper and the
+mathematics fix.  Every oracle function is tied here to something other than
+its own formula: the paper's worked example (Sec. 2), hand-worked
+aggregations, closed forms, invariants of smoothed aggregation with rigid-body
+modes (Sec. 2, Alg. 1), library routines for special cases, and dense direct
+solves (Eq. 1).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as o
+import q1elasticity as q
+
+
+# ---------------------------------------------------------------- Sec. 2 example
+def test_worked_example_unblock_matches_paper(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "sec2_block_example.json")))
+    b = g["block"]
+    A = o.unblock(g["bsr"]["ptr"], g["bsr"]["col"], np.array(g["bsr"]["val"]).reshape(-1, b * b),
+                  b, b)
+    assert A.ptr.tolist() == g["csr"]["ptr"]
+    assert A.col.tolist() == g["csr"]["col"]
+    assert A.val.tolist() == g["csr"]["val"]
+    assert np.array_equal(A.to_dense(), np.array(g["dense"]))
+    # four times fewer logical values, half the rows (Sec. 2)
+    assert len(g["bsr"]["col"]) * 4 == len(g["csr"]["col"])
+
+
+def test_worked_example_spmv(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "sec2_block_example.json")))
+    A = o.CSR(g["csr"]["ptr"], g["csr"]["col"], g["csr"]["val"], (6, 6))
+    x = np.arange(1.0, 7.0)
+    np.testing.assert_allclose(o.spmv(A, x), np.array(g["dense"]) @ x, rtol=1e-15)
+
+
+def test_unblock_keeps_explicit_zeros():
+    # a block with absent scalars: the scalar view keeps all of them as
+    # explicit zeros (the block pattern stays the scalar pattern)
+    val = np.array([[1.0, 0.0, 0.0, 2.0]])
+    A = o.unblock([0, 1], [0], val, 2, 2)
+    assert A.nnz == 4 and A.val.tolist() == [1.0, 0.0, 0.0, 2.0]
+
+
+# ---------------------------------------------------------------- strength, aggregation
+def _graph_matrix(case):
+    n = case["n"]
+    D = np.diag(case.get("diag", [1.0] * n))
+    for i, j, v in case["sym"]:
+        D[i, j] = D[j, i] = v
+    for i, j, v in case["directed"]:
+        D[i, j] = v
+    ptr = [0]
+    col, val = [], []
+    for i in range(n):
+        nz = np.nonzero(D[i])[0]
+        col += nz.tolist()
+        val += D[i, nz].tolist()
+        ptr.append(len(col))
+    return o.CSR(ptr, col, val, (n, n))
+
+
+def test_aggregation_hand_worked(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "aggregation_graphs.json")))
+    for case in g["cases"]:
+        agg, nagg = o.aggregate(_graph_matrix(case), 1, 0.08)
+        assert agg.tolist() == case["agg"], case["name"]
+        assert nagg == case["nagg"], case["name"]
+
+
+def test_strength_norms_and_eps_zero():
+    p = q.cube(3)
+    A = o.from_problem(p)
+    G = o.strength(A, 3, 0.0)
+    # node pattern = block pattern of the generator; norms = Frobenius^2
+    assert np.array_equal(G["ptr"], p.row_ptr.astype(np.int64))
+    assert np.array_equal(G["col"], p.col)
+    np.testing.assert_allclose(G["norm2"], np.linalg.norm(p.val, axis=(1, 2)) ** 2, rtol=1e-14)
+    rows = np.repeat(np.arange(p.nnodes), np.diff(p.row_ptr))
+    # eps = 0: every present off-diagonal block with a non-zero entry is strong
+    assert np.array_equal(G["strong"].astype(bool), (G["col"] != rows) & (G["norm2"] > 0))
+
+
+def test_strength_monotone_in_eps():
+    A = o.from_problem(q.inclusions(6))
+    prev = None
+    for eps in (0.0, 0.04, 0.08, 0.16, 0.5):
+        s = o.strength(A, 3, eps)["strong"].astype(bool)
+        if prev is not None:
+            assert not (s & ~prev).any()
+        prev = s
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (5, 3, 7)])
+def test_aggregates_partition_nonisolated_nodes(shape):
+    p = q.make_problem(shape, traction=(0, 0, -1), inclusion_frac=0.2)
+    A = o.from_problem(p)
+    G = o.strength(A, 3, 0.08)
+    agg, nagg = o.aggregate(A, 3, 0.08)
+    rows = np.repeat(np.arange(p.nnodes), np.diff(G["ptr"]))
+    has_strong = np.bincount(rows, weights=G["strong"], minlength=p.nnodes) > 0
+    assert np.array_equal(agg >= 0, has_strong)        # isolated <=> no strong neighbour
+    assert set(np.unique(agg[agg >= 0])) == set(range(nagg))  # ids 0..nagg-1 all used
+    clamped = p.coords[:, 0] == 0.0
+    assert (agg[clamped] == -1).all()                  # clamped nodes are isolated
+    # every aggregate is connected through strong links (each pass grows an
+    # aggregate only along strong connections)
+    import scipy.sparse as sp
+    import scipy.sparse.csgraph as cg
+    S = sp.csr_matrix((G["strong"].astype(float), G["col"], G["ptr"]), shape=(p.nnodes,) * 2)
+    S = S + S.T
+    for k in range(nagg):
+        m = np.nonzero(agg == k)[0]
+        ncomp, _ = cg.connected_components(S[m][:, m], directed=False)
+        assert ncomp == 1
+
+
+# ---------------------------------------------------------------- tentative prolongation
+def test_tentative_orthonormal_and_reproduces_B():
+    p = q.make_problem((4, 3, 3), clamp=False, body=(0, 0, -1))
+    A = o.from_problem(p)
+    agg, nagg = o.aggregate(A, 3, 0.08)
+    Pt, Bc = o.tentative(p.nnodes, 3, agg, nagg, p.B)
+    Pd = Pt.to_dense()
+    rows = np.repeat(agg >= 0, 3)
+    np.testing.assert_allclose(Pd[rows] @ Bc, p.B[rows], atol=1e-13)
+    for a in range(nagg):
+        m = np.repeat(agg == a, 3)
+        Q = Pd[np.ix_(m, np.arange(6 * a, 6 * a + 6))]
+        keep = np.abs(Q).sum(0) > 0
+        np.testing.assert_allclose(Q[:, keep].T @ Q[:, keep], np.eye(keep.sum()), atol=1e-13)
+        Ra = Bc[6 * a:6 * a + 6]
+        assert np.allclose(np.tril(Ra, -1), 0.0)
+        # thin QR is unique for full column rank with R_kk > 0: compare to LAPACK
+        if keep.all():
+            Qn, Rn = np.linalg.qr(p.B[m])
+            s = np.sign(np.diag(Rn))
+            np.testing.assert_allclose(Q, Qn * s, atol=1e-12)
+            np.testing.assert_allclose(Ra, s[:, None] * Rn, atol=1e-12 * np.abs(Rn).max())
+
+
+def test_tentative_single_node_aggregate_is_rank_three():
+    # one node: translations span its three rows, rotations are dependent
+    B = np.array([[1, 0, 0, 0, 0.3, -0.2], [0, 1, 0, -0.3, 0, 0.1], [0, 0, 1, 0.2, -0.1, 0]], float)
+    Pt, Bc = o.tentative(1, 3, np.array([0], np.int32), 1, B)
+    Q = Pt.to_dense()
+    assert np.count_nonzero(np.abs(Q).sum(0)) == 3
+    np.testing.assert_allclose(Q @ Bc, B, atol=1e-14)
+    assert np.count_nonzero(np.abs(Bc).sum(1)) == 3
+
+
+# ---------------------------------------------------------------- filtering, omega, P
+def test_filter_eps_zero_is_identity_and_row_sums_preserved():
+    p = q.inclusions(5)
+    A = o.from_problem(p)
+    AF, d, rho = o.filter_matrix(A, 3, 0.0)
+    np.testing.assert_array_equal(AF.to_dense(), A.to_dense())
+    AF, d, rho = o.filter_matrix(A, 3, 0.08)
+    Ad, Fd = A.to_dense(), AF.to_dense()
+    np.testing.assert_allclose(Fd.sum(1), Ad.sum(1), atol=1e-12 * np.abs(Ad).max())
+    np.testing.assert_array_equal(np.diag(Fd), d)
+    # Gershgorin: rho bounds the spectrum of D^{-1} A_F from above
+    lam = np.abs(np.linalg.eigvals(Fd / d[:, None])).max()
+    assert rho >= lam * (1 - 1e-12)
+
+
+def test_gershgorin_closed_form_on_laplacian():
+    # tridiag(-1, 2, -1): interior rows give (1 + 2 + 1) / 2 = 2 exactly
+    n = 9
+    ptr, col, val = [0], [], []
+    for i in range(n):
+        for j, v in ((i - 1, -1.0), (i, 2.0), (i + 1, -1.0)):
+            if 0 <= j < n:
+                col.append(j)
+                val.append(v)
+        ptr.append(len(col))
+    AF, d, rho = o.filter_matrix(o.CSR(ptr, col, val, (n, n)), 1, 0.0)
+    assert rho == 2.0 and (d == 2.0).all()
+
+
+def test_default_stop_rule_on_ten_cube():
+    # 3993 DOFs > 3000 coarsens once; 6 x (aggregates) < 3000 stops
+    H = o.Hierarchy(o.from_problem(q.cube(10)), 3, q.cube(10).B)
+    assert H.nlevels == 2
+    L1 = H.level(1)
+    assert L1["b"] == 6 and L1["n"] == 6 * H.level(0)["nagg"] <= 3000
+
+
+def _hierarchy(p, **kw):
+    return o.Hierarchy(o.from_problem(p), 3, p.B, **kw)
+
+
+def test_smoothed_prolongation_keeps_rigid_modes():
+    # eps = 0 on the unconstrained (singular) operator: A_F = A and A B = 0,
+    # so P B_c = (I - w D^-1 A) P_tent B_c = B - w D^-1 A B = B, and every
+    # Galerkin operator annihilates its restricted rigid-body modes.  The
+    # coarsening steps are chained by hand (a singular coarsest matrix has no
+    # Cholesky factor, so the full setup does not apply).
+    p = q.make_problem((6, 5, 4), clamp=False, body=(0, 0, -1))
+    A, B, b = o.from_problem(p), p.B, 3
+    for level in range(3):
+        nn = A.shape[0] // b
+        agg, nagg = o.aggregate(A, b, 0.0)
+        assert (agg >= 0).all() and nagg < nn
+        Pt, Bc = o.tentative(nn, b, agg, nagg, B)
+        AF, d, rho = o.filter_matrix(A, b, 0.0)
+        P = o.smooth_prolongation(AF, d, (4.0 / 3.0) / rho, Pt)
+        Ps = P.to_scipy()
+        assert np.abs(Ps @ Bc - B).max() <= 1e-10 * np.abs(B).max()
+        Ac = o.spgemm(o.transpose(P), o.spgemm(A, P))
+        As = Ac.to_scipy()
+        scale = max(abs(As).max(), abs(A.to_scipy()).max())  # A_c may vanish entirely
+        assert np.abs(As @ Bc).max() <= 1e-10 * scale * np.abs(Bc).max()
+        A, B, b = Ac, Bc, 6
+        if nagg < 2:
+            break
+
+
+def test_prolongation_and_galerkin_against_dense_algebra():
+    p = q.make_problem((4, 4, 3), traction=(0, 0, -1), inclusion_frac=0.2)
+    A = o.from_problem(p)
+    agg, nagg = o.aggregate(A, 3, 0.08)
+    Pt, Bc = o.tentative(p.nnodes, 3, agg, nagg, p.B)
+    AF, d, rho = o.filter_matrix(A, 3, 0.08)
+    w = (4.0 / 3.0) / rho
+    P = o.smooth_prolongation(AF, d, w, Pt)
+    Pd, Ptd, Fd = P.to_dense(), Pt.to_dense(), AF.to_dense()
+    dense = Ptd - w * (Fd / d[:, None]) @ Ptd
+    np.testing.assert_allclose(Pd, dense, atol=1e-14)
+    R = o.transpose(P)
+    np.testing.assert_array_equal(R.to_dense(), Pd.T)
+    Ac = o.spgemm(R, o.spgemm(A, P))
+    Acd = Ac.to_dense()
+    np.testing.assert_allclose(Acd, Pd.T @ A.to_dense() @ Pd, atol=1e-13 * np.abs(Acd).max())
+    assert np.abs(Acd - Acd.T).max() <= 1e-13 * np.abs(Acd).max()
+    # symbolic pattern: every P row of an aggregated node has whole 6-column groups
+    cnt = np.diff(P.ptr)
+    assert (cnt % 6 == 0).all()
+
+
+def test_spgemm_symbolic_pattern_keeps_cancellation():
+    A = o.CSR([0, 2, 4], [0, 1, 0, 1], [1.0, 1.0, 1.0, 1.0], (2, 2))
+    B = o.CSR([0, 1, 2], [0, 0], [1.0, -1.0], (2, 1))
+    C = o.spgemm(A, B)  # exact cancellation: entries stay, value 0
+    assert C.col.tolist() == [0, 0] and C.val.tolist() == [0.0, 0.0]
+
+
+# ---------------------------------------------------------------- smoother, coarse solver
+def test_spai0_diagonal_matrix_is_exact_inverse_and_minimal():
+    d = np.array([2.0, 4.0, 0.5])
+    A = o.CSR([0, 1, 2, 3], [0, 1, 2], d, (3, 3))
+    np.testing.assert_allclose(o.spai0(A), 1.0 / d, rtol=1e-15)
+    A = o.from_problem(q.cube(3))
+    m = o.spai0(A)
+    Ad = A.to_dense()
+    f0 = np.linalg.norm(np.eye(len(m)) - m[:, None] * Ad)
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        dm = 1e-3 * rng.standard_normal(len(m)) * np.abs(m)
+        assert np.linalg.norm(np.eye(len(m)) - (m + dm)[:, None] * Ad) > f0
+
+
+def test_cholesky_against_lapack_and_zero_rows():
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((12, 12))
+    S = X @ X.T + 12 * np.eye(12)
+    S[4, :] = S[:, 4] = 0.0
+    L, z, rc = o.cholesky(S)
+    assert rc == 0 and z.tolist() == [1 if i == 4 else 0 for i in range(12)]
+    f = rng.standard_normal(12)
+    u = o.cholesky_solve(L, z, f)
+    keep = np.arange(12) != 4
+    np.testing.assert_allclose(u[keep], np.linalg.solve(S[np.ix_(keep, keep)], f[keep]), rtol=1e-12)
+    assert u[4] == 0.0
+    L, z, rc = o.cholesky(-np.eye(3))
+    assert rc < 0
+
+
+# ---------------------------------------------------------------- V-cycle, CG
+def test_vcycle_is_symmetric():
+    p = q.inclusions(6)
+    H = _hierarchy(p, coarse_enough=200)
+    assert H.nlevels >= 2
+    rng = np.random.default_rng(3)
+    x, y = rng.standard_normal(p.ndof), rng.standard_normal(p.ndof)
+    a, b = x @ H.vcycle(y), y @ H.vcycle(x)
+    assert abs(a - b) <= 1e-12 * abs(a)
+
+
+def test_coarse_correction_is_a_projection():
+    # no smoothing, two levels: V = P A_c^-1 P^T, so (V A)^2 = V A
+    p = q.cube(6)
+    H = _hierarchy(p, coarse_enough=400, npre=0, npost=0)
+    assert H.nlevels == 2
+    A = o.from_problem(p).to_scipy()
+    x = np.random.default_rng(4).standard_normal(p.ndof)
+    vx = H.vcycle(A @ x)
+    np.testing.assert_allclose(H.vcycle(A @ vx), vx, atol=1e-9 * np.abs(vx).max())
+
+
+def test_one_level_hierarchy_is_a_direct_solve():
+    p = q.cube(3)
+    H = _hierarchy(p, coarse_enough=10 ** 6)
+    assert H.nlevels == 1
+    u, it, rel = H.solve(p.f, tol=1e-10)
+    assert it == 1 and rel <= 1e-10
+
+
+@pytest.mark.parametrize("shape,kw", [((4, 4, 4), {}), ((6, 3, 5), {"inclusion_frac": 0.2}),
+                                      ((8, 8, 8), {"inclusion_frac": 0.2})])
+def test_pcg_matches_dense_direct_solve(shape, kw):
+    p = q.make_problem(shape, traction=(0, 0, -1), **kw)
+    H = _hierarchy(p, coarse_enough=150)
+    assert H.nlevels >= 2
+    u, it, rel = H.solve(p.f, tol=1e-8)
+    us = np.linalg.solve(q.bsr_to_dense(p), p.f)
+    assert rel <= 1e-8
+    assert np.linalg.norm(u - us) <= 1e-7 * np.linalg.norm(us)
+    assert 1 <= it < 400
+
+
+def test_pcg_zero_rhs_and_warm_start():
+    p = q.cube(4)
+    H = _hierarchy(p, coarse_enough=150)
+    u, it, rel = H.solve(np.zeros(p.ndof))
+    assert it == 0 and not u.any()
+    us, _, _ = H.solve(p.f, tol=1e-12)
+    u, it, rel = H.solve(p.f, u0=us, tol=1e-8)
+    assert it == 0 and rel <= 1e-8
