@@ -1,0 +1,337 @@
+"""Benchmark: block SA-AMG preconditioned CG on a synthetic Q1 elasticity box.
+
+One step = the whole hot path on one problem: setup (Alg. 1: strength,
+aggregation, tentative prolongation, smoothed P, R, Galerkin R A P, SPAI0,
+coarse factor) followed by the PCG solve to relative residual 1e-8 (Alg. 2
+V-cycle preconditioner, Sec. 4).  `value` is the PCG time-to-1e-8 of the
+solve (hierarchy built, right-hand side resident in HBM), averaged over the
+timed steps; setup time is reported beside it.
+
+Workload (default): 80^3 Q1 hexahedra, 1.59 M DOFs, E = 1 matrix with E = 1000
+spherical inclusions at 20 % volume (SplitMix64 seed 2202), nu = 0.3,
+clamped at x = 0, traction (0, 0, -1) on x = 1.  Synthetic inputs stand in
+for the paper's two matrices, which are not available.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: one process per GPU (torchrun); every rank solves its own replica
+(the single solve does not shard), so scaling is weak and the reported time
+is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG time-to-1e-8 (s); BSR SpMV GB/s vs HBM peak; mixed/learned vs FP64"
+WORKLOADS = {
+    "inclusions80": dict(n=80, desc="q1-hex-80^3-inclusions-20pct-E1000", tol=1e-8),
+    "inclusions40": dict(n=40, desc="q1-hex-40^3-inclusions-20pct-E1000", tol=1e-8),
+    "cube10": dict(n=10, desc="q1-hex-10^3-cube-body-load", tol=1e-8),
+}
+
+
+def _problem(name):
+    import q1elasticity as q
+    w = WORKLOADS[name]
+    return q.cube(w["n"]) if name.startswith("cube") else q.inclusions(w["n"])
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _gpu_id(torch):
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    except Exception:
+        return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+
+
+def _spmv_roofline(amg, torch, rp, cl, val, n, nnzb, reps=40):
+    """Average duration of the fine-level 3x3 FP64 BSR SpMV on the launch stream."""
+    x = torch.randn(n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(5):
+        amg.bsr_spmv(rp, cl, val, x, y)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        amg.bsr_spmv(rp, cl, val, x, y)  # 1.07 GB of values per launch: larger than L2
+    e1.record(s)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    nbr = rp.numel() - 1
+    algo = nnzb * (72 + 4) + (nbr + 1) * 4 + n * 8 + n * 8
+    return t, algo
+
+
+def _traffic_from_profile(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it matches."""
+    path = os.path.join(ROOT, "profiles", "spmv_3x3_fp64_inclusions80.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_tag") == kernel_tag:
+            return d.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(sample_n=40):
+    """The oracle, as it stands, on a bounded sample of the workload: the same
+    material model on a sample_n^3 mesh, setup + PCG to 1e-8, single thread.
+    Reported as measured on the sample (seconds), with the sample named."""
+    import oracle
+    import q1elasticity as q
+    p = q.inclusions(sample_n)
+    A = oracle.from_problem(p)
+    t0 = time.perf_counter()
+    H = oracle.Hierarchy(A, 3, p.B)
+    t1 = time.perf_counter()
+    _, it, rel = H.solve(p.f, tol=1e-8, maxiter=3000)
+    t2 = time.perf_counter()
+    return {"value": t2 - t1, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle setup+PCG on the same material model at {sample_n}^3 elements "
+                      f"({p.ndof} DOFs, {it} iterations); value = its PCG time to 1e-8, "
+                      f"setup {t1 - t0:.2f} s",
+            "setup_s": t1 - t0, "iterations": it}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps = []
+    base = None
+    for _ in range(args.warmup + args.steps):
+        base = cpu_baseline(args.ref_sample)
+        steps.append(base["value"])
+    vals = steps[args.warmup:]
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * v,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "parallelism": "replicas"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": base["sample"], "value": v,
+                             "unit": "s"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="inclusions80", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=40)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2202_09056_gb300 as amg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    amg.load()
+    p = _problem(args.workload)
+    dev = torch.device("cuda", local)
+    rp = torch.from_numpy(p.row_ptr).to(dev)
+    cl = torch.from_numpy(p.col).to(dev)
+    val = torch.from_numpy(p.val).to(dev)
+    B = torch.from_numpy(p.B).to(dev)
+    f = torch.from_numpy(p.f).to(dev)
+    tol = WORKLOADS[args.workload]["tol"]
+    s = torch.cuda.current_stream()
+
+    def step(timings=None):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(s)
+        solver = amg.AMG(rp, cl, val, B)
+        ev[1].record(s)
+        u, it, res, st = solver.solve(f, tol=tol, maxiter=5000)
+        ev[2].record(s)
+        torch.cuda.synchronize()
+        if st != amg.AMG_OK:
+            raise RuntimeError(f"solve did not converge: status {st}, {it} its, res {res}")
+        if timings is not None:
+            timings.append((ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3,
+                            it, res))
+        return solver
+
+    for _ in range(args.warmup):
+        solver = step()
+        del solver
+    timings = []
+    launches0 = amg.kernel_launches()
+    barrier()
+    with ClockSampler(_gpu_id(torch)) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            solver = step(timings)
+        barrier()
+        wall = time.perf_counter() - t0
+    launches = amg.kernel_launches() - launches0
+    setup_t = float(np.mean([t[0] for t in timings]))
+    solve_t = float(np.mean([t[1] for t in timings]))
+    its = timings[-1][2]
+    res = timings[-1][3]
+    step_t = setup_t + solve_t
+    if dist is not None:
+        tt = torch.tensor([solve_t, step_t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        solve_t, step_t = float(tt[0]), float(tt[1])
+
+    # end to end through the public API: pinned host f -> device, solve, u -> host
+    fh = torch.from_numpy(p.f).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    fd = torch.empty_like(f)
+    e2e = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fd.copy_(fh, non_blocking=True)
+        u, it2, res2, st2 = solver.solve(fd, tol=tol, maxiter=5000)
+        uh.copy_(u, non_blocking=True)
+        e1.record(s)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e.append(e0.elapsed_time(e1) / 1e3)
+    e2e_t = float(np.mean(e2e))
+
+    stats = solver.stats()
+    info0 = solver.level_info(0)
+    levels = [solver.level_info(l) for l in range(stats["nlevels"])]
+    t_spmv, algo = _spmv_roofline(amg, torch, rp, cl, val, p.ndof, p.nnzb)
+    peak, peak_kind = _peaks()
+    achieved = algo / t_spmv / 1e9
+    kernel_tag = "bsr_spmv_kernel<3,3,double,double,PLAIN,NONE>:v1"
+    traffic = _traffic_from_profile(kernel_tag)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    line = {
+        "metric": METRIC, "value": solve_t, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * step_t, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "dofs": p.ndof,
+                   "nnzb": p.nnzb, "levels": stats["nlevels"],
+                   "level_rows": [l["nbrows"] * l["bs"] for l in levels],
+                   "coarse_n": stats["coarse_n"], "smoother": "SPAI0 x0.8, V(1,1)",
+                   "l2": "inputs larger than L2 (fine A values 1.0 GB)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "iterations": its, "rel_resid": res, "setup_s": setup_t, "total_s": step_t,
+        "operator_complexity": stats["operator_complexity"],
+        "memory_mb": stats["bytes_matrices"] / 1e6,
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_t, "unit": "s", "h2d_bytes_per_step": 8 * p.ndof,
+                "d2h_bytes_per_step": 8 * p.ndof},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": kernel_tag, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_kind, "algorithmic_bytes": algo,
+                     "launch_ms": 1e3 * t_spmv},
+        "wall_s": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.ref_sample)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,177 @@
+/*
+ * amg_gb300.h -- C ABI of the GB300 (sm_103a) block smoothed-aggregation AMG
+ * preconditioned CG solver for 3D elasticity with rigid-body near-nullspace
+ * modes.
+ *
+ * Method: D. E. Demidov, "Efficient solution of 3D elasticity problems with
+ * smoothed aggregation algebraic multigrid and block arithmetics" (2022).
+ *   - Alg. 1 (Sec. 2): setup.  Per level: prolongation P_i and next
+ *     near-nullspace B_{i+1} from (A_i, B_i); R_i = P_i^T; smoother S_i from
+ *     A_i; Galerkin operator A_{i+1} = R_i A_i P_i; a direct solver for the
+ *     coarsest A_L.
+ *   - Alg. 2 (Sec. 2): V-cycle, applied once per preconditioning step.
+ *   - Sec. 2/3: every matrix of the hierarchy is held in block CSR (BSR):
+ *     3x3 blocks on the finest level, 6x6 below it (six rigid-body modes);
+ *     only the tentative prolongation is built from B in scalar terms, and
+ *     here it is built per aggregate inside block-structured kernels (the
+ *     paper's "NS Block" route, Sec. 3, Listing 2 semantics).
+ *   - Sec. 4: conjugate gradients preconditioned by one V-cycle, stopping at
+ *     relative residual 1e-8.
+ *
+ * Conventions for every call:
+ *   - Matrix and vector pointers are DEVICE pointers unless a parameter says
+ *     "host".  The caller owns them; the library only borrows them for the
+ *     duration of the call (it copies what it keeps).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is ordered on that stream.  Calls that return results
+ *     through host pointers synchronise the stream before returning.
+ *   - DOF layout is node-major: scalar row 3*I + c is component c of node I.
+ *   - Every call returns an int status: AMG_OK (0), AMG_NOT_CONVERGED (1,
+ *     results written), or a negative error code; nothing aborts or traps.
+ *     amg_last_error() gives a message for the calling thread's last error.
+ */
+#ifndef AMG_GB300_H
+#define AMG_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMG_OK 0
+#define AMG_NOT_CONVERGED 1
+#define AMG_ERR_ARG (-1)          /* bad argument (shape, null pointer, block size) */
+#define AMG_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define AMG_ERR_BREAKDOWN (-3)    /* CG breakdown: p.Ap <= 0, r.z <= 0 or non-finite */
+#define AMG_ERR_COARSE (-4)       /* coarsest matrix not positive definite */
+#define AMG_ERR_LIMIT (-5)        /* a size exceeds a fixed internal limit */
+#define AMG_ERR_STATE (-6)        /* handle not usable for this call */
+
+#define AMG_PREC_FP64 0           /* V-cycle matrices and vectors in FP64 */
+#define AMG_PREC_FP32 1           /* V-cycle in FP32 storage, FP32 accumulation */
+#define AMG_PREC_BF16 2           /* V-cycle matrices stored BF16, FP32 accumulation */
+
+/* Block CSR matrix, borrowed for the duration of a call.
+ * row_ptr[nbrows+1] and col[nnzb] are int32 with columns strictly ascending
+ * within each block row; val holds nnzb blocks of bs_r x bs_c doubles, each
+ * block row-major.  All three arrays are device pointers. */
+typedef struct {
+    int32_t nbrows, nbcols;
+    int32_t bs_r, bs_c;
+    int64_t nnzb;
+    const int32_t *row_ptr;
+    const int32_t *col;
+    const double *val;
+} amg_bsr;
+
+/* Setup and cycle parameters (the paper names none of them; defaults are the
+ * readings of its silent points, see the design notes shipped with the
+ * library). */
+typedef struct {
+    double eps_strong;     /* strength threshold on level 1; halved per level (0.08) */
+    double relax;          /* multiplier of omega = (4/3)/rho in P smoothing (1.0) */
+    double smooth_relax;   /* damping of the SPAI0 smoother (0.8) */
+    int32_t coarse_enough; /* stop coarsening at <= this many scalar rows (3000) */
+    int32_t max_levels;    /* at most this many levels (15) */
+    int32_t npre, npost;   /* smoothing sweeps before / after the correction (1, 1) */
+    int32_t precision;     /* AMG_PREC_* of the V-cycle (AMG_PREC_FP64) */
+    int32_t reserved[7];   /* must be zero */
+} amg_params;
+
+typedef struct amg_handle_s *amg_handle;
+
+/* Per-level description filled by amg_level_info (host struct). */
+typedef struct {
+    int32_t nbrows;        /* block rows of A on this level */
+    int32_t bs;            /* block size of A (3 on level 0, 6 below) */
+    int64_t nnzb_A;
+    int64_t nnzb_P;        /* 0 on the coarsest level */
+    int32_t nagg;          /* aggregates = block rows of the next level (0 on the coarsest) */
+    int32_t is_coarsest;
+    double eps, omega, rho;
+} amg_level_desc;
+
+/* Whole-hierarchy statistics (host struct). */
+typedef struct {
+    int32_t nlevels;
+    int32_t coarse_n;          /* scalar size of the dense coarsest system */
+    double setup_seconds;      /* wall time of amg_setup (host clock, synchronised) */
+    int64_t bytes_matrices;    /* A, P, R of all levels + smoother + coarse inverse */
+    int64_t bytes_total;       /* everything the handle holds on the device */
+    double operator_complexity;/* sum of nnz over levels / nnz of the finest A */
+} amg_stats;
+
+/* Fill *prm with the defaults listed above.  Returns AMG_OK. */
+int amg_params_default(amg_params *prm);
+
+/* Alg. 1: build the hierarchy for A (3x3 BSR, square, symmetric positive
+ * definite) with near-nullspace B (device, row-major [nbrows*3][nb_ns],
+ * nb_ns = 6: three translations and three rotations).  prm may be NULL for
+ * the defaults.  On success *out owns every level on the device (allocated
+ * stream-ordered on `stream`).  A and B are only read. */
+int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params *prm,
+              void *stream, amg_handle *out);
+
+/* Alg. 2 used as a preconditioner: z = V(r), one V-cycle from a zero initial
+ * guess on every level.  r and z are device vectors of 3*nbrows doubles and
+ * must not overlap. */
+int amg_apply_vcycle(amg_handle h, const double *r, double *z, void *stream);
+
+/* Sec. 4: CG preconditioned by one V-cycle per iteration.  u (device) holds
+ * the initial guess on entry and the solution on exit; f is the right-hand
+ * side.  The loop runs on the device (a CUDA graph with a conditional while
+ * node) until the recurrence residual ||r||/||f|| <= tol is confirmed by the
+ * true residual, or maxiter iterations.  *iters (host) receives the number
+ * of A*p products and *rel_resid (host) the final true relative residual
+ * ||f - A u|| / ||f||.  Returns AMG_OK, AMG_NOT_CONVERGED or an error; the
+ * call synchronises `stream`. */
+int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxiter,
+              int32_t *iters, double *rel_resid, void *stream);
+
+/* Statistics of the hierarchy (host struct). */
+int amg_get_stats(amg_handle h, amg_stats *out);
+
+/* Description of level `level` (0 = finest). */
+int amg_level_info(amg_handle h, int32_t level, amg_level_desc *out);
+
+/* Copy one operator of a level to HOST buffers sized from amg_level_info:
+ * which = 0: A (nbrows+1, nnzb_A, nnzb_A*bs*bs), 1: P (bs x 6 blocks),
+ * 2: R (6 x bs blocks, nagg+1 row pointers).  Any pointer may be NULL.
+ * which = 3: the aggregate of every node (row_ptr receives nbrows int32,
+ * -1 for an isolated node); which = 4: the smoother diagonal (val receives
+ * nbrows*bs doubles); which = 5: the near-nullspace of the level (val
+ * receives nbrows*bs*6 doubles); which = 6: the strong-connection flags of A
+ * (row_ptr receives nnzb_A bytes).  Synchronises the stream it was set up on. */
+int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_ptr,
+                     int32_t *col, double *val);
+
+/* Release everything the handle owns.  NULL is ignored. */
+void amg_free(amg_handle h);
+
+/* Message of the calling thread's last error ("" if none). */
+const char *amg_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (a graph execution counts each kernel node once per loop iteration).
+ * Host-only bookkeeping; needs no GPU. */
+int64_t amg_kernel_launches(void);
+
+/* ---- primitives (the hot kernels on their own) ------------------------- */
+
+/* y = A x for a BSR matrix with block shape (bs_r, bs_c) in {(3,3), (6,6),
+ * (3,6), (6,3)}: the block SpMV of Sec. 2 (memory-bound primitive).  x has
+ * nbcols*bs_c and y nbrows*bs_r doubles (device, not overlapping). */
+int amg_bsr_spmv(const amg_bsr *A, const double *x, double *y, void *stream);
+
+/* y = A x and *dot_out (host) = x . y for a square 3x3 or 6x6 BSR matrix,
+ * with the dot product reduced in a fixed order (deterministic).  The
+ * reduction uses a device scratch array that the call allocates and frees
+ * stream-ordered.  Synchronises `stream`. */
+int amg_bsr_spmv_dot(const amg_bsr *A, const double *x, double *y, double *dot_out,
+                     void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMG_GB300_H */

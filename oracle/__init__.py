@@ -300,6 +300,21 @@ class Hierarchy:
             out["R"] = CSR._from_handle(lib.orc_level_matrix(self.h, l, 2), free=False)
         return out
 
+    def graph(self, l: int):
+        """Strength graph of level l (None on the coarsest level)."""
+        lib = _load()
+        g = lib.orc_level_graph(self.h, l)
+        if not g:
+            return None
+        s = np.zeros(2, dtype=np.int64)
+        lib.orc_graph_shape(g, _p(s))
+        ptr = np.empty(s[0] + 1, dtype=np.int64)
+        col = np.empty(s[1], dtype=np.int32)
+        nrm = np.empty(s[1])
+        strong = np.empty(s[1], dtype=np.uint8)
+        lib.orc_graph_copy(g, _p(ptr), _p(col), _p(nrm), _p(strong))
+        return {"ptr": ptr, "col": col, "norm2": nrm, "strong": strong}
+
     def coarse_factor(self):
         nc = self.level(self.nlevels - 1)["n"]
         L = np.empty((nc, nc))

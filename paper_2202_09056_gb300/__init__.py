@@ -1,0 +1,269 @@
+"""Block smoothed-aggregation AMG + PCG for 3D elasticity on GB300 (sm_103a).
+
+Thin ctypes binding of the C ABI declared in ``include/amg_gb300.h``.  It only
+marshals arguments: every step of setup and solve runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current CUDA stream.  There
+is no CPU fallback: without the compiled library every call raises.
+
+Method: Demidov (2022), Alg. 1 (setup), Alg. 2 (V-cycle), Sec. 3 (block
+arithmetic with rigid-body modes), Sec. 4 (CG, relative residual 1e-8).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+
+AMG_OK, AMG_NOT_CONVERGED = 0, 1
+_ERRORS = {-1: "bad argument", -2: "CUDA error", -3: "CG breakdown",
+           -4: "coarsest matrix not positive definite", -5: "size limit", -6: "bad state"}
+PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
+
+
+class AmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_ERRORS.get(status, status)} ({status}): {msg}")
+        self.status = status
+
+
+class Bsr(ctypes.Structure):
+    _fields_ = [("nbrows", ctypes.c_int32), ("nbcols", ctypes.c_int32),
+                ("bs_r", ctypes.c_int32), ("bs_c", ctypes.c_int32), ("nnzb", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("eps_strong", ctypes.c_double), ("relax", ctypes.c_double),
+                ("smooth_relax", ctypes.c_double), ("coarse_enough", ctypes.c_int32),
+                ("max_levels", ctypes.c_int32), ("npre", ctypes.c_int32),
+                ("npost", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class LevelDesc(ctypes.Structure):
+    _fields_ = [("nbrows", ctypes.c_int32), ("bs", ctypes.c_int32), ("nnzb_A", ctypes.c_int64),
+                ("nnzb_P", ctypes.c_int64), ("nagg", ctypes.c_int32),
+                ("is_coarsest", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("omega", ctypes.c_double), ("rho", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("nlevels", ctypes.c_int32), ("coarse_n", ctypes.c_int32),
+                ("setup_seconds", ctypes.c_double), ("bytes_matrices", ctypes.c_int64),
+                ("bytes_total", ctypes.c_int64), ("operator_complexity", ctypes.c_double)]
+
+
+EXPORTED = ["amg_params_default", "amg_setup", "amg_apply_vcycle", "amg_solve", "amg_get_stats",
+            "amg_level_info", "amg_level_export", "amg_free", "amg_last_error", "amg_bsr_spmv",
+            "amg_bsr_spmv_dot", "amg_kernel_launches"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it first if needed); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library missing: {_build.LIB} (run the build)")
+    lib = ctypes.CDLL(_build.LIB)
+    P, i32, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "amg_params_default": ([P], ctypes.c_int),
+        "amg_setup": ([P, P, i32, P, P, P], ctypes.c_int),
+        "amg_apply_vcycle": ([P, P, P, P], ctypes.c_int),
+        "amg_solve": ([P, P, P, d, i32, P, P, P], ctypes.c_int),
+        "amg_get_stats": ([P, P], ctypes.c_int),
+        "amg_level_info": ([P, i32, P], ctypes.c_int),
+        "amg_level_export": ([P, i32, i32, P, P, P], ctypes.c_int),
+        "amg_free": ([P], None),
+        "amg_last_error": ([], ctypes.c_char_p),
+        "amg_bsr_spmv": ([P, P, P, P], ctypes.c_int),
+        "amg_bsr_spmv_dot": ([P, P, P, P, P], ctypes.c_int),
+        "amg_kernel_launches": ([], ctypes.c_int64),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status, allow_not_converged=False):
+    if status == AMG_OK or (allow_not_converged and status == AMG_NOT_CONVERGED):
+        return status
+    msg = load().amg_last_error()
+    raise AmgError(status, msg.decode() if msg else "")
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _dptr(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def make_bsr(row_ptr, col, val, nbcols=None) -> Bsr:
+    """BSR view of CUDA tensors: int32 row_ptr, int32 col, float64 val [nnzb, br, bc]."""
+    import torch
+    br, bc = int(val.shape[1]), int(val.shape[2])
+    nbr = int(row_ptr.shape[0]) - 1
+    return Bsr(nbr, nbr if nbcols is None else int(nbcols), br, bc, int(col.shape[0]),
+               _dptr(row_ptr, torch.int32, "row_ptr"), _dptr(col, torch.int32, "col"),
+               _dptr(val, torch.float64, "val"))
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().amg_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().amg_kernel_launches())
+
+
+def bsr_spmv(row_ptr, col, val, x, y=None, nbcols=None, stream=None):
+    """y = A x (block SpMV kernel) on CUDA tensors."""
+    import torch
+    A = make_bsr(row_ptr, col, val, nbcols)
+    if y is None:
+        y = torch.empty(A.nbrows * A.bs_r, dtype=torch.float64, device=x.device)
+    _check(load().amg_bsr_spmv(ctypes.byref(A), _dptr(x, torch.float64, "x"),
+                               _dptr(y, torch.float64, "y"), _stream(stream)))
+    return y
+
+
+def bsr_spmv_dot(row_ptr, col, val, x, y=None, stream=None):
+    """(y = A x, x . y) with the deterministic fused reduction."""
+    import torch
+    A = make_bsr(row_ptr, col, val)
+    if y is None:
+        y = torch.empty(A.nbrows * A.bs_r, dtype=torch.float64, device=x.device)
+    d = ctypes.c_double(0.0)
+    _check(load().amg_bsr_spmv_dot(ctypes.byref(A), _dptr(x, torch.float64, "x"),
+                                   _dptr(y, torch.float64, "y"), ctypes.byref(d),
+                                   _stream(stream)))
+    return y, d.value
+
+
+class AMG:
+    """Hierarchy handle: setup (Alg. 1) on construction, V-cycle and PCG solve."""
+
+    def __init__(self, row_ptr, col, val, B, params: Params | None = None, stream=None, **kw):
+        import torch
+        self._lib = load()
+        self.params = params if params is not None else default_params(**kw)
+        A = make_bsr(row_ptr, col, val)
+        self.n = A.nbrows * A.bs_r
+        self.device = val.device
+        h = ctypes.c_void_p()
+        _check(self._lib.amg_setup(ctypes.byref(A), _dptr(B, torch.float64, "B"),
+                                   int(B.shape[1]), ctypes.byref(self.params),
+                                   _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.amg_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vcycle(self, r, z=None, stream=None):
+        import torch
+        if z is None:
+            z = torch.empty_like(r)
+        _check(self._lib.amg_apply_vcycle(self._h, _dptr(r, torch.float64, "r"),
+                                          _dptr(z, torch.float64, "z"), _stream(stream)))
+        return z
+
+    def solve(self, f, u=None, tol=1e-8, maxiter=1000, stream=None):
+        """(u, iterations, relative true residual, status)."""
+        import torch
+        if u is None:
+            u = torch.zeros_like(f)
+        it = ctypes.c_int32(0)
+        res = ctypes.c_double(0.0)
+        st = _check(self._lib.amg_solve(self._h, _dptr(f, torch.float64, "f"),
+                                        _dptr(u, torch.float64, "u"), float(tol), int(maxiter),
+                                        ctypes.byref(it), ctypes.byref(res), _stream(stream)),
+                    allow_not_converged=True)
+        return u, it.value, res.value, st
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self._lib.amg_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def level_info(self, l: int) -> dict:
+        d = LevelDesc()
+        _check(self._lib.amg_level_info(self._h, l, ctypes.byref(d)))
+        return {k: getattr(d, k) for k, _ in LevelDesc._fields_}
+
+    @property
+    def nlevels(self) -> int:
+        return self.stats()["nlevels"]
+
+    def export(self, l: int) -> dict:
+        """Host copies of level l: A, P, R (BSR), aggregates, smoother, B, strength flags."""
+        info = self.level_info(l)
+        nbr, bs = info["nbrows"], info["bs"]
+        out = {"info": info}
+
+        def bsr(which, nrows, nnz, br, bc):
+            rp = np.empty(nrows + 1, np.int32)
+            cl = np.empty(max(nnz, 1), np.int32)
+            vl = np.empty((max(nnz, 1), br, bc))
+            _check(self._lib.amg_level_export(self._h, l, which, rp.ctypes.data, cl.ctypes.data,
+                                              vl.ctypes.data))
+            return rp, cl[:nnz], vl[:nnz]
+
+        out["A"] = bsr(0, nbr, info["nnzb_A"], bs, bs)
+        if not info["is_coarsest"]:
+            out["P"] = bsr(1, nbr, info["nnzb_P"], bs, 6)
+            out["R"] = bsr(2, info["nagg"], info["nnzb_P"], 6, bs)
+            agg = np.empty(nbr, np.int32)
+            _check(self._lib.amg_level_export(self._h, l, 3, agg.ctypes.data, None, None))
+            out["agg"] = agg
+            M = np.empty(nbr * bs)
+            _check(self._lib.amg_level_export(self._h, l, 4, None, None, M.ctypes.data))
+            out["M"] = M
+            strong = np.empty(max(info["nnzb_A"], 1), np.uint8)
+            _check(self._lib.amg_level_export(self._h, l, 6, strong.ctypes.data, None, None))
+            out["strong"] = strong[:info["nnzb_A"]]
+        B = np.empty((nbr * bs, 6))
+        _check(self._lib.amg_level_export(self._h, l, 5, None, None, B.ctypes.data))
+        out["B"] = B
+        return out

@@ -1,0 +1,156 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/amg_gb300.h"
+
+namespace amg {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+void clear_error();
+
+// Kernel launch accounting: every launch site reports itself; launches
+// recorded into a graph under capture are counted per graph execution.
+void count_launch(long long n);
+void begin_launch_capture(long long *counter);
+void end_launch_capture();
+
+#define AMG_TRY_CUDA(call)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            ::amg::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,                 \
+                             cudaGetErrorString(e_));                                   \
+            return AMG_ERR_CUDA;                                                        \
+        }                                                                               \
+    } while (0)
+
+#define AMG_TRY(call)                                                                   \
+    do {                                                                                \
+        int s_ = (call);                                                                \
+        if (s_ < 0) return s_;                                                          \
+    } while (0)
+
+// ---------------------------------------------------------------- device memory
+// Stream-ordered device allocations owned by a handle (or a call).
+struct DevArena {
+    cudaStream_t stream = nullptr;
+    std::vector<void *> ptrs;
+    size_t bytes = 0;
+    int alloc(void **p, size_t n);
+    template <class T> int alloc_n(T **p, size_t n) { return alloc((void **)p, n * sizeof(T)); }
+    void release(void *p);   // free one pointer early
+    void release_all();
+};
+
+// A device BSR matrix owned by the library.  Values are stored in T.
+template <class T> struct Bsr {
+    int nbr = 0, nbc = 0, br = 0, bc = 0;
+    int64_t nnzb = 0;
+    int *row_ptr = nullptr;
+    int *col = nullptr;
+    T *val = nullptr;
+};
+using BsrD = Bsr<double>;
+
+// ---------------------------------------------------------------- launch geometry
+struct Geom {
+    int num_sms = 0;
+    int max_ctas = 0;       // grid size cap for grid-stride kernels (= partials capacity)
+};
+int query_geom(Geom *g);
+
+// ---------------------------------------------------------------- CG device state
+struct CgState {
+    double tol, nf;        // tolerance, ||f||
+    double rz, pq, alpha, beta, res, res_true;
+    int it, maxiter;
+    int check;             // recurrence residual reached tol: confirm with the true one
+    int replace;           // true residual failed: replace r by it
+    int converged;
+    int stop;              // loop ends after this iteration (converged, maxiter, breakdown)
+    int no_check;          // early-exit flag of the true-residual kernel (= !check)
+    int no_replace;        // early-exit flag of the replacement kernel
+    int status;            // AMG_OK / AMG_NOT_CONVERGED / AMG_ERR_BREAKDOWN
+};
+
+// ---------------------------------------------------------------- kernels (spmv.cu)
+enum SpmvMode {
+    SPMV_PLAIN = 0,   // y = A x
+    SPMV_RESID = 1,   // y = f - A x
+    SPMV_SMOOTH = 2,  // y = x + M (f - A x)           (x = u, square A)
+    SPMV_AXPY = 3,    // y = u + A x                  (prolongation, y may alias u)
+    SPMV_RESTRICT = 4,// y = A x ; y2 = M y           (restriction + next pre-smoothing)
+};
+
+enum DotMode {
+    DOT_NONE = 0,
+    DOT_XY = 1,       // sum_i x_i y_i over the output rows (square A: q = A p, p.q)
+    DOT_FY = 2,       // sum_i f_i y_i                (post-smoothing on level 0: r.z)
+    DOT_YY = 3,       // sum_i y_i y_i                (true residual norm)
+};
+
+// Vector element type of the V-cycle (double, or float for the reduced-precision forms).
+template <class TV> struct SpmvArgs {
+    const int *row_ptr;
+    const int *col;
+    const void *val;     // value type chosen by the launcher
+    int nbr;
+    const TV *x;
+    const TV *f;
+    const TV *u;
+    const TV *M;
+    TV *y;
+    TV *y2;
+    double *partials;    // one per CTA when a dot is fused
+    const int *stop;     // early exit when *stop != 0 (may be null)
+};
+
+// Launch y = op(A) x with the given mode.  VT = value type of the blocks.
+int spmv_grid(int nbr, const Geom &g);
+
+template <class VT, class TV>
+int launch_spmv(int br, int bc, int mode, int dot, const SpmvArgs<TV> &a, const Geom &g,
+                cudaStream_t s, int *grid_out = nullptr);
+
+// Deterministic reduction of `n` partials into out[0] (single CTA), with an
+// optional finisher applied by one thread.
+int launch_reduce_sum(const double *partials, int n, double *out, cudaStream_t s);
+
+// Dense GEMV on the coarsest level: y = Ainv * x (n x n row-major).
+template <class TV>
+int launch_coarse_gemv(const double *Ainv, int n, const TV *x, TV *y, const Geom &g,
+                       cudaStream_t s);
+
+// ---------------------------------------------------------------- setup (setup.cu)
+struct LevelBuild {
+    // outputs of one coarsening step on device
+    BsrD P, R, Ac;
+    double *Bc = nullptr;
+    int *agg = nullptr;
+    int nagg = 0;
+    double omega = 0, rho = 0;
+};
+
+int exclusive_scan_i32(const int *in, int *out, int n, int *total_host, DevArena &tmp,
+                       cudaStream_t s);
+int compute_strength(const BsrD &A, double eps, uint8_t *strong, cudaStream_t s);
+int aggregate_host(int nn, const int *row_ptr, const int *col, const uint8_t *strong,
+                   int *agg, int *nagg);   // host arrays
+int build_transfer(const BsrD &A, const double *B, const uint8_t *strong, const int *agg_h,
+                   int nagg, double relax, DevArena &keep, DevArena &tmp, cudaStream_t s,
+                   LevelBuild *out);
+int galerkin(const BsrD &A, const BsrD &P, const BsrD &R, DevArena &keep, DevArena &tmp,
+             cudaStream_t s, BsrD *Ac);
+int spai0_diag(const BsrD &A, double scale, double *M, cudaStream_t s);
+int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
+                   double **Ainv_out);
+
+}  // namespace amg

@@ -1,0 +1,903 @@
+// Setup kernels of Alg. 1 (Sec. 2) in block arithmetic: strength of
+// connection on block norms, tentative prolongation from the rigid-body modes
+// (per-aggregate modified Gram-Schmidt QR, the step Sec. 2 says needs scalar
+// arithmetic, done here inside block-shaped kernels), filtering and the
+// Gershgorin estimate for the prolongation smoother, the smoothed
+// prolongation P = (I - omega D^-1 A_F) P_tent, R = P^T, the block Galerkin
+// product A_c = R (A P) (Sec. 3: the expensive step kept in block form),
+// the SPAI0 smoother, and the dense coarsest-level factorisation.
+//
+// Patterns are symbolic (structurally present products kept, zeros
+// included) and column-sorted; every floating-point sum runs in a fixed
+// order.  The strength norms are computed without fused multiply-adds so
+// that the aggregation sees the same bits on every run and platform.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "amg_internal.cuh"
+
+namespace amg {
+
+constexpr int T1D = 256;
+static inline int nblk(int64_t n, int t = T1D) { return (int)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------- scan
+constexpr int SCAN_T = 512;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_T * SCAN_ITEMS;
+
+__global__ void __launch_bounds__(SCAN_T) scan_tile_kernel(const int *__restrict__ in,
+                                                           int *__restrict__ out, int n,
+                                                           long long *__restrict__ tile_sum)
+{
+    __shared__ long long sh[SCAN_T];
+    const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    long long v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0;
+        s += v[i];
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < SCAN_T; off <<= 1) {
+        long long t = (threadIdx.x >= (unsigned)off) ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    long long run = sh[threadIdx.x] - s;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (base + i < n) out[base + i] = (int)run;  // tile-local, fixed below
+        run += v[i];
+    }
+    if (threadIdx.x == SCAN_T - 1) tile_sum[blockIdx.x] = sh[SCAN_T - 1];
+}
+
+__global__ void scan_add_kernel(int *out, int n, const int *__restrict__ tile_off)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += tile_off[i / SCAN_TILE];
+}
+
+// out[0..n] = exclusive prefix sum of in[0..n-1]; out[n] = total.  The tile
+// totals are combined on the host in 64-bit so that an int32 overflow is
+// reported instead of wrapping.
+int exclusive_scan_i32(const int *in, int *out, int n, int *total_host, DevArena &tmp,
+                       cudaStream_t s)
+{
+    if (n == 0) {
+        AMG_TRY_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
+        if (total_host) *total_host = 0;
+        return AMG_OK;
+    }
+    const int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    long long *tsum = nullptr;
+    int *toff = nullptr;
+    AMG_TRY(tmp.alloc_n(&tsum, ntiles));
+    AMG_TRY(tmp.alloc_n(&toff, ntiles));
+    scan_tile_kernel<<<ntiles, SCAN_T, 0, s>>>(in, out, n, tsum); ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    std::vector<long long> h(ntiles);
+    AMG_TRY_CUDA(cudaMemcpyAsync(h.data(), tsum, sizeof(long long) * ntiles,
+                                 cudaMemcpyDeviceToHost, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> off(ntiles);
+    long long run = 0;
+    for (int t = 0; t < ntiles; ++t) {
+        off[t] = (int)run;
+        run += h[t];
+        if (run > 2147483647LL) {
+            set_error("prefix sum exceeds int32 (%lld)", run);
+            return AMG_ERR_LIMIT;
+        }
+    }
+    AMG_TRY_CUDA(cudaMemcpyAsync(toff, off.data(), sizeof(int) * ntiles,
+                                 cudaMemcpyHostToDevice, s));
+    scan_add_kernel<<<nblk(n), T1D, 0, s>>>(out, n, toff); ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    const int total = (int)run;
+    AMG_TRY_CUDA(cudaMemcpyAsync(out + n, &total, sizeof(int), cudaMemcpyHostToDevice, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));  // `off` and `total` are host stack memory
+    tmp.release(tsum);
+    tmp.release(toff);
+    if (total_host) *total_host = total;
+    return AMG_OK;
+}
+
+// ---------------------------------------------------------------- strength
+// ||A_IJ||_F^2 with squares summed in row-major order, no FMA contraction.
+__device__ __forceinline__ double block_norm2(const double *blk, int bb)
+{
+    double s = 0.0;
+    for (int e = 0; e < bb; ++e) s = __dadd_rn(s, __dmul_rn(blk[e], blk[e]));
+    return s;
+}
+
+__global__ void diag_norm_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                                 const double *__restrict__ val, int nbr, int b,
+                                 double *__restrict__ dn)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nbr) return;
+    double v = 0.0;
+    for (int p = rp[I]; p < rp[I + 1]; ++p)
+        if (col[p] == I) v = __dsqrt_rn(block_norm2(val + (int64_t)p * b * b, b * b));
+    dn[I] = v;
+}
+
+// J != I is strong iff ||A_IJ||^2 > (eps^2 ||A_II||) ||A_JJ||.
+__global__ void strength_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                                const double *__restrict__ val, int nbr, int b, double e2,
+                                const double *__restrict__ dn, uint8_t *__restrict__ strong)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nbr) return;
+    const double dI = dn[I];
+    for (int p = rp[I]; p < rp[I + 1]; ++p) {
+        const int J = col[p];
+        uint8_t st = 0;
+        if (J != I) {
+            const double n2 = block_norm2(val + (int64_t)p * b * b, b * b);
+            double thr = __dmul_rn(e2, dI);
+            thr = __dmul_rn(thr, dn[J]);
+            st = n2 > thr ? 1 : 0;
+        }
+        strong[p] = st;
+    }
+}
+
+int compute_strength(const BsrD &A, double eps, uint8_t *strong, cudaStream_t s)
+{
+    if (A.nbr == 0) return AMG_OK;
+    double *dn = nullptr;
+    AMG_TRY_CUDA(cudaMallocAsync((void **)&dn, sizeof(double) * A.nbr, s));
+    diag_norm_kernel<<<nblk(A.nbr), T1D, 0, s>>>(A.row_ptr, A.col, A.val, A.nbr, A.br, dn); ::amg::count_launch(1);
+    const double e2 = eps * eps;
+    strength_kernel<<<nblk(A.nbr), T1D, 0, s>>>(A.row_ptr, A.col, A.val, A.nbr, A.br, e2, dn,
+                                                strong); ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    AMG_TRY_CUDA(cudaFreeAsync(dn, s));
+    return AMG_OK;
+}
+
+// ---------------------------------------------------------------- tentative P
+template <class T> __device__ __forceinline__ T wsum(T v)
+{
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    return v;
+}
+
+// One warp per aggregate.  The member rows of B (ascending node order, b rows
+// per node) are stacked into Qs (row-major, 6 columns) and orthonormalised by
+// modified Gram-Schmidt with one re-orthogonalisation pass; a column whose
+// norm drops to <= 1e-10 of its original norm is dropped (zero Q column and
+// zero R row).  Every lane owns rows lane, lane+32, ... of the stack, so only
+// the reductions cross lanes.
+__global__ void tentative_kernel(int nagg, int b, const int *__restrict__ agg_ptr,
+                                 const int *__restrict__ members, const double *__restrict__ B,
+                                 double *__restrict__ Qs, double *__restrict__ ptent,
+                                 double *__restrict__ Bc)
+{
+    const int lane = threadIdx.x & 31;
+    const int a = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    if (a >= nagg) return;
+    const int m0 = agg_ptr[a], m = (agg_ptr[a + 1] - m0) * b;
+    double *Q = Qs + (int64_t)m0 * b * 6;
+    for (int i = lane; i < m; i += 32) {
+        const int node = members[m0 + i / b], r = i % b;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Q[i * 6 + k] = B[((int64_t)node * b + r) * 6 + k];
+    }
+    double R[6][6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) R[j][k] = 0.0;
+    bool dropped[6] = {false, false, false, false, false, false};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        double s = 0.0;
+        for (int i = lane; i < m; i += 32) s += Q[i * 6 + k] * Q[i * 6 + k];
+        const double pre = sqrt(wsum(s));
+        for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+            for (int j = 0; j < k; ++j) {
+                if (dropped[j]) continue;
+                double t = 0.0;
+                for (int i = lane; i < m; i += 32) t += Q[i * 6 + j] * Q[i * 6 + k];
+                const double d = wsum(t);
+                R[j][k] += d;
+                for (int i = lane; i < m; i += 32) Q[i * 6 + k] -= d * Q[i * 6 + j];
+            }
+        }
+        s = 0.0;
+        for (int i = lane; i < m; i += 32) s += Q[i * 6 + k] * Q[i * 6 + k];
+        const double post = sqrt(wsum(s));
+        if (post <= 1e-10 * pre) {
+            dropped[k] = true;
+            for (int i = lane; i < m; i += 32) Q[i * 6 + k] = 0.0;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) R[k][j] = 0.0;
+        } else {
+            for (int i = lane; i < m; i += 32) Q[i * 6 + k] /= post;
+            R[k][k] = post;
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+#pragma unroll
+            for (int j = 0; j < 6; ++j) Bc[(int64_t)a * 36 + k * 6 + j] = R[k][j];
+    }
+    for (int i = lane; i < m; i += 32) {
+        const int node = members[m0 + i / b], r = i % b;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ptent[((int64_t)node * b + r) * 6 + k] = Q[i * 6 + k];
+    }
+}
+
+// ---------------------------------------------------------------- filter, rho
+// d_i = a_ii + sum of the weak blocks' entries of scalar row i (ascending
+// columns); g_i = sum_{kept j} |a^F_ij| / |d_i|; rho = max g_i (atomic max on
+// the bits of a non-negative double, order independent).
+__global__ void filter_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                              const double *__restrict__ val, int nbr, int b,
+                              const uint8_t *__restrict__ strong, double *__restrict__ d,
+                              unsigned long long *__restrict__ rho_bits)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nbr) return;
+    const int bb = b * b;
+    int pd = -1;
+    for (int p = rp[I]; p < rp[I + 1]; ++p)
+        if (col[p] == I) pd = p;
+    for (int r = 0; r < b; ++r) {
+        double dia = (pd >= 0) ? val[(int64_t)pd * bb + r * b + r] : 0.0;
+        for (int p = rp[I]; p < rp[I + 1]; ++p)
+            if (col[p] != I && !strong[p])
+                for (int c = 0; c < b; ++c) dia = __dadd_rn(dia, val[(int64_t)p * bb + r * b + c]);
+        d[(int64_t)I * b + r] = dia;
+        double s = 0.0;
+        for (int p = rp[I]; p < rp[I + 1]; ++p) {
+            if (col[p] != I && !strong[p]) continue;
+            for (int c = 0; c < b; ++c) {
+                const double v = (col[p] == I && c == r) ? dia : val[(int64_t)p * bb + r * b + c];
+                s = __dadd_rn(s, fabs(v));
+            }
+        }
+        if (dia != 0.0) {
+            const double g = __ddiv_rn(s, fabs(dia));
+            atomicMax(rho_bits, (unsigned long long)__double_as_longlong(g));
+        }
+    }
+}
+
+// ---------------------------------------------------------------- small sorted sets
+template <int CAP> struct SortedSet {
+    int n = 0;
+    int v[CAP];
+    __device__ __forceinline__ bool insert(int x)
+    {
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (v[mid] < x) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo < n && v[lo] == x) return true;
+        if (n == CAP) return false;
+        for (int t = n; t > lo; --t) v[t] = v[t - 1];
+        v[lo] = x;
+        ++n;
+        return true;
+    }
+};
+
+constexpr int CAP_P = 128;
+constexpr int CAP_AP = 256;
+constexpr int CAP_AC = 512;
+
+__device__ __forceinline__ int find_sorted(const int *a, int lo, int hi, int x)
+{
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// P pattern, row I: the aggregates of I and of its strong neighbours (sorted,
+// unique, isolated nodes skipped).  write = false counts, true fills.
+template <bool WRITE>
+__global__ void p_pattern_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                                 const uint8_t *__restrict__ strong, const int *__restrict__ agg,
+                                 int nbr, int *__restrict__ cnt, const int *__restrict__ prp,
+                                 int *__restrict__ pcol, int *__restrict__ err)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nbr) return;
+    SortedSet<CAP_P> S;
+    for (int p = rp[I]; p < rp[I + 1]; ++p) {
+        const int J = col[p];
+        if ((J == I || strong[p]) && agg[J] >= 0)
+            if (!S.insert(agg[J])) {
+                atomicExch(err, 1);
+                return;
+            }
+    }
+    if (!WRITE) {
+        cnt[I] = S.n;
+    } else {
+        for (int t = 0; t < S.n; ++t) pcol[prp[I] + t] = S.v[t];
+    }
+}
+
+__global__ void block_rows_kernel(const int *__restrict__ rp, int nbr, int *__restrict__ brow)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nbr) return;
+    for (int p = rp[I]; p < rp[I + 1]; ++p) brow[p] = I;
+}
+
+// P block (I, a) = [a == agg(I)] Pt_I - diag(omega / d) sum_{J strong or I,
+// agg(J) = a} A^F_IJ Pt_J, sums over J ascending then the inner index.
+template <int B>
+__global__ void p_values_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                                const double *__restrict__ val, const uint8_t *__restrict__ strong,
+                                const int *__restrict__ agg, const double *__restrict__ ptent,
+                                const double *__restrict__ d, double omega,
+                                const int *__restrict__ pbrow, const int *__restrict__ pcol,
+                                int64_t nnzp, double *__restrict__ pval)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nnzp) return;
+    const int I = pbrow[k], a = pcol[k];
+    double acc[B][6];
+#pragma unroll
+    for (int r = 0; r < B; ++r)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) acc[r][q] = 0.0;
+    for (int p = rp[I]; p < rp[I + 1]; ++p) {
+        const int J = col[p];
+        if (!((J == I || strong[p]) && agg[J] == a)) continue;
+        const double *blk = val + (int64_t)p * B * B;
+        const double *pt = ptent + (int64_t)J * B * 6;
+#pragma unroll
+        for (int r = 0; r < B; ++r)
+#pragma unroll
+            for (int c = 0; c < B; ++c) {
+                const double af = (J == I && r == c) ? d[(int64_t)I * B + r] : blk[r * B + c];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) acc[r][q] += af * pt[c * 6 + q];
+            }
+    }
+    const bool own = agg[I] == a;
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        const double dr = d[(int64_t)I * B + r];
+        const double sc = (dr != 0.0) ? omega / dr : 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const double pt = own ? ptent[((int64_t)I * B + r) * 6 + q] : 0.0;
+            pval[k * B * 6 + r * 6 + q] = pt - sc * acc[r][q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- transpose
+__global__ void col_count_kernel(const int *__restrict__ col, int64_t nnz, int *__restrict__ cnt)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < nnz) atomicAdd(cnt + col[k], 1);
+}
+
+__global__ void transpose_scatter_kernel(const int *__restrict__ brow, const int *__restrict__ col,
+                                         int64_t nnz, const int *__restrict__ trp,
+                                         int *__restrict__ fill, int *__restrict__ tcol,
+                                         int *__restrict__ tsrc)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nnz) return;
+    const int c = col[k];
+    const int pos = trp[c] + atomicAdd(fill + c, 1);
+    tcol[pos] = brow[k];
+    tsrc[pos] = (int)k;
+}
+
+// Sort each transposed row by column (the scatter order is arbitrary): the
+// result does not depend on the order of the atomics.
+__global__ void row_sort_kernel(const int *__restrict__ trp, int nrows, int *__restrict__ tcol,
+                                int *__restrict__ tsrc)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const int lo = trp[r], hi = trp[r + 1];
+    for (int i = lo + 1; i < hi; ++i) {
+        const int c = tcol[i], s = tsrc[i];
+        int j = i - 1;
+        while (j >= lo && tcol[j] > c) {
+            tcol[j + 1] = tcol[j];
+            tsrc[j + 1] = tsrc[j];
+            --j;
+        }
+        tcol[j + 1] = c;
+        tsrc[j + 1] = s;
+    }
+}
+
+// R block q = (P block src)^T : (BR x BC) -> (BC x BR)
+__global__ void transpose_values_kernel(const int *__restrict__ tsrc, int64_t nnz, int br, int bc,
+                                        const double *__restrict__ pval, double *__restrict__ rval)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nnz) return;
+    const double *src = pval + (int64_t)tsrc[q] * br * bc;
+    double *dst = rval + q * br * bc;
+    for (int r = 0; r < br; ++r)
+        for (int c = 0; c < bc; ++c) dst[c * br + r] = src[r * bc + c];
+}
+
+static int transpose_bsr(const BsrD &P, const int *pbrow, DevArena &keep, DevArena &tmp,
+                         cudaStream_t s, BsrD *R)
+{
+    R->nbr = P.nbc;
+    R->nbc = P.nbr;
+    R->br = P.bc;
+    R->bc = P.br;
+    R->nnzb = P.nnzb;
+    int *cnt = nullptr, *fill = nullptr, *tsrc = nullptr;
+    AMG_TRY(tmp.alloc_n(&cnt, (size_t)R->nbr + 1));
+    AMG_TRY(tmp.alloc_n(&fill, (size_t)R->nbr + 1));
+    AMG_TRY(tmp.alloc_n(&tsrc, (size_t)std::max<int64_t>(P.nnzb, 1)));
+    AMG_TRY(keep.alloc_n(&R->row_ptr, (size_t)R->nbr + 1));
+    AMG_TRY(keep.alloc_n(&R->col, (size_t)std::max<int64_t>(P.nnzb, 1)));
+    AMG_TRY(keep.alloc_n(&R->val, (size_t)std::max<int64_t>(P.nnzb, 1) * P.br * P.bc));
+    AMG_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (R->nbr + 1), s));
+    AMG_TRY_CUDA(cudaMemsetAsync(fill, 0, sizeof(int) * (R->nbr + 1), s));
+    if (P.nnzb > 0) {
+        col_count_kernel<<<nblk(P.nnzb), T1D, 0, s>>>(P.col, P.nnzb, cnt); ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
+    int total = 0;
+    AMG_TRY(exclusive_scan_i32(cnt, R->row_ptr, R->nbr, &total, tmp, s));
+    if (P.nnzb > 0) {
+        transpose_scatter_kernel<<<nblk(P.nnzb), T1D, 0, s>>>(pbrow, P.col, P.nnzb, R->row_ptr,
+                                                               fill, R->col, tsrc); ::amg::count_launch(1);
+        row_sort_kernel<<<nblk(R->nbr), T1D, 0, s>>>(R->row_ptr, R->nbr, R->col, tsrc); ::amg::count_launch(1);
+        transpose_values_kernel<<<nblk(P.nnzb), T1D, 0, s>>>(tsrc, P.nnzb, P.br, P.bc, P.val,
+                                                              R->val); ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
+    tmp.release(cnt);
+    tmp.release(fill);
+    tmp.release(tsrc);
+    return AMG_OK;
+}
+
+// ---------------------------------------------------------------- SpGEMM
+// Row pattern of C = X Y: the union of Y's row patterns over X's columns.
+template <int CAP, bool WRITE>
+__global__ void spgemm_pattern_kernel(const int *__restrict__ xrp, const int *__restrict__ xcol,
+                                      const int *__restrict__ yrp, const int *__restrict__ ycol,
+                                      int nrows, int *__restrict__ cnt, const int *__restrict__ crp,
+                                      int *__restrict__ ccol, int *__restrict__ err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows) return;
+    SortedSet<CAP> S;
+    for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
+        const int k = xcol[p];
+        for (int q = yrp[k]; q < yrp[k + 1]; ++q)
+            if (!S.insert(ycol[q])) {
+                atomicExch(err, 1);
+                return;
+            }
+    }
+    if (!WRITE) {
+        cnt[i] = S.n;
+    } else {
+        for (int t = 0; t < S.n; ++t) ccol[crp[i] + t] = S.v[t];
+    }
+}
+
+// C block (i, j) = sum over X row i (ascending) of X_ik Y_kj; blocks XR x XC
+// and XC x YC, the inner sums over k ascending then the inner index.
+template <int XR, int XC, int YC>
+__global__ void spgemm_values_kernel(const int *__restrict__ xrp, const int *__restrict__ xcol,
+                                     const double *__restrict__ xval, const int *__restrict__ yrp,
+                                     const int *__restrict__ ycol, const double *__restrict__ yval,
+                                     const int *__restrict__ cbrow, const int *__restrict__ ccol,
+                                     int64_t nnzc, double *__restrict__ cval)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nnzc) return;
+    const int i = cbrow[q], j = ccol[q];
+    double acc[XR][YC];
+#pragma unroll
+    for (int r = 0; r < XR; ++r)
+#pragma unroll
+        for (int c = 0; c < YC; ++c) acc[r][c] = 0.0;
+    for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
+        const int k = xcol[p];
+        const int lo = yrp[k], hi = yrp[k + 1];
+        const int t = find_sorted(ycol, lo, hi, j);
+        if (t >= hi || ycol[t] != j) continue;
+        const double *xb = xval + (int64_t)p * XR * XC;
+        const double *yb = yval + (int64_t)t * XC * YC;
+#pragma unroll
+        for (int r = 0; r < XR; ++r)
+#pragma unroll
+            for (int m = 0; m < XC; ++m) {
+                const double xv = xb[r * XC + m];
+#pragma unroll
+                for (int c = 0; c < YC; ++c) acc[r][c] += xv * yb[m * YC + c];
+            }
+    }
+#pragma unroll
+    for (int r = 0; r < XR; ++r)
+#pragma unroll
+        for (int c = 0; c < YC; ++c) cval[q * XR * YC + r * YC + c] = acc[r][c];
+}
+
+template <int CAP>
+static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, cudaStream_t s,
+                  BsrD *C)
+{
+    C->nbr = X.nbr;
+    C->nbc = Y.nbc;
+    C->br = X.br;
+    C->bc = Y.bc;
+    int *cnt = nullptr, *err = nullptr;
+    AMG_TRY(tmp.alloc_n(&cnt, (size_t)X.nbr + 1));
+    AMG_TRY(tmp.alloc_n(&err, 1));
+    AMG_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    AMG_TRY(keep.alloc_n(&C->row_ptr, (size_t)X.nbr + 1));
+    if (X.nbr > 0) {
+        spgemm_pattern_kernel<CAP, false><<<nblk(X.nbr), T1D, 0, s>>>(
+            X.row_ptr, X.col, Y.row_ptr, Y.col, X.nbr, cnt, nullptr, nullptr, err);
+        ::amg::count_launch(1);
+    }
+    AMG_TRY_CUDA(cudaGetLastError());
+    int total = 0;
+    AMG_TRY(exclusive_scan_i32(cnt, C->row_ptr, X.nbr, &total, tmp, s));
+    int herr = 0;
+    AMG_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    if (herr) {
+        set_error("sparse product row has more than %d distinct block columns", CAP);
+        return AMG_ERR_LIMIT;
+    }
+    C->nnzb = total;
+    AMG_TRY(keep.alloc_n(&C->col, (size_t)std::max(total, 1)));
+    AMG_TRY(keep.alloc_n(&C->val, (size_t)std::max(total, 1) * C->br * C->bc));
+    int *cbrow = nullptr;
+    AMG_TRY(tmp.alloc_n(&cbrow, (size_t)std::max(total, 1)));
+    if (X.nbr > 0) {
+        spgemm_pattern_kernel<CAP, true><<<nblk(X.nbr), T1D, 0, s>>>(
+            X.row_ptr, X.col, Y.row_ptr, Y.col, X.nbr, nullptr, C->row_ptr, C->col, err); ::amg::count_launch(1);
+        block_rows_kernel<<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, X.nbr, cbrow); ::amg::count_launch(1);
+    }
+    AMG_TRY_CUDA(cudaGetLastError());
+    if (total > 0) {
+        const int g = nblk(total, 128);
+        const int xr = X.br, xc = X.bc, yc = Y.bc;
+#define AMG_SPGEMM_VALS(XR_, XC_, YC_)                                                       \
+    spgemm_values_kernel<XR_, XC_, YC_><<<g, 128, 0, s>>>(X.row_ptr, X.col, X.val, Y.row_ptr, \
+                                                          Y.col, Y.val, cbrow, C->col, total, \
+                                                          C->val)
+        if (xr == 3 && xc == 3 && yc == 6) AMG_SPGEMM_VALS(3, 3, 6);
+        else if (xr == 6 && xc == 6 && yc == 6) AMG_SPGEMM_VALS(6, 6, 6);
+        else if (xr == 6 && xc == 3 && yc == 6) AMG_SPGEMM_VALS(6, 3, 6);
+        else {
+            set_error("unsupported block product %dx%d * %dx%d", xr, xc, X.bc, yc);
+            return AMG_ERR_ARG;
+        }
+        ::amg::count_launch(1);
+#undef AMG_SPGEMM_VALS
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
+    tmp.release(cnt);
+    tmp.release(err);
+    tmp.release(cbrow);
+    return AMG_OK;
+}
+
+// Galerkin operator A_c = R (A P) (Alg. 1), block SpGEMM twice.
+int galerkin(const BsrD &A, const BsrD &P, const BsrD &R, DevArena &keep, DevArena &tmp,
+             cudaStream_t s, BsrD *Ac)
+{
+    BsrD AP;
+    DevArena apmem;
+    apmem.stream = s;
+    int st = spgemm<CAP_AP>(A, P, apmem, tmp, s, &AP);
+    if (st >= 0) st = spgemm<CAP_AC>(R, AP, keep, tmp, s, Ac);
+    apmem.release_all();
+    return st;
+}
+
+// ---------------------------------------------------------------- transfer operators
+int build_transfer(const BsrD &A, const double *B, const uint8_t *strong, const int *agg_h,
+                   int nagg, double relax, DevArena &keep, DevArena &tmp, cudaStream_t s,
+                   LevelBuild *out)
+{
+    const int nn = A.nbr, b = A.br;
+    // aggregate membership lists (ascending node order) from the host aggregation
+    std::vector<int> aptr(nagg + 1, 0), mem;
+    for (int I = 0; I < nn; ++I)
+        if (agg_h[I] >= 0) aptr[agg_h[I] + 1]++;
+    for (int a = 0; a < nagg; ++a) aptr[a + 1] += aptr[a];
+    mem.resize(std::max(aptr[nagg], 1));
+    {
+        std::vector<int> fill(aptr.begin(), aptr.end() - 1);
+        for (int I = 0; I < nn; ++I)
+            if (agg_h[I] >= 0) mem[fill[agg_h[I]]++] = I;
+    }
+    int *d_aptr = nullptr, *d_mem = nullptr;
+    double *Qs = nullptr, *ptent = nullptr, *d = nullptr;
+    unsigned long long *rho_bits = nullptr;
+    AMG_TRY(tmp.alloc_n(&d_aptr, nagg + 1));
+    AMG_TRY(tmp.alloc_n(&d_mem, mem.size()));
+    AMG_TRY(keep.alloc_n(&out->agg, std::max(nn, 1)));
+    AMG_TRY(tmp.alloc_n(&Qs, (size_t)std::max(aptr[nagg], 1) * b * 6));
+    AMG_TRY(tmp.alloc_n(&ptent, (size_t)std::max(nn, 1) * b * 6));
+    AMG_TRY(tmp.alloc_n(&d, (size_t)std::max(nn, 1) * b));
+    AMG_TRY(tmp.alloc_n(&rho_bits, 1));
+    AMG_TRY(keep.alloc_n(&out->Bc, (size_t)std::max(nagg, 1) * 36));
+    AMG_TRY_CUDA(cudaMemcpyAsync(d_aptr, aptr.data(), sizeof(int) * (nagg + 1),
+                                 cudaMemcpyHostToDevice, s));
+    AMG_TRY_CUDA(cudaMemcpyAsync(d_mem, mem.data(), sizeof(int) * mem.size(),
+                                 cudaMemcpyHostToDevice, s));
+    AMG_TRY_CUDA(cudaMemcpyAsync(out->agg, agg_h, sizeof(int) * nn, cudaMemcpyHostToDevice, s));
+    AMG_TRY_CUDA(cudaMemsetAsync(ptent, 0, sizeof(double) * (size_t)nn * b * 6, s));
+    AMG_TRY_CUDA(cudaMemsetAsync(rho_bits, 0, sizeof(unsigned long long), s));
+    out->nagg = nagg;
+    if (nagg > 0) {
+        tentative_kernel<<<nblk((int64_t)nagg * 32), T1D, 0, s>>>(nagg, b, d_aptr, d_mem, B, Qs,
+                                                                   ptent, out->Bc); ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
+    filter_kernel<<<nblk(nn), T1D, 0, s>>>(A.row_ptr, A.col, A.val, nn, b, strong, d, rho_bits); ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    unsigned long long rb = 0;
+    AMG_TRY_CUDA(cudaMemcpyAsync(&rb, rho_bits, sizeof(rb), cudaMemcpyDeviceToHost, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope after this
+    double rho;
+    std::memcpy(&rho, &rb, sizeof rho);
+    out->rho = rho;
+    out->omega = (rho > 0.0) ? relax * (4.0 / 3.0) / rho : 0.0;
+
+    // P pattern and values
+    BsrD &P = out->P;
+    P.nbr = nn;
+    P.nbc = nagg;
+    P.br = b;
+    P.bc = 6;
+    int *cnt = nullptr, *err = nullptr;
+    AMG_TRY(tmp.alloc_n(&cnt, (size_t)nn + 1));
+    AMG_TRY(tmp.alloc_n(&err, 1));
+    AMG_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    AMG_TRY(keep.alloc_n(&P.row_ptr, (size_t)nn + 1));
+    p_pattern_kernel<false><<<nblk(nn), T1D, 0, s>>>(A.row_ptr, A.col, strong, out->agg, nn, cnt,
+                                                     nullptr, nullptr, err); ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    int nnzp = 0;
+    AMG_TRY(exclusive_scan_i32(cnt, P.row_ptr, nn, &nnzp, tmp, s));
+    int herr = 0;
+    AMG_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    if (herr) {
+        set_error("prolongation row has more than %d aggregates", CAP_P);
+        return AMG_ERR_LIMIT;
+    }
+    P.nnzb = nnzp;
+    int *pbrow = nullptr;
+    AMG_TRY(keep.alloc_n(&P.col, (size_t)std::max(nnzp, 1)));
+    AMG_TRY(keep.alloc_n(&P.val, (size_t)std::max(nnzp, 1) * b * 6));
+    AMG_TRY(tmp.alloc_n(&pbrow, (size_t)std::max(nnzp, 1)));
+    p_pattern_kernel<true><<<nblk(nn), T1D, 0, s>>>(A.row_ptr, A.col, strong, out->agg, nn,
+                                                    nullptr, P.row_ptr, P.col, err); ::amg::count_launch(1);
+    block_rows_kernel<<<nblk(nn), T1D, 0, s>>>(P.row_ptr, nn, pbrow); ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    if (nnzp > 0) {
+        if (b == 3)
+            p_values_kernel<3><<<nblk(nnzp, 128), 128, 0, s>>>(A.row_ptr, A.col, A.val, strong,
+                                                               out->agg, ptent, d, out->omega,
+                                                               pbrow, P.col, nnzp, P.val);
+        else if (b == 6)
+            p_values_kernel<6><<<nblk(nnzp, 128), 128, 0, s>>>(A.row_ptr, A.col, A.val, strong,
+                                                               out->agg, ptent, d, out->omega,
+                                                               pbrow, P.col, nnzp, P.val);
+        else {
+            set_error("unsupported node block size %d", b);
+            return AMG_ERR_ARG;
+        }
+        ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
+    AMG_TRY(transpose_bsr(P, pbrow, keep, tmp, s, &out->R));
+    tmp.release(d_aptr);
+    tmp.release(d_mem);
+    tmp.release(Qs);
+    tmp.release(ptent);
+    tmp.release(d);
+    tmp.release(rho_bits);
+    tmp.release(cnt);
+    tmp.release(err);
+    tmp.release(pbrow);
+    return AMG_OK;
+}
+
+// ---------------------------------------------------------------- SPAI0
+// m_i = scale * a_ii / sum_j a_ij^2 over scalar row i (0 for an empty row).
+__global__ void spai0_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                             const double *__restrict__ val, int nbr, int b, double scale,
+                             double *__restrict__ M)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nbr) return;
+    const int bb = b * b;
+    for (int r = 0; r < b; ++r) {
+        double dia = 0.0, s = 0.0;
+        for (int p = rp[I]; p < rp[I + 1]; ++p)
+            for (int c = 0; c < b; ++c) {
+                const double v = val[(int64_t)p * bb + r * b + c];
+                if (col[p] == I && c == r) dia = v;
+                s += v * v;
+            }
+        const double m = (s != 0.0) ? dia / s : 0.0;
+        M[(int64_t)I * b + r] = scale * m;
+    }
+}
+
+int spai0_diag(const BsrD &A, double scale, double *M, cudaStream_t s)
+{
+    if (A.nbr == 0) return AMG_OK;
+    spai0_kernel<<<nblk(A.nbr), T1D, 0, s>>>(A.row_ptr, A.col, A.val, A.nbr, A.br, scale, M); ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    return AMG_OK;
+}
+
+// ---------------------------------------------------------------- coarsest level
+__global__ void densify_kernel(const int *__restrict__ brow, const int *__restrict__ col,
+                               const double *__restrict__ val, int64_t nnzb, int b, int n,
+                               double *__restrict__ D)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nnzb) return;
+    const int I = brow[k], J = col[k];
+    for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c)
+            D[(int64_t)(I * b + r) * n + (J * b + c)] = val[k * b * b + r * b + c];
+}
+
+__global__ void zero_rows_kernel(const double *__restrict__ D, int n, uint8_t *__restrict__ z)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint8_t zr = 1;
+    for (int j = 0; j < n; ++j)
+        if (D[(int64_t)i * n + j] != 0.0) zr = 0;
+    z[i] = zr;
+}
+
+// Right-looking Cholesky, column j: pivot and scaled column below it.
+__global__ void chol_column_kernel(double *__restrict__ D, int n, int j,
+                                   const uint8_t *__restrict__ zrow, int *__restrict__ err)
+{
+    __shared__ double ljj;
+    if (threadIdx.x == 0) {
+        double s = D[(int64_t)j * n + j];
+        if (zrow[j]) s = 1.0;
+        if (!(s > 0.0)) {
+            atomicExch(err, j + 1);
+            s = 1.0;
+        }
+        ljj = sqrt(s);
+        D[(int64_t)j * n + j] = ljj;
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) D[(int64_t)i * n + j] /= ljj;
+}
+
+// trailing update D[i][k] -= L[i][j] L[k][j] for j < k <= i < n
+__global__ void chol_update_kernel(double *__restrict__ D, int n, int j)
+{
+    const int m = n - j - 1;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)m * m) return;
+    const int i = j + 1 + (int)(t / m), k = j + 1 + (int)(t % m);
+    if (k > i) return;
+    D[(int64_t)i * n + k] -= D[(int64_t)i * n + j] * D[(int64_t)k * n + j];
+}
+
+// X[:, k] = A^{-1} e_k by forward/backward substitution with L (lower
+// triangle of D), one CTA per column; zero rows give zero rows/columns.
+__global__ void chol_inverse_kernel(const double *__restrict__ D, int n,
+                                    const uint8_t *__restrict__ zrow, double *__restrict__ X)
+{
+    extern __shared__ double y[];
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (i == k) ? 1.0 : 0.0;
+        __syncthreads();
+        for (int i = 0; i < n; ++i) {  // L y = e_k
+            if (threadIdx.x == 0) y[i] = zrow[i] ? 0.0 : y[i] / D[(int64_t)i * n + i];
+            __syncthreads();
+            const double yi = y[i];
+            for (int m = i + 1 + threadIdx.x; m < n; m += blockDim.x)
+                y[m] -= D[(int64_t)m * n + i] * yi;
+            __syncthreads();
+        }
+        for (int i = n - 1; i >= 0; --i) {  // L^T x = y
+            if (threadIdx.x == 0) y[i] = y[i] / D[(int64_t)i * n + i];
+            __syncthreads();
+            const double xi = y[i];
+            for (int m = threadIdx.x; m < i; m += blockDim.x) y[m] -= D[(int64_t)i * n + m] * xi;
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            X[(int64_t)i * n + k] = (zrow[i] || zrow[k]) ? 0.0 : y[i];
+        __syncthreads();
+    }
+}
+
+constexpr int COARSE_MAX = 20000;
+
+int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
+                   double **Ainv_out)
+{
+    const int n = A.nbr * A.br;
+    if (n > COARSE_MAX) {
+        set_error("coarsest system has %d unknowns (limit %d)", n, COARSE_MAX);
+        return AMG_ERR_LIMIT;
+    }
+    double *D = nullptr, *X = nullptr;
+    uint8_t *z = nullptr;
+    int *brow = nullptr, *err = nullptr;
+    AMG_TRY(tmp.alloc_n(&D, (size_t)n * n));
+    AMG_TRY(keep.alloc_n(&X, (size_t)n * n));
+    AMG_TRY(tmp.alloc_n(&z, n));
+    AMG_TRY(tmp.alloc_n(&brow, (size_t)std::max<int64_t>(A.nnzb, 1)));
+    AMG_TRY(tmp.alloc_n(&err, 1));
+    AMG_TRY_CUDA(cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n * n, s));
+    AMG_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    block_rows_kernel<<<nblk(A.nbr), T1D, 0, s>>>(A.row_ptr, A.nbr, brow); ::amg::count_launch(1);
+    if (A.nnzb > 0) {
+        densify_kernel<<<nblk(A.nnzb), T1D, 0, s>>>(brow, A.col, A.val, A.nnzb, A.br, n, D); ::amg::count_launch(1); }
+    zero_rows_kernel<<<nblk(n), T1D, 0, s>>>(D, n, z); ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    for (int j = 0; j < n; ++j) {
+        chol_column_kernel<<<1, 256, 0, s>>>(D, n, j, z, err); ::amg::count_launch(1);
+        const int64_t m = (int64_t)(n - j - 1) * (n - j - 1);
+        if (m > 0) { chol_update_kernel<<<nblk(m), T1D, 0, s>>>(D, n, j); ::amg::count_launch(1); }
+    }
+    AMG_TRY_CUDA(cudaGetLastError());
+    int herr = 0;
+    AMG_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    if (herr) {
+        set_error("coarsest matrix is not positive definite (pivot %d)", herr - 1);
+        return AMG_ERR_COARSE;
+    }
+    const size_t smem = sizeof(double) * (size_t)n;
+    if (smem > 48 * 1024)
+        AMG_TRY_CUDA(cudaFuncSetAttribute(chol_inverse_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = n < 1 ? 1 : n;
+    if (grid > 4096) grid = 4096;
+    if (n > 0) { chol_inverse_kernel<<<grid, 256, smem, s>>>(D, n, z, X); ::amg::count_launch(1); }
+    AMG_TRY_CUDA(cudaGetLastError());
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    tmp.release(D);
+    tmp.release(z);
+    tmp.release(brow);
+    tmp.release(err);
+    *Ainv_out = X;
+    return AMG_OK;
+}
+
+}  // namespace amg

@@ -1,0 +1,938 @@
+// The hierarchy handle, the setup loop (Alg. 1), the V-cycle (Alg. 2) and the
+// device-resident preconditioned CG of Sec. 4, and the C ABI around them.
+//
+// The CG loop is one CUDA graph: a conditional WHILE node whose body holds
+// one full iteration (V-cycle, direction update, A p with the fused p.Ap,
+// u/r updates with the fused ||r||^2, the true-residual confirmation).  All
+// scalars (alpha, beta, norms, counters, flags) live in device memory; the
+// last kernel of the body clears the loop condition once the solve has
+// converged, reached maxiter or broken down.  The host synchronises only
+// before the loop (initial residual) and after it.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "amg_internal.cuh"
+
+namespace amg {
+const char *last_error();
+
+struct Level {
+    BsrD A, P, R;
+    double *M = nullptr;      // damped SPAI0 diagonal (scalar rows)
+    double *B = nullptr;      // near-nullspace, n x 6
+    int *agg = nullptr;       // aggregate of each node (device)
+    uint8_t *strong = nullptr;
+    int nagg = 0;
+    bool coarsest = false;
+    double eps = 0, omega = 0, rho = 0;
+    double *f = nullptr, *u = nullptr, *e = nullptr, *z = nullptr, *t = nullptr;
+    int n() const { return A.nbr * A.br; }
+};
+
+constexpr int FIN_THREADS = 256;
+
+template <int NT> __device__ __forceinline__ double block_sum_fixed(const double *p, int n)
+{
+    __shared__ double red[NT];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += NT) v += p[i];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = NT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < (unsigned)w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    return red[0];
+}
+
+__global__ void __launch_bounds__(256) vec_dot_kernel(const double *__restrict__ x,
+                                                      const double *__restrict__ y, int64_t n,
+                                                      double *__restrict__ partials)
+{
+    double v = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v += x[i] * y[i];
+    __shared__ double red[256];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < (unsigned)w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+// t = M r (pre-smoothing from a zero guess) or t = 0 when there is no pre-smoothing.
+__global__ void scale_kernel(const double *__restrict__ M, const double *__restrict__ r,
+                             double *__restrict__ t, int64_t n, int zero)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        t[i] = zero ? 0.0 : M[i] * r[i];
+}
+
+__global__ void cg_start_kernel(CgState *st, const double *__restrict__ scal, double tol,
+                                int maxiter)
+{
+    const double nf = sqrt(scal[0]);
+    st->tol = tol;
+    st->maxiter = maxiter;
+    st->nf = nf;
+    st->res = nf > 0.0 ? sqrt(scal[1]) / nf : 0.0;
+    st->res_true = st->res;
+    st->rz = st->pq = st->alpha = st->beta = 0.0;
+    st->it = 0;
+    st->check = st->replace = st->converged = st->stop = 0;
+    st->no_check = 1;
+    st->no_replace = 1;
+    st->status = AMG_NOT_CONVERGED;
+}
+
+// beta = (r.z)_new / (r.z)_old (0 on the first iteration)
+__global__ void __launch_bounds__(FIN_THREADS) cg_beta_kernel(CgState *st,
+                                                             const double *__restrict__ part,
+                                                             int np)
+{
+    const double rz = block_sum_fixed<FIN_THREADS>(part, np);
+    if (threadIdx.x != 0 || st->stop) return;
+    if (!(rz > 0.0) || !isfinite(rz)) {
+        st->status = AMG_ERR_BREAKDOWN;
+        st->stop = 1;
+        st->no_check = 1;
+        st->no_replace = 1;
+        return;
+    }
+    st->beta = (st->it == 0) ? 0.0 : rz / st->rz;
+    st->rz = rz;
+}
+
+__global__ void cg_direction_kernel(const double *__restrict__ z, double *__restrict__ p,
+                                    const CgState *__restrict__ st, int64_t n)
+{
+    if (st->stop) return;
+    const double beta = st->beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+}
+
+__global__ void __launch_bounds__(FIN_THREADS) cg_alpha_kernel(CgState *st,
+                                                              const double *__restrict__ part,
+                                                              int np)
+{
+    const double pq = block_sum_fixed<FIN_THREADS>(part, np);
+    if (threadIdx.x != 0 || st->stop) return;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+        st->status = AMG_ERR_BREAKDOWN;
+        st->stop = 1;
+        st->no_check = 1;
+        st->no_replace = 1;
+        return;
+    }
+    st->pq = pq;
+    st->alpha = st->rz / pq;
+}
+
+// u += alpha p ; r -= alpha q ; t0 = M r (next pre-smoothing) ; partial r.r
+__global__ void __launch_bounds__(256) cg_update_kernel(double *__restrict__ u, double *__restrict__ r,
+                                                        const double *__restrict__ p,
+                                                        const double *__restrict__ q,
+                                                        const double *__restrict__ M,
+                                                        double *__restrict__ t0,
+                                                        const CgState *__restrict__ st, int64_t n,
+                                                        int pre, double *__restrict__ partials)
+{
+    if (st->stop) return;
+    const double alpha = st->alpha;
+    double v = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        u[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        if (t0) t0[i] = pre ? M[i] * ri : 0.0;
+        v += ri * ri;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < (unsigned)w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(FIN_THREADS) cg_resnorm_kernel(CgState *st,
+                                                                const double *__restrict__ part,
+                                                                int np)
+{
+    const double rr = block_sum_fixed<FIN_THREADS>(part, np);
+    if (threadIdx.x != 0 || st->stop) return;
+    st->res = sqrt(rr) / st->nf;
+    st->it += 1;
+    st->no_check = (st->res <= st->tol) ? 0 : 1;
+}
+
+// Confirmation with the true residual and the loop decision.
+__global__ void __launch_bounds__(FIN_THREADS) cg_decide_kernel(CgState *st,
+                                                               const double *__restrict__ part,
+                                                               int np,
+                                                               cudaGraphConditionalHandle cond,
+                                                               int use_cond)
+{
+    const double rr = block_sum_fixed<FIN_THREADS>(part, np);
+    if (threadIdx.x != 0) return;
+    if (!st->stop) {
+        st->replace = 0;
+        if (!st->no_check) {
+            const double tr = sqrt(rr) / st->nf;
+            st->res_true = tr;
+            if (tr <= st->tol) {
+                st->converged = 1;
+                st->stop = 1;
+                st->status = AMG_OK;
+            } else {
+                st->replace = 1;
+            }
+        }
+        st->no_replace = st->replace ? 0 : 1;
+        if (!st->stop && st->it >= st->maxiter) {
+            st->stop = 1;
+            st->status = AMG_NOT_CONVERGED;
+        }
+    }
+    if (st->stop) {
+        st->no_replace = 1;
+        if (use_cond) cudaGraphSetConditional(cond, 0);
+    }
+}
+
+// r = r_true (residual replacement) and the matching pre-smoothed t0.
+__global__ void cg_replace_kernel(double *__restrict__ r, const double *__restrict__ rt,
+                                  const double *__restrict__ M, double *__restrict__ t0,
+                                  const CgState *__restrict__ st, int64_t n, int pre)
+{
+    if (st->no_replace) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = rt[i];
+        r[i] = ri;
+        if (t0) t0[i] = pre ? M[i] * ri : 0.0;
+    }
+}
+
+}  // namespace amg
+
+using namespace amg;
+
+struct amg_handle_s {
+    amg_params prm;
+    cudaStream_t stream = nullptr;
+    Geom geom;
+    DevArena mem;
+    std::vector<Level> lv;
+    double *Ainv = nullptr;
+    int nc = 0;
+    double *ff = nullptr, *uu = nullptr, *r = nullptr, *p = nullptr, *q = nullptr,
+           *z = nullptr, *rt = nullptr, *partials = nullptr, *scal = nullptr;
+    CgState *st = nullptr;
+    CgState *st_h = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long body_kernels = 0;   // kernels in one iteration of the graph body
+    double setup_seconds = 0.0;
+};
+
+static SpmvArgs<double> args_for(const BsrD &A)
+{
+    SpmvArgs<double> a{};
+    a.row_ptr = A.row_ptr;
+    a.col = A.col;
+    a.val = A.val;
+    a.nbr = A.nbr;
+    return a;
+}
+
+static int vgrid(amg_handle h, int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    if (g > h->geom.max_ctas) g = h->geom.max_ctas;
+    return (int)std::max<int64_t>(g, 1);
+}
+
+// One V-cycle (Alg. 2) from a zero initial guess: z0 = V(f0).  lv[0].u must
+// already hold the first pre-smoothing sweep M_0 f0 (or zero without
+// pre-smoothing).  With rz_partials, the last level-0 kernel also leaves the
+// per-CTA partial sums of f0 . z0.
+static int record_vcycle(amg_handle h, const double *f0, double *z0, double *rz_partials,
+                         cudaStream_t s)
+{
+    const int L = (int)h->lv.size() - 1;
+    const int npre = h->prm.npre, npost = h->prm.npost;
+    const Geom &g = h->geom;
+    std::vector<double *> ucur(L + 1, nullptr), spare(L + 1, nullptr);
+    for (int l = 0; l < L; ++l) {
+        Level &C = h->lv[l];
+        Level &N = h->lv[l + 1];
+        const double *f = (l == 0) ? f0 : C.f;
+        double *u = C.u, *t = C.t;
+        for (int sweep = 1; sweep < npre; ++sweep) {  // further pre-smoothing sweeps
+            SpmvArgs<double> a = args_for(C.A);
+            a.x = u;
+            a.f = f;
+            a.M = C.M;
+            a.y = t;
+            AMG_TRY((launch_spmv<double, double>(C.A.br, C.A.bc, SPMV_SMOOTH, DOT_NONE, a, g, s)));
+            std::swap(u, t);
+        }
+        ucur[l] = u;
+        spare[l] = t;
+        {  // e = f - A u
+            SpmvArgs<double> a = args_for(C.A);
+            a.x = u;
+            a.f = f;
+            a.y = C.e;
+            AMG_TRY((launch_spmv<double, double>(C.A.br, C.A.bc, SPMV_RESID, DOT_NONE, a, g, s)));
+        }
+        {  // f_{l+1} = R e ; u_{l+1} = M_{l+1} f_{l+1}
+            SpmvArgs<double> a = args_for(C.R);
+            a.x = C.e;
+            a.y = N.f;
+            const bool next_smooths = (l + 1 < L);
+            a.y2 = next_smooths ? N.u : nullptr;
+            a.M = (next_smooths && npre > 0) ? N.M : nullptr;
+            AMG_TRY((launch_spmv<double, double>(C.R.br, C.R.bc, SPMV_RESTRICT, DOT_NONE, a, g,
+                                                 s)));
+        }
+    }
+    {  // coarsest: direct solve with the dense inverse
+        Level &Cc = h->lv[L];
+        const double *fL = (L == 0) ? f0 : Cc.f;
+        double *zL = (L == 0) ? z0 : Cc.z;
+        AMG_TRY(launch_coarse_gemv<double>(h->Ainv, h->nc, fL, zL, g, s));
+        if (L == 0 && rz_partials) {
+            vec_dot_kernel<<<vgrid(h, h->nc), 256, 0, s>>>(f0, z0, h->nc, rz_partials); ::amg::count_launch(1);
+            AMG_TRY_CUDA(cudaGetLastError());
+        }
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        Level &C = h->lv[l];
+        Level &N = h->lv[l + 1];
+        const double *f = (l == 0) ? f0 : C.f;
+        double *u = ucur[l], *t = spare[l];
+        double *zl = (l == 0) ? z0 : C.z;
+        {  // u += P z_{l+1}
+            SpmvArgs<double> a = args_for(C.P);
+            a.x = N.z;
+            a.u = u;
+            a.y = u;
+            AMG_TRY((launch_spmv<double, double>(C.P.br, C.P.bc, SPMV_AXPY, DOT_NONE, a, g, s)));
+        }
+        const double *w = u;
+        for (int sweep = 0; sweep < npost; ++sweep) {  // u += M (f - A u)
+            const bool last = (sweep == npost - 1);
+            double *out = last ? zl : t;
+            SpmvArgs<double> a = args_for(C.A);
+            a.x = w;
+            a.f = f;
+            a.M = C.M;
+            a.y = out;
+            a.partials = rz_partials;
+            const int dot = (l == 0 && last && rz_partials) ? DOT_FY : DOT_NONE;
+            AMG_TRY((launch_spmv<double, double>(C.A.br, C.A.bc, SPMV_SMOOTH, dot, a, g, s)));
+            w = out;
+            t = (out == t) ? u : t;  // ping-pong between u and t
+        }
+        if (npost == 0) {
+            AMG_TRY_CUDA(cudaMemcpyAsync(zl, u, sizeof(double) * C.n(), cudaMemcpyDeviceToDevice, s));
+            if (l == 0 && rz_partials) {
+                vec_dot_kernel<<<vgrid(h, C.n()), 256, 0, s>>>(f0, z0, C.n(), rz_partials); ::amg::count_launch(1);
+                AMG_TRY_CUDA(cudaGetLastError());
+            }
+        }
+    }
+    return AMG_OK;
+}
+
+// Number of partial sums the level-0 fused r.z leaves (= the grid of the
+// kernel that computes it).
+static int rz_parts(amg_handle h)
+{
+    const Level &L0 = h->lv[0];
+    if (h->lv.size() == 1) return vgrid(h, h->nc);
+    if (h->prm.npost == 0) return vgrid(h, L0.n());
+    return spmv_grid(L0.A.nbr, h->geom);
+}
+
+// One CG iteration, as recorded into the body of the conditional while node.
+static int record_cg_iteration(amg_handle h, cudaStream_t s, cudaGraphConditionalHandle cond,
+                               int use_cond)
+{
+    Level &L0 = h->lv[0];
+    const int64_t n = L0.n();
+    const int npre = h->prm.npre;
+    const bool multi = h->lv.size() > 1;
+    const Geom &g = h->geom;
+    // z = V(r), partial r.z
+    AMG_TRY(record_vcycle(h, h->r, h->z, h->partials, s));
+    cg_beta_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, rz_parts(h)); ::amg::count_launch(1);
+    cg_direction_kernel<<<vgrid(h, n), 256, 0, s>>>(h->z, h->p, h->st, n); ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    int grid = 0;
+    {  // q = A p, partial p.q
+        SpmvArgs<double> a = args_for(L0.A);
+        a.x = h->p;
+        a.y = h->q;
+        a.partials = h->partials;
+        a.stop = &h->st->stop;
+        AMG_TRY((launch_spmv<double, double>(3, 3, SPMV_PLAIN, DOT_XY, a, g, s, &grid)));
+    }
+    cg_alpha_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, grid); ::amg::count_launch(1);
+    cg_update_kernel<<<vgrid(h, n), 256, 0, s>>>(h->uu, h->r, h->p, h->q, L0.M,
+                                                 multi ? L0.u : nullptr, h->st, n, npre > 0,
+                                                 h->partials); ::amg::count_launch(1);
+    cg_resnorm_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, vgrid(h, n)); ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    {  // true residual, only when the recurrence residual reached tol
+        SpmvArgs<double> a = args_for(L0.A);
+        a.x = h->uu;
+        a.f = h->ff;
+        a.y = h->rt;
+        a.partials = h->partials;
+        a.stop = &h->st->no_check;
+        AMG_TRY((launch_spmv<double, double>(3, 3, SPMV_RESID, DOT_YY, a, g, s, &grid)));
+    }
+    cg_decide_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, grid, cond, use_cond); ::amg::count_launch(1);
+    cg_replace_kernel<<<vgrid(h, n), 256, 0, s>>>(h->r, h->rt, L0.M, multi ? L0.u : nullptr,
+                                                  h->st, n, npre > 0); ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    return AMG_OK;
+}
+
+static int build_graph(amg_handle h)
+{
+    if (h->exec) return AMG_OK;
+    cudaGraph_t graph = nullptr;
+    AMG_TRY_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    AMG_TRY_CUDA(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    AMG_TRY_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    AMG_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    AMG_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+    long long nbody = 0;
+    begin_launch_capture(&nbody);
+    int st = record_cg_iteration(h, cs, cond, 1);
+    end_launch_capture();
+    h->body_kernels = nbody;
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
+    if (st < 0) {
+        cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        set_error("graph capture: %s", cudaGetErrorString(e));
+        return AMG_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&h->exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        h->exec = nullptr;
+        set_error("graph instantiate: %s", cudaGetErrorString(e));
+        return AMG_ERR_CUDA;
+    }
+    h->graph = graph;
+    return AMG_OK;
+}
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+int amg_params_default(amg_params *prm)
+{
+    if (!prm) return AMG_ERR_ARG;
+    std::memset(prm, 0, sizeof *prm);
+    prm->eps_strong = 0.08;
+    prm->relax = 1.0;
+    prm->smooth_relax = 0.8;
+    prm->coarse_enough = 3000;
+    prm->max_levels = 15;
+    prm->npre = 1;
+    prm->npost = 1;
+    prm->precision = AMG_PREC_FP64;
+    return AMG_OK;
+}
+
+const char *amg_last_error(void) { return amg::last_error(); }
+
+static int check_bsr(const amg_bsr *A, int want_square)
+{
+    if (!A) {
+        set_error("null matrix");
+        return AMG_ERR_ARG;
+    }
+    if (A->nbrows < 0 || A->nbcols < 0 || A->nnzb < 0 || A->nnzb > 2147483647LL) {
+        set_error("bad matrix dimensions");
+        return AMG_ERR_ARG;
+    }
+    if (want_square && (A->nbrows != A->nbcols || A->bs_r != A->bs_c)) {
+        set_error("matrix must be square with square blocks");
+        return AMG_ERR_ARG;
+    }
+    if (!A->row_ptr || (A->nnzb > 0 && (!A->col || !A->val))) {
+        set_error("null matrix array");
+        return AMG_ERR_ARG;
+    }
+    return AMG_OK;
+}
+
+static void destroy(amg_handle h)
+{
+    if (!h) return;
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->mem.release_all();
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    if (h->st_h) cudaFreeHost(h->st_h);
+    delete h;
+}
+
+static int setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
+{
+    cudaStream_t s = h->stream;
+    const amg_params &prm = h->prm;
+    DevArena tmp;
+    tmp.stream = s;
+    struct TmpGuard {
+        DevArena &t;
+        ~TmpGuard() { t.release_all(); }
+    } guard{tmp};
+    AMG_TRY(query_geom(&h->geom));
+    {  // level 0: own copy of A and B
+        Level L0;
+        BsrD &A = L0.A;
+        A.nbr = Ain->nbrows;
+        A.nbc = Ain->nbcols;
+        A.br = Ain->bs_r;
+        A.bc = Ain->bs_c;
+        A.nnzb = Ain->nnzb;
+        AMG_TRY(h->mem.alloc_n(&A.row_ptr, (size_t)A.nbr + 1));
+        AMG_TRY(h->mem.alloc_n(&A.col, (size_t)std::max<int64_t>(A.nnzb, 1)));
+        AMG_TRY(h->mem.alloc_n(&A.val, (size_t)std::max<int64_t>(A.nnzb, 1) * 9));
+        AMG_TRY(h->mem.alloc_n(&L0.B, (size_t)A.nbr * 3 * 6));
+        AMG_TRY_CUDA(cudaMemcpyAsync(A.row_ptr, Ain->row_ptr, sizeof(int) * (A.nbr + 1),
+                                     cudaMemcpyDeviceToDevice, s));
+        AMG_TRY_CUDA(cudaMemcpyAsync(A.col, Ain->col, sizeof(int) * A.nnzb,
+                                     cudaMemcpyDeviceToDevice, s));
+        AMG_TRY_CUDA(cudaMemcpyAsync(A.val, Ain->val, sizeof(double) * 9 * A.nnzb,
+                                     cudaMemcpyDeviceToDevice, s));
+        AMG_TRY_CUDA(cudaMemcpyAsync(L0.B, B, sizeof(double) * 18 * A.nbr,
+                                     cudaMemcpyDeviceToDevice, s));
+        L0.eps = prm.eps_strong;
+        // validate the pattern on the host before any kernel indexes with it
+        std::vector<int> rp(A.nbr + 1), cl(std::max<int64_t>(A.nnzb, 1));
+        AMG_TRY_CUDA(cudaMemcpyAsync(rp.data(), A.row_ptr, sizeof(int) * (A.nbr + 1),
+                                     cudaMemcpyDeviceToHost, s));
+        AMG_TRY_CUDA(cudaMemcpyAsync(cl.data(), A.col, sizeof(int) * A.nnzb,
+                                     cudaMemcpyDeviceToHost, s));
+        AMG_TRY_CUDA(cudaStreamSynchronize(s));
+        if (rp[0] != 0 || rp[A.nbr] != A.nnzb) {
+            set_error("row_ptr must start at 0 and end at nnzb");
+            return AMG_ERR_ARG;
+        }
+        for (int I = 0; I < A.nbr; ++I) {
+            if (rp[I + 1] < rp[I]) {
+                set_error("row_ptr decreases at block row %d", I);
+                return AMG_ERR_ARG;
+            }
+            bool diag = false;
+            for (int k = rp[I]; k < rp[I + 1]; ++k) {
+                if (cl[k] < 0 || cl[k] >= A.nbc || (k > rp[I] && cl[k] <= cl[k - 1])) {
+                    set_error("block row %d: columns must be ascending and in range", I);
+                    return AMG_ERR_ARG;
+                }
+                diag |= cl[k] == I;
+            }
+            if (!diag) {
+                set_error("block row %d has no diagonal block", I);
+                return AMG_ERR_ARG;
+            }
+        }
+        h->lv.push_back(L0);
+    }
+    for (;;) {
+        Level &C = h->lv.back();
+        const int nn = C.A.nbr, n = C.n();
+        if (n <= prm.coarse_enough || (int)h->lv.size() >= prm.max_levels) break;
+        AMG_TRY(h->mem.alloc_n(&C.strong, (size_t)std::max<int64_t>(C.A.nnzb, 1)));
+        AMG_TRY(compute_strength(C.A, C.eps, C.strong, s));
+        std::vector<int> rp(nn + 1), cl(std::max<int64_t>(C.A.nnzb, 1)), agg(std::max(nn, 1));
+        std::vector<uint8_t> sf(std::max<int64_t>(C.A.nnzb, 1));
+        AMG_TRY_CUDA(cudaMemcpyAsync(rp.data(), C.A.row_ptr, sizeof(int) * (nn + 1),
+                                     cudaMemcpyDeviceToHost, s));
+        AMG_TRY_CUDA(cudaMemcpyAsync(cl.data(), C.A.col, sizeof(int) * C.A.nnzb,
+                                     cudaMemcpyDeviceToHost, s));
+        AMG_TRY_CUDA(cudaMemcpyAsync(sf.data(), C.strong, C.A.nnzb, cudaMemcpyDeviceToHost, s));
+        AMG_TRY_CUDA(cudaStreamSynchronize(s));
+        int nagg = 0;
+        AMG_TRY(aggregate_host(nn, rp.data(), cl.data(), sf.data(), agg.data(), &nagg));
+        if (nagg == 0 || (double)nagg >= 0.9 * (double)nn) break;
+        LevelBuild lb;
+        AMG_TRY(build_transfer(C.A, C.B, C.strong, agg.data(), nagg, prm.relax, h->mem, tmp, s,
+                               &lb));
+        C.P = lb.P;
+        C.R = lb.R;
+        C.agg = lb.agg;
+        C.nagg = nagg;
+        C.omega = lb.omega;
+        C.rho = lb.rho;
+        Level N;
+        AMG_TRY(galerkin(C.A, C.P, C.R, h->mem, tmp, s, &N.A));
+        N.B = lb.Bc;
+        N.eps = C.eps * 0.5;
+        AMG_TRY(h->mem.alloc_n(&C.M, (size_t)std::max(n, 1)));
+        AMG_TRY(spai0_diag(C.A, prm.smooth_relax, C.M, s));
+        h->lv.push_back(N);
+    }
+    Level &Cc = h->lv.back();
+    Cc.coarsest = true;
+    AMG_TRY(coarse_inverse(Cc.A, h->mem, tmp, s, &h->Ainv));
+    h->nc = Cc.n();
+    for (size_t l = 0; l < h->lv.size(); ++l) {
+        Level &L = h->lv[l];
+        const size_t n = (size_t)std::max(L.n(), 1);
+        if (l > 0) AMG_TRY(h->mem.alloc_n(&L.f, n));
+        AMG_TRY(h->mem.alloc_n(&L.u, n));
+        AMG_TRY(h->mem.alloc_n(&L.e, n));
+        AMG_TRY(h->mem.alloc_n(&L.z, n));
+        AMG_TRY(h->mem.alloc_n(&L.t, n));
+    }
+    const size_t n0 = (size_t)std::max(h->lv[0].n(), 1);
+    AMG_TRY(h->mem.alloc_n(&h->ff, n0));
+    AMG_TRY(h->mem.alloc_n(&h->uu, n0));
+    AMG_TRY(h->mem.alloc_n(&h->r, n0));
+    AMG_TRY(h->mem.alloc_n(&h->p, n0));
+    AMG_TRY(h->mem.alloc_n(&h->q, n0));
+    AMG_TRY(h->mem.alloc_n(&h->z, n0));
+    AMG_TRY(h->mem.alloc_n(&h->rt, n0));
+    AMG_TRY(h->mem.alloc_n(&h->partials, (size_t)h->geom.max_ctas + 1));
+    AMG_TRY(h->mem.alloc_n(&h->scal, 8));
+    AMG_TRY(h->mem.alloc_n(&h->st, 1));
+    AMG_TRY_CUDA(cudaMallocHost((void **)&h->st_h, sizeof(CgState)));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params *prm,
+              void *stream, amg_handle *out)
+{
+    clear_error();
+    if (!out) {
+        set_error("null output handle");
+        return AMG_ERR_ARG;
+    }
+    *out = nullptr;
+    AMG_TRY(check_bsr(A, 1));
+    if (A->bs_r != 3 || A->nbrows < 1) {
+        set_error("amg_setup expects a non-empty 3x3 block matrix");
+        return AMG_ERR_ARG;
+    }
+    if (nb_ns != 6 || !B) {
+        set_error("amg_setup expects the six rigid-body modes (nb_ns = 6)");
+        return AMG_ERR_ARG;
+    }
+    amg_params p;
+    amg_params_default(&p);
+    if (prm) p = *prm;
+    if (p.npre < 0 || p.npost < 0 || p.max_levels < 1 || p.coarse_enough < 0 ||
+        !(p.eps_strong >= 0.0) || p.precision != AMG_PREC_FP64) {
+        set_error("bad parameters");
+        return AMG_ERR_ARG;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    amg_handle h = new amg_handle_s();
+    h->prm = p;
+    h->stream = (cudaStream_t)stream;
+    h->mem.stream = h->stream;
+    int st = setup_impl(h, A, B);
+    if (st < 0) {
+        std::string msg = amg::last_error();
+        destroy(h);
+        set_error("%s", msg.c_str());
+        return st;
+    }
+    h->setup_seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return AMG_OK;
+}
+
+void amg_free(amg_handle h) { destroy(h); }
+
+int amg_apply_vcycle(amg_handle h, const double *r, double *z, void *stream)
+{
+    clear_error();
+    if (!h || !r || !z) {
+        set_error("null argument");
+        return AMG_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Level &L0 = h->lv[0];
+    const int64_t n = L0.n();
+    if (h->lv.size() > 1) {
+        scale_kernel<<<vgrid(h, n), 256, 0, s>>>(L0.M, r, L0.u, n, h->prm.npre == 0); ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
+    return record_vcycle(h, r, z, nullptr, s);
+}
+
+int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxiter,
+              int32_t *iters, double *rel_resid, void *stream)
+{
+    clear_error();
+    if (!h || !f || !u) {
+        set_error("null argument");
+        return AMG_ERR_ARG;
+    }
+    if (!(tol > 0.0) || maxiter < 0 || maxiter > 1000000) {
+        set_error("bad tolerance or iteration limit");
+        return AMG_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Level &L0 = h->lv[0];
+    const int64_t n = L0.n();
+    const bool multi = h->lv.size() > 1;
+    AMG_TRY_CUDA(cudaMemcpyAsync(h->ff, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    AMG_TRY_CUDA(cudaMemcpyAsync(h->uu, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    vec_dot_kernel<<<vgrid(h, n), 256, 0, s>>>(h->ff, h->ff, n, h->partials); ::amg::count_launch(1);
+    AMG_TRY(launch_reduce_sum(h->partials, vgrid(h, n), h->scal, s));
+    int grid = 0;
+    {
+        SpmvArgs<double> a = args_for(L0.A);
+        a.x = h->uu;
+        a.f = h->ff;
+        a.y = h->r;
+        a.partials = h->partials;
+        AMG_TRY((launch_spmv<double, double>(3, 3, SPMV_RESID, DOT_YY, a, h->geom, s, &grid)));
+    }
+    AMG_TRY(launch_reduce_sum(h->partials, grid, h->scal + 1, s));
+    cg_start_kernel<<<1, 1, 0, s>>>(h->st, h->scal, tol, maxiter); ::amg::count_launch(1);
+    if (multi) {
+        scale_kernel<<<vgrid(h, n), 256, 0, s>>>(L0.M, h->r, L0.u, n, h->prm.npre == 0); ::amg::count_launch(1); }
+    AMG_TRY_CUDA(cudaGetLastError());
+    AMG_TRY_CUDA(cudaMemcpyAsync(h->st_h, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    int status;
+    if (h->st_h->nf == 0.0) {
+        AMG_TRY_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, s));
+        AMG_TRY_CUDA(cudaStreamSynchronize(s));
+        if (iters) *iters = 0;
+        if (rel_resid) *rel_resid = 0.0;
+        return AMG_OK;
+    }
+    if (h->st_h->res <= tol || maxiter == 0) {
+        if (iters) *iters = 0;
+        if (rel_resid) *rel_resid = h->st_h->res;
+        return h->st_h->res <= tol ? AMG_OK : AMG_NOT_CONVERGED;
+    }
+    AMG_TRY(build_graph(h));
+    AMG_TRY_CUDA(cudaGraphLaunch(h->exec, s));
+    AMG_TRY_CUDA(cudaMemcpyAsync(h->st_h, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    status = h->st_h->status;
+    count_launch(h->body_kernels * (long long)h->st_h->it);
+    double res = h->st_h->res_true;
+    if (status != AMG_OK) {  // report the true residual of the returned iterate
+        SpmvArgs<double> a = args_for(L0.A);
+        a.x = h->uu;
+        a.f = h->ff;
+        a.y = h->rt;
+        a.partials = h->partials;
+        AMG_TRY((launch_spmv<double, double>(3, 3, SPMV_RESID, DOT_YY, a, h->geom, s, &grid)));
+        AMG_TRY(launch_reduce_sum(h->partials, grid, h->scal + 2, s));
+        double rr = 0.0;
+        AMG_TRY_CUDA(cudaMemcpyAsync(&rr, h->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+        AMG_TRY_CUDA(cudaStreamSynchronize(s));
+        res = std::sqrt(rr) / h->st_h->nf;
+    }
+    AMG_TRY_CUDA(cudaMemcpyAsync(u, h->uu, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    if (iters) *iters = h->st_h->it;
+    if (rel_resid) *rel_resid = res;
+    if (status == AMG_ERR_BREAKDOWN) set_error("CG breakdown at iteration %d", h->st_h->it);
+    return status;
+}
+
+int amg_get_stats(amg_handle h, amg_stats *out)
+{
+    if (!h || !out) return AMG_ERR_ARG;
+    std::memset(out, 0, sizeof *out);
+    out->nlevels = (int)h->lv.size();
+    out->coarse_n = h->nc;
+    out->setup_seconds = h->setup_seconds;
+    int64_t bytes = 0, nnz0 = 0, nnz = 0;
+    auto bsr_bytes = [](const BsrD &m) -> int64_t {
+        if (!m.row_ptr) return 0;
+        return (int64_t)(m.nbr + 1) * 4 + m.nnzb * 4 + m.nnzb * m.br * m.bc * 8;
+    };
+    for (size_t l = 0; l < h->lv.size(); ++l) {
+        const Level &L = h->lv[l];
+        bytes += bsr_bytes(L.A) + bsr_bytes(L.P) + bsr_bytes(L.R);
+        if (L.M) bytes += (int64_t)L.n() * 8;
+        const int64_t z = L.A.nnzb * L.A.br * L.A.bc;
+        if (l == 0) nnz0 = z;
+        nnz += z;
+    }
+    bytes += (int64_t)h->nc * h->nc * 8;
+    out->bytes_matrices = bytes;
+    out->bytes_total = (int64_t)h->mem.bytes;
+    out->operator_complexity = nnz0 ? (double)nnz / (double)nnz0 : 0.0;
+    return AMG_OK;
+}
+
+int amg_level_info(amg_handle h, int32_t level, amg_level_desc *out)
+{
+    if (!h || !out || level < 0 || level >= (int)h->lv.size()) {
+        set_error("bad level");
+        return AMG_ERR_ARG;
+    }
+    const Level &L = h->lv[level];
+    std::memset(out, 0, sizeof *out);
+    out->nbrows = L.A.nbr;
+    out->bs = L.A.br;
+    out->nnzb_A = L.A.nnzb;
+    out->nnzb_P = L.P.nnzb;
+    out->nagg = L.nagg;
+    out->is_coarsest = L.coarsest;
+    out->eps = L.eps;
+    out->omega = L.omega;
+    out->rho = L.rho;
+    return AMG_OK;
+}
+
+static int export_bsr(const BsrD &m, int32_t *rp, int32_t *cl, double *vl, cudaStream_t s)
+{
+    if (!m.row_ptr) {
+        set_error("operator not present on this level");
+        return AMG_ERR_STATE;
+    }
+    if (rp) AMG_TRY_CUDA(cudaMemcpyAsync(rp, m.row_ptr, sizeof(int) * (m.nbr + 1), cudaMemcpyDeviceToHost, s));
+    if (cl) AMG_TRY_CUDA(cudaMemcpyAsync(cl, m.col, sizeof(int) * m.nnzb, cudaMemcpyDeviceToHost, s));
+    if (vl)
+        AMG_TRY_CUDA(cudaMemcpyAsync(vl, m.val, sizeof(double) * m.nnzb * m.br * m.bc,
+                                     cudaMemcpyDeviceToHost, s));
+    return AMG_OK;
+}
+
+int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_ptr, int32_t *col,
+                     double *val)
+{
+    clear_error();
+    if (!h || level < 0 || level >= (int)h->lv.size()) {
+        set_error("bad level");
+        return AMG_ERR_ARG;
+    }
+    const Level &L = h->lv[level];
+    cudaStream_t s = h->stream;
+    switch (which) {
+    case 0: AMG_TRY(export_bsr(L.A, row_ptr, col, val, s)); break;
+    case 1: AMG_TRY(export_bsr(L.P, row_ptr, col, val, s)); break;
+    case 2: AMG_TRY(export_bsr(L.R, row_ptr, col, val, s)); break;
+    case 3:
+        if (!L.agg) { set_error("no aggregates on this level"); return AMG_ERR_STATE; }
+        if (row_ptr) AMG_TRY_CUDA(cudaMemcpyAsync(row_ptr, L.agg, sizeof(int) * L.A.nbr, cudaMemcpyDeviceToHost, s));
+        break;
+    case 4:
+        if (!L.M) { set_error("no smoother on this level"); return AMG_ERR_STATE; }
+        if (val) AMG_TRY_CUDA(cudaMemcpyAsync(val, L.M, sizeof(double) * L.n(), cudaMemcpyDeviceToHost, s));
+        break;
+    case 5:
+        if (val) AMG_TRY_CUDA(cudaMemcpyAsync(val, L.B, sizeof(double) * L.n() * 6, cudaMemcpyDeviceToHost, s));
+        break;
+    case 6:
+        if (!L.strong) { set_error("no strength flags on this level"); return AMG_ERR_STATE; }
+        if (row_ptr) AMG_TRY_CUDA(cudaMemcpyAsync(row_ptr, L.strong, L.A.nnzb, cudaMemcpyDeviceToHost, s));
+        break;
+    default: set_error("bad operator id %d", which); return AMG_ERR_ARG;
+    }
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+int amg_bsr_spmv(const amg_bsr *A, const double *x, double *y, void *stream)
+{
+    clear_error();
+    AMG_TRY(check_bsr(A, 0));
+    if (!x || !y) {
+        set_error("null vector");
+        return AMG_ERR_ARG;
+    }
+    Geom g;
+    AMG_TRY(query_geom(&g));
+    SpmvArgs<double> a{};
+    a.row_ptr = A->row_ptr;
+    a.col = A->col;
+    a.val = A->val;
+    a.nbr = A->nbrows;
+    a.x = x;
+    a.y = y;
+    return launch_spmv<double, double>(A->bs_r, A->bs_c, SPMV_PLAIN, DOT_NONE, a, g,
+                                       (cudaStream_t)stream);
+}
+
+int amg_bsr_spmv_dot(const amg_bsr *A, const double *x, double *y, double *dot_out, void *stream)
+{
+    clear_error();
+    AMG_TRY(check_bsr(A, 1));
+    if (!x || !y || !dot_out) {
+        set_error("null argument");
+        return AMG_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Geom g;
+    AMG_TRY(query_geom(&g));
+    DevArena tmp;
+    tmp.stream = s;
+    double *part = nullptr;
+    AMG_TRY(tmp.alloc_n(&part, (size_t)g.max_ctas + 1));
+    SpmvArgs<double> a{};
+    a.row_ptr = A->row_ptr;
+    a.col = A->col;
+    a.val = A->val;
+    a.nbr = A->nbrows;
+    a.x = x;
+    a.y = y;
+    a.partials = part;
+    int grid = 0;
+    int st = launch_spmv<double, double>(A->bs_r, A->bs_c, SPMV_PLAIN, DOT_XY, a, g, s, &grid);
+    if (st >= 0) st = launch_reduce_sum(part, grid, part + g.max_ctas, s);
+    if (st >= 0) {
+        cudaError_t e = cudaMemcpyAsync(dot_out, part + g.max_ctas, sizeof(double),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error("%s", cudaGetErrorString(e));
+            st = AMG_ERR_CUDA;
+        }
+    }
+    tmp.release_all();
+    cudaStreamSynchronize(s);
+    return st;
+}
+
+}  // extern "C"
