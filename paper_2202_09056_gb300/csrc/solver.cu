@@ -878,7 +878,8 @@ int amg_bsr_spmv(const amg_bsr *A, const double *x, double *y, void *stream)
 {
     clear_error();
     AMG_TRY(check_bsr(A, 0));
-    if (!x || !y) {
+    if (A->nbrows == 0) return AMG_OK;
+    if (!y || (A->nnzb > 0 && !x)) {
         set_error("null vector");
         return AMG_ERR_ARG;
     }

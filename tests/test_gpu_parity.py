@@ -92,9 +92,12 @@ def _compare_hierarchy(p, coarse_enough, tol_val=1e-12):
         assert np.array_equal(gl["strong"], og["strong"]), l
         assert np.array_equal(gl["agg"], ol["agg"]), l
         info = gl["info"]
-        assert info["nagg"] == ol["nagg"]
-        assert abs(info["rho"] - ol["rho"]) <= 1e-14 * ol["rho"]
-        assert abs(info["omega"] - ol["omega"]) <= 1e-14 * ol["omega"]
+        assert info["nagg"] == ol["nagg"], l
+        # level 0 sees identical input bits and sums in the same order: exact;
+        # coarser levels inherit A_c rounding differences (values bar 1e-12)
+        rtol = 0.0 if l == 0 else 1e-12
+        assert abs(info["rho"] - ol["rho"]) <= rtol * ol["rho"], l
+        assert abs(info["omega"] - ol["omega"]) <= rtol * ol["omega"], l
         gP, gR = gl["P"], gl["R"]
         cP = o.unblock(gP[0], gP[1], gP[2].reshape(len(gP[1]), -1), b, 6, nbcols=info["nagg"])
         cR = o.unblock(gR[0], gR[1], gR[2].reshape(len(gR[1]), -1), 6, b, nbcols=info["nbrows"])
@@ -102,7 +105,7 @@ def _compare_hierarchy(p, coarse_enough, tol_val=1e-12):
         assert np.array_equal(cR.ptr, ol["R"].ptr) and np.array_equal(cR.col, ol["R"].col), l
         assert _rel(cP.val, ol["P"].val) <= tol_val, l
         assert _rel(cR.val, ol["R"].val) <= tol_val, l
-        assert _rel(gl["M"], ol["M"]) <= 1e-14, l
+        assert _rel(gl["M"], ol["M"]) <= (1e-14 if l == 0 else tol_val), l
     return H, G
 
 
