@@ -146,6 +146,17 @@ int amg_level_info(amg_handle h, int32_t level, amg_level_desc *out);
 int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_ptr,
                      int32_t *col, double *val);
 
+/* y = op x with the hierarchy's own V-cycle kernel for operator `which` of
+ * level `level` (0: A, 1: P, 2: R), in the sliced block-ELL layout the solve
+ * uses.  x has (columns x block columns) and y (rows x block rows) doubles,
+ * device, not overlapping.  Asynchronous on `stream`. */
+int amg_level_spmv(amg_handle h, int32_t level, int32_t which, const double *x, double *y,
+                   void *stream);
+
+/* Padding of the sliced layout of A, P, R on `level` (host double[3]): extra
+ * stored blocks / structural blocks (0 for an absent operator). */
+int amg_level_padding(amg_handle h, int32_t level, double *pad3);
+
 /* Release everything the handle owns.  NULL is ignored. */
 void amg_free(amg_handle h);
 

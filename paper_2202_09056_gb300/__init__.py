@@ -61,7 +61,7 @@ class Stats(ctypes.Structure):
 
 EXPORTED = ["amg_params_default", "amg_setup", "amg_apply_vcycle", "amg_solve", "amg_get_stats",
             "amg_level_info", "amg_level_export", "amg_free", "amg_last_error", "amg_bsr_spmv",
-            "amg_bsr_spmv_dot", "amg_kernel_launches"]
+            "amg_bsr_spmv_dot", "amg_kernel_launches", "amg_level_spmv", "amg_level_padding"]
 
 
 def library_path() -> str:
@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True):
         "amg_bsr_spmv": ([P, P, P, P], ctypes.c_int),
         "amg_bsr_spmv_dot": ([P, P, P, P, P], ctypes.c_int),
         "amg_kernel_launches": ([], ctypes.c_int64),
+        "amg_level_spmv": ([P, i32, i32, P, P, P], ctypes.c_int),
+        "amg_level_padding": ([P, i32, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -231,6 +233,18 @@ class AMG:
         d = LevelDesc()
         _check(self._lib.amg_level_info(self._h, l, ctypes.byref(d)))
         return {k: getattr(d, k) for k, _ in LevelDesc._fields_}
+
+    def level_spmv(self, l: int, which: int, x, y, stream=None):
+        """y = op x with the solve's own kernel; which = 0 (A), 1 (P), 2 (R)."""
+        import torch
+        _check(self._lib.amg_level_spmv(self._h, l, which, _dptr(x, torch.float64, "x"),
+                                        _dptr(y, torch.float64, "y"), _stream(stream)))
+        return y
+
+    def padding(self, l: int) -> tuple:
+        out = (ctypes.c_double * 3)()
+        _check(self._lib.amg_level_padding(self._h, l, out))
+        return tuple(out)
 
     @property
     def nlevels(self) -> int:

@@ -129,6 +129,41 @@ template <class TV>
 int launch_coarse_gemv(const double *Ainv, int n, const TV *x, TV *y, const Geom &g,
                        cudaStream_t s);
 
+// ---------------------------------------------------------------- SELL-32 (sell.cu)
+// Sliced block-ELL: 32 block rows per slice, blocks of a slice interleaved
+// so that lane t of a warp owns row 32 s + t (or perm[32 s + t]).
+template <class T> struct Sell {
+    int nrows = 0, nbc = 0, br = 0, bc = 0, nslices = 0;
+    int64_t nslots = 0;          // block slots including padding (multiple of 32)
+    int64_t *slice_ptr = nullptr;// [nslices + 1] slot offsets
+    int *col = nullptr;          // [nslots]
+    T *val = nullptr;            // [nslots * br * bc]
+    int *perm = nullptr;         // optional row of each lane slot (-1 = padding lane)
+};
+
+template <class TV> struct SellArgs {
+    int nrows, nslices;
+    const int64_t *slice_ptr;
+    const int *col;
+    const void *val;
+    const int *perm;
+    const TV *x;
+    const TV *f;
+    const TV *u;
+    const TV *M;
+    TV *y;
+    TV *y2;
+    double *partials;
+    const int *stop;
+};
+
+int sell_grid(int nslices, const Geom &g);
+template <class VT, class TV>
+int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom &g,
+                cudaStream_t s, int *grid_out = nullptr);
+template <class T>
+int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, double *padding);
+
 // ---------------------------------------------------------------- setup (setup.cu)
 struct LevelBuild {
     // outputs of one coarsening step on device

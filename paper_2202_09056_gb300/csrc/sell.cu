@@ -1,0 +1,265 @@
+// Sliced block-ELL (SELL-32) layout and SpMV kernels for the V-cycle and CG.
+//
+// Why this layout on GB300: the FP64 pipe of sm_103a issues about two FP64
+// lane-operations per clock per SM, 1/64 of the FP32 rate, so a 3x3 FP64
+// block SpMV is bounded by its multiply-adds almost as much as by HBM
+// (9 DFMA per 72 value bytes).  A kernel that splits a block row across the
+// lanes of a warp pays for the cross-lane FP64 reductions and for predicated
+// accumulations in that same pipe.  Here one THREAD owns one block row: it
+// performs exactly br*bc DFMAs per block and needs no reduction at all.
+// To keep the loads coalesced, 32 consecutive block rows form a slice whose
+// blocks are stored interleaved: entry e of the k-th block of the row held by
+// lane t sits at  (slice_base + 32 k) * bb + 32 e + t , so every value load
+// of a warp is one contiguous 256-byte segment.  A slice is as wide as its
+// longest row; shorter rows are padded with zero blocks that point at
+// column 0 (the padding is counted as overhead, not as algorithmic bytes).
+//
+// The epilogues are those of the CSR kernels (residual, smoothing,
+// prolongation-correction, restriction with the next pre-smoothing, fused
+// dot products), computed per thread; dots are reduced per CTA in a fixed
+// order, so results are bitwise reproducible for a fixed launch.
+#include <algorithm>
+
+#include "amg_internal.cuh"
+
+namespace amg {
+
+__device__ __forceinline__ double sldv(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ float sldv(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ float sldv(const __nv_bfloat16 *p)
+{
+    unsigned short bits = __ldcs(reinterpret_cast<const unsigned short *>(p));
+    return __uint_as_float(((unsigned int)bits) << 16);
+}
+
+template <int NT> __device__ __forceinline__ double cta_sum_d(double v)
+{
+    __shared__ double red[NT / 32];
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NT / 32; ++k) s += red[k];
+    }
+    return s;
+}
+
+constexpr int SELL_THREADS = 128;
+
+template <int BR, int BC, class VT, class TV, int MODE, int DOT>
+__global__ void __launch_bounds__(SELL_THREADS) sell_spmv_kernel(SellArgs<TV> a)
+{
+    using Acc = TV;
+    constexpr int BB = BR * BC;
+    if (a.stop && *a.stop) return;
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
+    const VT *__restrict__ val = static_cast<const VT *>(a.val);
+    const int *__restrict__ col = a.col;
+    const TV *__restrict__ x = a.x;
+    double dot = 0.0;
+    for (int s = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5); s < a.nslices;
+         s += nw) {
+        const int slot = s * 32 + lane;
+        const int row = a.perm ? a.perm[slot] : slot;
+        const int64_t base = a.slice_ptr[s];
+        const int w = (int)((a.slice_ptr[s + 1] - base) >> 5);
+        const VT *vp = val + base * BB + lane;
+        const int *cp = col + base + lane;
+        Acc acc[BR];
+#pragma unroll
+        for (int r = 0; r < BR; ++r) acc[r] = Acc(0);
+        int jn = (w > 0) ? __ldg(cp) : 0;
+#pragma unroll 2
+        for (int k = 0; k < w; ++k) {
+            const int j = jn;
+            if (k + 1 < w) jn = __ldg(cp + (k + 1) * 32);
+            Acc xv[BC];
+#pragma unroll
+            for (int c = 0; c < BC; ++c) xv[c] = (Acc)__ldg(x + (int64_t)j * BC + c);
+            const VT *vb = vp + (int64_t)k * 32 * BB;
+#pragma unroll
+            for (int r = 0; r < BR; ++r)
+#pragma unroll
+                for (int c = 0; c < BC; ++c)
+                    acc[r] = fma((Acc)sldv(vb + (r * BC + c) * 32), xv[c], acc[r]);
+        }
+        if (row >= 0 && row < a.nrows) {
+#pragma unroll
+            for (int r = 0; r < BR; ++r) {
+                const int64_t i = (int64_t)row * BR + r;
+                Acc out;
+                if (MODE == SPMV_PLAIN) out = acc[r];
+                else if (MODE == SPMV_RESID) out = a.f[i] - acc[r];
+                else if (MODE == SPMV_SMOOTH) out = x[i] + a.M[i] * (a.f[i] - acc[r]);
+                else if (MODE == SPMV_AXPY) out = a.u[i] + acc[r];
+                else out = acc[r];
+                a.y[i] = out;
+                if (MODE == SPMV_RESTRICT && a.y2) a.y2[i] = a.M ? a.M[i] * out : Acc(0);
+                if (DOT == DOT_XY) dot += (double)x[i] * (double)out;
+                if (DOT == DOT_FY) dot += (double)a.f[i] * (double)out;
+                if (DOT == DOT_YY) dot += (double)out * (double)out;
+            }
+        }
+    }
+    if (DOT != DOT_NONE) {
+        const double t = cta_sum_d<SELL_THREADS>(dot);
+        if (threadIdx.x == 0) a.partials[blockIdx.x] = t;
+    }
+}
+
+int sell_grid(int nslices, const Geom &g)
+{
+    const int per_cta = SELL_THREADS / 32;
+    int grid = (nslices + per_cta - 1) / per_cta;
+    const int cap = g.num_sms * 16;
+    if (grid > cap) grid = cap;
+    return std::max(grid, 1);
+}
+
+template <int BR, int BC, class VT, class TV, int MODE>
+static int sell_dot(int dot, const SellArgs<TV> &a, int grid, cudaStream_t s)
+{
+    switch (dot) {
+    case DOT_NONE: sell_spmv_kernel<BR, BC, VT, TV, MODE, DOT_NONE><<<grid, SELL_THREADS, 0, s>>>(a); break;
+    case DOT_XY: sell_spmv_kernel<BR, BC, VT, TV, MODE, DOT_XY><<<grid, SELL_THREADS, 0, s>>>(a); break;
+    case DOT_FY: sell_spmv_kernel<BR, BC, VT, TV, MODE, DOT_FY><<<grid, SELL_THREADS, 0, s>>>(a); break;
+    case DOT_YY: sell_spmv_kernel<BR, BC, VT, TV, MODE, DOT_YY><<<grid, SELL_THREADS, 0, s>>>(a); break;
+    default: set_error("bad dot mode %d", dot); return AMG_ERR_ARG;
+    }
+    count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    return AMG_OK;
+}
+
+// Only the (mode, dot) pairs the solver records are instantiated.
+template <int BR, int BC, class VT, class TV>
+static int sell_mode(int mode, int dot, const SellArgs<TV> &a, int grid, cudaStream_t s)
+{
+    switch (mode) {
+    case SPMV_PLAIN: return sell_dot<BR, BC, VT, TV, SPMV_PLAIN>(dot, a, grid, s);
+    case SPMV_RESID: return sell_dot<BR, BC, VT, TV, SPMV_RESID>(dot, a, grid, s);
+    case SPMV_SMOOTH: return sell_dot<BR, BC, VT, TV, SPMV_SMOOTH>(dot, a, grid, s);
+    case SPMV_AXPY: return sell_dot<BR, BC, VT, TV, SPMV_AXPY>(dot, a, grid, s);
+    case SPMV_RESTRICT: return sell_dot<BR, BC, VT, TV, SPMV_RESTRICT>(dot, a, grid, s);
+    default: set_error("bad spmv mode %d", mode); return AMG_ERR_ARG;
+    }
+}
+
+template <class VT, class TV>
+int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom &g,
+                cudaStream_t s, int *grid_out)
+{
+    a.nrows = A.nrows;
+    a.nslices = A.nslices;
+    a.slice_ptr = A.slice_ptr;
+    a.col = A.col;
+    a.val = A.val;
+    a.perm = A.perm;
+    const int grid = sell_grid(A.nslices, g);
+    if (grid_out) *grid_out = grid;
+    if (A.nrows == 0) {
+        if (dot != DOT_NONE) AMG_TRY_CUDA(cudaMemsetAsync(a.partials, 0, sizeof(double), s));
+        return AMG_OK;
+    }
+    const int br = A.br, bc = A.bc;
+    if (br == 3 && bc == 3) return sell_mode<3, 3, VT, TV>(mode, dot, a, grid, s);
+    if (br == 6 && bc == 6) return sell_mode<6, 6, VT, TV>(mode, dot, a, grid, s);
+    if (br == 3 && bc == 6) return sell_mode<3, 6, VT, TV>(mode, dot, a, grid, s);
+    if (br == 6 && bc == 3) return sell_mode<6, 3, VT, TV>(mode, dot, a, grid, s);
+    set_error("unsupported block shape %dx%d", br, bc);
+    return AMG_ERR_ARG;
+}
+
+template int launch_sell<double, double>(const Sell<double> &, int, int, SellArgs<double>,
+                                         const Geom &, cudaStream_t, int *);
+
+// ---------------------------------------------------------------- conversion
+__global__ void sell_width_kernel(const int *__restrict__ rp, int nrows, int nslices,
+                                  const int *__restrict__ perm, int *__restrict__ width)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslices) return;
+    int w = 0;
+    for (int t = 0; t < 32; ++t) {
+        const int slot = s * 32 + t;
+        const int row = perm ? perm[slot] : slot;
+        if (row >= 0 && row < nrows) w = max(w, rp[row + 1] - rp[row]);
+    }
+    width[s] = w;
+}
+
+template <class T>
+__global__ void sell_fill_kernel(const int *__restrict__ rp, const int *__restrict__ bcol,
+                                 const double *__restrict__ bval, int nrows, int nslices, int bb,
+                                 const int *__restrict__ perm, const int64_t *__restrict__ sp,
+                                 int *__restrict__ col, T *__restrict__ val)
+{
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= nslices * 32) return;
+    const int s = slot >> 5, lane = slot & 31;
+    const int row = perm ? perm[slot] : slot;
+    const bool live = row >= 0 && row < nrows;
+    const int len = live ? rp[row + 1] - rp[row] : 0;
+    const int64_t base = sp[s];
+    const int w = (int)((sp[s + 1] - base) >> 5);
+    for (int k = 0; k < w; ++k) {
+        const int64_t q = base + (int64_t)k * 32 + lane;
+        const int64_t src = live ? (int64_t)rp[row] + k : 0;
+        const bool have = k < len;
+        col[q] = have ? bcol[src] : 0;
+        for (int e = 0; e < bb; ++e)
+            val[(base + (int64_t)k * 32) * bb + (int64_t)e * 32 + lane] =
+                have ? (T)bval[src * bb + e] : (T)0.0;
+    }
+}
+
+template <class T>
+int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, double *padding)
+{
+    Sell<T> S;
+    S.nrows = B.nbr;
+    S.nbc = B.nbc;
+    S.br = B.br;
+    S.bc = B.bc;
+    S.nslices = (B.nbr + 31) / 32;
+    const int bb = B.br * B.bc;
+    int *width = nullptr;
+    AMG_TRY_CUDA(cudaMallocAsync((void **)&width, sizeof(int) * std::max(S.nslices, 1), s));
+    if (S.nslices > 0) {
+        sell_width_kernel<<<(S.nslices + 255) / 256, 256, 0, s>>>(B.row_ptr, B.nbr, S.nslices,
+                                                                  nullptr, width);
+        count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
+    std::vector<int> wh(std::max(S.nslices, 1));
+    AMG_TRY_CUDA(cudaMemcpyAsync(wh.data(), width, sizeof(int) * S.nslices, cudaMemcpyDeviceToHost, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    AMG_TRY_CUDA(cudaFreeAsync(width, s));
+    std::vector<int64_t> sp(S.nslices + 1, 0);
+    for (int i = 0; i < S.nslices; ++i) sp[i + 1] = sp[i] + 32LL * wh[i];
+    S.nslots = sp[S.nslices];
+    AMG_TRY(keep.alloc_n(&S.slice_ptr, S.nslices + 1));
+    AMG_TRY(keep.alloc_n(&S.col, (size_t)std::max<int64_t>(S.nslots, 1)));
+    AMG_TRY(keep.alloc_n(&S.val, (size_t)std::max<int64_t>(S.nslots, 1) * bb));
+    AMG_TRY_CUDA(cudaMemcpyAsync(S.slice_ptr, sp.data(), sizeof(int64_t) * (S.nslices + 1),
+                                 cudaMemcpyHostToDevice, s));
+    if (S.nslices > 0) {
+        sell_fill_kernel<T><<<(S.nslices * 32 + 127) / 128, 128, 0, s>>>(
+            B.row_ptr, B.col, B.val, B.nbr, S.nslices, bb, nullptr, S.slice_ptr, S.col, S.val);
+        count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));  // sp is host memory
+    if (padding) *padding = B.nnzb ? (double)(S.nslots - B.nnzb) / (double)B.nnzb : 0.0;
+    *out = S;
+    return AMG_OK;
+}
+
+template int bsr_to_sell<double>(const BsrD &, DevArena &, cudaStream_t, Sell<double> *, double *);
+
+}  // namespace amg

@@ -20,6 +20,8 @@ const char *last_error();
 
 struct Level {
     BsrD A, P, R;
+    Sell<double> sA, sP, sR;  // V-cycle copies of A, P, R in the SELL-32 layout
+    double pad_A = 0, pad_P = 0, pad_R = 0;
     double *M = nullptr;      // damped SPAI0 diagonal (scalar rows)
     double *B = nullptr;      // near-nullspace, n x 6
     int *agg = nullptr;       // aggregate of each node (device)
@@ -247,16 +249,6 @@ struct amg_handle_s {
     double setup_seconds = 0.0;
 };
 
-static SpmvArgs<double> args_for(const BsrD &A)
-{
-    SpmvArgs<double> a{};
-    a.row_ptr = A.row_ptr;
-    a.col = A.col;
-    a.val = A.val;
-    a.nbr = A.nbr;
-    return a;
-}
-
 static int vgrid(amg_handle h, int64_t n)
 {
     int64_t g = (n + 255) / 256;
@@ -281,31 +273,31 @@ static int record_vcycle(amg_handle h, const double *f0, double *z0, double *rz_
         const double *f = (l == 0) ? f0 : C.f;
         double *u = C.u, *t = C.t;
         for (int sweep = 1; sweep < npre; ++sweep) {  // further pre-smoothing sweeps
-            SpmvArgs<double> a = args_for(C.A);
+            SellArgs<double> a{};
             a.x = u;
             a.f = f;
             a.M = C.M;
             a.y = t;
-            AMG_TRY((launch_spmv<double, double>(C.A.br, C.A.bc, SPMV_SMOOTH, DOT_NONE, a, g, s)));
+            AMG_TRY((launch_sell<double, double>(C.sA, SPMV_SMOOTH, DOT_NONE, a, g, s)));
             std::swap(u, t);
         }
         ucur[l] = u;
         spare[l] = t;
         {  // e = f - A u
-            SpmvArgs<double> a = args_for(C.A);
+            SellArgs<double> a{};
             a.x = u;
             a.f = f;
             a.y = C.e;
-            AMG_TRY((launch_spmv<double, double>(C.A.br, C.A.bc, SPMV_RESID, DOT_NONE, a, g, s)));
+            AMG_TRY((launch_sell<double, double>(C.sA, SPMV_RESID, DOT_NONE, a, g, s)));
         }
         {  // f_{l+1} = R e ; u_{l+1} = M_{l+1} f_{l+1}
-            SpmvArgs<double> a = args_for(C.R);
+            SellArgs<double> a{};
             a.x = C.e;
             a.y = N.f;
             const bool next_smooths = (l + 1 < L);
             a.y2 = next_smooths ? N.u : nullptr;
             a.M = (next_smooths && npre > 0) ? N.M : nullptr;
-            AMG_TRY((launch_spmv<double, double>(C.R.br, C.R.bc, SPMV_RESTRICT, DOT_NONE, a, g,
+            AMG_TRY((launch_sell<double, double>(C.sR, SPMV_RESTRICT, DOT_NONE, a, g,
                                                  s)));
         }
     }
@@ -326,24 +318,24 @@ static int record_vcycle(amg_handle h, const double *f0, double *z0, double *rz_
         double *u = ucur[l], *t = spare[l];
         double *zl = (l == 0) ? z0 : C.z;
         {  // u += P z_{l+1}
-            SpmvArgs<double> a = args_for(C.P);
+            SellArgs<double> a{};
             a.x = N.z;
             a.u = u;
             a.y = u;
-            AMG_TRY((launch_spmv<double, double>(C.P.br, C.P.bc, SPMV_AXPY, DOT_NONE, a, g, s)));
+            AMG_TRY((launch_sell<double, double>(C.sP, SPMV_AXPY, DOT_NONE, a, g, s)));
         }
         const double *w = u;
         for (int sweep = 0; sweep < npost; ++sweep) {  // u += M (f - A u)
             const bool last = (sweep == npost - 1);
             double *out = last ? zl : t;
-            SpmvArgs<double> a = args_for(C.A);
+            SellArgs<double> a{};
             a.x = w;
             a.f = f;
             a.M = C.M;
             a.y = out;
             a.partials = rz_partials;
             const int dot = (l == 0 && last && rz_partials) ? DOT_FY : DOT_NONE;
-            AMG_TRY((launch_spmv<double, double>(C.A.br, C.A.bc, SPMV_SMOOTH, dot, a, g, s)));
+            AMG_TRY((launch_sell<double, double>(C.sA, SPMV_SMOOTH, dot, a, g, s)));
             w = out;
             t = (out == t) ? u : t;  // ping-pong between u and t
         }
@@ -365,7 +357,7 @@ static int rz_parts(amg_handle h)
     const Level &L0 = h->lv[0];
     if (h->lv.size() == 1) return vgrid(h, h->nc);
     if (h->prm.npost == 0) return vgrid(h, L0.n());
-    return spmv_grid(L0.A.nbr, h->geom);
+    return sell_grid(L0.sA.nslices, h->geom);
 }
 
 // One CG iteration, as recorded into the body of the conditional while node.
@@ -384,12 +376,12 @@ static int record_cg_iteration(amg_handle h, cudaStream_t s, cudaGraphConditiona
     AMG_TRY_CUDA(cudaGetLastError());
     int grid = 0;
     {  // q = A p, partial p.q
-        SpmvArgs<double> a = args_for(L0.A);
+        SellArgs<double> a{};
         a.x = h->p;
         a.y = h->q;
         a.partials = h->partials;
         a.stop = &h->st->stop;
-        AMG_TRY((launch_spmv<double, double>(3, 3, SPMV_PLAIN, DOT_XY, a, g, s, &grid)));
+        AMG_TRY((launch_sell<double, double>(L0.sA, SPMV_PLAIN, DOT_XY, a, g, s, &grid)));
     }
     cg_alpha_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, grid); ::amg::count_launch(1);
     cg_update_kernel<<<vgrid(h, n), 256, 0, s>>>(h->uu, h->r, h->p, h->q, L0.M,
@@ -398,13 +390,13 @@ static int record_cg_iteration(amg_handle h, cudaStream_t s, cudaGraphConditiona
     cg_resnorm_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, vgrid(h, n)); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     {  // true residual, only when the recurrence residual reached tol
-        SpmvArgs<double> a = args_for(L0.A);
+        SellArgs<double> a{};
         a.x = h->uu;
         a.f = h->ff;
         a.y = h->rt;
         a.partials = h->partials;
         a.stop = &h->st->no_check;
-        AMG_TRY((launch_spmv<double, double>(3, 3, SPMV_RESID, DOT_YY, a, g, s, &grid)));
+        AMG_TRY((launch_sell<double, double>(L0.sA, SPMV_RESID, DOT_YY, a, g, s, &grid)));
     }
     cg_decide_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, grid, cond, use_cond); ::amg::count_launch(1);
     cg_replace_kernel<<<vgrid(h, n), 256, 0, s>>>(h->r, h->rt, L0.M, multi ? L0.u : nullptr,
@@ -613,6 +605,14 @@ static int setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
     Cc.coarsest = true;
     AMG_TRY(coarse_inverse(Cc.A, h->mem, tmp, s, &h->Ainv));
     h->nc = Cc.n();
+    for (size_t l = 0; l < h->lv.size(); ++l) {  // V-cycle operators in SELL-32
+        Level &L = h->lv[l];
+        if (!L.coarsest || l == 0) AMG_TRY(bsr_to_sell(L.A, h->mem, s, &L.sA, &L.pad_A));
+        if (!L.coarsest) {
+            AMG_TRY(bsr_to_sell(L.P, h->mem, s, &L.sP, &L.pad_P));
+            AMG_TRY(bsr_to_sell(L.R, h->mem, s, &L.sR, &L.pad_R));
+        }
+    }
     for (size_t l = 0; l < h->lv.size(); ++l) {
         Level &L = h->lv[l];
         const size_t n = (size_t)std::max(L.n(), 1);
@@ -723,12 +723,12 @@ int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxi
     AMG_TRY(launch_reduce_sum(h->partials, vgrid(h, n), h->scal, s));
     int grid = 0;
     {
-        SpmvArgs<double> a = args_for(L0.A);
+        SellArgs<double> a{};
         a.x = h->uu;
         a.f = h->ff;
         a.y = h->r;
         a.partials = h->partials;
-        AMG_TRY((launch_spmv<double, double>(3, 3, SPMV_RESID, DOT_YY, a, h->geom, s, &grid)));
+        AMG_TRY((launch_sell<double, double>(L0.sA, SPMV_RESID, DOT_YY, a, h->geom, s, &grid)));
     }
     AMG_TRY(launch_reduce_sum(h->partials, grid, h->scal + 1, s));
     cg_start_kernel<<<1, 1, 0, s>>>(h->st, h->scal, tol, maxiter); ::amg::count_launch(1);
@@ -758,12 +758,12 @@ int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxi
     count_launch(h->body_kernels * (long long)h->st_h->it);
     double res = h->st_h->res_true;
     if (status != AMG_OK) {  // report the true residual of the returned iterate
-        SpmvArgs<double> a = args_for(L0.A);
+        SellArgs<double> a{};
         a.x = h->uu;
         a.f = h->ff;
         a.y = h->rt;
         a.partials = h->partials;
-        AMG_TRY((launch_spmv<double, double>(3, 3, SPMV_RESID, DOT_YY, a, h->geom, s, &grid)));
+        AMG_TRY((launch_sell<double, double>(L0.sA, SPMV_RESID, DOT_YY, a, h->geom, s, &grid)));
         AMG_TRY(launch_reduce_sum(h->partials, grid, h->scal + 2, s));
         double rr = 0.0;
         AMG_TRY_CUDA(cudaMemcpyAsync(&rr, h->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -871,6 +871,36 @@ int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_pt
     default: set_error("bad operator id %d", which); return AMG_ERR_ARG;
     }
     AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+int amg_level_spmv(amg_handle h, int32_t level, int32_t which, const double *x, double *y,
+                   void *stream)
+{
+    clear_error();
+    if (!h || level < 0 || level >= (int)h->lv.size() || which < 0 || which > 2 || !x || !y) {
+        set_error("bad argument");
+        return AMG_ERR_ARG;
+    }
+    const Level &L = h->lv[level];
+    const Sell<double> &S = which == 0 ? L.sA : which == 1 ? L.sP : L.sR;
+    if (!S.slice_ptr) {
+        set_error("operator not present on this level");
+        return AMG_ERR_STATE;
+    }
+    SellArgs<double> a{};
+    a.x = x;
+    a.y = y;
+    return launch_sell<double, double>(S, SPMV_PLAIN, DOT_NONE, a, h->geom, (cudaStream_t)stream);
+}
+
+int amg_level_padding(amg_handle h, int32_t level, double *pad3)
+{
+    if (!h || !pad3 || level < 0 || level >= (int)h->lv.size()) return AMG_ERR_ARG;
+    const Level &L = h->lv[level];
+    pad3[0] = L.pad_A;
+    pad3[1] = L.pad_P;
+    pad3[2] = L.pad_R;
     return AMG_OK;
 }
 

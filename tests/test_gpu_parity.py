@@ -207,3 +207,24 @@ def test_full_size_inclusions_80_sampled():
     A = sp.bsr_matrix((p.val, p.col, p.row_ptr), shape=(p.ndof, p.ndof))
     un = u.cpu().numpy()
     assert np.linalg.norm(p.f - A @ un) / np.linalg.norm(p.f) <= 1.0001e-8
+
+
+def test_level_spmv_sell_matches_oracle():
+    """The solve's own sliced-ELL kernels for A, P and R of every level."""
+    p = q.make_problem((13, 9, 11), traction=(0, 0, -1), inclusion_frac=0.2)
+    rp, cl, val, B = _dev(p)
+    G = amg.AMG(rp, cl, val, B, coarse_enough=150)
+    rng = np.random.default_rng(7)
+    for l in range(G.nlevels - 1):
+        ex = G.export(l)
+        b, nagg = ex["info"]["bs"], ex["info"]["nagg"]
+        nb = ex["info"]["nbrows"]
+        for which, (mat, br, bc, ncols) in enumerate([(ex["A"], b, b, nb), (ex["P"], b, 6, nagg),
+                                                       (ex["R"], 6, b, nb)]):
+            x = rng.standard_normal(ncols * bc)
+            y = torch.empty((len(mat[0]) - 1) * br, dtype=torch.float64, device="cuda")
+            G.level_spmv(l, which, torch.from_numpy(x).cuda(), y)
+            ref = o.spmv(o.unblock(mat[0], mat[1], mat[2].reshape(len(mat[1]), -1), br, bc,
+                                   nbcols=ncols), x)
+            assert np.abs(y.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max(), (l, which)
+        assert all(x >= 0 for x in G.padding(l))
