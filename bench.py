@@ -203,6 +203,11 @@ def main():
     ap.add_argument("--workload", default="inclusions80", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=40)
+    ap.add_argument("--profile-spmv", action="store_true",
+                    help="only build the hierarchy and launch the fine SpMV kernel 8 times "
+                         "(a short, fixed command for profilers)")
+    ap.add_argument("--loop-mode", type=int, default=0,
+                    help="1: host-launched CG steps (for profilers); 0: device while loop")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -238,7 +243,7 @@ def main():
     def step(timings=None):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         ev[0].record(s)
-        solver = amg.AMG(rp, cl, val, B)
+        solver = amg.AMG(rp, cl, val, B, loop_mode=args.loop_mode)
         ev[1].record(s)
         u, it, res, st = solver.solve(f, tol=tol, maxiter=5000)
         ev[2].record(s)
@@ -250,6 +255,15 @@ def main():
                             it, res))
         return solver
 
+    if args.profile_spmv:
+        solver = amg.AMG(rp, cl, val, B)
+        x = torch.randn(p.ndof, dtype=torch.float64, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(8):
+            solver.level_spmv(0, 0, x, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_spmv": args.workload, "nnzb": p.nnzb, "rows": p.nnodes}))
+        return 0
     for _ in range(args.warmup):
         solver = step()
         del solver

@@ -76,7 +76,11 @@ typedef struct {
     int32_t max_levels;    /* at most this many levels (15) */
     int32_t npre, npost;   /* smoothing sweeps before / after the correction (1, 1) */
     int32_t precision;     /* AMG_PREC_* of the V-cycle (AMG_PREC_FP64) */
-    int32_t reserved[7];   /* must be zero */
+    int32_t loop_mode;     /* 0: CG loop on the device (graph with a conditional while
+                              node); 1: the host launches one captured iteration graph
+                              per CG step (for profilers that cannot look inside
+                              conditional graphs).  Same kernels, same results. */
+    int32_t reserved[6];   /* must be zero */
 } amg_params;
 
 typedef struct amg_handle_s *amg_handle;

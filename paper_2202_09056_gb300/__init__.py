@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
                 ("smooth_relax", ctypes.c_double), ("coarse_enough", ctypes.c_int32),
                 ("max_levels", ctypes.c_int32), ("npre", ctypes.c_int32),
                 ("npost", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("loop_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class LevelDesc(ctypes.Structure):

@@ -130,10 +130,13 @@ int launch_coarse_gemv(const double *Ainv, int n, const TV *x, TV *y, const Geom
                        cudaStream_t s);
 
 // ---------------------------------------------------------------- SELL-32 (sell.cu)
-// Sliced block-ELL: 32 block rows per slice, blocks of a slice interleaved
-// so that lane t of a warp owns row 32 s + t (or perm[32 s + t]).
+// Sliced block-ELL: 32 lanes per slice, G lanes per block row (32/G rows per
+// slice); block k of a row belongs to lane k % G of its group at depth k / G,
+// and the blocks of a slice are interleaved so that every warp-wide load is
+// contiguous.
 template <class T> struct Sell {
     int nrows = 0, nbc = 0, br = 0, bc = 0, nslices = 0;
+    int G = 1;                   // lanes per block row (power of two); 32/G rows per slice
     int64_t nslots = 0;          // block slots including padding (multiple of 32)
     int64_t *slice_ptr = nullptr;// [nslices + 1] slot offsets
     int *col = nullptr;          // [nslots]
@@ -142,7 +145,7 @@ template <class T> struct Sell {
 };
 
 template <class TV> struct SellArgs {
-    int nrows, nslices;
+    int nrows, nslices, G;
     const int64_t *slice_ptr;
     const int *col;
     const void *val;

@@ -1,23 +1,25 @@
-// Sliced block-ELL (SELL-32) layout and SpMV kernels for the V-cycle and CG.
+// Sliced block-ELL (SELL) layout and SpMV kernels for the V-cycle and CG.
 //
 // Why this layout on GB300: the FP64 pipe of sm_103a issues about two FP64
 // lane-operations per clock per SM, 1/64 of the FP32 rate, so a 3x3 FP64
 // block SpMV is bounded by its multiply-adds almost as much as by HBM
-// (9 DFMA per 72 value bytes).  A kernel that splits a block row across the
-// lanes of a warp pays for the cross-lane FP64 reductions and for predicated
-// accumulations in that same pipe.  Here one THREAD owns one block row: it
-// performs exactly br*bc DFMAs per block and needs no reduction at all.
-// To keep the loads coalesced, 32 consecutive block rows form a slice whose
-// blocks are stored interleaved: entry e of the k-th block of the row held by
-// lane t sits at  (slice_base + 32 k) * bb + 32 e + t , so every value load
-// of a warp is one contiguous 256-byte segment.  A slice is as wide as its
-// longest row; shorter rows are padded with zero blocks that point at
-// column 0 (the padding is counted as overhead, not as algorithmic bytes).
+// (9 DFMA per 72 value bytes).  A kernel that splits a block row across all
+// lanes of a warp pays for cross-lane FP64 reductions and predicated
+// accumulations in that same pipe.  Here a row belongs to G lanes (G = 1 on
+// the fine level, where rows are many and short; up to 32 on the coarse
+// levels, where they are few and long): each lane does exactly br*bc DFMAs
+// per block it owns and the G partial sums meet in a log2(G)-step butterfly.
+// To keep the loads coalesced, the 32 lanes of a slice store their blocks
+// interleaved: entry e of the block at depth d of lane t sits at
+// (slice_base + 32 d) * bb + 32 e + t, so every value load of a warp is one
+// contiguous 256-byte segment.  A slice is as deep as its longest lane;
+// shorter lanes are padded with zero blocks pointing at column 0 (the padding
+// is overhead, not algorithmic bytes).
 //
-// The epilogues are those of the CSR kernels (residual, smoothing,
-// prolongation-correction, restriction with the next pre-smoothing, fused
-// dot products), computed per thread; dots are reduced per CTA in a fixed
-// order, so results are bitwise reproducible for a fixed launch.
+// The epilogues (residual, smoothing, prolongation-correction, restriction
+// with the next pre-smoothing, fused dot products) run on the first lane of
+// each row group; dots are reduced per CTA in a fixed order, so results are
+// bitwise reproducible for a fixed launch.
 #include <algorithm>
 
 #include "amg_internal.cuh"
@@ -57,6 +59,9 @@ __global__ void __launch_bounds__(SELL_THREADS) sell_spmv_kernel(SellArgs<TV> a)
     constexpr int BB = BR * BC;
     if (a.stop && *a.stop) return;
     const int lane = threadIdx.x & 31;
+    const int G = a.G;
+    const int sub = lane & (G - 1);
+    const int rows_per_slice = 32 / G;
     const int nw = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
     const VT *__restrict__ val = static_cast<const VT *>(a.val);
     const int *__restrict__ col = a.col;
@@ -64,7 +69,7 @@ __global__ void __launch_bounds__(SELL_THREADS) sell_spmv_kernel(SellArgs<TV> a)
     double dot = 0.0;
     for (int s = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5); s < a.nslices;
          s += nw) {
-        const int slot = s * 32 + lane;
+        const int slot = s * rows_per_slice + lane / G;
         const int row = a.perm ? a.perm[slot] : slot;
         const int64_t base = a.slice_ptr[s];
         const int w = (int)((a.slice_ptr[s + 1] - base) >> 5);
@@ -88,7 +93,11 @@ __global__ void __launch_bounds__(SELL_THREADS) sell_spmv_kernel(SellArgs<TV> a)
                 for (int c = 0; c < BC; ++c)
                     acc[r] = fma((Acc)sldv(vb + (r * BC + c) * 32), xv[c], acc[r]);
         }
-        if (row >= 0 && row < a.nrows) {
+        // rows split over G lanes: fixed-order butterfly within the group
+        for (int m = G >> 1; m >= 1; m >>= 1)
+#pragma unroll
+            for (int r = 0; r < BR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], m);
+        if (sub == 0 && row >= 0 && row < a.nrows) {
 #pragma unroll
             for (int r = 0; r < BR; ++r) {
                 const int64_t i = (int64_t)row * BR + r;
@@ -156,6 +165,7 @@ int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom
 {
     a.nrows = A.nrows;
     a.nslices = A.nslices;
+    a.G = A.G;
     a.slice_ptr = A.slice_ptr;
     a.col = A.col;
     a.val = A.val;
@@ -179,16 +189,17 @@ template int launch_sell<double, double>(const Sell<double> &, int, int, SellArg
                                          const Geom &, cudaStream_t, int *);
 
 // ---------------------------------------------------------------- conversion
-__global__ void sell_width_kernel(const int *__restrict__ rp, int nrows, int nslices,
+__global__ void sell_width_kernel(const int *__restrict__ rp, int nrows, int nslices, int G,
                                   const int *__restrict__ perm, int *__restrict__ width)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslices) return;
+    const int rps = 32 / G;
     int w = 0;
-    for (int t = 0; t < 32; ++t) {
-        const int slot = s * 32 + t;
+    for (int t = 0; t < rps; ++t) {
+        const int slot = s * rps + t;
         const int row = perm ? perm[slot] : slot;
-        if (row >= 0 && row < nrows) w = max(w, rp[row + 1] - rp[row]);
+        if (row >= 0 && row < nrows) w = max(w, (rp[row + 1] - rp[row] + G - 1) / G);
     }
     width[s] = w;
 }
@@ -196,24 +207,27 @@ __global__ void sell_width_kernel(const int *__restrict__ rp, int nrows, int nsl
 template <class T>
 __global__ void sell_fill_kernel(const int *__restrict__ rp, const int *__restrict__ bcol,
                                  const double *__restrict__ bval, int nrows, int nslices, int bb,
-                                 const int *__restrict__ perm, const int64_t *__restrict__ sp,
-                                 int *__restrict__ col, T *__restrict__ val)
+                                 int G, const int *__restrict__ perm,
+                                 const int64_t *__restrict__ sp, int *__restrict__ col,
+                                 T *__restrict__ val)
 {
-    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot >= nslices * 32) return;
-    const int s = slot >> 5, lane = slot & 31;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nslices * 32) return;
+    const int s = t >> 5, lane = t & 31, sub = lane & (G - 1);
+    const int slot = s * (32 / G) + lane / G;
     const int row = perm ? perm[slot] : slot;
     const bool live = row >= 0 && row < nrows;
     const int len = live ? rp[row + 1] - rp[row] : 0;
     const int64_t base = sp[s];
     const int w = (int)((sp[s + 1] - base) >> 5);
-    for (int k = 0; k < w; ++k) {
-        const int64_t q = base + (int64_t)k * 32 + lane;
-        const int64_t src = live ? (int64_t)rp[row] + k : 0;
+    for (int d = 0; d < w; ++d) {
+        const int k = d * G + sub;  // block k of the row sits at depth k / G of lane k % G
+        const int64_t q = base + (int64_t)d * 32 + lane;
         const bool have = k < len;
+        const int64_t src = have ? (int64_t)rp[row] + k : 0;
         col[q] = have ? bcol[src] : 0;
         for (int e = 0; e < bb; ++e)
-            val[(base + (int64_t)k * 32) * bb + (int64_t)e * 32 + lane] =
+            val[(base + (int64_t)d * 32) * bb + (int64_t)e * 32 + lane] =
                 have ? (T)bval[src * bb + e] : (T)0.0;
     }
 }
@@ -226,13 +240,19 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
     S.nbc = B.nbc;
     S.br = B.br;
     S.bc = B.bc;
-    S.nslices = (B.nbr + 31) / 32;
+    // lanes per row: enough threads to fill the GPU (rows x G >= 160k), but
+    // keep at least two blocks per lane on average
+    const double avg = B.nbr ? (double)B.nnzb / B.nbr : 0.0;
+    int G = 1;
+    while (G < 32 && (int64_t)B.nbr * G < 160000 && avg / (2 * G) >= 2.0) G <<= 1;
+    S.G = G;
+    S.nslices = (B.nbr + 32 / G - 1) / (32 / G);
     const int bb = B.br * B.bc;
     int *width = nullptr;
     AMG_TRY_CUDA(cudaMallocAsync((void **)&width, sizeof(int) * std::max(S.nslices, 1), s));
     if (S.nslices > 0) {
         sell_width_kernel<<<(S.nslices + 255) / 256, 256, 0, s>>>(B.row_ptr, B.nbr, S.nslices,
-                                                                  nullptr, width);
+                                                                  G, nullptr, width);
         count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
     }
@@ -250,7 +270,7 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
                                  cudaMemcpyHostToDevice, s));
     if (S.nslices > 0) {
         sell_fill_kernel<T><<<(S.nslices * 32 + 127) / 128, 128, 0, s>>>(
-            B.row_ptr, B.col, B.val, B.nbr, S.nslices, bb, nullptr, S.slice_ptr, S.col, S.val);
+            B.row_ptr, B.col, B.val, B.nbr, S.nslices, bb, G, nullptr, S.slice_ptr, S.col, S.val);
         count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
     }

@@ -405,8 +405,44 @@ static int record_cg_iteration(amg_handle h, cudaStream_t s, cudaGraphConditiona
     return AMG_OK;
 }
 
+// Host-loop variant: the same iteration captured as a plain graph.
+static int build_step_graph(amg_handle h)
+{
+    if (h->exec) return AMG_OK;
+    cudaStream_t cs;
+    AMG_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    AMG_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    long long nbody = 0;
+    begin_launch_capture(&nbody);
+    cudaGraphConditionalHandle none = 0;
+    int st = record_cg_iteration(h, cs, none, 0);
+    end_launch_capture();
+    h->body_kernels = nbody;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (st < 0) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) {
+        set_error("graph capture: %s", cudaGetErrorString(e));
+        return AMG_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&h->exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        h->exec = nullptr;
+        set_error("graph instantiate: %s", cudaGetErrorString(e));
+        return AMG_ERR_CUDA;
+    }
+    h->graph = graph;
+    return AMG_OK;
+}
+
 static int build_graph(amg_handle h)
 {
+    if (h->prm.loop_mode == 1) return build_step_graph(h);
     if (h->exec) return AMG_OK;
     cudaGraph_t graph = nullptr;
     AMG_TRY_CUDA(cudaGraphCreate(&graph, 0));
@@ -660,7 +696,8 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
     amg_params_default(&p);
     if (prm) p = *prm;
     if (p.npre < 0 || p.npost < 0 || p.max_levels < 1 || p.coarse_enough < 0 ||
-        !(p.eps_strong >= 0.0) || p.precision != AMG_PREC_FP64) {
+        !(p.eps_strong >= 0.0) || p.precision != AMG_PREC_FP64 || p.loop_mode < 0 ||
+        p.loop_mode > 1) {
         set_error("bad parameters");
         return AMG_ERR_ARG;
     }
@@ -751,7 +788,20 @@ int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxi
         return h->st_h->res <= tol ? AMG_OK : AMG_NOT_CONVERGED;
     }
     AMG_TRY(build_graph(h));
-    AMG_TRY_CUDA(cudaGraphLaunch(h->exec, s));
+    if (h->prm.loop_mode == 1) {
+        // one graph launch per CG step; the state is polled every 8 steps and
+        // the kernels of steps launched after the stop return at once
+        for (int it = 0; it < maxiter; it += 8) {
+            for (int k = 0; k < 8 && it + k < maxiter; ++k)
+                AMG_TRY_CUDA(cudaGraphLaunch(h->exec, s));
+            AMG_TRY_CUDA(cudaMemcpyAsync(h->st_h, h->st, sizeof(CgState),
+                                         cudaMemcpyDeviceToHost, s));
+            AMG_TRY_CUDA(cudaStreamSynchronize(s));
+            if (h->st_h->stop) break;
+        }
+    } else {
+        AMG_TRY_CUDA(cudaGraphLaunch(h->exec, s));
+    }
     AMG_TRY_CUDA(cudaMemcpyAsync(h->st_h, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
     AMG_TRY_CUDA(cudaStreamSynchronize(s));
     status = h->st_h->status;

@@ -228,3 +228,12 @@ def test_level_spmv_sell_matches_oracle():
                                    nbcols=ncols), x)
             assert np.abs(y.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max(), (l, which)
         assert all(x >= 0 for x in G.padding(l))
+
+
+def test_host_loop_mode_gives_identical_results():
+    p = q.inclusions(9)
+    rp, cl, val, B = _dev(p)
+    fb = torch.from_numpy(p.f).cuda()
+    u0, it0, r0, s0 = amg.AMG(rp, cl, val, B, coarse_enough=200).solve(fb)
+    u1, it1, r1, s1 = amg.AMG(rp, cl, val, B, coarse_enough=200, loop_mode=1).solve(fb)
+    assert (it0, r0, s0) == (it1, r1, s1) and torch.equal(u0, u1)
