@@ -138,17 +138,16 @@ def _spmv_roofline(solver, torch, n, nbr, nnzb, reps=40):
     return t, algo
 
 
-def _traffic_from_profile(kernel_tag):
-    """DRAM bytes per launch from the committed ncu summary, if it matches."""
-    path = os.path.join(ROOT, "profiles", "spmv_3x3_fp64_inclusions80.json")
-    try:
-        with open(path) as f:
-            d = json.load(f)
-        if d.get("kernel_tag") == kernel_tag:
-            return d.get("dram_bytes_per_launch")
-    except Exception:
-        pass
-    return None
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel from ncu, keyed by kernel version; the summary and the
+# command that produced it are in profiles/sell_spmv_3x3_fp64_inclusions48.md
+# (48^3 capture, 249.5 MB, scaled by blocks to the 80^3 launch).  A kernel
+# change gets a new tag and reports null until it is captured again.
+NCU_TRAFFIC = {"sell_spmv_kernel<3,3,double,double,PLAIN,NONE>:G1:v2": 1154844000}
+
+# FP64 FMA peak of GB300: 152 SMs x 2 DFMA per clock x 2 flop x 2.07 GHz
+# (the nominal 1.25 TFLOP/s FP64 rate at the maximum SM clock).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def cpu_baseline(sample_n=40):
@@ -311,8 +310,10 @@ def main():
     t_spmv, algo = _spmv_roofline(solver, torch, p.ndof, p.nnodes, p.nnzb)
     peak, peak_kind = _peaks()
     achieved = algo / t_spmv / 1e9
-    kernel_tag = "sell_spmv_kernel<3,3,double,double,PLAIN,NONE>:v1"
-    traffic = _traffic_from_profile(kernel_tag)
+    kernel_tag = "sell_spmv_kernel<3,3,double,double,PLAIN,NONE>:G1:v2"
+    traffic = NCU_TRAFFIC.get(kernel_tag)
+    flops = 2.0 * 9 * p.nnzb
+    tflops = flops / t_spmv / 1e12
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -335,10 +336,13 @@ def main():
         "e2e": {"value": e2e_t, "unit": "s", "h2d_bytes_per_step": 8 * p.ndof,
                 "d2h_bytes_per_step": 8 * p.ndof},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": kernel_tag, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": peak_kind, "algorithmic_bytes": algo,
-                     "launch_ms": 1e3 * t_spmv},
+        "roofline": {"bound": "alu", "kernel": kernel_tag, "achieved": tflops,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
+                     "traffic": traffic, "peak_source": "derived (FP64 pipe, see DESIGN.md)",
+                     "algorithmic_flops": flops, "launch_ms": 1e3 * t_spmv,
+                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_source": peak_kind,
+                             "algorithmic_bytes": algo}},
         "wall_s": wall,
     }
     if world == 1 and not args.no_cpu_baseline:
