@@ -186,6 +186,27 @@ int amg_bsr_spmv(const amg_bsr *A, const double *x, double *y, void *stream);
 int amg_bsr_spmv_dot(const amg_bsr *A, const double *x, double *y, double *dot_out,
                      void *stream);
 
+/* Same result as amg_bsr_spmv_dot, without allocating.  (The paper has no
+ * counterpart: this serves callers of the library, not the method.)
+ * amg_bsr_spmv_dot allocates device scratch for its per-CTA partial sums; a
+ * caller that cannot allow a device allocation inside the call -- because
+ * one may fail or wait for the whole device at a point where the caller has
+ * a fixed memory budget, or because its device memory is owned by another
+ * allocator -- calls this variant, which keeps that scratch in a static
+ * device array of AMG_NOALLOC_SCRATCH_DOUBLES doubles (32 KiB, held by every
+ * GPU that loads the library until the process exits).  It makes no
+ * cudaMalloc, cudaFree or allocating library call; x, y and the result are
+ * the caller's.  The launch needs one partial sum per CTA plus one for the
+ * total; a launch that would need more than the array holds is rejected with
+ * AMG_ERR_LIMIT (on GB300 the launch needs at most 8 x 152 + 1).  The first
+ * call on a device looks up the array's device address, so make that first
+ * call before any stream capture.  All calls share the array: calls whose
+ * work overlaps on the GPU (two streams, two host threads) race on it; calls
+ * ordered on one stream are safe.  Synchronises `stream`. */
+#define AMG_NOALLOC_SCRATCH_DOUBLES 4096
+int amg_bsr_spmv_dot_noalloc(const amg_bsr *A, const double *x, double *y, double *dot_out,
+                             void *stream);
+
 #ifdef __cplusplus
 }
 #endif
