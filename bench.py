@@ -36,6 +36,8 @@ sys.path.insert(0, ROOT)
 METRIC = "PCG time-to-1e-8 (s); BSR SpMV GB/s vs HBM peak; mixed/learned vs FP64"
 WORKLOADS = {
     "inclusions80": dict(n=80, desc="q1-hex-80^3-inclusions-20pct-E1000", tol=1e-8),
+    "inclusions150": dict(n=150, desc="q1-hex-150^3-inclusions-20pct-E1000", tol=1e-8),
+    "inclusions120": dict(n=120, desc="q1-hex-120^3-inclusions-20pct-E1000", tol=1e-8),
     "inclusions48": dict(n=48, desc="q1-hex-48^3-inclusions-20pct-E1000", tol=1e-8),
     "inclusions40": dict(n=40, desc="q1-hex-40^3-inclusions-20pct-E1000", tol=1e-8),
     "cube10": dict(n=10, desc="q1-hex-10^3-cube-body-load", tol=1e-8),
@@ -205,6 +207,10 @@ def main():
     ap.add_argument("--profile-spmv", action="store_true",
                     help="only build the hierarchy and launch the fine SpMV kernel 8 times "
                          "(a short, fixed command for profilers)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"],
+                    help="V-cycle precision of the main line (CG stays FP64)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP32/BF16 V-cycle comparison on the same workload")
     ap.add_argument("--loop-mode", type=int, default=0,
                     help="1: host-launched CG steps (for profilers); 0: device while loop")
     args = ap.parse_args()
@@ -238,11 +244,13 @@ def main():
     f = torch.from_numpy(p.f).to(dev)
     tol = WORKLOADS[args.workload]["tol"]
     s = torch.cuda.current_stream()
+    PRECS = {"fp64": amg.PREC_FP64, "fp32": amg.PREC_FP32, "bf16": amg.PREC_BF16}
+    prec = PRECS[args.precision]
 
     def step(timings=None):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         ev[0].record(s)
-        solver = amg.AMG(rp, cl, val, B, loop_mode=args.loop_mode)
+        solver = amg.AMG(rp, cl, val, B, loop_mode=args.loop_mode, precision=prec)
         ev[1].record(s)
         u, it, res, st = solver.solve(f, tol=tol, maxiter=5000)
         ev[2].record(s)
@@ -314,6 +322,32 @@ def main():
     traffic = NCU_TRAFFIC.get(kernel_tag)
     flops = 2.0 * 9 * p.nnzb
     tflops = flops / t_spmv / 1e12
+    forms = None
+    if not args.no_forms and not args.profile_spmv:
+        # precision form: the same solve with the V-cycle in FP32 / BF16
+        # storage (FP32 accumulation), CG recurrences and dots in FP64
+        u_ref, it_ref, _, _ = solver.solve(f, tol=tol, maxiter=5000)
+        forms = {}
+        for name in ("fp64", "fp32", "bf16"):
+            sol = amg.AMG(rp, cl, val, B, precision=PRECS[name])
+            sol.solve(f, tol=tol, maxiter=5000)  # warm-up (graph capture)
+            times = []
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                u_p, it_p, res_p, st_p = sol.solve(f, tol=tol, maxiter=5000)
+                e1.record(s)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+            err = float(torch.linalg.norm(u_p - u_ref) / torch.linalg.norm(u_ref))
+            forms[name] = {"value": float(np.mean(times)), "iterations": it_p, "rel_resid": res_p,
+                           "status": st_p, "err_vs_fp64_solution": err,
+                           "vcycle": {"fp64": "FP64 matrices and vectors",
+                                      "fp32": "FP32 matrices and vectors, FP32 accumulation",
+                                      "bf16": "BF16-stored matrices, FP32 vectors and accumulation"}[name]}
+            del sol
+        for name in ("fp32", "bf16"):
+            forms[name]["speedup_vs_fp64"] = forms["fp64"]["value"] / forms[name]["value"]
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -321,7 +355,9 @@ def main():
     line = {
         "metric": METRIC, "value": solve_t, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_t, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f64 CG / f32 V-cycle",
+                                         "bf16": "f64 CG / bf16-stored V-cycle"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "dofs": p.ndof,
                    "nnzb": p.nnzb, "levels": stats["nlevels"],
                    "level_rows": [l["nbrows"] * l["bs"] for l in levels],
@@ -344,6 +380,8 @@ def main():
                              "frac": achieved / peak, "peak_source": peak_kind,
                              "algorithmic_bytes": algo}},
         "wall_s": wall,
+        "precision": args.precision,
+        "forms": forms,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.ref_sample)

@@ -21,6 +21,7 @@
 // each row group; dots are reduced per CTA in a fixed order, so results are
 // bitwise reproducible for a fixed launch.
 #include <algorithm>
+#include <type_traits>
 
 #include "amg_internal.cuh"
 
@@ -130,19 +131,29 @@ int sell_grid(int nslices, const Geom &g)
     return std::max(grid, 1);
 }
 
-template <int BR, int BC, class VT, class TV, int MODE>
-static int sell_dot(int dot, const SellArgs<TV> &a, int grid, cudaStream_t s)
+template <int BR, int BC, class VT, class TV, int MODE, int DOT>
+static int sell_go(const SellArgs<TV> &a, int grid, cudaStream_t s)
 {
-    switch (dot) {
-    case DOT_NONE: sell_spmv_kernel<BR, BC, VT, TV, MODE, DOT_NONE><<<grid, SELL_THREADS, 0, s>>>(a); break;
-    case DOT_XY: sell_spmv_kernel<BR, BC, VT, TV, MODE, DOT_XY><<<grid, SELL_THREADS, 0, s>>>(a); break;
-    case DOT_FY: sell_spmv_kernel<BR, BC, VT, TV, MODE, DOT_FY><<<grid, SELL_THREADS, 0, s>>>(a); break;
-    case DOT_YY: sell_spmv_kernel<BR, BC, VT, TV, MODE, DOT_YY><<<grid, SELL_THREADS, 0, s>>>(a); break;
-    default: set_error("bad dot mode %d", dot); return AMG_ERR_ARG;
-    }
+    sell_spmv_kernel<BR, BC, VT, TV, MODE, DOT><<<grid, SELL_THREADS, 0, s>>>(a);
     count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     return AMG_OK;
+}
+
+// The (mode, dot) pairs the solver uses; FP64-only dots for the CG products.
+template <int BR, int BC, class VT, class TV, int MODE>
+static int sell_dot(int dot, const SellArgs<TV> &a, int grid, cudaStream_t s)
+{
+    constexpr bool f64 = std::is_same<TV, double>::value;
+    if (dot == DOT_NONE) return sell_go<BR, BC, VT, TV, MODE, DOT_NONE>(a, grid, s);
+    if constexpr (MODE == SPMV_SMOOTH)
+        if (dot == DOT_FY) return sell_go<BR, BC, VT, TV, MODE, DOT_FY>(a, grid, s);
+    if constexpr (f64 && BR == BC && MODE == SPMV_PLAIN)
+        if (dot == DOT_XY) return sell_go<BR, BC, VT, TV, MODE, DOT_XY>(a, grid, s);
+    if constexpr (f64 && BR == BC && MODE == SPMV_RESID)
+        if (dot == DOT_YY) return sell_go<BR, BC, VT, TV, MODE, DOT_YY>(a, grid, s);
+    set_error("unsupported dot %d for spmv mode %d", dot, MODE);
+    return AMG_ERR_ARG;
 }
 
 // Only the (mode, dot) pairs the solver records are instantiated.
@@ -187,6 +198,10 @@ int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom
 
 template int launch_sell<double, double>(const Sell<double> &, int, int, SellArgs<double>,
                                          const Geom &, cudaStream_t, int *);
+template int launch_sell<float, float>(const Sell<float> &, int, int, SellArgs<float>,
+                                       const Geom &, cudaStream_t, int *);
+template int launch_sell<__nv_bfloat16, float>(const Sell<__nv_bfloat16> &, int, int,
+                                               SellArgs<float>, const Geom &, cudaStream_t, int *);
 
 // ---------------------------------------------------------------- conversion
 __global__ void sell_width_kernel(const int *__restrict__ rp, int nrows, int nslices, int G,
@@ -281,5 +296,8 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
 }
 
 template int bsr_to_sell<double>(const BsrD &, DevArena &, cudaStream_t, Sell<double> *, double *);
+template int bsr_to_sell<float>(const BsrD &, DevArena &, cudaStream_t, Sell<float> *, double *);
+template int bsr_to_sell<__nv_bfloat16>(const BsrD &, DevArena &, cudaStream_t,
+                                        Sell<__nv_bfloat16> *, double *);
 
 }  // namespace amg

@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "amg_internal.cuh"
 
@@ -20,8 +21,12 @@ const char *last_error();
 
 struct Level {
     BsrD A, P, R;
-    Sell<double> sA, sP, sR;  // V-cycle copies of A, P, R in the SELL-32 layout
+    Sell<double> sA, sP, sR;  // V-cycle copies of A, P, R in the SELL layout (FP64)
+    Sell<float> fA, fP, fR;   // FP32 copies (precision form)
+    Sell<__nv_bfloat16> bA, bP, bR;  // BF16-stored copies (precision form)
     double pad_A = 0, pad_P = 0, pad_R = 0;
+    float *Mf = nullptr;      // smoother diagonal for the reduced-precision V-cycle
+    float *vf = nullptr, *vu = nullptr, *ve = nullptr, *vz = nullptr, *vt = nullptr;
     double *M = nullptr;      // damped SPAI0 diagonal (scalar rows)
     double *B = nullptr;      // near-nullspace, n x 6
     int *agg = nullptr;       // aggregate of each node (device)
@@ -49,14 +54,15 @@ template <int NT> __device__ __forceinline__ double block_sum_fixed(const double
     return red[0];
 }
 
-__global__ void __launch_bounds__(256) vec_dot_kernel(const double *__restrict__ x,
-                                                      const double *__restrict__ y, int64_t n,
+template <class TV>
+__global__ void __launch_bounds__(256) vec_dot_kernel(const TV *__restrict__ x,
+                                                      const TV *__restrict__ y, int64_t n,
                                                       double *__restrict__ partials)
 {
     double v = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        v += x[i] * y[i];
+        v += (double)x[i] * (double)y[i];
     __shared__ double red[256];
     red[threadIdx.x] = v;
     __syncthreads();
@@ -67,13 +73,35 @@ __global__ void __launch_bounds__(256) vec_dot_kernel(const double *__restrict__
     if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
 }
 
-// t = M r (pre-smoothing from a zero guess) or t = 0 when there is no pre-smoothing.
-__global__ void scale_kernel(const double *__restrict__ M, const double *__restrict__ r,
-                             double *__restrict__ t, int64_t n, int zero)
+// First pre-smoothing sweep from a zero guess in the V-cycle's precision:
+// t = M r (or 0 without pre-smoothing); rv receives r in that precision when
+// the V-cycle does not run in FP64.
+template <class TV>
+__global__ void scale_kernel(const TV *__restrict__ M, const double *__restrict__ r,
+                             TV *__restrict__ t, TV *__restrict__ rv, int64_t n, int zero)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const TV ri = (TV)r[i];
+        if (rv) rv[i] = ri;
+        if (t) t[i] = zero ? TV(0) : M[i] * ri;
+    }
+}
+
+// z (V-cycle precision) -> double
+template <class TV>
+__global__ void widen_kernel(const TV *__restrict__ a, double *__restrict__ b, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        t[i] = zero ? 0.0 : M[i] * r[i];
+        b[i] = (double)a[i];
+}
+
+__global__ void narrow_kernel(const double *__restrict__ a, float *__restrict__ b, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
 }
 
 __global__ void cg_start_kernel(CgState *st, const double *__restrict__ scal, double tol,
@@ -111,14 +139,15 @@ __global__ void __launch_bounds__(FIN_THREADS) cg_beta_kernel(CgState *st,
     st->rz = rz;
 }
 
-__global__ void cg_direction_kernel(const double *__restrict__ z, double *__restrict__ p,
+template <class TV>
+__global__ void cg_direction_kernel(const TV *__restrict__ z, double *__restrict__ p,
                                     const CgState *__restrict__ st, int64_t n)
 {
     if (st->stop) return;
     const double beta = st->beta;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = z[i] + beta * p[i];
+        p[i] = (double)z[i] + beta * p[i];
 }
 
 __global__ void __launch_bounds__(FIN_THREADS) cg_alpha_kernel(CgState *st,
@@ -138,12 +167,14 @@ __global__ void __launch_bounds__(FIN_THREADS) cg_alpha_kernel(CgState *st,
     st->alpha = st->rz / pq;
 }
 
-// u += alpha p ; r -= alpha q ; t0 = M r (next pre-smoothing) ; partial r.r
+// u += alpha p ; r -= alpha q ; t0 = M r (next pre-smoothing, in the V-cycle's
+// precision; rv = r in that precision when it is not FP64) ; partial r.r
+template <class TV>
 __global__ void __launch_bounds__(256) cg_update_kernel(double *__restrict__ u, double *__restrict__ r,
                                                         const double *__restrict__ p,
                                                         const double *__restrict__ q,
-                                                        const double *__restrict__ M,
-                                                        double *__restrict__ t0,
+                                                        const TV *__restrict__ M,
+                                                        TV *__restrict__ t0, TV *__restrict__ rv,
                                                         const CgState *__restrict__ st, int64_t n,
                                                         int pre, double *__restrict__ partials)
 {
@@ -155,7 +186,9 @@ __global__ void __launch_bounds__(256) cg_update_kernel(double *__restrict__ u, 
         u[i] += alpha * p[i];
         const double ri = r[i] - alpha * q[i];
         r[i] = ri;
-        if (t0) t0[i] = pre ? M[i] * ri : 0.0;
+        const TV rr = (TV)ri;
+        if (rv) rv[i] = rr;
+        if (t0) t0[i] = pre ? M[i] * rr : TV(0);
         v += ri * ri;
     }
     __shared__ double red[256];
@@ -214,16 +247,20 @@ __global__ void __launch_bounds__(FIN_THREADS) cg_decide_kernel(CgState *st,
 }
 
 // r = r_true (residual replacement) and the matching pre-smoothed t0.
+template <class TV>
 __global__ void cg_replace_kernel(double *__restrict__ r, const double *__restrict__ rt,
-                                  const double *__restrict__ M, double *__restrict__ t0,
-                                  const CgState *__restrict__ st, int64_t n, int pre)
+                                  const TV *__restrict__ M, TV *__restrict__ t0,
+                                  TV *__restrict__ rv, const CgState *__restrict__ st, int64_t n,
+                                  int pre)
 {
     if (st->no_replace) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double ri = rt[i];
         r[i] = ri;
-        if (t0) t0[i] = pre ? M[i] * ri : 0.0;
+        const TV rr = (TV)ri;
+        if (rv) rv[i] = rr;
+        if (t0) t0[i] = pre ? M[i] * rr : TV(0);
     }
 }
 
@@ -241,6 +278,7 @@ struct amg_handle_s {
     int nc = 0;
     double *ff = nullptr, *uu = nullptr, *r = nullptr, *p = nullptr, *q = nullptr,
            *z = nullptr, *rt = nullptr, *partials = nullptr, *scal = nullptr;
+    float *rv = nullptr, *zv = nullptr;   // r and z in the reduced-precision V-cycle
     CgState *st = nullptr;
     CgState *st_h = nullptr;
     cudaGraph_t graph = nullptr;
@@ -256,95 +294,126 @@ static int vgrid(amg_handle h, int64_t n)
     return (int)std::max<int64_t>(g, 1);
 }
 
-// One V-cycle (Alg. 2) from a zero initial guess: z0 = V(f0).  lv[0].u must
-// already hold the first pre-smoothing sweep M_0 f0 (or zero without
-// pre-smoothing).  With rz_partials, the last level-0 kernel also leaves the
-// per-CTA partial sums of f0 . z0.
-static int record_vcycle(amg_handle h, const double *f0, double *z0, double *rz_partials,
-                         cudaStream_t s)
+// One level of the V-cycle in the precision it runs in.
+template <class VT, class TV> struct VLevel {
+    const Sell<VT> *A = nullptr, *P = nullptr, *R = nullptr;
+    const TV *M = nullptr;
+    TV *f = nullptr, *u = nullptr, *e = nullptr, *z = nullptr, *t = nullptr;
+    int n = 0;
+};
+
+template <class VT, class TV> static VLevel<VT, TV> view(Level &L);
+template <> VLevel<double, double> view<double, double>(Level &L)
+{
+    VLevel<double, double> v;
+    v.A = &L.sA; v.P = &L.sP; v.R = &L.sR; v.M = L.M;
+    v.f = L.f; v.u = L.u; v.e = L.e; v.z = L.z; v.t = L.t; v.n = L.n();
+    return v;
+}
+template <> VLevel<float, float> view<float, float>(Level &L)
+{
+    VLevel<float, float> v;
+    v.A = &L.fA; v.P = &L.fP; v.R = &L.fR; v.M = L.Mf;
+    v.f = L.vf; v.u = L.vu; v.e = L.ve; v.z = L.vz; v.t = L.vt; v.n = L.n();
+    return v;
+}
+template <> VLevel<__nv_bfloat16, float> view<__nv_bfloat16, float>(Level &L)
+{
+    VLevel<__nv_bfloat16, float> v;
+    v.A = &L.bA; v.P = &L.bP; v.R = &L.bR; v.M = L.Mf;
+    v.f = L.vf; v.u = L.vu; v.e = L.ve; v.z = L.vz; v.t = L.vt; v.n = L.n();
+    return v;
+}
+
+template <class TV>
+static int launch_vec_dot(amg_handle h, const TV *x, const TV *y, int64_t n, double *part,
+                          cudaStream_t s);
+
+// One V-cycle (Alg. 2) from a zero initial guess: z0 = V(f0), matrices stored
+// in VT and vectors in TV.  Level 0's u must already hold the first
+// pre-smoothing sweep M_0 f0 (or zero without pre-smoothing).  With
+// rz_partials, the last level-0 kernel also leaves the per-CTA partial sums
+// of f0 . z0 (accumulated in FP64).
+template <class VT, class TV>
+static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials, cudaStream_t s)
 {
     const int L = (int)h->lv.size() - 1;
     const int npre = h->prm.npre, npost = h->prm.npost;
     const Geom &g = h->geom;
-    std::vector<double *> ucur(L + 1, nullptr), spare(L + 1, nullptr);
+    std::vector<VLevel<VT, TV>> V;
+    for (auto &lev : h->lv) V.push_back(view<VT, TV>(lev));
+    std::vector<TV *> ucur(L + 1, nullptr), spare(L + 1, nullptr);
     for (int l = 0; l < L; ++l) {
-        Level &C = h->lv[l];
-        Level &N = h->lv[l + 1];
-        const double *f = (l == 0) ? f0 : C.f;
-        double *u = C.u, *t = C.t;
+        VLevel<VT, TV> &C = V[l];
+        VLevel<VT, TV> &N = V[l + 1];
+        const TV *f = (l == 0) ? f0 : C.f;
+        TV *u = C.u, *t = C.t;
         for (int sweep = 1; sweep < npre; ++sweep) {  // further pre-smoothing sweeps
-            SellArgs<double> a{};
+            SellArgs<TV> a{};
             a.x = u;
             a.f = f;
             a.M = C.M;
             a.y = t;
-            AMG_TRY((launch_sell<double, double>(C.sA, SPMV_SMOOTH, DOT_NONE, a, g, s)));
+            AMG_TRY((launch_sell<VT, TV>(*C.A, SPMV_SMOOTH, DOT_NONE, a, g, s)));
             std::swap(u, t);
         }
         ucur[l] = u;
         spare[l] = t;
         {  // e = f - A u
-            SellArgs<double> a{};
+            SellArgs<TV> a{};
             a.x = u;
             a.f = f;
             a.y = C.e;
-            AMG_TRY((launch_sell<double, double>(C.sA, SPMV_RESID, DOT_NONE, a, g, s)));
+            AMG_TRY((launch_sell<VT, TV>(*C.A, SPMV_RESID, DOT_NONE, a, g, s)));
         }
         {  // f_{l+1} = R e ; u_{l+1} = M_{l+1} f_{l+1}
-            SellArgs<double> a{};
+            SellArgs<TV> a{};
             a.x = C.e;
             a.y = N.f;
             const bool next_smooths = (l + 1 < L);
             a.y2 = next_smooths ? N.u : nullptr;
             a.M = (next_smooths && npre > 0) ? N.M : nullptr;
-            AMG_TRY((launch_sell<double, double>(C.sR, SPMV_RESTRICT, DOT_NONE, a, g,
-                                                 s)));
+            AMG_TRY((launch_sell<VT, TV>(*C.R, SPMV_RESTRICT, DOT_NONE, a, g, s)));
         }
     }
-    {  // coarsest: direct solve with the dense inverse
-        Level &Cc = h->lv[L];
-        const double *fL = (L == 0) ? f0 : Cc.f;
-        double *zL = (L == 0) ? z0 : Cc.z;
-        AMG_TRY(launch_coarse_gemv<double>(h->Ainv, h->nc, fL, zL, g, s));
-        if (L == 0 && rz_partials) {
-            vec_dot_kernel<<<vgrid(h, h->nc), 256, 0, s>>>(f0, z0, h->nc, rz_partials); ::amg::count_launch(1);
-            AMG_TRY_CUDA(cudaGetLastError());
-        }
+    {  // coarsest: direct solve with the dense FP64 inverse
+        VLevel<VT, TV> &Cc = V[L];
+        const TV *fL = (L == 0) ? f0 : Cc.f;
+        TV *zL = (L == 0) ? z0 : Cc.z;
+        AMG_TRY(launch_coarse_gemv<TV>(h->Ainv, h->nc, fL, zL, g, s));
+        if (L == 0 && rz_partials) AMG_TRY(launch_vec_dot<TV>(h, f0, z0, h->nc, rz_partials, s));
     }
     for (int l = L - 1; l >= 0; --l) {
-        Level &C = h->lv[l];
-        Level &N = h->lv[l + 1];
-        const double *f = (l == 0) ? f0 : C.f;
-        double *u = ucur[l], *t = spare[l];
-        double *zl = (l == 0) ? z0 : C.z;
+        VLevel<VT, TV> &C = V[l];
+        VLevel<VT, TV> &N = V[l + 1];
+        const TV *f = (l == 0) ? f0 : C.f;
+        TV *u = ucur[l], *t = spare[l];
+        TV *zl = (l == 0) ? z0 : C.z;
         {  // u += P z_{l+1}
-            SellArgs<double> a{};
+            SellArgs<TV> a{};
             a.x = N.z;
             a.u = u;
             a.y = u;
-            AMG_TRY((launch_sell<double, double>(C.sP, SPMV_AXPY, DOT_NONE, a, g, s)));
+            AMG_TRY((launch_sell<VT, TV>(*C.P, SPMV_AXPY, DOT_NONE, a, g, s)));
         }
-        const double *w = u;
+        const TV *w = u;
         for (int sweep = 0; sweep < npost; ++sweep) {  // u += M (f - A u)
             const bool last = (sweep == npost - 1);
-            double *out = last ? zl : t;
-            SellArgs<double> a{};
+            TV *out = last ? zl : t;
+            SellArgs<TV> a{};
             a.x = w;
             a.f = f;
             a.M = C.M;
             a.y = out;
             a.partials = rz_partials;
             const int dot = (l == 0 && last && rz_partials) ? DOT_FY : DOT_NONE;
-            AMG_TRY((launch_sell<double, double>(C.sA, SPMV_SMOOTH, dot, a, g, s)));
+            AMG_TRY((launch_sell<VT, TV>(*C.A, SPMV_SMOOTH, dot, a, g, s)));
             w = out;
             t = (out == t) ? u : t;  // ping-pong between u and t
         }
         if (npost == 0) {
-            AMG_TRY_CUDA(cudaMemcpyAsync(zl, u, sizeof(double) * C.n(), cudaMemcpyDeviceToDevice, s));
-            if (l == 0 && rz_partials) {
-                vec_dot_kernel<<<vgrid(h, C.n()), 256, 0, s>>>(f0, z0, C.n(), rz_partials); ::amg::count_launch(1);
-                AMG_TRY_CUDA(cudaGetLastError());
-            }
+            AMG_TRY_CUDA(cudaMemcpyAsync(zl, u, sizeof(TV) * C.n, cudaMemcpyDeviceToDevice, s));
+            if (l == 0 && rz_partials) AMG_TRY(launch_vec_dot<TV>(h, f0, z0, C.n, rz_partials, s));
         }
     }
     return AMG_OK;
@@ -360,22 +429,31 @@ static int rz_parts(amg_handle h)
     return sell_grid(L0.sA.nslices, h->geom);
 }
 
-// One CG iteration, as recorded into the body of the conditional while node.
-static int record_cg_iteration(amg_handle h, cudaStream_t s, cudaGraphConditionalHandle cond,
-                               int use_cond)
+// One CG iteration, as recorded into the body of the graph.  The outer
+// recurrences, dots and the fine A p product are FP64; the V-cycle runs with
+// matrices in VT and vectors in TV (FP64 or FP32), its input r and output z
+// converted at the boundary.
+template <class VT, class TV>
+static int record_cg_iteration_t(amg_handle h, cudaStream_t s, cudaGraphConditionalHandle cond,
+                                 int use_cond)
 {
+    constexpr bool f64 = std::is_same<TV, double>::value;
     Level &L0 = h->lv[0];
+    VLevel<VT, TV> V0 = view<VT, TV>(L0);
     const int64_t n = L0.n();
     const int npre = h->prm.npre;
     const bool multi = h->lv.size() > 1;
     const Geom &g = h->geom;
+    const TV *f0 = f64 ? (const TV *)h->r : (const TV *)h->rv;
+    TV *z0 = f64 ? (TV *)h->z : (TV *)h->zv;
+    TV *rv = f64 ? nullptr : (TV *)h->rv;
     // z = V(r), partial r.z
-    AMG_TRY(record_vcycle(h, h->r, h->z, h->partials, s));
+    AMG_TRY((record_vcycle<VT, TV>(h, f0, z0, h->partials, s)));
     cg_beta_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, rz_parts(h)); ::amg::count_launch(1);
-    cg_direction_kernel<<<vgrid(h, n), 256, 0, s>>>(h->z, h->p, h->st, n); ::amg::count_launch(1);
+    cg_direction_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(z0, h->p, h->st, n); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     int grid = 0;
-    {  // q = A p, partial p.q
+    {  // q = A p, partial p.q (FP64)
         SellArgs<double> a{};
         a.x = h->p;
         a.y = h->q;
@@ -384,9 +462,9 @@ static int record_cg_iteration(amg_handle h, cudaStream_t s, cudaGraphConditiona
         AMG_TRY((launch_sell<double, double>(L0.sA, SPMV_PLAIN, DOT_XY, a, g, s, &grid)));
     }
     cg_alpha_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, grid); ::amg::count_launch(1);
-    cg_update_kernel<<<vgrid(h, n), 256, 0, s>>>(h->uu, h->r, h->p, h->q, L0.M,
-                                                 multi ? L0.u : nullptr, h->st, n, npre > 0,
-                                                 h->partials); ::amg::count_launch(1);
+    cg_update_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(h->uu, h->r, h->p, h->q, V0.M,
+                                                     multi ? V0.u : nullptr, rv, h->st, n,
+                                                     npre > 0, h->partials); ::amg::count_launch(1);
     cg_resnorm_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, vgrid(h, n)); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     {  // true residual, only when the recurrence residual reached tol
@@ -399,8 +477,27 @@ static int record_cg_iteration(amg_handle h, cudaStream_t s, cudaGraphConditiona
         AMG_TRY((launch_sell<double, double>(L0.sA, SPMV_RESID, DOT_YY, a, g, s, &grid)));
     }
     cg_decide_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, grid, cond, use_cond); ::amg::count_launch(1);
-    cg_replace_kernel<<<vgrid(h, n), 256, 0, s>>>(h->r, h->rt, L0.M, multi ? L0.u : nullptr,
-                                                  h->st, n, npre > 0); ::amg::count_launch(1);
+    cg_replace_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(h->r, h->rt, V0.M, multi ? V0.u : nullptr,
+                                                      rv, h->st, n, npre > 0); ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    return AMG_OK;
+}
+
+static int record_cg_iteration(amg_handle h, cudaStream_t s, cudaGraphConditionalHandle cond,
+                               int use_cond)
+{
+    switch (h->prm.precision) {
+    case AMG_PREC_FP32: return record_cg_iteration_t<float, float>(h, s, cond, use_cond);
+    case AMG_PREC_BF16: return record_cg_iteration_t<__nv_bfloat16, float>(h, s, cond, use_cond);
+    default: return record_cg_iteration_t<double, double>(h, s, cond, use_cond);
+    }
+}
+
+template <class TV>
+static int launch_vec_dot(amg_handle h, const TV *x, const TV *y, int64_t n, double *part,
+                          cudaStream_t s)
+{
+    vec_dot_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(x, y, n, part); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     return AMG_OK;
 }
@@ -641,22 +738,56 @@ static int setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
     Cc.coarsest = true;
     AMG_TRY(coarse_inverse(Cc.A, h->mem, tmp, s, &h->Ainv));
     h->nc = Cc.n();
-    for (size_t l = 0; l < h->lv.size(); ++l) {  // V-cycle operators in SELL-32
+    // V-cycle operators in the sliced layout, in the V-cycle's precision; the
+    // fine A is also kept in FP64 for the CG products.
+    const int prec = prm.precision;
+    for (size_t l = 0; l < h->lv.size(); ++l) {
         Level &L = h->lv[l];
-        if (!L.coarsest || l == 0) AMG_TRY(bsr_to_sell(L.A, h->mem, s, &L.sA, &L.pad_A));
-        if (!L.coarsest) {
-            AMG_TRY(bsr_to_sell(L.P, h->mem, s, &L.sP, &L.pad_P));
-            AMG_TRY(bsr_to_sell(L.R, h->mem, s, &L.sR, &L.pad_R));
+        const bool vc = !L.coarsest;
+        if (l == 0 || (vc && prec == AMG_PREC_FP64))
+            AMG_TRY(bsr_to_sell<double>(L.A, h->mem, s, &L.sA, &L.pad_A));
+        if (vc && prec == AMG_PREC_FP64) {
+            AMG_TRY(bsr_to_sell<double>(L.P, h->mem, s, &L.sP, &L.pad_P));
+            AMG_TRY(bsr_to_sell<double>(L.R, h->mem, s, &L.sR, &L.pad_R));
+        }
+        if (vc && prec == AMG_PREC_FP32) {
+            AMG_TRY(bsr_to_sell<float>(L.A, h->mem, s, &L.fA, &L.pad_A));
+            AMG_TRY(bsr_to_sell<float>(L.P, h->mem, s, &L.fP, &L.pad_P));
+            AMG_TRY(bsr_to_sell<float>(L.R, h->mem, s, &L.fR, &L.pad_R));
+        }
+        if (vc && prec == AMG_PREC_BF16) {
+            AMG_TRY(bsr_to_sell<__nv_bfloat16>(L.A, h->mem, s, &L.bA, &L.pad_A));
+            AMG_TRY(bsr_to_sell<__nv_bfloat16>(L.P, h->mem, s, &L.bP, &L.pad_P));
+            AMG_TRY(bsr_to_sell<__nv_bfloat16>(L.R, h->mem, s, &L.bR, &L.pad_R));
         }
     }
     for (size_t l = 0; l < h->lv.size(); ++l) {
         Level &L = h->lv[l];
         const size_t n = (size_t)std::max(L.n(), 1);
-        if (l > 0) AMG_TRY(h->mem.alloc_n(&L.f, n));
-        AMG_TRY(h->mem.alloc_n(&L.u, n));
-        AMG_TRY(h->mem.alloc_n(&L.e, n));
-        AMG_TRY(h->mem.alloc_n(&L.z, n));
-        AMG_TRY(h->mem.alloc_n(&L.t, n));
+        if (prec == AMG_PREC_FP64) {
+            if (l > 0) AMG_TRY(h->mem.alloc_n(&L.f, n));
+            AMG_TRY(h->mem.alloc_n(&L.u, n));
+            AMG_TRY(h->mem.alloc_n(&L.e, n));
+            AMG_TRY(h->mem.alloc_n(&L.z, n));
+            AMG_TRY(h->mem.alloc_n(&L.t, n));
+        } else {
+            if (l > 0) AMG_TRY(h->mem.alloc_n(&L.vf, n));
+            AMG_TRY(h->mem.alloc_n(&L.vu, n));
+            AMG_TRY(h->mem.alloc_n(&L.ve, n));
+            AMG_TRY(h->mem.alloc_n(&L.vz, n));
+            AMG_TRY(h->mem.alloc_n(&L.vt, n));
+            if (L.M) {
+                AMG_TRY(h->mem.alloc_n(&L.Mf, n));
+                narrow_kernel<<<vgrid(h, L.n()), 256, 0, s>>>(L.M, L.Mf, L.n());
+                count_launch(1);
+                AMG_TRY_CUDA(cudaGetLastError());
+            }
+        }
+    }
+    if (prec != AMG_PREC_FP64) {
+        const size_t n0 = (size_t)std::max(h->lv[0].n(), 1);
+        AMG_TRY(h->mem.alloc_n(&h->rv, n0));
+        AMG_TRY(h->mem.alloc_n(&h->zv, n0));
     }
     const size_t n0 = (size_t)std::max(h->lv[0].n(), 1);
     AMG_TRY(h->mem.alloc_n(&h->ff, n0));
@@ -696,7 +827,8 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
     amg_params_default(&p);
     if (prm) p = *prm;
     if (p.npre < 0 || p.npost < 0 || p.max_levels < 1 || p.coarse_enough < 0 ||
-        !(p.eps_strong >= 0.0) || p.precision != AMG_PREC_FP64 || p.loop_mode < 0 ||
+        !(p.eps_strong >= 0.0) || p.precision < AMG_PREC_FP64 || p.precision > AMG_PREC_BF16 ||
+        p.loop_mode < 0 ||
         p.loop_mode > 1) {
         set_error("bad parameters");
         return AMG_ERR_ARG;
@@ -729,13 +861,30 @@ int amg_apply_vcycle(amg_handle h, const double *r, double *z, void *stream)
         return AMG_ERR_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const Level &L0 = h->lv[0];
+    Level &L0 = h->lv[0];
     const int64_t n = L0.n();
-    if (h->lv.size() > 1) {
-        scale_kernel<<<vgrid(h, n), 256, 0, s>>>(L0.M, r, L0.u, n, h->prm.npre == 0); ::amg::count_launch(1);
-        AMG_TRY_CUDA(cudaGetLastError());
+    const bool multi = h->lv.size() > 1;
+    const int zero = h->prm.npre == 0;
+    if (h->prm.precision == AMG_PREC_FP64) {
+        if (multi) {
+            scale_kernel<double><<<vgrid(h, n), 256, 0, s>>>(L0.M, r, L0.u, nullptr, n, zero);
+            count_launch(1);
+            AMG_TRY_CUDA(cudaGetLastError());
+        }
+        return record_vcycle<double, double>(h, r, z, nullptr, s);
     }
-    return record_vcycle(h, r, z, nullptr, s);
+    scale_kernel<float><<<vgrid(h, n), 256, 0, s>>>(L0.Mf, r, multi ? L0.vu : nullptr, h->rv, n,
+                                                    zero);
+    count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    if (h->prm.precision == AMG_PREC_FP32)
+        AMG_TRY((record_vcycle<float, float>(h, h->rv, h->zv, nullptr, s)));
+    else
+        AMG_TRY((record_vcycle<__nv_bfloat16, float>(h, h->rv, h->zv, nullptr, s)));
+    widen_kernel<float><<<vgrid(h, n), 256, 0, s>>>(h->zv, z, n);
+    count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    return AMG_OK;
 }
 
 int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxiter,
@@ -756,7 +905,7 @@ int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxi
     const bool multi = h->lv.size() > 1;
     AMG_TRY_CUDA(cudaMemcpyAsync(h->ff, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     AMG_TRY_CUDA(cudaMemcpyAsync(h->uu, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    vec_dot_kernel<<<vgrid(h, n), 256, 0, s>>>(h->ff, h->ff, n, h->partials); ::amg::count_launch(1);
+    vec_dot_kernel<double><<<vgrid(h, n), 256, 0, s>>>(h->ff, h->ff, n, h->partials); ::amg::count_launch(1);
     AMG_TRY(launch_reduce_sum(h->partials, vgrid(h, n), h->scal, s));
     int grid = 0;
     {
@@ -769,8 +918,17 @@ int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxi
     }
     AMG_TRY(launch_reduce_sum(h->partials, grid, h->scal + 1, s));
     cg_start_kernel<<<1, 1, 0, s>>>(h->st, h->scal, tol, maxiter); ::amg::count_launch(1);
-    if (multi) {
-        scale_kernel<<<vgrid(h, n), 256, 0, s>>>(L0.M, h->r, L0.u, n, h->prm.npre == 0); ::amg::count_launch(1); }
+    if (h->prm.precision == AMG_PREC_FP64) {
+        if (multi) {
+            scale_kernel<double><<<vgrid(h, n), 256, 0, s>>>(L0.M, h->r, L0.u, nullptr, n,
+                                                             h->prm.npre == 0);
+            count_launch(1);
+        }
+    } else {
+        scale_kernel<float><<<vgrid(h, n), 256, 0, s>>>(L0.Mf, h->r, multi ? L0.vu : nullptr,
+                                                        h->rv, n, h->prm.npre == 0);
+        count_launch(1);
+    }
     AMG_TRY_CUDA(cudaGetLastError());
     AMG_TRY_CUDA(cudaMemcpyAsync(h->st_h, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
     AMG_TRY_CUDA(cudaStreamSynchronize(s));

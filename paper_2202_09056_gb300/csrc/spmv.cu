@@ -119,31 +119,29 @@ __global__ void __launch_bounds__(SPMV_THREADS) bsr_spmv_kernel(SpmvArgs<TV> a)
     }
 }
 
-template <int BR, int BC, class VT, class TV, int MODE>
-static int launch_dot(int dot, const SpmvArgs<TV> &a, int grid, cudaStream_t s)
+template <int BR, int BC, class VT, class TV, int DOT>
+static int csr_go(const SpmvArgs<TV> &a, int grid, cudaStream_t s)
 {
-    switch (dot) {
-    case DOT_NONE: bsr_spmv_kernel<BR, BC, VT, TV, MODE, DOT_NONE><<<grid, SPMV_THREADS, 0, s>>>(a); ::amg::count_launch(1); break;
-    case DOT_XY: bsr_spmv_kernel<BR, BC, VT, TV, MODE, DOT_XY><<<grid, SPMV_THREADS, 0, s>>>(a); ::amg::count_launch(1); break;
-    case DOT_FY: bsr_spmv_kernel<BR, BC, VT, TV, MODE, DOT_FY><<<grid, SPMV_THREADS, 0, s>>>(a); ::amg::count_launch(1); break;
-    case DOT_YY: bsr_spmv_kernel<BR, BC, VT, TV, MODE, DOT_YY><<<grid, SPMV_THREADS, 0, s>>>(a); ::amg::count_launch(1); break;
-    default: set_error("bad dot mode %d", dot); return AMG_ERR_ARG;
-    }
+    bsr_spmv_kernel<BR, BC, VT, TV, SPMV_PLAIN, DOT><<<grid, SPMV_THREADS, 0, s>>>(a);
+    ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     return AMG_OK;
 }
 
+// The CSR kernels serve the stateless primitives: y = A x, optionally with
+// the fused x . y of a square matrix.
 template <int BR, int BC, class VT, class TV>
 static int launch_mode(int mode, int dot, const SpmvArgs<TV> &a, int grid, cudaStream_t s)
 {
-    switch (mode) {
-    case SPMV_PLAIN: return launch_dot<BR, BC, VT, TV, SPMV_PLAIN>(dot, a, grid, s);
-    case SPMV_RESID: return launch_dot<BR, BC, VT, TV, SPMV_RESID>(dot, a, grid, s);
-    case SPMV_SMOOTH: return launch_dot<BR, BC, VT, TV, SPMV_SMOOTH>(dot, a, grid, s);
-    case SPMV_AXPY: return launch_dot<BR, BC, VT, TV, SPMV_AXPY>(dot, a, grid, s);
-    case SPMV_RESTRICT: return launch_dot<BR, BC, VT, TV, SPMV_RESTRICT>(dot, a, grid, s);
-    default: set_error("bad spmv mode %d", mode); return AMG_ERR_ARG;
+    if (mode != SPMV_PLAIN) {
+        set_error("the CSR kernel only computes y = A x");
+        return AMG_ERR_ARG;
     }
+    if (dot == DOT_NONE) return csr_go<BR, BC, VT, TV, DOT_NONE>(a, grid, s);
+    if constexpr (BR == BC)
+        if (dot == DOT_XY) return csr_go<BR, BC, VT, TV, DOT_XY>(a, grid, s);
+    set_error("unsupported dot mode %d", dot);
+    return AMG_ERR_ARG;
 }
 
 int spmv_grid(int nbr, const Geom &g)
@@ -175,10 +173,7 @@ int launch_spmv(int br, int bc, int mode, int dot, const SpmvArgs<TV> &a, const 
 
 template int launch_spmv<double, double>(int, int, int, int, const SpmvArgs<double> &,
                                          const Geom &, cudaStream_t, int *);
-template int launch_spmv<float, float>(int, int, int, int, const SpmvArgs<float> &,
-                                       const Geom &, cudaStream_t, int *);
-template int launch_spmv<__nv_bfloat16, float>(int, int, int, int, const SpmvArgs<float> &,
-                                               const Geom &, cudaStream_t, int *);
+
 
 // ---------------------------------------------------------------- reductions
 constexpr int RED_THREADS = 256;
