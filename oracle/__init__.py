@@ -63,7 +63,7 @@ def _load():
         "orc_strength": ([P, i, d], P),
         "orc_aggregate": ([P, P], i64),
         "orc_tentative": ([i64, i, P, i64, P, P], P),
-        "orc_filter": ([P, i, P, P, P], P),
+        "orc_jacobi_rho": ([P, P, P], None),
         "orc_spgemm": ([P, P], P),
         "orc_transpose": ([P], P),
         "orc_smooth_prolongation": ([P, P, d, P], P),
@@ -206,16 +206,13 @@ def tentative(nnodes: int, b: int, agg: np.ndarray, nagg: int, B: np.ndarray):
     return CSR._from_handle(h), Bc
 
 
-def filter_matrix(A: CSR, b: int, eps: float):
-    """(A_F, d, rho) for the strength graph with threshold eps."""
-    lib = _load()
+def jacobi_rho(A: CSR):
+    """(d, rho): diagonal of A and the Gershgorin bound of rho(D^-1 A)."""
     o = _Owned(A)
-    g = lib.orc_strength(o.h, b, eps)
     d = np.empty(A.shape[0])
     rho = np.zeros(1)
-    h = lib.orc_filter(o.h, b, g, _p(d), _p(rho))
-    lib.orc_graph_free(g)
-    return CSR._from_handle(h), d, float(rho[0])
+    _load().orc_jacobi_rho(o.h, _p(d), _p(rho))
+    return d, float(rho[0])
 
 
 def spgemm(A: CSR, B: CSR) -> CSR:
@@ -228,8 +225,8 @@ def transpose(A: CSR) -> CSR:
     return CSR._from_handle(_load().orc_transpose(o.h))
 
 
-def smooth_prolongation(AF: CSR, d: np.ndarray, omega: float, Pt: CSR) -> CSR:
-    oa, op = _Owned(AF), _Owned(Pt)
+def smooth_prolongation(A: CSR, d: np.ndarray, omega: float, Pt: CSR) -> CSR:
+    oa, op = _Owned(A), _Owned(Pt)
     d = np.ascontiguousarray(d, dtype=np.float64)
     return CSR._from_handle(_load().orc_smooth_prolongation(oa.h, _p(d), omega, op.h))
 

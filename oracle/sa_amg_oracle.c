@@ -31,11 +31,14 @@
  *               re-orthogonalisation pass; a column whose norm after
  *               orthogonalisation is <= 1e-10 x its norm before is dropped
  *               (zero Q column, zero R row).  B_{i+1} = R.
- *   filter:     weak blocks are removed and added to the scalar diagonal,
- *               d_i = a_ii + sum_{weak j} a_ij (row sums preserved);
- *               rho = max_i sum_j |a^F_ij| / |d_i| (Gershgorin),
- *               omega = (4/3) / rho;
- *               P = P_tent - omega D^{-1} A_F P_tent with the symbolic pattern.
+ *   P smoother: damped Jacobi on the unfiltered matrix, P = P_tent -
+ *               omega D^{-1} A P_tent with D = diag(A), rho = max_i
+ *               sum_j |a_ij| / |a_ii| (Gershgorin), omega = (4/3) / rho, and
+ *               the symbolic pattern.  The strength graph drives only the
+ *               aggregation: lumping weak entries into the diagonal (the
+ *               classical filtered matrix) leaves near-zero and negative
+ *               diagonals on elasticity matrices, which collapses omega.  With
+ *               A B = 0, P B_{i+1} = B holds for any threshold.
  *   coarsening stops when n <= coarse_enough, at max_levels levels, or when
  *               the aggregates are not fewer than 0.9 x the nodes.
  *   smoother:   damped SPAI0, M = w_s diag(a_ii / sum_j a_ij^2) (0 for an
@@ -401,63 +404,26 @@ orc_csr *orc_tentative(int64_t nnodes, int b, const int32_t *agg, int64_t nagg, 
     return P;
 }
 
-/* Filtered matrix A_F (strong blocks and the diagonal block kept, weak
- * blocks added to the scalar diagonal), its diagonal d, and the Gershgorin
- * estimate rho = max_i sum_j |a^F_ij| / |d_i| over rows with d_i != 0. */
-orc_csr *orc_filter(const orc_csr *A, int b, const orc_graph *G, double *d, double *rho_out)
+/* Data of the damped-Jacobi prolongation smoother (Alg. 1, "construct P_i
+ * from A_i"): the scalar diagonal d = diag(A) and the Gershgorin estimate
+ * rho = max_i sum_j |a_ij| / |a_ii| of rho(D^{-1} A) over rows with
+ * a_ii != 0 (entries summed in ascending column order). */
+void orc_jacobi_rho(const orc_csr *A, double *d, double *rho_out)
 {
-    int64_t n = A->nrows, nn = G->nnodes;
-    /* strong-or-diagonal flag per node column, looked up through a row map */
-    int64_t *mark = (int64_t *)malloc(sizeof(int64_t) * (size_t)nn);
-    uint8_t *keep = (uint8_t *)malloc((size_t)nn);
-    for (int64_t J = 0; J < nn; ++J) mark[J] = -1;
-    int64_t nnz = 0;
-    for (int64_t I = 0; I < nn; ++I) {
-        for (int64_t p = G->ptr[I]; p < G->ptr[I + 1]; ++p) {
-            mark[G->col[p]] = I;
-            keep[G->col[p]] = (G->col[p] == I) || G->strong[p];
-        }
-        for (int r = 0; r < b; ++r)
-            for (int64_t p = A->ptr[I * b + r]; p < A->ptr[I * b + r + 1]; ++p)
-                if (keep[A->col[p] / b]) ++nnz;
-    }
-    orc_csr *F = csr_new(n, A->ncols, nnz);
-    for (int64_t J = 0; J < nn; ++J) mark[J] = -1;
-    int64_t q = 0;
     double rho = 0.0;
-    for (int64_t I = 0; I < nn; ++I) {
-        for (int64_t p = G->ptr[I]; p < G->ptr[I + 1]; ++p) {
-            mark[G->col[p]] = I;
-            keep[G->col[p]] = (G->col[p] == I) || G->strong[p];
+    for (int64_t i = 0; i < A->nrows; ++i) {
+        double dia = 0.0, s = 0.0;
+        for (int64_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p) {
+            if (A->col[p] == i) dia = A->val[p];
+            s += fabs(A->val[p]);
         }
-        for (int r = 0; r < b; ++r) {
-            int64_t i = I * b + r;
-            double dia = 0.0;
-            for (int64_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p)
-                if (A->col[p] == i) dia = A->val[p];
-            for (int64_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p)
-                if (!keep[A->col[p] / b]) dia = dia + A->val[p];
-            d[i] = dia;
-            double s = 0.0;
-            for (int64_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p) {
-                if (!keep[A->col[p] / b]) continue;
-                double v = (A->col[p] == i) ? dia : A->val[p];
-                F->col[q] = A->col[p];
-                F->val[q] = v;
-                s += fabs(v);
-                ++q;
-            }
-            F->ptr[i + 1] = q;
-            if (dia != 0.0) {
-                double g = s / fabs(dia);
-                if (g > rho) rho = g;
-            }
+        d[i] = dia;
+        if (dia != 0.0) {
+            double g = s / fabs(dia);
+            if (g > rho) rho = g;
         }
     }
-    free(mark);
-    free(keep);
     *rho_out = rho;
-    return F;
 }
 
 /* C = A B (Gustavson), symbolic pattern: every structurally present product
@@ -525,12 +491,12 @@ orc_csr *orc_transpose(const orc_csr *A)
     return T;
 }
 
-/* Smoothed prolongation P = P_tent - omega D^{-1} (A_F P_tent); a row with
+/* Smoothed prolongation P = P_tent - omega D^{-1} (A P_tent); a row with
  * d_i = 0 keeps its tentative values.  Pattern = union of both patterns. */
-orc_csr *orc_smooth_prolongation(const orc_csr *AF, const double *d, double omega,
+orc_csr *orc_smooth_prolongation(const orc_csr *A, const double *d, double omega,
                                  const orc_csr *Pt)
 {
-    orc_csr *AP = orc_spgemm(AF, Pt);
+    orc_csr *AP = orc_spgemm(A, Pt);
     int64_t n = AP->nrows;
     int64_t *ptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     for (int64_t i = 0; i < n; ++i) { /* merge count */
@@ -733,10 +699,9 @@ orc_hier *orc_setup(const orc_csr *A0, int bs, const double *B0, const orc_param
         N->B = (double *)malloc(sizeof(double) * (size_t)(C->nagg * 36));
         orc_csr *Pt = orc_tentative(nn, C->b, C->agg, C->nagg, C->B, N->B);
         C->d = (double *)malloc(sizeof(double) * (size_t)n);
-        orc_csr *AF = orc_filter(C->A, C->b, C->G, C->d, &C->rho);
+        orc_jacobi_rho(C->A, C->d, &C->rho);
         C->omega = (C->rho > 0.0) ? prm->relax * (4.0 / 3.0) / C->rho : 0.0;
-        C->P = orc_smooth_prolongation(AF, C->d, C->omega, Pt);
-        orc_csr_free(AF);
+        C->P = orc_smooth_prolongation(C->A, C->d, C->omega, Pt);
         orc_csr_free(Pt);
         C->R = orc_transpose(C->P);
         orc_csr *AP = orc_spgemm(C->A, C->P);

@@ -63,7 +63,8 @@ using BsrD = Bsr<double>;
 // ---------------------------------------------------------------- launch geometry
 struct Geom {
     int num_sms = 0;
-    int max_ctas = 0;       // grid size cap for grid-stride kernels (= partials capacity)
+    int max_ctas = 0;       // grid cap of the 256-thread grid-stride kernels
+    int max_partials = 0;   // largest grid of any kernel with a fused dot (per-CTA partials)
 };
 int query_geom(Geom *g);
 

@@ -126,7 +126,7 @@ int sell_grid(int nslices, const Geom &g)
 {
     const int per_cta = SELL_THREADS / 32;
     int grid = (nslices + per_cta - 1) / per_cta;
-    const int cap = g.num_sms * 16;
+    const int cap = g.num_sms * 16;  // = Geom::max_partials
     if (grid > cap) grid = cap;
     return std::max(grid, 1);
 }
@@ -183,6 +183,10 @@ int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom
     a.perm = A.perm;
     const int grid = sell_grid(A.nslices, g);
     if (grid_out) *grid_out = grid;
+    if (dot != DOT_NONE && grid > g.max_partials) {
+        set_error("fused dot needs %d partial sums, the buffer holds %d", grid, g.max_partials);
+        return AMG_ERR_LIMIT;
+    }
     if (A.nrows == 0) {
         if (dot != DOT_NONE) AMG_TRY_CUDA(cudaMemsetAsync(a.partials, 0, sizeof(double), s));
         return AMG_OK;

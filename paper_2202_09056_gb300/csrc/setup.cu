@@ -1,9 +1,9 @@
 // Setup kernels of Alg. 1 (Sec. 2) in block arithmetic: strength of
 // connection on block norms, tentative prolongation from the rigid-body modes
 // (per-aggregate modified Gram-Schmidt QR, the step Sec. 2 says needs scalar
-// arithmetic, done here inside block-shaped kernels), filtering and the
-// Gershgorin estimate for the prolongation smoother, the smoothed
-// prolongation P = (I - omega D^-1 A_F) P_tent, R = P^T, the block Galerkin
+// arithmetic, done here inside block-shaped kernels), the Gershgorin
+// estimate for the damped-Jacobi prolongation smoother, the smoothed
+// prolongation P = (I - omega D^-1 A) P_tent, R = P^T, the block Galerkin
 // product A_c = R (A P) (Sec. 3: the expensive step kept in block form),
 // the SPAI0 smoother, and the dense coarsest-level factorisation.
 //
@@ -240,35 +240,27 @@ __global__ void tentative_kernel(int nagg, int b, const int *__restrict__ agg_pt
     }
 }
 
-// ---------------------------------------------------------------- filter, rho
-// d_i = a_ii + sum of the weak blocks' entries of scalar row i (ascending
-// columns); g_i = sum_{kept j} |a^F_ij| / |d_i|; rho = max g_i (atomic max on
-// the bits of a non-negative double, order independent).
-__global__ void filter_kernel(const int *__restrict__ rp, const int *__restrict__ col,
-                              const double *__restrict__ val, int nbr, int b,
-                              const uint8_t *__restrict__ strong, double *__restrict__ d,
-                              unsigned long long *__restrict__ rho_bits)
+// ---------------------------------------------------------------- Jacobi diagonal, rho
+// d_i = a_ii; g_i = sum_j |a_ij| / |a_ii| over scalar row i (blocks ascending,
+// then columns); rho = max g_i (atomic max on the bits of a non-negative
+// double, order independent).  This is the damped-Jacobi prolongation
+// smoother's data on the unfiltered matrix.
+__global__ void jacobi_rho_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                                  const double *__restrict__ val, int nbr, int b,
+                                  double *__restrict__ d, unsigned long long *__restrict__ rho_bits)
 {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nbr) return;
     const int bb = b * b;
-    int pd = -1;
-    for (int p = rp[I]; p < rp[I + 1]; ++p)
-        if (col[p] == I) pd = p;
     for (int r = 0; r < b; ++r) {
-        double dia = (pd >= 0) ? val[(int64_t)pd * bb + r * b + r] : 0.0;
+        double dia = 0.0, s = 0.0;
         for (int p = rp[I]; p < rp[I + 1]; ++p)
-            if (col[p] != I && !strong[p])
-                for (int c = 0; c < b; ++c) dia = __dadd_rn(dia, val[(int64_t)p * bb + r * b + c]);
-        d[(int64_t)I * b + r] = dia;
-        double s = 0.0;
-        for (int p = rp[I]; p < rp[I + 1]; ++p) {
-            if (col[p] != I && !strong[p]) continue;
             for (int c = 0; c < b; ++c) {
-                const double v = (col[p] == I && c == r) ? dia : val[(int64_t)p * bb + r * b + c];
+                const double v = val[(int64_t)p * bb + r * b + c];
+                if (col[p] == I && c == r) dia = v;
                 s = __dadd_rn(s, fabs(v));
             }
-        }
+        d[(int64_t)I * b + r] = dia;
         if (dia != 0.0) {
             const double g = __ddiv_rn(s, fabs(dia));
             atomicMax(rho_bits, (unsigned long long)__double_as_longlong(g));
@@ -297,9 +289,7 @@ template <int CAP> struct SortedSet {
     }
 };
 
-constexpr int CAP_P = 128;
-constexpr int CAP_AP = 256;
-constexpr int CAP_AC = 512;
+constexpr int SYM_CAP = 128;  // per-thread sorted set of the first symbolic pass
 
 __device__ __forceinline__ int find_sorted(const int *a, int lo, int hi, int x)
 {
@@ -311,30 +301,153 @@ __device__ __forceinline__ int find_sorted(const int *a, int lo, int hi, int x)
     return lo;
 }
 
-// P pattern, row I: the aggregates of I and of its strong neighbours (sorted,
-// unique, isolated nodes skipped).  write = false counts, true fills.
+// Symbolic C = X Y, first pass: one thread per row keeps the row's distinct
+// columns in a sorted local set.  Count mode writes the row length, or -1
+// and appends the row to `overflow` when the row has more than SYM_CAP
+// distinct columns; write mode fills the rows that fit.
 template <bool WRITE>
-__global__ void p_pattern_kernel(const int *__restrict__ rp, const int *__restrict__ col,
-                                 const uint8_t *__restrict__ strong, const int *__restrict__ agg,
-                                 int nbr, int *__restrict__ cnt, const int *__restrict__ prp,
-                                 int *__restrict__ pcol, int *__restrict__ err)
+__global__ void sym_small_kernel(const int *__restrict__ xrp, const int *__restrict__ xcol,
+                                 const int *__restrict__ yrp, const int *__restrict__ ycol,
+                                 int nrows, int *__restrict__ cnt, const int *__restrict__ crp,
+                                 int *__restrict__ ccol, int *__restrict__ overflow,
+                                 int *__restrict__ noverflow)
 {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nbr) return;
-    SortedSet<CAP_P> S;
-    for (int p = rp[I]; p < rp[I + 1]; ++p) {
-        const int J = col[p];
-        if ((J == I || strong[p]) && agg[J] >= 0)
-            if (!S.insert(agg[J])) {
-                atomicExch(err, 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows) return;
+    if (WRITE && cnt[i] < 0) return;
+    SortedSet<SYM_CAP> S;
+    for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
+        const int k = xcol[p];
+        for (int q = yrp[k]; q < yrp[k + 1]; ++q)
+            if (!S.insert(ycol[q])) {
+                if (!WRITE) {
+                    cnt[i] = -1;
+                    overflow[atomicAdd(noverflow, 1)] = i;
+                }
                 return;
             }
     }
-    if (!WRITE) {
-        cnt[I] = S.n;
-    } else {
-        for (int t = 0; t < S.n; ++t) pcol[prp[I] + t] = S.v[t];
+    if (!WRITE) cnt[i] = S.n;
+    else
+        for (int t = 0; t < S.n; ++t) ccol[crp[i] + t] = S.v[t];
+}
+
+// Symbolic C = X Y, second pass for the long rows: one CTA per row marks the
+// row's columns in a shared-memory bitmap over the column range; counting is
+// a popcount, and the fill walks the bitmap in order, so the columns come
+// out sorted without a sort.
+constexpr int SYM_T = 256;
+template <bool WRITE>
+__global__ void __launch_bounds__(SYM_T) sym_bitmap_kernel(
+    const int *__restrict__ xrp, const int *__restrict__ xcol, const int *__restrict__ yrp,
+    const int *__restrict__ ycol, int ncols, const int *__restrict__ rows, int nlist,
+    int *__restrict__ cnt, const int *__restrict__ crp, int *__restrict__ ccol)
+{
+    extern __shared__ unsigned bits[];
+    __shared__ int scan[SYM_T];
+    const int nwords = (ncols + 31) >> 5;
+    const int chunk = (nwords + SYM_T - 1) / SYM_T;
+    for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
+        const int i = rows[li];
+        for (int w = threadIdx.x; w < nwords; w += SYM_T) bits[w] = 0u;
+        __syncthreads();
+        for (int p = xrp[i] + threadIdx.x; p < xrp[i + 1]; p += SYM_T) {
+            const int k = xcol[p];
+            for (int q = yrp[k]; q < yrp[k + 1]; ++q) {
+                const int c = ycol[q];
+                atomicOr(&bits[c >> 5], 1u << (c & 31));
+            }
+        }
+        __syncthreads();
+        const int w0 = threadIdx.x * chunk, w1 = min(w0 + chunk, nwords);
+        int mine = 0;
+        for (int w = w0; w < w1; ++w) mine += __popc(bits[w]);
+        scan[threadIdx.x] = mine;
+        __syncthreads();
+        for (int off = 1; off < SYM_T; off <<= 1) {  // inclusive scan of the chunk counts
+            const int t = (threadIdx.x >= (unsigned)off) ? scan[threadIdx.x - off] : 0;
+            __syncthreads();
+            scan[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (!WRITE) {
+            if (threadIdx.x == SYM_T - 1) cnt[i] = scan[SYM_T - 1];
+        } else {
+            int o = crp[i] + scan[threadIdx.x] - mine;
+            for (int w = w0; w < w1; ++w) {
+                unsigned m = bits[w];
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    ccol[o++] = (w << 5) + b;
+                    m &= m - 1;
+                }
+            }
+        }
+        __syncthreads();
     }
+}
+
+// Row pattern of C = X Y (sorted columns, symbolic: every structurally
+// present product creates an entry).  Allocates C's row pointers and columns
+// in `keep`.
+static int spgemm_symbolic(const int *xrp, const int *xcol, int nrows, const int *yrp,
+                           const int *ycol, int ncols, DevArena &keep, DevArena &tmp,
+                           cudaStream_t s, int **crp_out, int **ccol_out, int *nnz_out)
+{
+    int *cnt = nullptr, *ovf = nullptr, *novf = nullptr, *crp = nullptr, *ccol = nullptr;
+    AMG_TRY(tmp.alloc_n(&cnt, (size_t)nrows + 1));
+    AMG_TRY(tmp.alloc_n(&ovf, (size_t)std::max(nrows, 1)));
+    AMG_TRY(tmp.alloc_n(&novf, 1));
+    AMG_TRY(keep.alloc_n(&crp, (size_t)nrows + 1));
+    AMG_TRY_CUDA(cudaMemsetAsync(novf, 0, sizeof(int), s));
+    if (nrows > 0) {
+        sym_small_kernel<false><<<nblk(nrows), T1D, 0, s>>>(xrp, xcol, yrp, ycol, nrows, cnt,
+                                                            nullptr, nullptr, ovf, novf);
+        ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
+    int nlong = 0;
+    AMG_TRY_CUDA(cudaMemcpyAsync(&nlong, novf, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    const size_t smem = sizeof(unsigned) * (size_t)((ncols + 31) / 32);
+    if (nlong > 0) {
+        if (smem > 200 * 1024) {
+            set_error("sparse product with %d block columns exceeds the bitmap limit", ncols);
+            return AMG_ERR_LIMIT;
+        }
+        if (smem > 48 * 1024) {
+            AMG_TRY_CUDA(cudaFuncSetAttribute(sym_bitmap_kernel<false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            AMG_TRY_CUDA(cudaFuncSetAttribute(sym_bitmap_kernel<true>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        }
+        sym_bitmap_kernel<false><<<std::min(nlong, 4096), SYM_T, smem, s>>>(
+            xrp, xcol, yrp, ycol, ncols, ovf, nlong, cnt, nullptr, nullptr);
+        ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
+    int total = 0;
+    AMG_TRY(exclusive_scan_i32(cnt, crp, nrows, &total, tmp, s));
+    AMG_TRY(keep.alloc_n(&ccol, (size_t)std::max(total, 1)));
+    if (nrows > 0) {
+        sym_small_kernel<true><<<nblk(nrows), T1D, 0, s>>>(xrp, xcol, yrp, ycol, nrows, cnt, crp,
+                                                           ccol, nullptr, nullptr);
+        ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
+    if (nlong > 0) {
+        sym_bitmap_kernel<true><<<std::min(nlong, 4096), SYM_T, smem, s>>>(
+            xrp, xcol, yrp, ycol, ncols, ovf, nlong, cnt, crp, ccol);
+        ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
+    tmp.release(cnt);
+    tmp.release(ovf);
+    tmp.release(novf);
+    *crp_out = crp;
+    *ccol_out = ccol;
+    *nnz_out = total;
+    return AMG_OK;
 }
 
 __global__ void block_rows_kernel(const int *__restrict__ rp, int nbr, int *__restrict__ brow)
@@ -344,8 +457,8 @@ __global__ void block_rows_kernel(const int *__restrict__ rp, int nbr, int *__re
     for (int p = rp[I]; p < rp[I + 1]; ++p) brow[p] = I;
 }
 
-// P block (I, a) = [a == agg(I)] Pt_I - diag(omega / d) sum_{J strong or I,
-// agg(J) = a} A^F_IJ Pt_J, sums over J ascending then the inner index.
+// P block (I, a) = [a == agg(I)] Pt_I - diag(omega / d) sum_{J: agg(J) = a}
+// A_IJ Pt_J, sums over J ascending then the inner index.
 template <int B>
 __global__ void p_values_kernel(const int *__restrict__ rp, const int *__restrict__ col,
                                 const double *__restrict__ val, const uint8_t *__restrict__ strong,
@@ -364,14 +477,14 @@ __global__ void p_values_kernel(const int *__restrict__ rp, const int *__restric
         for (int q = 0; q < 6; ++q) acc[r][q] = 0.0;
     for (int p = rp[I]; p < rp[I + 1]; ++p) {
         const int J = col[p];
-        if (!((J == I || strong[p]) && agg[J] == a)) continue;
+        if (agg[J] != a) continue;
         const double *blk = val + (int64_t)p * B * B;
         const double *pt = ptent + (int64_t)J * B * 6;
 #pragma unroll
         for (int r = 0; r < B; ++r)
 #pragma unroll
             for (int c = 0; c < B; ++c) {
-                const double af = (J == I && r == c) ? d[(int64_t)I * B + r] : blk[r * B + c];
+                const double af = blk[r * B + c];
 #pragma unroll
                 for (int q = 0; q < 6; ++q) acc[r][q] += af * pt[c * 6 + q];
             }
@@ -480,31 +593,6 @@ static int transpose_bsr(const BsrD &P, const int *pbrow, DevArena &keep, DevAre
 }
 
 // ---------------------------------------------------------------- SpGEMM
-// Row pattern of C = X Y: the union of Y's row patterns over X's columns.
-template <int CAP, bool WRITE>
-__global__ void spgemm_pattern_kernel(const int *__restrict__ xrp, const int *__restrict__ xcol,
-                                      const int *__restrict__ yrp, const int *__restrict__ ycol,
-                                      int nrows, int *__restrict__ cnt, const int *__restrict__ crp,
-                                      int *__restrict__ ccol, int *__restrict__ err)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nrows) return;
-    SortedSet<CAP> S;
-    for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
-        const int k = xcol[p];
-        for (int q = yrp[k]; q < yrp[k + 1]; ++q)
-            if (!S.insert(ycol[q])) {
-                atomicExch(err, 1);
-                return;
-            }
-    }
-    if (!WRITE) {
-        cnt[i] = S.n;
-    } else {
-        for (int t = 0; t < S.n; ++t) ccol[crp[i] + t] = S.v[t];
-    }
-}
-
 // C block (i, j) = sum over X row i (ascending) of X_ik Y_kj; blocks XR x XC
 // and XC x YC, the inner sums over k ascending then the inner index.
 template <int XR, int XC, int YC>
@@ -544,7 +632,6 @@ __global__ void spgemm_values_kernel(const int *__restrict__ xrp, const int *__r
         for (int c = 0; c < YC; ++c) cval[q * XR * YC + r * YC + c] = acc[r][c];
 }
 
-template <int CAP>
 static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, cudaStream_t s,
                   BsrD *C)
 {
@@ -552,35 +639,16 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
     C->nbc = Y.nbc;
     C->br = X.br;
     C->bc = Y.bc;
-    int *cnt = nullptr, *err = nullptr;
-    AMG_TRY(tmp.alloc_n(&cnt, (size_t)X.nbr + 1));
-    AMG_TRY(tmp.alloc_n(&err, 1));
-    AMG_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    AMG_TRY(keep.alloc_n(&C->row_ptr, (size_t)X.nbr + 1));
-    if (X.nbr > 0) {
-        spgemm_pattern_kernel<CAP, false><<<nblk(X.nbr), T1D, 0, s>>>(
-            X.row_ptr, X.col, Y.row_ptr, Y.col, X.nbr, cnt, nullptr, nullptr, err);
-        ::amg::count_launch(1);
-    }
-    AMG_TRY_CUDA(cudaGetLastError());
     int total = 0;
-    AMG_TRY(exclusive_scan_i32(cnt, C->row_ptr, X.nbr, &total, tmp, s));
-    int herr = 0;
-    AMG_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    AMG_TRY_CUDA(cudaStreamSynchronize(s));
-    if (herr) {
-        set_error("sparse product row has more than %d distinct block columns", CAP);
-        return AMG_ERR_LIMIT;
-    }
+    AMG_TRY(spgemm_symbolic(X.row_ptr, X.col, X.nbr, Y.row_ptr, Y.col, Y.nbc, keep, tmp, s,
+                            &C->row_ptr, &C->col, &total));
     C->nnzb = total;
-    AMG_TRY(keep.alloc_n(&C->col, (size_t)std::max(total, 1)));
     AMG_TRY(keep.alloc_n(&C->val, (size_t)std::max(total, 1) * C->br * C->bc));
     int *cbrow = nullptr;
     AMG_TRY(tmp.alloc_n(&cbrow, (size_t)std::max(total, 1)));
     if (X.nbr > 0) {
-        spgemm_pattern_kernel<CAP, true><<<nblk(X.nbr), T1D, 0, s>>>(
-            X.row_ptr, X.col, Y.row_ptr, Y.col, X.nbr, nullptr, C->row_ptr, C->col, err); ::amg::count_launch(1);
-        block_rows_kernel<<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, X.nbr, cbrow); ::amg::count_launch(1);
+        block_rows_kernel<<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, X.nbr, cbrow);
+        ::amg::count_launch(1);
     }
     AMG_TRY_CUDA(cudaGetLastError());
     if (total > 0) {
@@ -601,8 +669,6 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
 #undef AMG_SPGEMM_VALS
         AMG_TRY_CUDA(cudaGetLastError());
     }
-    tmp.release(cnt);
-    tmp.release(err);
     tmp.release(cbrow);
     return AMG_OK;
 }
@@ -614,8 +680,8 @@ int galerkin(const BsrD &A, const BsrD &P, const BsrD &R, DevArena &keep, DevAre
     BsrD AP;
     DevArena apmem;
     apmem.stream = s;
-    int st = spgemm<CAP_AP>(A, P, apmem, tmp, s, &AP);
-    if (st >= 0) st = spgemm<CAP_AC>(R, AP, keep, tmp, s, Ac);
+    int st = spgemm(A, P, apmem, tmp, s, &AP);
+    if (st >= 0) st = spgemm(R, AP, keep, tmp, s, Ac);
     apmem.release_all();
     return st;
 }
@@ -661,7 +727,7 @@ int build_transfer(const BsrD &A, const double *B, const uint8_t *strong, const 
                                                                    ptent, out->Bc); ::amg::count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
     }
-    filter_kernel<<<nblk(nn), T1D, 0, s>>>(A.row_ptr, A.col, A.val, nn, b, strong, d, rho_bits); ::amg::count_launch(1);
+    jacobi_rho_kernel<<<nblk(nn), T1D, 0, s>>>(A.row_ptr, A.col, A.val, nn, b, d, rho_bits); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     unsigned long long rb = 0;
     AMG_TRY_CUDA(cudaMemcpyAsync(&rb, rho_bits, sizeof(rb), cudaMemcpyDeviceToHost, s));
@@ -671,36 +737,31 @@ int build_transfer(const BsrD &A, const double *B, const uint8_t *strong, const 
     out->rho = rho;
     out->omega = (rho > 0.0) ? relax * (4.0 / 3.0) / rho : 0.0;
 
-    // P pattern and values
+    // P pattern: the symbolic product of A's pattern with the tentative
+    // prolongation's (one column, agg(J), per aggregated node J)
     BsrD &P = out->P;
     P.nbr = nn;
     P.nbc = nagg;
     P.br = b;
     P.bc = 6;
-    int *cnt = nullptr, *err = nullptr;
-    AMG_TRY(tmp.alloc_n(&cnt, (size_t)nn + 1));
-    AMG_TRY(tmp.alloc_n(&err, 1));
-    AMG_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    AMG_TRY(keep.alloc_n(&P.row_ptr, (size_t)nn + 1));
-    p_pattern_kernel<false><<<nblk(nn), T1D, 0, s>>>(A.row_ptr, A.col, strong, out->agg, nn, cnt,
-                                                     nullptr, nullptr, err); ::amg::count_launch(1);
-    AMG_TRY_CUDA(cudaGetLastError());
-    int nnzp = 0;
-    AMG_TRY(exclusive_scan_i32(cnt, P.row_ptr, nn, &nnzp, tmp, s));
-    int herr = 0;
-    AMG_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    AMG_TRY_CUDA(cudaStreamSynchronize(s));
-    if (herr) {
-        set_error("prolongation row has more than %d aggregates", CAP_P);
-        return AMG_ERR_LIMIT;
+    std::vector<int> trp(nn + 1, 0), tcl;
+    for (int J = 0; J < nn; ++J) {
+        trp[J + 1] = trp[J] + (agg_h[J] >= 0 ? 1 : 0);
+        if (agg_h[J] >= 0) tcl.push_back(agg_h[J]);
     }
+    tcl.resize(std::max<size_t>(tcl.size(), 1));
+    int *d_trp = nullptr, *d_tcl = nullptr;
+    AMG_TRY(tmp.alloc_n(&d_trp, (size_t)nn + 1));
+    AMG_TRY(tmp.alloc_n(&d_tcl, tcl.size()));
+    AMG_TRY_CUDA(cudaMemcpyAsync(d_trp, trp.data(), sizeof(int) * (nn + 1), cudaMemcpyHostToDevice, s));
+    AMG_TRY_CUDA(cudaMemcpyAsync(d_tcl, tcl.data(), sizeof(int) * tcl.size(), cudaMemcpyHostToDevice, s));
+    int nnzp = 0;
+    AMG_TRY(spgemm_symbolic(A.row_ptr, A.col, nn, d_trp, d_tcl, nagg, keep, tmp, s, &P.row_ptr,
+                            &P.col, &nnzp));  // synchronises: trp/tcl may go out of scope
     P.nnzb = nnzp;
     int *pbrow = nullptr;
-    AMG_TRY(keep.alloc_n(&P.col, (size_t)std::max(nnzp, 1)));
     AMG_TRY(keep.alloc_n(&P.val, (size_t)std::max(nnzp, 1) * b * 6));
     AMG_TRY(tmp.alloc_n(&pbrow, (size_t)std::max(nnzp, 1)));
-    p_pattern_kernel<true><<<nblk(nn), T1D, 0, s>>>(A.row_ptr, A.col, strong, out->agg, nn,
-                                                    nullptr, P.row_ptr, P.col, err); ::amg::count_launch(1);
     block_rows_kernel<<<nblk(nn), T1D, 0, s>>>(P.row_ptr, nn, pbrow); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     if (nnzp > 0) {
@@ -726,8 +787,8 @@ int build_transfer(const BsrD &A, const double *B, const uint8_t *strong, const 
     tmp.release(ptent);
     tmp.release(d);
     tmp.release(rho_bits);
-    tmp.release(cnt);
-    tmp.release(err);
+    tmp.release(d_trp);
+    tmp.release(d_tcl);
     tmp.release(pbrow);
     return AMG_OK;
 }

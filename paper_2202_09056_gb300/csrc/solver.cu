@@ -797,7 +797,8 @@ static int setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
     AMG_TRY(h->mem.alloc_n(&h->q, n0));
     AMG_TRY(h->mem.alloc_n(&h->z, n0));
     AMG_TRY(h->mem.alloc_n(&h->rt, n0));
-    AMG_TRY(h->mem.alloc_n(&h->partials, (size_t)h->geom.max_ctas + 1));
+    AMG_TRY(h->mem.alloc_n(&h->partials,
+                           (size_t)std::max(h->geom.max_ctas, h->geom.max_partials) + 1));
     AMG_TRY(h->mem.alloc_n(&h->scal, 8));
     AMG_TRY(h->mem.alloc_n(&h->st, 1));
     AMG_TRY_CUDA(cudaMallocHost((void **)&h->st_h, sizeof(CgState)));
