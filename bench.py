@@ -41,6 +41,8 @@ WORKLOADS = {
     "inclusions48": dict(n=48, desc="q1-hex-48^3-inclusions-20pct-E1000", tol=1e-8),
     "inclusions40": dict(n=40, desc="q1-hex-40^3-inclusions-20pct-E1000", tol=1e-8),
     "cube10": dict(n=10, desc="q1-hex-10^3-cube-body-load", tol=1e-8),
+    "batch64": dict(n=0, desc="64 q1-hex boxes 20^3-60^3, nu U[0.2,0.45], 1-16 body-load RHS each",
+                    tol=1e-8),
 }
 
 
@@ -195,6 +197,81 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args, amg, torch):
+    """64 independent boxes (seeded sizes 20^3-60^3, nu in [0.2, 0.45], 1-16
+    random unit body loads each): one batched solve of every right-hand side
+    against a loop of single FP64 solves of the same systems."""
+    import q1elasticity as q
+    dev = torch.device("cuda", 0)
+    specs = q.batch_specs(64)
+    mats, Bs, F, nrhs = [], [], [], []
+    for sp in specs:
+        p = q.make_problem(sp["n"], nu=sp["nu"], body=sp["body"])
+        mats.append((torch.from_numpy(p.row_ptr).to(dev), torch.from_numpy(p.col).to(dev),
+                     torch.from_numpy(p.val).to(dev)))
+        Bs.append(torch.from_numpy(p.B).to(dev))
+        F.append(torch.from_numpy(np.atleast_2d(p.f).copy()).to(dev))
+        nrhs.append(sp["nrhs"])
+    s = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    bat = amg.AMGBatch(mats, Bs, nrhs)
+    torch.cuda.synchronize()
+    setup_t = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        bat.solve(F)
+    times = []
+    launches0 = amg.kernel_launches()
+    with ClockSampler(_gpu_id(torch)) as clk:
+        for _ in range(args.steps):
+            e0, e1 = ev(), ev()
+            e0.record(s)
+            U, its, res, st = bat.solve(F)
+            e1.record(s)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    launches = amg.kernel_launches() - launches0
+    assert st == amg.AMG_OK, st
+    info = bat.info()
+    del bat
+    # the same systems, one FP64 solve per rhs through amg_solve
+    loop_setup, loop_solve, its_single, errs = 0.0, 0.0, [], []
+    for i in range(64):
+        t0 = time.perf_counter()
+        one = amg.AMG(*mats[i], Bs[i])
+        torch.cuda.synchronize()
+        loop_setup += time.perf_counter() - t0
+        for j in range(nrhs[i]):
+            one.solve(F[i][j])  # warm graph
+            e0, e1 = ev(), ev()
+            e0.record(s)
+            u1, it1, r1, st1 = one.solve(F[i][j])
+            e1.record(s)
+            torch.cuda.synchronize()
+            loop_solve += e0.elapsed_time(e1) / 1e3
+            its_single.append(it1)
+            errs.append(float(torch.linalg.norm(U[i][j] - u1) / torch.linalg.norm(u1)))
+        del one
+    v = float(np.mean(times))
+    return {
+        "metric": METRIC, "value": v, "unit": "s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["batch64"]["desc"], "instances": 64,
+                   "rhs_total": int(sum(nrhs)), "dofs_total": int(info["dofs_total"]),
+                   "l2": "inputs larger than L2", "parallelism": "single"},
+        "batch": {"setup_s": setup_t, "rhs_tile_per_level_A_P_R": info["rhs_tile"],
+                  "iterations_max": int(max(max(x) for x in its)),
+                  "iterations_mean": float(np.mean([y for x in its for y in x])),
+                  "rel_resid_max": float(max(max(x) for x in res)),
+                  "loop_of_single_solves_s": loop_solve, "loop_setup_s": loop_setup,
+                  "speedup_vs_loop": loop_solve / v,
+                  "max_rel_diff_vs_single_solves": max(errs),
+                  "single_iterations_mean": float(np.mean(its_single))},
+        "clocks": clk.summary(), "gpu_launches": int(launches),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -235,6 +312,10 @@ def main():
         torch.cuda.synchronize()
 
     amg.load()
+    if args.workload == "batch64":
+        line = run_batch(args, amg, torch)
+        print(json.dumps(line), flush=True)
+        return 0
     p = _problem(args.workload)
     dev = torch.device("cuda", local)
     rp = torch.from_numpy(p.row_ptr).to(dev)

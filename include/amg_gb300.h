@@ -186,6 +186,48 @@ int amg_bsr_spmv(const amg_bsr *A, const double *x, double *y, void *stream);
 int amg_bsr_spmv_dot(const amg_bsr *A, const double *x, double *y, double *dot_out,
                      void *stream);
 
+/* ---- batched form ------------------------------------------------------ */
+
+typedef struct amg_batch_s *amg_batch;
+
+/* Description of a batch (host struct). */
+typedef struct {
+    int32_t ninst;          /* instances */
+    int32_t nrhs_total;     /* right-hand sides over all instances */
+    int32_t nlevels;        /* deepest hierarchy */
+    int32_t reserved0;
+    double setup_seconds;
+    int64_t dofs_total;     /* fine-level unknowns over all instances */
+    int64_t bytes_total;    /* device memory held by the batch */
+    int32_t rhs_tile[48];   /* autotuned right-hand-side tile of A, P, R per level */
+} amg_batch_desc;
+
+/* Many independent instances of Eq. 1, each with its own near-nullspace and
+ * nrhs[i] (1..16) load cases, solved together.  Builds one hierarchy per
+ * instance exactly as amg_setup would (Alg. 1, same parameters, FP64, V(1,1))
+ * and the grouped structures of the batched V-cycle: level l of every
+ * instance in one concatenated sliced operator, right-hand sides interleaved
+ * so the SpMM reads each block once per tile of right-hand sides, and the
+ * tile chosen per operator by timing the candidates (1, 2, 4).
+ * A[i] (3x3 BSR) and B[i] (n_i x 6) are device arrays, read only. */
+int amg_batch_setup(int32_t ninst, const amg_bsr *A, const double *const *B, const int32_t *nrhs,
+                    const amg_params *prm, void *stream, amg_batch *out);
+
+/* CG preconditioned by one V-cycle (Sec. 4) for every (instance, rhs) pair at
+ * once, each pair with its own scalars and stopping test (relative residual
+ * tol confirmed by the true residual, or maxiter); the loop is one graph with
+ * a conditional while node.  F[i] and U[i] are device arrays of nrhs[i]
+ * contiguous vectors of 3 n_i doubles (U[i]: initial guesses in, solutions
+ * out).  iters and rel_resid (host, optional) receive one value per rhs in
+ * instance order.  Returns AMG_OK when every rhs converged, AMG_NOT_CONVERGED
+ * or an error otherwise.  Synchronises `stream`.  A pair's iterates do not
+ * depend on the other pairs of the batch. */
+int amg_batch_solve(amg_batch h, const double *const *F, double *const *U, double tol,
+                    int32_t maxiter, int32_t *iters, double *rel_resid, void *stream);
+
+int amg_batch_info(amg_batch h, amg_batch_desc *out);
+void amg_batch_free(amg_batch h);
+
 /* Same result as amg_bsr_spmv_dot, without allocating.  (The paper has no
  * counterpart: this serves callers of the library, not the method.)
  * amg_bsr_spmv_dot allocates device scratch for its per-CTA partial sums; a

@@ -59,9 +59,17 @@ class Stats(ctypes.Structure):
                 ("bytes_total", ctypes.c_int64), ("operator_complexity", ctypes.c_double)]
 
 
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("ninst", ctypes.c_int32), ("nrhs_total", ctypes.c_int32),
+                ("nlevels", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("setup_seconds", ctypes.c_double), ("dofs_total", ctypes.c_int64),
+                ("bytes_total", ctypes.c_int64), ("rhs_tile", ctypes.c_int32 * 48)]
+
+
 EXPORTED = ["amg_params_default", "amg_setup", "amg_apply_vcycle", "amg_solve", "amg_get_stats",
             "amg_level_info", "amg_level_export", "amg_free", "amg_last_error", "amg_bsr_spmv",
-            "amg_bsr_spmv_dot", "amg_kernel_launches", "amg_level_spmv", "amg_level_padding"]
+            "amg_bsr_spmv_dot", "amg_kernel_launches", "amg_level_spmv", "amg_level_padding",
+            "amg_batch_setup", "amg_batch_solve", "amg_batch_info", "amg_batch_free"]
 
 
 def library_path() -> str:
@@ -94,6 +102,10 @@ def load(build_if_missing: bool = True):
         "amg_kernel_launches": ([], ctypes.c_int64),
         "amg_level_spmv": ([P, i32, i32, P, P, P], ctypes.c_int),
         "amg_level_padding": ([P, i32, P], ctypes.c_int),
+        "amg_batch_setup": ([i32, P, P, P, P, P, P], ctypes.c_int),
+        "amg_batch_solve": ([P, P, P, d, i32, P, P, P], ctypes.c_int),
+        "amg_batch_info": ([P, P], ctypes.c_int),
+        "amg_batch_free": ([P], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -280,4 +292,65 @@ class AMG:
         B = np.empty((nbr * bs, 6))
         _check(self._lib.amg_level_export(self._h, l, 5, None, None, B.ctypes.data))
         out["B"] = B
+        return out
+
+
+class AMGBatch:
+    """Batched form: independent instances, each with several right-hand sides,
+    one hierarchy per instance and one graph-launched solve for all of them."""
+
+    def __init__(self, mats, Bs, nrhs, params: Params | None = None, stream=None, **kw):
+        import torch
+        self._lib = load()
+        self.params = params if params is not None else default_params(**kw)
+        n = len(mats)
+        if not (len(Bs) == len(nrhs) == n):
+            raise ValueError("mats, Bs and nrhs must have the same length")
+        self._keep = [m for m in mats] + list(Bs)
+        arr = (Bsr * n)(*[make_bsr(*m) for m in mats])
+        bptr = (ctypes.c_void_p * n)(*[_dptr(b, torch.float64, "B") for b in Bs])
+        k = (ctypes.c_int32 * n)(*[int(x) for x in nrhs])
+        self.nrhs = [int(x) for x in nrhs]
+        self.ndof = [int(m[0].shape[0] - 1) * 3 for m in mats]
+        h = ctypes.c_void_p()
+        _check(self._lib.amg_batch_setup(n, arr, bptr, k, ctypes.byref(self.params),
+                                         _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.amg_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, F, U=None, tol=1e-8, maxiter=1000, stream=None):
+        """F: list of CUDA tensors [nrhs_i, 3 n_i]; returns (U, iters, resid, status)."""
+        import torch
+        n = len(F)
+        if U is None:
+            U = [torch.zeros_like(f) for f in F]
+        fp = (ctypes.c_void_p * n)(*[_dptr(f, torch.float64, "F") for f in F])
+        up = (ctypes.c_void_p * n)(*[_dptr(u, torch.float64, "U") for u in U])
+        tot = sum(self.nrhs)
+        it = (ctypes.c_int32 * tot)()
+        res = (ctypes.c_double * tot)()
+        st = _check(self._lib.amg_batch_solve(self._h, fp, up, float(tol), int(maxiter), it, res,
+                                              _stream(stream)), allow_not_converged=True)
+        out_it, out_res, g = [], [], 0
+        for k in self.nrhs:
+            out_it.append(list(it[g:g + k]))
+            out_res.append(list(res[g:g + k]))
+            g += k
+        return U, out_it, out_res, st
+
+    def info(self) -> dict:
+        d = BatchDesc()
+        _check(self._lib.amg_batch_info(self._h, ctypes.byref(d)))
+        out = {k: getattr(d, k) for k, _ in BatchDesc._fields_ if k != "rhs_tile"}
+        out["rhs_tile"] = [[d.rhs_tile[3 * l + j] for j in range(3)] for l in range(d.nlevels)]
         return out

@@ -15,6 +15,7 @@ namespace amg {
 // ---------------------------------------------------------------- errors
 void set_error(const char *fmt, ...);
 void clear_error();
+const char *last_error();
 
 // Kernel launch accounting: every launch site reports itself; launches
 // recorded into a graph under capture are counted per graph execution.
@@ -192,4 +193,50 @@ int spai0_diag(const BsrD &A, double scale, double *M, cudaStream_t s);
 int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
                    double **Ainv_out);
 
+// ---------------------------------------------------------------- hierarchy (solver.cu)
+struct Level {
+    BsrD A, P, R;
+    Sell<double> sA, sP, sR;  // V-cycle copies of A, P, R in the SELL layout (FP64)
+    Sell<float> fA, fP, fR;   // FP32 copies (precision form)
+    Sell<__nv_bfloat16> bA, bP, bR;  // BF16-stored copies (precision form)
+    double pad_A = 0, pad_P = 0, pad_R = 0;
+    float *Mf = nullptr;      // smoother diagonal for the reduced-precision V-cycle
+    float *vf = nullptr, *vu = nullptr, *ve = nullptr, *vz = nullptr, *vt = nullptr;
+    double *M = nullptr;      // damped SPAI0 diagonal (scalar rows)
+    double *B = nullptr;      // near-nullspace, n x 6
+    int *agg = nullptr;       // aggregate of each node (device)
+    uint8_t *strong = nullptr;
+    int nagg = 0;
+    bool coarsest = false;
+    double eps = 0, omega = 0, rho = 0;
+    double *f = nullptr, *u = nullptr, *e = nullptr, *z = nullptr, *t = nullptr;
+    int n() const { return A.nbr * A.br; }
+};
+
+}  // namespace amg
+
+// The hierarchy handle behind the C ABI's opaque amg_handle.
+struct amg_handle_s {
+    amg_params prm;
+    cudaStream_t stream = nullptr;
+    amg::Geom geom;
+    amg::DevArena mem;
+    std::vector<amg::Level> lv;
+    double *Ainv = nullptr;
+    int nc = 0;
+    double *ff = nullptr, *uu = nullptr, *r = nullptr, *p = nullptr, *q = nullptr,
+           *z = nullptr, *rt = nullptr, *partials = nullptr, *scal = nullptr;
+    float *rv = nullptr, *zv = nullptr;   // r and z in the reduced-precision V-cycle
+    amg::CgState *st = nullptr;
+    amg::CgState *st_h = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long body_kernels = 0;   // kernels in one iteration of the graph body
+    double setup_seconds = 0.0;
+};
+
+
+namespace amg {
+int setup_impl(amg_handle h, const amg_bsr *Ain, const double *B);
+void destroy_handle(amg_handle h);
 }  // namespace amg

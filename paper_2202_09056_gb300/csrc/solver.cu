@@ -19,25 +19,6 @@
 namespace amg {
 const char *last_error();
 
-struct Level {
-    BsrD A, P, R;
-    Sell<double> sA, sP, sR;  // V-cycle copies of A, P, R in the SELL layout (FP64)
-    Sell<float> fA, fP, fR;   // FP32 copies (precision form)
-    Sell<__nv_bfloat16> bA, bP, bR;  // BF16-stored copies (precision form)
-    double pad_A = 0, pad_P = 0, pad_R = 0;
-    float *Mf = nullptr;      // smoother diagonal for the reduced-precision V-cycle
-    float *vf = nullptr, *vu = nullptr, *ve = nullptr, *vz = nullptr, *vt = nullptr;
-    double *M = nullptr;      // damped SPAI0 diagonal (scalar rows)
-    double *B = nullptr;      // near-nullspace, n x 6
-    int *agg = nullptr;       // aggregate of each node (device)
-    uint8_t *strong = nullptr;
-    int nagg = 0;
-    bool coarsest = false;
-    double eps = 0, omega = 0, rho = 0;
-    double *f = nullptr, *u = nullptr, *e = nullptr, *z = nullptr, *t = nullptr;
-    int n() const { return A.nbr * A.br; }
-};
-
 constexpr int FIN_THREADS = 256;
 
 template <int NT> __device__ __forceinline__ double block_sum_fixed(const double *p, int n)
@@ -267,25 +248,6 @@ __global__ void cg_replace_kernel(double *__restrict__ r, const double *__restri
 }  // namespace amg
 
 using namespace amg;
-
-struct amg_handle_s {
-    amg_params prm;
-    cudaStream_t stream = nullptr;
-    Geom geom;
-    DevArena mem;
-    std::vector<Level> lv;
-    double *Ainv = nullptr;
-    int nc = 0;
-    double *ff = nullptr, *uu = nullptr, *r = nullptr, *p = nullptr, *q = nullptr,
-           *z = nullptr, *rt = nullptr, *partials = nullptr, *scal = nullptr;
-    float *rv = nullptr, *zv = nullptr;   // r and z in the reduced-precision V-cycle
-    CgState *st = nullptr;
-    CgState *st_h = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    long long body_kernels = 0;   // kernels in one iteration of the graph body
-    double setup_seconds = 0.0;
-};
 
 static int vgrid(amg_handle h, int64_t n)
 {
@@ -625,7 +587,9 @@ static int check_bsr(const amg_bsr *A, int want_square)
     return AMG_OK;
 }
 
-static void destroy(amg_handle h)
+}  // extern "C"
+
+void amg::destroy_handle(amg_handle h)
 {
     if (!h) return;
     if (h->exec) cudaGraphExecDestroy(h->exec);
@@ -637,7 +601,7 @@ static void destroy(amg_handle h)
     delete h;
 }
 
-static int setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
+int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
 {
     cudaStream_t s = h->stream;
     const amg_params &prm = h->prm;
@@ -806,6 +770,8 @@ static int setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
     return AMG_OK;
 }
 
+extern "C" {
+
 int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params *prm,
               void *stream, amg_handle *out)
 {
@@ -842,7 +808,7 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
     int st = setup_impl(h, A, B);
     if (st < 0) {
         std::string msg = amg::last_error();
-        destroy(h);
+        destroy_handle(h);
         set_error("%s", msg.c_str());
         return st;
     }
@@ -852,7 +818,7 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
     return AMG_OK;
 }
 
-void amg_free(amg_handle h) { destroy(h); }
+void amg_free(amg_handle h) { destroy_handle(h); }
 
 int amg_apply_vcycle(amg_handle h, const double *r, double *z, void *stream)
 {

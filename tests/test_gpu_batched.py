@@ -1,0 +1,92 @@
+"""Batched form (GPU): independent instances with several load cases each.
+
+Bars: every (instance, rhs) solution within 1e-7 of the FP64 oracle's
+solution of that system, iterations within +-1; an instance solved inside a
+batch is bitwise identical (iterations and solution) to the same instance and
+right-hand side solved alone through the batched path; zero right-hand sides
+give zero solutions.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+import q1elasticity as q
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+amg = pytest.importorskip("paper_2202_09056_gb300")
+
+
+def _instances():
+    specs = [((6, 5, 7), 0.25, 3), ((9, 9, 9), 0.3, 1), ((8, 6, 10), 0.42, 5), ((5, 5, 5), 0.33, 2)]
+    out = []
+    for k, (shape, nu, nrhs) in enumerate(specs):
+        dirs, _ = q.splitmix64_uniform(100 + k, 3 * nrhs)
+        body = (dirs.reshape(nrhs, 3) - 0.5)
+        p = q.make_problem(shape, nu=nu, body=body, inclusion_frac=0.2 if k % 2 else 0.0)
+        out.append((p, nrhs))
+    return out
+
+
+def _dev(p):
+    d = torch.device("cuda:0")
+    return (torch.from_numpy(p.row_ptr).to(d), torch.from_numpy(p.col).to(d),
+            torch.from_numpy(p.val).to(d)), torch.from_numpy(p.B).to(d)
+
+
+def test_batch_matches_oracle_per_rhs():
+    inst = _instances()
+    mats, Bs, nrhs, F = [], [], [], []
+    for p, k in inst:
+        m, B = _dev(p)
+        mats.append(m)
+        Bs.append(B)
+        nrhs.append(k)
+        F.append(torch.from_numpy(np.atleast_2d(p.f).copy()).cuda())
+    bat = amg.AMGBatch(mats, Bs, nrhs, coarse_enough=150)
+    U, its, res, st = bat.solve(F, tol=1e-8)
+    assert st == amg.AMG_OK
+    info = bat.info()
+    assert info["ninst"] == 4 and info["nrhs_total"] == sum(nrhs)
+    assert all(t in (1, 2, 4) for lev in info["rhs_tile"] for t in lev)
+    for i, (p, k) in enumerate(inst):
+        H = o.Hierarchy(o.from_problem(p), 3, p.B, coarse_enough=150)
+        fs = np.atleast_2d(p.f)
+        for j in range(k):
+            uo, ito, _ = H.solve(fs[j], tol=1e-8)
+            u = U[i][j].cpu().numpy()
+            assert res[i][j] <= 1e-8
+            assert abs(its[i][j] - ito) <= 1, (i, j, its[i][j], ito)
+            assert np.linalg.norm(u - uo) <= 1e-7 * np.linalg.norm(uo), (i, j)
+
+
+def test_instance_in_batch_equals_instance_alone():
+    inst = _instances()
+    mats, Bs, nrhs, F = [], [], [], []
+    for p, k in inst:
+        m, B = _dev(p)
+        mats.append(m)
+        Bs.append(B)
+        nrhs.append(k)
+        F.append(torch.from_numpy(np.atleast_2d(p.f).copy()).cuda())
+    bat = amg.AMGBatch(mats, Bs, nrhs, coarse_enough=150)
+    U, its, res, _ = bat.solve(F, tol=1e-8)
+    for i in (0, 2):
+        for j in range(nrhs[i]):
+            one = amg.AMGBatch([mats[i]], [Bs[i]], [1], coarse_enough=150)
+            U1, it1, res1, _ = one.solve([F[i][j:j + 1].clone()], tol=1e-8)
+            assert it1[0][0] == its[i][j]
+            assert torch.equal(U1[0][0], U[i][j]), (i, j)
+            assert res1[0][0] == res[i][j]
+
+
+def test_batch_zero_rhs_and_cap():
+    p = q.make_problem((5, 4, 6), body=[(0, 0, -1), (0, 0, 0), (1, 0, 0)])
+    m, B = _dev(p)
+    F = torch.from_numpy(p.f.copy()).cuda()
+    bat = amg.AMGBatch([m], [B], [3], coarse_enough=100)
+    U, its, res, st = bat.solve([F], tol=1e-8)
+    assert st == amg.AMG_OK
+    assert its[0][1] == 0 and not U[0][1].any()
+    U, its, res, st = bat.solve([F], tol=1e-14, maxiter=2)
+    assert st == amg.AMG_NOT_CONVERGED and its[0][0] == 2
