@@ -81,6 +81,7 @@ def _load():
         "orc_level_graph": ([P, i], P),
         "orc_level_vectors": ([P, i, P, P, P, P], None),
         "orc_coarse_factor": ([P, P, P], None),
+        "orc_set_block_smoother": ([P, i, P], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -311,6 +312,12 @@ class Hierarchy:
         strong = np.empty(s[1], dtype=np.uint8)
         lib.orc_graph_copy(g, _p(ptr), _p(col), _p(nrm), _p(strong))
         return {"ptr": ptr, "col": col, "norm2": nrm, "strong": strong}
+
+    def set_block_smoother(self, l: int, Mb: np.ndarray):
+        """Use symmetric 3x3 blocks [N, 3, 3] as the smoother of level l."""
+        Mb = np.ascontiguousarray(Mb, dtype=np.float64)
+        if _load().orc_set_block_smoother(self.h, l, _p(Mb)) != 0:
+            raise ValueError("level has no 3x3 smoother")
 
     def coarse_factor(self):
         nc = self.level(self.nlevels - 1)["n"]

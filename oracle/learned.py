@@ -1,0 +1,138 @@
+"""ORACLE -- test infrastructure only.  FP64 reference of the learned smoother.
+
+The learned smoother replaces the fine-level SPAI0 diagonal by a 3x3 block per
+node, produced by a small MLP from unit-free features of the node's block row:
+
+  features x_I (12): A_II / ||A_II||_F (9, row-major),
+                     sum_{J != I} ||A_IJ||_F^2 / ||A_II||_F^2,
+                     max_{J != I} ||A_IJ||_F / ||A_II||_F,
+                     (number of blocks in row I) / 27;
+  network:           h = relu(W1 x + b1) (64), o = W2 h + b2 (6);
+  smoother block:    M_I = S_I (I + Delta_I) S_I, S_I = diag(sqrt(m)) with m the
+                     damped SPAI0 diagonal of the node's three scalar rows and
+                     Delta_I the symmetric 3x3 matrix
+                     [[o0, o3, o4], [o3, o1, o5], [o4, o5, o2]].
+
+A zero output layer gives M_I = diag(m): plain SPAI0.  The training loss over
+residual samples r_s is L = (1/S) sum_s ||r_s - A M r_s||^2 / ||r_s||^2 (one
+smoothing step from a zero guess); its gradient with respect to M_I is
+-(2/S) sum_s (A s_s)_I r_{s,I}^T / ||r_s||^2 with s_s = r_s - A M r_s (A is
+symmetric).  Everything here is plain numpy in FP64; only tests and the
+benchmark's CPU leg use it.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+NF = 12        # features
+NH = 64        # hidden units
+NO = 6         # outputs (symmetric 3x3)
+SYM = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+
+
+def features(row_ptr, col, val):
+    """Unit-free features of every block row of a 3x3 BSR matrix, [N, 12]."""
+    n = row_ptr.shape[0] - 1
+    X = np.zeros((n, NF))
+    for I in range(n):
+        s, e = row_ptr[I], row_ptr[I + 1]
+        nrm = np.linalg.norm(val[s:e].reshape(e - s, 9), axis=1)
+        d = np.nonzero(col[s:e] == I)[0][0] + s
+        nI = np.linalg.norm(val[d])
+        X[I, :9] = (val[d] / nI).ravel()
+        off = [k for k in range(s, e) if k != d]
+        if off:
+            X[I, 9] = np.sum(nrm[np.array(off) - s] ** 2) / nI ** 2
+            X[I, 10] = np.max(nrm[np.array(off) - s]) / nI
+        X[I, 11] = (e - s) / 27.0
+    return X
+
+
+def init_params(seed=0, scale=0.3):
+    """W1 small seeded Gaussian, W2 = 0 and biases 0: the start is SPAI0."""
+    rng = np.random.default_rng(seed)
+    return {"W1": scale * rng.standard_normal((NH, NF)) / np.sqrt(NF), "b1": np.zeros(NH),
+            "W2": np.zeros((NO, NH)), "b2": np.zeros(NO)}
+
+
+def flatten(p):
+    return np.concatenate([p["W1"].ravel(), p["b1"], p["W2"].ravel(), p["b2"]])
+
+
+def unflatten(v):
+    v = np.asarray(v, dtype=np.float64)
+    i = 0
+    out = {}
+    for k, shape in (("W1", (NH, NF)), ("b1", (NH,)), ("W2", (NO, NH)), ("b2", (NO,))):
+        size = int(np.prod(shape))
+        out[k] = v[i:i + size].reshape(shape)
+        i += size
+    return out
+
+
+NPARAM = NH * NF + NH + NO * NH + NO
+
+
+def forward(p, X):
+    pre = X @ p["W1"].T + p["b1"]
+    h = np.maximum(pre, 0.0)
+    o = h @ p["W2"].T + p["b2"]
+    return o, h, pre
+
+
+def delta_from_output(o):
+    D = np.zeros((o.shape[0], 3, 3))
+    for k, (a, b) in enumerate(SYM):
+        D[:, a, b] = o[:, k]
+        D[:, b, a] = o[:, k]
+    return D
+
+
+def smoother_blocks(m, o):
+    """M_I = S (I + Delta) S with S = diag(sqrt(m_I)), [N, 3, 3]."""
+    S = np.sqrt(np.asarray(m).reshape(-1, 3))
+    M = np.eye(3)[None] + delta_from_output(o)
+    return S[:, :, None] * M * S[:, None, :]
+
+
+def apply_blocks(M, r):
+    return np.einsum("nab,nb->na", M, r.reshape(-1, 3)).ravel()
+
+
+def loss_and_grad_M(A: sp.spmatrix, M, R):
+    """L and dL/dM (unsymmetrised, [N, 3, 3]) for residual samples R [S, n]."""
+    S = R.shape[0]
+    L = 0.0
+    G = np.zeros_like(M)
+    for r in R:
+        t = A @ apply_blocks(M, r)
+        s = r - t
+        rr = r @ r
+        L += (s @ s) / rr
+        g = A @ s
+        G += np.einsum("na,nb->nab", (-2.0 / rr) * g.reshape(-1, 3), r.reshape(-1, 3))
+    return L / S, G / S
+
+
+def grad_params(p, X, m, A, R):
+    """(L, flat gradient) of the loss with respect to (W1, b1, W2, b2)."""
+    o, h, pre = forward(p, X)
+    M = smoother_blocks(m, o)
+    L, GM = loss_and_grad_M(A, M, R)
+    S = np.sqrt(np.asarray(m).reshape(-1, 3))
+    GD = S[:, :, None] * GM * S[:, None, :]          # dL/dDelta (entrywise)
+    do = np.zeros((X.shape[0], NO))
+    for k, (a, b) in enumerate(SYM):
+        do[:, k] = GD[:, a, a] if a == b else GD[:, a, b] + GD[:, b, a]
+    gW2 = do.T @ h
+    gb2 = do.sum(0)
+    dh = (do @ p["W2"]) * (pre > 0)
+    gW1 = dh.T @ X
+    gb1 = dh.sum(0)
+    return L, np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2])
+
+
+def loss(p, X, m, A, R):
+    o, _, _ = forward(p, X)
+    return loss_and_grad_M(A, smoother_blocks(m, o), R)[0]

@@ -609,6 +609,7 @@ typedef struct {
     int b;
     double eps, omega, rho;
     double *M;  /* SPAI0 diagonal */
+    double *Mb; /* optional block smoother (3x3 per node, row-major), replaces M */
     double *B;  /* near-nullspace of this level, n x 6 */
     double *d;  /* filtered diagonal */
 } orc_level;
@@ -654,6 +655,7 @@ void orc_free(orc_hier *H)
         orc_graph_free(L->G);
         free(L->agg);
         free(L->M);
+        free(L->Mb);
         free(L->B);
         free(L->d);
     }
@@ -739,6 +741,35 @@ orc_hier *orc_setup(const orc_csr *A0, int bs, const double *B0, const orc_param
     return H;
 }
 
+/* out = M x (diagonal SPAI0) or the 3x3 block smoother when one is set;
+ * with add != 0, out += M x. */
+static void apply_smoother(const orc_level *L, int64_t n, const double *x, double *out, int add)
+{
+    if (L->Mb) {
+        for (int64_t I = 0; I < n / 3; ++I)
+            for (int a = 0; a < 3; ++a) {
+                double v = 0.0;
+                for (int b = 0; b < 3; ++b) v += L->Mb[I * 9 + a * 3 + b] * x[I * 3 + b];
+                out[I * 3 + a] = add ? out[I * 3 + a] + v : v;
+            }
+    } else {
+        for (int64_t i = 0; i < n; ++i) out[i] = add ? out[i] + L->M[i] * x[i] : L->M[i] * x[i];
+    }
+}
+
+/* Replace the smoother of level l by symmetric 3x3 blocks (node block size
+ * 3 only).  Returns 0, or -1 if the level has no smoother or other blocks. */
+int orc_set_block_smoother(orc_hier *H, int l, const double *Mb)
+{
+    if (l < 0 || l >= H->nlev - 1 || H->lv[l].b != 3) return -1;
+    orc_level *L = &H->lv[l];
+    int64_t n = L->A->nrows;
+    free(L->Mb);
+    L->Mb = (double *)malloc(sizeof(double) * (size_t)(3 * n));
+    memcpy(L->Mb, Mb, sizeof(double) * (size_t)(3 * n));
+    return 0;
+}
+
 /* Alg. 2, one cycle from a zero initial guess on every level. */
 static void vcycle_level(orc_hier *H, int l, const double *f, double *u, double *work)
 {
@@ -750,10 +781,13 @@ static void vcycle_level(orc_hier *H, int l, const double *f, double *u, double 
     }
     double *e = work, *fc = work + n, *uc = fc + L->R->nrows, *next = uc + L->R->nrows;
     /* pre-smoothing from u = 0: the first sweep gives u = M f */
-    for (int64_t i = 0; i < n; ++i) u[i] = (H->npre > 0) ? L->M[i] * f[i] : 0.0;
+    if (H->npre > 0) apply_smoother(L, n, f, u, 0);
+    else
+        for (int64_t i = 0; i < n; ++i) u[i] = 0.0;
     for (int s = 1; s < H->npre; ++s) {
         orc_spmv(L->A, u, e);
-        for (int64_t i = 0; i < n; ++i) u[i] += L->M[i] * (f[i] - e[i]);
+        for (int64_t i = 0; i < n; ++i) e[i] = f[i] - e[i];
+        apply_smoother(L, n, e, u, 1);
     }
     /* residual and restriction: f_{l+1} = R (f - A u) */
     orc_spmv(L->A, u, e);
@@ -766,7 +800,8 @@ static void vcycle_level(orc_hier *H, int l, const double *f, double *u, double 
     /* post-smoothing */
     for (int s = 0; s < H->npost; ++s) {
         orc_spmv(L->A, u, e);
-        for (int64_t i = 0; i < n; ++i) u[i] += L->M[i] * (f[i] - e[i]);
+        for (int64_t i = 0; i < n; ++i) e[i] = f[i] - e[i];
+        apply_smoother(L, n, e, u, 1);
     }
 }
 
