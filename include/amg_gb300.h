@@ -146,7 +146,9 @@ int amg_level_info(amg_handle h, int32_t level, amg_level_desc *out);
  * -1 for an isolated node); which = 4: the smoother diagonal (val receives
  * nbrows*bs doubles); which = 5: the near-nullspace of the level (val
  * receives nbrows*bs*6 doubles); which = 6: the strong-connection flags of A
- * (row_ptr receives nnzb_A bytes).  Synchronises the stream it was set up on. */
+ * (row_ptr receives nnzb_A bytes); which = 7: the learned smoother blocks of
+ * level 0 (val receives nbrows*9 doubles).  Synchronises the stream it was set
+ * up on. */
 int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_ptr,
                      int32_t *col, double *val);
 
@@ -227,6 +229,58 @@ int amg_batch_solve(amg_batch h, const double *const *F, double *const *U, doubl
 
 int amg_batch_info(amg_batch h, amg_batch_desc *out);
 void amg_batch_free(amg_batch h);
+
+/* ---- learned smoother ---------------------------------------------------- */
+
+/* Parameters of the smoother network, FP32, flat in this order:
+ * W1 [64][12], b1 [64], W2 [6][64], b2 [6] (AMG_LEARNED_NPARAM values). */
+#define AMG_LEARNED_NPARAM 1222
+
+/* Replace the fine-level SPAI0 smoother of h by learned 3x3 blocks
+ * M_I = S_I (I + Delta_I) S_I, S_I = diag(sqrt(SPAI0 diagonal of node I)),
+ * Delta_I the symmetric 3x3 matrix [[o0,o3,o4],[o3,o1,o5],[o4,o5,o2]] with
+ * o = W2 relu(W1 x_I + b1) + b2 and x_I the node's unit-free features (the
+ * diagonal block over its Frobenius norm, the sum of squared and the largest
+ * neighbour-block norms relative to it, the block count / 27).  The network
+ * runs on the tensor cores (BF16 operands, FP32 accumulation).  The paper
+ * uses a fixed smoother (Sec. 3 names SPAI); this data-driven stand-in keeps
+ * SPAI0 as its fallback: if any I + Delta_I is not positive definite the
+ * call keeps SPAI0 and sets *fell_back (host) to 1; if 20 power iterations
+ * estimate lambda_max(M A) >= 1.9 on level 0 (the smoothing step would not
+ * contract the energy norm, and the V-cycle could stop being positive
+ * definite) it keeps SPAI0 and sets *fell_back to 2.  params is host memory.
+ * Later amg_solve / amg_apply_vcycle calls use the blocks (FP64 V-cycle). */
+int amg_set_learned_smoother(amg_handle h, const float *params, int32_t *fell_back, void *stream);
+
+/* Back to the SPAI0 smoother. */
+int amg_clear_learned_smoother(amg_handle h);
+
+typedef struct amg_trainer_s *amg_trainer;
+
+/* Trainer of the smoother network: Adam (learning rate lr) on FP32 master
+ * weights, loss L = mean over problems and error samples of the energy-norm
+ * error reduction of one smoothing step, ||e_s - M A e_s||_A^2 / ||e_s||_A^2,
+ * gradients from the project's own forward/backward kernels.  params: host,
+ * initial values.  Problems are borrowed hierarchies that must outlive the
+ * trainer. */
+int amg_trainer_create(const float *params, double lr, void *stream, amg_trainer *out);
+/* Add a problem with given error samples R (device, [nsamples][3 nbrows]). */
+int amg_trainer_add_samples(amg_trainer t, amg_handle h, const double *R, int32_t nsamples,
+                            void *stream);
+/* Add a problem with error samples the method produces: for random e0
+ * (SplitMix64 of seed and the index), even samples e = e0 - V(A e0), the error
+ * one of the hierarchy's SPAI0 V-cycles leaves, odd samples e = e0 (white
+ * noise, so that the loss also sees the top of the spectrum). */
+int amg_trainer_add_generated(amg_trainer t, amg_handle h, int32_t nsamples, uint64_t seed,
+                              void *stream);
+/* Loss and gradient (host, AMG_LEARNED_NPARAM floats; may be NULL) at the
+ * current parameters, without an update. */
+int amg_trainer_eval(amg_trainer t, double *loss, float *grad, void *stream);
+/* nsteps Adam steps; *loss (host) = the loss before the last step. */
+int amg_trainer_step(amg_trainer t, int32_t nsteps, double *loss, void *stream);
+/* Current parameters (host, AMG_LEARNED_NPARAM floats). */
+int amg_trainer_params(amg_trainer t, float *out);
+void amg_trainer_free(amg_trainer t);
 
 /* Same result as amg_bsr_spmv_dot, without allocating.  (The paper has no
  * counterpart: this serves callers of the library, not the method.)

@@ -13,12 +13,14 @@ node, produced by a small MLP from unit-free features of the node's block row:
                      Delta_I the symmetric 3x3 matrix
                      [[o0, o3, o4], [o3, o1, o5], [o4, o5, o2]].
 
-A zero output layer gives M_I = diag(m): plain SPAI0.  The training loss over
-residual samples r_s is L = (1/S) sum_s ||r_s - A M r_s||^2 / ||r_s||^2 (one
-smoothing step from a zero guess); its gradient with respect to M_I is
--(2/S) sum_s (A s_s)_I r_{s,I}^T / ||r_s||^2 with s_s = r_s - A M r_s (A is
-symmetric).  Everything here is plain numpy in FP64; only tests and the
-benchmark's CPU leg use it.
+A zero output layer gives M_I = diag(m): plain SPAI0.  The training loss is
+the energy-norm error reduction of one smoothing step over error samples e_s,
+L = (1/S) sum_s ||e_s - M A e_s||_A^2 / ||e_s||_A^2; with r = A e and
+e' = e - M r its gradient with respect to M_I is
+-(2/S) sum_s (A e'_s)_I r_{s,I}^T / (e_s . r_s) (A is symmetric).  A step that
+amplifies some error (lambda(M A) > 2) raises the loss, so minimising it keeps
+the smoother convergent.  Everything here is plain numpy in FP64; only tests
+and the benchmark's CPU leg use it.
 """
 from __future__ import annotations
 
@@ -100,23 +102,24 @@ def apply_blocks(M, r):
     return np.einsum("nab,nb->na", M, r.reshape(-1, 3)).ravel()
 
 
-def loss_and_grad_M(A: sp.spmatrix, M, R):
-    """L and dL/dM (unsymmetrised, [N, 3, 3]) for residual samples R [S, n]."""
-    S = R.shape[0]
+def loss_and_grad_M(A: sp.spmatrix, M, E):
+    """L and dL/dM (unsymmetrised, [N, 3, 3]) for error samples E [S, n]."""
+    S = E.shape[0]
     L = 0.0
     G = np.zeros_like(M)
-    for r in R:
-        t = A @ apply_blocks(M, r)
-        s = r - t
-        rr = r @ r
-        L += (s @ s) / rr
-        g = A @ s
-        G += np.einsum("na,nb->nab", (-2.0 / rr) * g.reshape(-1, 3), r.reshape(-1, 3))
+    for e in E:
+        r = A @ e
+        den = e @ r
+        ep = e - apply_blocks(M, r)
+        g = A @ ep
+        L += (ep @ g) / den
+        G += np.einsum("na,nb->nab", (-2.0 / den) * g.reshape(-1, 3), r.reshape(-1, 3))
     return L / S, G / S
 
 
 def grad_params(p, X, m, A, R):
-    """(L, flat gradient) of the loss with respect to (W1, b1, W2, b2)."""
+    """(L, flat gradient) of the loss over error samples R with respect to
+    (W1, b1, W2, b2)."""
     o, h, pre = forward(p, X)
     M = smoother_blocks(m, o)
     L, GM = loss_and_grad_M(A, M, R)

@@ -69,7 +69,12 @@ class BatchDesc(ctypes.Structure):
 EXPORTED = ["amg_params_default", "amg_setup", "amg_apply_vcycle", "amg_solve", "amg_get_stats",
             "amg_level_info", "amg_level_export", "amg_free", "amg_last_error", "amg_bsr_spmv",
             "amg_bsr_spmv_dot", "amg_kernel_launches", "amg_level_spmv", "amg_level_padding",
-            "amg_batch_setup", "amg_batch_solve", "amg_batch_info", "amg_batch_free"]
+            "amg_batch_setup", "amg_batch_solve", "amg_batch_info", "amg_batch_free",
+            "amg_set_learned_smoother", "amg_clear_learned_smoother", "amg_trainer_create",
+            "amg_trainer_add_samples", "amg_trainer_add_generated", "amg_trainer_eval",
+            "amg_trainer_step", "amg_trainer_params", "amg_trainer_free"]
+
+LEARNED_NPARAM = 1222   # W1 [64][12], b1 [64], W2 [6][64], b2 [6]
 
 
 def library_path() -> str:
@@ -106,6 +111,15 @@ def load(build_if_missing: bool = True):
         "amg_batch_solve": ([P, P, P, d, i32, P, P, P], ctypes.c_int),
         "amg_batch_info": ([P, P], ctypes.c_int),
         "amg_batch_free": ([P], None),
+        "amg_set_learned_smoother": ([P, P, P, P], ctypes.c_int),
+        "amg_clear_learned_smoother": ([P], ctypes.c_int),
+        "amg_trainer_create": ([P, d, P, P], ctypes.c_int),
+        "amg_trainer_add_samples": ([P, P, P, i32, P], ctypes.c_int),
+        "amg_trainer_add_generated": ([P, P, i32, ctypes.c_uint64, P], ctypes.c_int),
+        "amg_trainer_eval": ([P, P, P, P], ctypes.c_int),
+        "amg_trainer_step": ([P, i32, P, P], ctypes.c_int),
+        "amg_trainer_params": ([P, P], ctypes.c_int),
+        "amg_trainer_free": ([P], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -246,6 +260,26 @@ class AMG:
         _check(self._lib.amg_level_info(self._h, l, ctypes.byref(d)))
         return {k: getattr(d, k) for k, _ in LevelDesc._fields_}
 
+    def set_learned_smoother(self, params, stream=None) -> int:
+        """Use the network's 3x3 blocks on level 0.  Returns 0, or the reason it
+        kept SPAI0: 1 a block not positive definite, 2 lambda_max(M A) >= 1.9."""
+        w = np.ascontiguousarray(params, dtype=np.float32)
+        if w.size != LEARNED_NPARAM:
+            raise ValueError(f"expected {LEARNED_NPARAM} parameters")
+        fb = ctypes.c_int32(0)
+        _check(self._lib.amg_set_learned_smoother(self._h, w.ctypes.data, ctypes.byref(fb),
+                                                  _stream(stream)))
+        return int(fb.value)
+
+    def clear_learned_smoother(self):
+        _check(self._lib.amg_clear_learned_smoother(self._h))
+
+    def learned_blocks(self) -> np.ndarray:
+        info = self.level_info(0)
+        out = np.empty((info["nbrows"], 3, 3))
+        _check(self._lib.amg_level_export(self._h, 0, 7, None, None, out.ctypes.data))
+        return out
+
     def level_spmv(self, l: int, which: int, x, y, stream=None):
         """y = op x with the solve's own kernel; which = 0 (A), 1 (P), 2 (R)."""
         import torch
@@ -354,3 +388,64 @@ class AMGBatch:
         out = {k: getattr(d, k) for k, _ in BatchDesc._fields_ if k != "rhs_tile"}
         out["rhs_tile"] = [[d.rhs_tile[3 * l + j] for j in range(3)] for l in range(d.nlevels)]
         return out
+
+
+def learned_init(seed: int = 0, scale: float = 0.3) -> np.ndarray:
+    """Initial network: W1 seeded Gaussian / sqrt(12), everything else zero
+    (the zero output layer makes the learned smoother equal to SPAI0)."""
+    rng = np.random.default_rng(seed)
+    w = np.zeros(LEARNED_NPARAM, dtype=np.float32)
+    w[:64 * 12] = (scale * rng.standard_normal(64 * 12) / np.sqrt(12)).astype(np.float32)
+    return w
+
+
+class Trainer:
+    """Training of the smoother network on the device (own kernels, Adam)."""
+
+    def __init__(self, params, lr=1e-3, stream=None):
+        self._lib = load()
+        w = np.ascontiguousarray(params, dtype=np.float32)
+        t = ctypes.c_void_p()
+        _check(self._lib.amg_trainer_create(w.ctypes.data, float(lr), _stream(stream),
+                                            ctypes.byref(t)))
+        self._t = t
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "_t", None):
+            self._lib.amg_trainer_free(self._t)
+            self._t = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_samples(self, solver: "AMG", R, stream=None):
+        import torch
+        self._keep.append(solver)
+        _check(self._lib.amg_trainer_add_samples(self._t, solver._h, _dptr(R, torch.float64, "R"),
+                                                 int(R.shape[0]), _stream(stream)))
+
+    def add_generated(self, solver: "AMG", nsamples: int, seed: int = 0, stream=None):
+        self._keep.append(solver)
+        _check(self._lib.amg_trainer_add_generated(self._t, solver._h, int(nsamples),
+                                                   ctypes.c_uint64(seed), _stream(stream)))
+
+    def eval(self, stream=None):
+        loss = ctypes.c_double(0.0)
+        g = np.empty(LEARNED_NPARAM, dtype=np.float32)
+        _check(self._lib.amg_trainer_eval(self._t, ctypes.byref(loss), g.ctypes.data,
+                                          _stream(stream)))
+        return loss.value, g
+
+    def step(self, nsteps=1, stream=None) -> float:
+        loss = ctypes.c_double(0.0)
+        _check(self._lib.amg_trainer_step(self._t, int(nsteps), ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def params(self) -> np.ndarray:
+        w = np.empty(LEARNED_NPARAM, dtype=np.float32)
+        _check(self._lib.amg_trainer_params(self._t, w.ctypes.data))
+        return w

@@ -90,6 +90,7 @@ enum SpmvMode {
     SPMV_SMOOTH = 2,  // y = x + M (f - A x)           (x = u, square A)
     SPMV_AXPY = 3,    // y = u + A x                  (prolongation, y may alias u)
     SPMV_RESTRICT = 4,// y = A x ; y2 = M y           (restriction + next pre-smoothing)
+    SPMV_SMOOTHB = 5, // y = x + Mb (f - A x)          (3x3 block smoother, Mb 9 per row)
 };
 
 enum DotMode {
@@ -147,6 +148,7 @@ template <class T> struct Sell {
 };
 
 template <class TV> struct SellArgs {
+    const double *Mb;    // 3x3 smoother blocks (SPMV_SMOOTHB)
     int nrows, nslices, G;
     const int64_t *slice_ptr;
     const int *col;
@@ -210,6 +212,7 @@ struct Level {
     bool coarsest = false;
     double eps = 0, omega = 0, rho = 0;
     double *f = nullptr, *u = nullptr, *e = nullptr, *z = nullptr, *t = nullptr;
+    double *Mb = nullptr;     // learned 3x3 smoother blocks (level 0), replaces M when set
     int n() const { return A.nbr * A.br; }
 };
 
@@ -233,10 +236,15 @@ struct amg_handle_s {
     cudaGraphExec_t exec = nullptr;
     long long body_kernels = 0;   // kernels in one iteration of the graph body
     double setup_seconds = 0.0;
+    int learned = 0;              // level 0 smooths with the learned blocks
+    double learned_lambda = 0.0;  // estimated lambda_max(M A) of the learned smoother
 };
 
 
 namespace amg {
 int setup_impl(amg_handle h, const amg_bsr *Ain, const double *B);
 void destroy_handle(amg_handle h);
+// out_I = Mb_I r_I for every 3-row node (learned smoother, learned.cu)
+int launch_block_apply(const double *Mb, const double *r, double *out, int nrows, const Geom &g,
+                       cudaStream_t s);
 }  // namespace amg

@@ -98,7 +98,23 @@ __global__ void __launch_bounds__(SELL_THREADS) sell_spmv_kernel(SellArgs<TV> a)
         for (int m = G >> 1; m >= 1; m >>= 1)
 #pragma unroll
             for (int r = 0; r < BR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], m);
-        if (sub == 0 && row >= 0 && row < a.nrows) {
+        if (MODE == SPMV_SMOOTHB && sub == 0 && row >= 0 && row < a.nrows) {
+            // u + Mb (f - A u) with the row's 3x3 block (BR == 3)
+            Acc res[BR];
+#pragma unroll
+            for (int r = 0; r < BR; ++r) res[r] = a.f[(int64_t)row * BR + r] - acc[r];
+            const double *mb = a.Mb + (int64_t)row * BR * BR;
+#pragma unroll
+            for (int r = 0; r < BR; ++r) {
+                const int64_t i = (int64_t)row * BR + r;
+                Acc corr = Acc(0);
+#pragma unroll
+                for (int c = 0; c < BR; ++c) corr = fma((Acc)mb[r * BR + c], res[c], corr);
+                const Acc out = x[i] + corr;
+                a.y[i] = out;
+                if (DOT == DOT_FY) dot += (double)a.f[i] * (double)out;
+            }
+        } else if (sub == 0 && row >= 0 && row < a.nrows) {
 #pragma unroll
             for (int r = 0; r < BR; ++r) {
                 const int64_t i = (int64_t)row * BR + r;
@@ -146,7 +162,7 @@ static int sell_dot(int dot, const SellArgs<TV> &a, int grid, cudaStream_t s)
 {
     constexpr bool f64 = std::is_same<TV, double>::value;
     if (dot == DOT_NONE) return sell_go<BR, BC, VT, TV, MODE, DOT_NONE>(a, grid, s);
-    if constexpr (MODE == SPMV_SMOOTH)
+    if constexpr (MODE == SPMV_SMOOTH || MODE == SPMV_SMOOTHB)
         if (dot == DOT_FY) return sell_go<BR, BC, VT, TV, MODE, DOT_FY>(a, grid, s);
     if constexpr (f64 && BR == BC && MODE == SPMV_PLAIN)
         if (dot == DOT_XY) return sell_go<BR, BC, VT, TV, MODE, DOT_XY>(a, grid, s);
@@ -166,6 +182,11 @@ static int sell_mode(int mode, int dot, const SellArgs<TV> &a, int grid, cudaStr
     case SPMV_SMOOTH: return sell_dot<BR, BC, VT, TV, SPMV_SMOOTH>(dot, a, grid, s);
     case SPMV_AXPY: return sell_dot<BR, BC, VT, TV, SPMV_AXPY>(dot, a, grid, s);
     case SPMV_RESTRICT: return sell_dot<BR, BC, VT, TV, SPMV_RESTRICT>(dot, a, grid, s);
+    case SPMV_SMOOTHB:
+        if constexpr (BR == 3 && BC == 3 && std::is_same<TV, double>::value)
+            return sell_dot<BR, BC, VT, TV, SPMV_SMOOTHB>(dot, a, grid, s);
+        set_error("block smoothing needs 3x3 FP64 blocks");
+        return AMG_ERR_ARG;
     default: set_error("bad spmv mode %d", mode); return AMG_ERR_ARG;
     }
 }

@@ -311,12 +311,15 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
         const TV *f = (l == 0) ? f0 : C.f;
         TV *u = C.u, *t = C.t;
         for (int sweep = 1; sweep < npre; ++sweep) {  // further pre-smoothing sweeps
+            const bool blocks = std::is_same<TV, double>::value && l == 0 && h->learned;
             SellArgs<TV> a{};
             a.x = u;
             a.f = f;
             a.M = C.M;
+            a.Mb = h->lv[0].Mb;
             a.y = t;
-            AMG_TRY((launch_sell<VT, TV>(*C.A, SPMV_SMOOTH, DOT_NONE, a, g, s)));
+            AMG_TRY((launch_sell<VT, TV>(*C.A, blocks ? SPMV_SMOOTHB : SPMV_SMOOTH, DOT_NONE, a, g,
+                                         s)));
             std::swap(u, t);
         }
         ucur[l] = u;
@@ -359,6 +362,7 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
             AMG_TRY((launch_sell<VT, TV>(*C.P, SPMV_AXPY, DOT_NONE, a, g, s)));
         }
         const TV *w = u;
+        const bool blocks = std::is_same<TV, double>::value && l == 0 && h->learned;
         for (int sweep = 0; sweep < npost; ++sweep) {  // u += M (f - A u)
             const bool last = (sweep == npost - 1);
             TV *out = last ? zl : t;
@@ -366,10 +370,11 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
             a.x = w;
             a.f = f;
             a.M = C.M;
+            a.Mb = h->lv[0].Mb;
             a.y = out;
             a.partials = rz_partials;
             const int dot = (l == 0 && last && rz_partials) ? DOT_FY : DOT_NONE;
-            AMG_TRY((launch_sell<VT, TV>(*C.A, SPMV_SMOOTH, dot, a, g, s)));
+            AMG_TRY((launch_sell<VT, TV>(*C.A, blocks ? SPMV_SMOOTHB : SPMV_SMOOTH, dot, a, g, s)));
             w = out;
             t = (out == t) ? u : t;  // ping-pong between u and t
         }
@@ -424,9 +429,10 @@ static int record_cg_iteration_t(amg_handle h, cudaStream_t s, cudaGraphConditio
         AMG_TRY((launch_sell<double, double>(L0.sA, SPMV_PLAIN, DOT_XY, a, g, s, &grid)));
     }
     cg_alpha_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, grid); ::amg::count_launch(1);
+    const bool blocks = f64 && h->learned && multi && npre > 0;
     cg_update_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(h->uu, h->r, h->p, h->q, V0.M,
-                                                     multi ? V0.u : nullptr, rv, h->st, n,
-                                                     npre > 0, h->partials); ::amg::count_launch(1);
+                                                     (multi && !blocks) ? V0.u : nullptr, rv, h->st,
+                                                     n, npre > 0, h->partials); ::amg::count_launch(1);
     cg_resnorm_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, vgrid(h, n)); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     {  // true residual, only when the recurrence residual reached tol
@@ -439,9 +445,12 @@ static int record_cg_iteration_t(amg_handle h, cudaStream_t s, cudaGraphConditio
         AMG_TRY((launch_sell<double, double>(L0.sA, SPMV_RESID, DOT_YY, a, g, s, &grid)));
     }
     cg_decide_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, grid, cond, use_cond); ::amg::count_launch(1);
-    cg_replace_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(h->r, h->rt, V0.M, multi ? V0.u : nullptr,
-                                                      rv, h->st, n, npre > 0); ::amg::count_launch(1);
+    cg_replace_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(h->r, h->rt, V0.M,
+                                                      (multi && !blocks) ? V0.u : nullptr, rv, h->st,
+                                                      n, npre > 0); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
+    if (blocks)  // next pre-smoothing with the learned blocks: u0 = Mb r
+        AMG_TRY(launch_block_apply(L0.Mb, h->r, (double *)V0.u, L0.A.nbr, g, s));
     return AMG_OK;
 }
 
@@ -833,7 +842,9 @@ int amg_apply_vcycle(amg_handle h, const double *r, double *z, void *stream)
     const bool multi = h->lv.size() > 1;
     const int zero = h->prm.npre == 0;
     if (h->prm.precision == AMG_PREC_FP64) {
-        if (multi) {
+        if (multi && h->learned && !zero) {
+            AMG_TRY(launch_block_apply(L0.Mb, r, L0.u, L0.A.nbr, h->geom, s));
+        } else if (multi) {
             scale_kernel<double><<<vgrid(h, n), 256, 0, s>>>(L0.M, r, L0.u, nullptr, n, zero);
             count_launch(1);
             AMG_TRY_CUDA(cudaGetLastError());
@@ -886,7 +897,9 @@ int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxi
     AMG_TRY(launch_reduce_sum(h->partials, grid, h->scal + 1, s));
     cg_start_kernel<<<1, 1, 0, s>>>(h->st, h->scal, tol, maxiter); ::amg::count_launch(1);
     if (h->prm.precision == AMG_PREC_FP64) {
-        if (multi) {
+        if (multi && h->learned && h->prm.npre > 0) {
+            AMG_TRY(launch_block_apply(L0.Mb, h->r, L0.u, L0.A.nbr, h->geom, s));
+        } else if (multi) {
             scale_kernel<double><<<vgrid(h, n), 256, 0, s>>>(L0.M, h->r, L0.u, nullptr, n,
                                                              h->prm.npre == 0);
             count_launch(1);
@@ -1038,6 +1051,10 @@ int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_pt
         break;
     case 5:
         if (val) AMG_TRY_CUDA(cudaMemcpyAsync(val, L.B, sizeof(double) * L.n() * 6, cudaMemcpyDeviceToHost, s));
+        break;
+    case 7:
+        if (!L.Mb || !h->learned) { set_error("no learned smoother blocks on this level"); return AMG_ERR_STATE; }
+        if (val) AMG_TRY_CUDA(cudaMemcpyAsync(val, L.Mb, sizeof(double) * L.A.nbr * 9, cudaMemcpyDeviceToHost, s));
         break;
     case 6:
         if (!L.strong) { set_error("no strength flags on this level"); return AMG_ERR_STATE; }

@@ -61,16 +61,27 @@ def test_grad_M_matches_dense_derivative():
     M = lo.smoother_blocks(m, o_)
     L, G = lo.loss_and_grad_M(A, M, R[:1])
     Ad = A.toarray()
-    r = R[0]
-    # dense: L(M) = |r - A Mb r|^2 / |r|^2 with Mb block diagonal
-    n = len(r)
+    e = R[0]
+    # dense: L(Mb) = e'^T A e' / e^T A e with e' = (I - Mb A) e, Mb block diagonal
+    n = len(e)
     Mb = np.zeros((n, n))
     for I in range(n // 3):
         Mb[3 * I:3 * I + 3, 3 * I:3 * I + 3] = M[I]
-    s = r - Ad @ Mb @ r
-    Gd = -2.0 * np.outer(Ad.T @ s, r) / (r @ r)
+    ep = e - Mb @ Ad @ e
+    assert np.isclose(L, ep @ Ad @ ep / (e @ Ad @ e), rtol=1e-12)
+    Gd = -2.0 * np.outer(Ad @ ep, Ad @ e) / (e @ Ad @ e)
     for I in range(n // 3):
         np.testing.assert_allclose(G[I], Gd[3 * I:3 * I + 3, 3 * I:3 * I + 3], rtol=1e-10, atol=1e-14)
+
+
+def test_loss_penalises_an_unstable_smoother():
+    # scaling SPAI0 up until lambda_max(M A) passes 2 makes the energy-norm
+    # loss on white-noise errors exceed 1 (some errors grow)
+    p, A, H, m, X, R = _setup((5, 5, 5))
+    base = np.einsum("ni,ij->nij", m.reshape(-1, 3), np.eye(3))
+    L1, _ = lo.loss_and_grad_M(A, base, R)
+    L3, _ = lo.loss_and_grad_M(A, 3.0 * base, R)
+    assert L1 < 1.0 < L3
 
 
 def test_zero_output_layer_is_spai0():
