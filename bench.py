@@ -197,6 +197,66 @@ def run_reference(args):
     return 0
 
 
+LEARN_TRAIN = ((20, 11), (26, 12), (32, 13), (40, 14))  # (elements per side, inclusion seed)
+
+
+def learned_form(amg, torch, solver, f, tol, u_ref, t_spai0, it_spai0, steps):
+    """Learned smoother: train the block-smoother network on the GPU on four
+    smaller meshes of the same material model (error samples the SPAI0
+    V-cycle leaves, and white noise), then solve the benchmark system with it
+    in place of SPAI0 on level 0; SPAI0 stays the fallback and the judge."""
+    import q1elasticity as q
+    dev = f.device
+    s = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    train_solvers = []
+    T = amg.Trainer(amg.learned_init(0), lr=3e-3)
+    for k, (n, seed) in enumerate(LEARN_TRAIN):
+        p = q.inclusions(n, seed=seed)
+        S = amg.AMG(torch.from_numpy(p.row_ptr).to(dev), torch.from_numpy(p.col).to(dev),
+                    torch.from_numpy(p.val).to(dev), torch.from_numpy(p.B).to(dev))
+        T.add_generated(S, 8, seed=100 + k)
+        train_solvers.append(S)
+    loss0, _ = T.eval()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    T.step(200)
+    loss1, _ = T.eval()
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    w = T.params()
+    T.close()
+    del train_solvers
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    fb = solver.set_learned_smoother(w)
+    torch.cuda.synchronize()
+    t_infer = time.perf_counter() - t2
+    st = solver.stats()
+    out = {"training": {"meshes": [f"{n}^3 seed {sd}" for n, sd in LEARN_TRAIN],
+                        "samples_per_mesh": 8, "adam_steps": 200, "lr": 3e-3,
+                        "loss_before": loss0, "loss_after": loss1, "train_s": t_train,
+                        "problem_setup_s": t1 - t0},
+           "inference_s": t_infer, "fallback": fb, "lambda_max_MA": st["learned_lambda"],
+           "lambda_max_MA_spai0": st["spai0_lambda"], "spai0_value": t_spai0,
+           "spai0_iterations": it_spai0,
+           "vcycle": "FP64; level 0 smoothed with learned symmetric 3x3 blocks"}
+    solver.solve(f, tol=tol, maxiter=5000)  # warm-up (graph capture)
+    times = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        u_l, it_l, res_l, st_l = solver.solve(f, tol=tol, maxiter=5000)
+        e1.record(s)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    solver.clear_learned_smoother()
+    out.update(value=float(np.mean(times)), iterations=it_l, rel_resid=res_l, status=st_l,
+               err_vs_fp64_solution=float(torch.linalg.norm(u_l - u_ref) / torch.linalg.norm(u_ref)),
+               speedup_vs_fp64=t_spai0 / float(np.mean(times)))
+    return out
+
+
 def run_batch(args, amg, torch):
     """64 independent boxes (seeded sizes 20^3-60^3, nu in [0.2, 0.45], 1-16
     random unit body loads each): one batched solve of every right-hand side
@@ -287,7 +347,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"],
                     help="V-cycle precision of the main line (CG stays FP64)")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the FP32/BF16 V-cycle comparison on the same workload")
+                    help="skip the FP32/BF16 V-cycle and learned-smoother comparisons "
+                         "on the same workload")
     ap.add_argument("--loop-mode", type=int, default=0,
                     help="1: host-launched CG steps (for profilers); 0: device while loop")
     args = ap.parse_args()
@@ -429,6 +490,10 @@ def main():
             del sol
         for name in ("fp32", "bf16"):
             forms[name]["speedup_vs_fp64"] = forms["fp64"]["value"] / forms[name]["value"]
+        if args.precision == "fp64":
+            forms["learned"] = learned_form(amg, torch, solver, f, tol, u_ref,
+                                            forms["fp64"]["value"], forms["fp64"]["iterations"],
+                                            args.steps)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()

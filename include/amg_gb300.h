@@ -104,6 +104,11 @@ typedef struct {
     int64_t bytes_matrices;    /* A, P, R of all levels + smoother + coarse inverse */
     int64_t bytes_total;       /* everything the handle holds on the device */
     double operator_complexity;/* sum of nnz over levels / nnz of the finest A */
+    int32_t learned;           /* 1 while level 0 smooths with learned 3x3 blocks */
+    int32_t reserved0;
+    double learned_lambda;     /* lambda_max(M A) estimate of the last learned smoother
+                                  offered to amg_set_learned_smoother (0 if none) */
+    double spai0_lambda;       /* the same estimate for SPAI0 (0 until one was offered) */
 } amg_stats;
 
 /* Fill *prm with the defaults listed above.  Returns AMG_OK. */
@@ -237,18 +242,19 @@ void amg_batch_free(amg_batch h);
 #define AMG_LEARNED_NPARAM 1222
 
 /* Replace the fine-level SPAI0 smoother of h by learned 3x3 blocks
- * M_I = S_I (I + Delta_I) S_I, S_I = diag(sqrt(SPAI0 diagonal of node I)),
- * Delta_I the symmetric 3x3 matrix [[o0,o3,o4],[o3,o1,o5],[o4,o5,o2]] with
+ * M_I = S_I L_I L_I^T S_I, S_I = diag(sqrt(SPAI0 diagonal of node I)),
+ * L_I the lower triangular factor [[1+o0,0,0],[o3,1+o1,0],[o4,o5,1+o2]] with
  * o = W2 relu(W1 x_I + b1) + b2 and x_I the node's unit-free features (the
  * diagonal block over its Frobenius norm, the sum of squared and the largest
  * neighbour-block norms relative to it, the block count / 27).  The network
  * runs on the tensor cores (BF16 operands, FP32 accumulation).  The paper
  * uses a fixed smoother (Sec. 3 names SPAI); this data-driven stand-in keeps
- * SPAI0 as its fallback: if any I + Delta_I is not positive definite the
- * call keeps SPAI0 and sets *fell_back (host) to 1; if 20 power iterations
- * estimate lambda_max(M A) >= 1.9 on level 0 (the smoothing step would not
- * contract the energy norm, and the V-cycle could stop being positive
- * definite) it keeps SPAI0 and sets *fell_back to 2.  params is host memory.
+ * SPAI0 as its fallback: if any L_I is singular (M_I only semidefinite) the
+ * call keeps SPAI0 and sets *fell_back (host) to 1; if the estimate of
+ * lambda_max(M A) on level 0 (20 power iterations) reaches max(1.9, the same
+ * estimate for SPAI0) it keeps SPAI0 and sets *fell_back to 2 (the smoothing
+ * step contracts the energy norm only while lambda_max(M A) < 2, and beyond
+ * that the V-cycle can stop being positive definite).  params is host memory.
  * Later amg_solve / amg_apply_vcycle calls use the blocks (FP64 V-cycle). */
 int amg_set_learned_smoother(amg_handle h, const float *params, int32_t *fell_back, void *stream);
 

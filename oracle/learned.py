@@ -8,12 +8,14 @@ node, produced by a small MLP from unit-free features of the node's block row:
                      max_{J != I} ||A_IJ||_F / ||A_II||_F,
                      (number of blocks in row I) / 27;
   network:           h = relu(W1 x + b1) (64), o = W2 h + b2 (6);
-  smoother block:    M_I = S_I (I + Delta_I) S_I, S_I = diag(sqrt(m)) with m the
+  smoother block:    M_I = S_I L_I L_I^T S_I, S_I = diag(sqrt(m)) with m the
                      damped SPAI0 diagonal of the node's three scalar rows and
-                     Delta_I the symmetric 3x3 matrix
-                     [[o0, o3, o4], [o3, o1, o5], [o4, o5, o2]].
+                     L_I the lower-triangular factor
+                     [[1 + o0, 0, 0], [o3, 1 + o1, 0], [o4, o5, 1 + o2]].
 
-A zero output layer gives M_I = diag(m): plain SPAI0.  The training loss is
+M_I is symmetric positive semidefinite for every output, and definite unless
+a diagonal entry of L_I is zero.  A zero output layer gives M_I = diag(m):
+plain SPAI0.  The training loss is
 the energy-norm error reduction of one smoothing step over error samples e_s,
 L = (1/S) sum_s ||e_s - M A e_s||_A^2 / ||e_s||_A^2; with r = A e and
 e' = e - M r its gradient with respect to M_I is
@@ -30,7 +32,7 @@ import scipy.sparse as sp
 NF = 12        # features
 NH = 64        # hidden units
 NO = 6         # outputs (symmetric 3x3)
-SYM = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+TRI = [(0, 0), (1, 1), (2, 2), (1, 0), (2, 0), (2, 1)]   # entry of L_I set by o_k
 
 
 def features(row_ptr, col, val):
@@ -83,19 +85,21 @@ def forward(p, X):
     return o, h, pre
 
 
-def delta_from_output(o):
-    D = np.zeros((o.shape[0], 3, 3))
-    for k, (a, b) in enumerate(SYM):
-        D[:, a, b] = o[:, k]
-        D[:, b, a] = o[:, k]
-    return D
+def factor_from_output(o):
+    """L_I = I + the lower-triangular matrix holding the six outputs, [N, 3, 3]."""
+    L = np.zeros((o.shape[0], 3, 3))
+    L[:] = np.eye(3)
+    for k, (a, b) in enumerate(TRI):
+        L[:, a, b] += o[:, k]
+    return L
 
 
 def smoother_blocks(m, o):
-    """M_I = S (I + Delta) S with S = diag(sqrt(m_I)), [N, 3, 3]."""
+    """M_I = S L L^T S with S = diag(sqrt(m_I)), [N, 3, 3]."""
     S = np.sqrt(np.asarray(m).reshape(-1, 3))
-    M = np.eye(3)[None] + delta_from_output(o)
-    return S[:, :, None] * M * S[:, None, :]
+    L = factor_from_output(o)
+    K = L @ np.transpose(L, (0, 2, 1))
+    return S[:, :, None] * K * S[:, None, :]
 
 
 def apply_blocks(M, r):
@@ -124,10 +128,11 @@ def grad_params(p, X, m, A, R):
     M = smoother_blocks(m, o)
     L, GM = loss_and_grad_M(A, M, R)
     S = np.sqrt(np.asarray(m).reshape(-1, 3))
-    GD = S[:, :, None] * GM * S[:, None, :]          # dL/dDelta (entrywise)
+    GK = S[:, :, None] * GM * S[:, None, :]          # dL/dK, K = L L^T
+    GL = (GK + np.transpose(GK, (0, 2, 1))) @ factor_from_output(o)   # dL/dL
     do = np.zeros((X.shape[0], NO))
-    for k, (a, b) in enumerate(SYM):
-        do[:, k] = GD[:, a, a] if a == b else GD[:, a, b] + GD[:, b, a]
+    for k, (a, b) in enumerate(TRI):
+        do[:, k] = GL[:, a, b]
     gW2 = do.T @ h
     gb2 = do.sum(0)
     dh = (do @ p["W2"]) * (pre > 0)

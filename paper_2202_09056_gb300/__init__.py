@@ -56,7 +56,9 @@ class LevelDesc(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("nlevels", ctypes.c_int32), ("coarse_n", ctypes.c_int32),
                 ("setup_seconds", ctypes.c_double), ("bytes_matrices", ctypes.c_int64),
-                ("bytes_total", ctypes.c_int64), ("operator_complexity", ctypes.c_double)]
+                ("bytes_total", ctypes.c_int64), ("operator_complexity", ctypes.c_double),
+                ("learned", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("learned_lambda", ctypes.c_double), ("spai0_lambda", ctypes.c_double)]
 
 
 class BatchDesc(ctypes.Structure):
@@ -262,7 +264,7 @@ class AMG:
 
     def set_learned_smoother(self, params, stream=None) -> int:
         """Use the network's 3x3 blocks on level 0.  Returns 0, or the reason it
-        kept SPAI0: 1 a block not positive definite, 2 lambda_max(M A) >= 1.9."""
+        kept SPAI0: 1 a singular block, 2 lambda_max(M A) >= max(1.9, SPAI0's)."""
         w = np.ascontiguousarray(params, dtype=np.float32)
         if w.size != LEARNED_NPARAM:
             raise ValueError(f"expected {LEARNED_NPARAM} parameters")

@@ -238,6 +238,7 @@ struct amg_handle_s {
     double setup_seconds = 0.0;
     int learned = 0;              // level 0 smooths with the learned blocks
     double learned_lambda = 0.0;  // estimated lambda_max(M A) of the learned smoother
+    double spai0_lambda = 0.0;    // the same estimate for SPAI0 (0 until first needed)
 };
 
 

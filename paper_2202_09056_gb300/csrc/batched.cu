@@ -38,6 +38,8 @@ struct BSell {
     int *col = nullptr;
     double *val = nullptr;
     int *s_inst = nullptr, *s_local = nullptr, *s_G = nullptr;
+    int *perm = nullptr;         // concatenated slot -> row maps of the sorted parts
+    int64_t *s_pbase = nullptr;  // per slice: its first slot in perm, or -1 (natural order)
 };
 
 struct BArgs {
@@ -46,6 +48,8 @@ struct BArgs {
     const int *col;
     const double *val;
     const int *s_inst, *s_local, *s_G;
+    const int *perm;
+    const int64_t *s_pbase;
     const int *K;           // right-hand sides per instance
     const int *nrows;       // block rows of the output space per instance
     const int64_t *xoff;    // instance offsets of x's space
@@ -67,9 +71,10 @@ __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
         const int inst = a.s_inst[s];
         if (!a.enable[inst]) continue;
         const int G = a.s_G[s], sub = lane & (G - 1);
-        const int row = a.s_local[s] * (32 / G) + lane / G;
+        const int64_t pb = a.s_pbase[s];
+        const int row = pb >= 0 ? a.perm[pb + lane / G] : a.s_local[s] * (32 / G) + lane / G;
         const int K = a.K[inst];
-        const bool live = row < a.nrows[inst];
+        const bool live = row >= 0 && row < a.nrows[inst];
         const int64_t base = a.slice_ptr[s];
         const int w = (int)((a.slice_ptr[s + 1] - base) >> 5);
         const double *vp = a.val + base * BB + lane;
@@ -171,6 +176,8 @@ static int launch_bspmm(const BSell &S, int kt, int mode, BArgs a, const Geom &g
     a.s_inst = S.s_inst;
     a.s_local = S.s_local;
     a.s_G = S.s_G;
+    a.perm = S.perm;
+    a.s_pbase = S.s_pbase;
     int grid = (S.nslices + BT / 32 - 1) / (BT / 32);
     grid = std::min(grid, g.num_sms * 16);
     if (S.br == 3 && S.bc == 3) return bspmm_mode<3, 3>(S, kt, mode, a, grid, s);
@@ -765,8 +772,8 @@ static int concat_sell(amg_batch h, int l, int which, BSell *out)
     cudaStream_t s = h->stream;
     BSell S;
     std::vector<int> s_inst, s_local, s_G;
-    std::vector<int64_t> sp(1, 0);
-    int64_t nslots = 0;
+    std::vector<int64_t> sp(1, 0), s_pbase;
+    int64_t nslots = 0, nperm = 0;
     int bb = 0;
     std::vector<const Sell<double> *> parts(h->ninst, nullptr);
     for (int i = 0; i < h->ninst; ++i) {
@@ -781,13 +788,16 @@ static int concat_sell(amg_batch h, int l, int which, BSell *out)
         AMG_TRY_CUDA(cudaMemcpyAsync(xsp.data(), X.slice_ptr, sizeof(int64_t) * (X.nslices + 1),
                                      cudaMemcpyDeviceToHost, s));
         AMG_TRY_CUDA(cudaStreamSynchronize(s));
+        const int rps = 32 / X.G;
         for (int k = 0; k < X.nslices; ++k) {
             s_inst.push_back(i);
             s_local.push_back(k);
             s_G.push_back(X.G);
             sp.push_back(nslots + xsp[k + 1]);
+            s_pbase.push_back(X.perm ? nperm + (int64_t)k * rps : -1);
         }
         nslots += X.nslots;
+        if (X.perm) nperm += (int64_t)X.nslices * rps;
     }
     S.nslices = (int)s_inst.size();
     if (S.nslices == 0) {
@@ -798,12 +808,20 @@ static int concat_sell(amg_batch h, int l, int which, BSell *out)
     AMG_TRY(upload(h->mem, s_inst, &S.s_inst, s));
     AMG_TRY(upload(h->mem, s_local, &S.s_local, s));
     AMG_TRY(upload(h->mem, s_G, &S.s_G, s));
+    AMG_TRY(upload(h->mem, s_pbase, &S.s_pbase, s));
+    AMG_TRY(h->mem.alloc_n(&S.perm, (size_t)std::max<int64_t>(nperm, 1)));
     AMG_TRY(h->mem.alloc_n(&S.col, (size_t)nslots));
     AMG_TRY(h->mem.alloc_n(&S.val, (size_t)nslots * bb));
-    int64_t at = 0;
+    int64_t at = 0, pat = 0;
     for (int i = 0; i < h->ninst; ++i) {
         if (!parts[i]) continue;
         const Sell<double> &X = *parts[i];
+        if (X.perm) {
+            const int64_t np = (int64_t)X.nslices * (32 / X.G);
+            AMG_TRY_CUDA(cudaMemcpyAsync(S.perm + pat, X.perm, sizeof(int) * np,
+                                         cudaMemcpyDeviceToDevice, s));
+            pat += np;
+        }
         AMG_TRY_CUDA(cudaMemcpyAsync(S.col + at, X.col, sizeof(int) * X.nslots,
                                      cudaMemcpyDeviceToDevice, s));
         AMG_TRY_CUDA(cudaMemcpyAsync(S.val + at * bb, X.val, sizeof(double) * X.nslots * bb,

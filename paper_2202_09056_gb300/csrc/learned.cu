@@ -5,12 +5,12 @@
 // neighbour-block norms and the largest neighbour-block norm relative to it,
 // the number of blocks / 27), computes h = relu(W1 x + b1) (64 units) and
 // o = W2 h + b2 (6 outputs), and the smoother block is
-//     M_I = S_I (I + Delta(o)) S_I,   S_I = diag(sqrt(m_I)),
-// m_I the damped SPAI0 diagonal of the node's three rows and Delta(o) the
-// symmetric 3x3 matrix [[o0,o3,o4],[o3,o1,o5],[o4,o5,o2]].  A zero output
-// layer is exactly SPAI0; M_I is symmetric, so the V-cycle stays symmetric
-// for CG; a block whose I + Delta is not positive definite makes the whole
-// smoother fall back to SPAI0.
+//     M_I = S_I L_I L_I^T S_I,   S_I = diag(sqrt(m_I)),
+// m_I the damped SPAI0 diagonal of the node's three rows and L_I the lower
+// triangular factor [[1+o0,0,0],[o3,1+o1,0],[o4,o5,1+o2]].  A zero output
+// layer is exactly SPAI0; M_I is symmetric positive semidefinite for every
+// output, so the V-cycle stays symmetric for CG; a block with a zero on the
+// diagonal of L_I (singular) makes the whole smoother fall back to SPAI0.
 //
 // The two dense layers run on the tensor cores (mma.sync m16n8k16, BF16
 // operands, FP32 accumulation): one warp per 16-row tile, the first layer's
@@ -173,22 +173,24 @@ __global__ void mlp_forward_kernel(const __nv_bfloat16 *__restrict__ X, int nrow
     }
 }
 
-// M_I = S (I + Delta) S and the positive-definiteness check of I + Delta.
+// M_I = S L L^T S and the check that L (hence M_I) is nonsingular.
 __global__ void mblocks_kernel(const float *__restrict__ O, const double *__restrict__ m, int nrows,
                                double *__restrict__ Mb, int *__restrict__ bad)
 {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nrows) return;
     const float *o = O + (int64_t)I * LOP;
-    double D[3][3] = {{1.0 + o[0], o[3], o[4]}, {o[3], 1.0 + o[1], o[5]}, {o[4], o[5], 1.0 + o[2]}};
+    const double L[3][3] = {{1.0 + o[0], 0.0, 0.0}, {o[3], 1.0 + o[1], 0.0}, {o[4], o[5], 1.0 + o[2]}};
     const double S[3] = {sqrt(m[3 * (int64_t)I]), sqrt(m[3 * (int64_t)I + 1]), sqrt(m[3 * (int64_t)I + 2])};
-    for (int a = 0; a < 3; ++a)  // (S_a S_b) D_ab: bitwise symmetric
-        for (int b = 0; b < 3; ++b) Mb[(int64_t)I * 9 + a * 3 + b] = (S[a] * S[b]) * D[a][b];
-    const double m1 = D[0][0], m2 = D[0][0] * D[1][1] - D[0][1] * D[1][0];
-    const double m3 = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) -
-                      D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
-                      D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
-    if (!(m1 > 0.0 && m2 > 0.0 && m3 > 0.0)) atomicOr(bad, 1);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            // K_ab = sum_k L_ak L_bk in k order, (S_a S_b) K_ab: bitwise symmetric
+            double k = 0.0;
+            for (int c = 0; c < 3; ++c) k += L[a][c] * L[b][c];
+            Mb[(int64_t)I * 9 + a * 3 + b] = (S[a] * S[b]) * k;
+        }
+    const double det = L[0][0] * L[1][1] * L[2][2];
+    if (!(det * det > 0.0)) atomicOr(bad, 1);
 }
 
 // ---------------------------------------------------------------- training kernels
@@ -253,24 +255,34 @@ __global__ void lgrad_kernel(const double *__restrict__ g, const double *__restr
         for (int b = 0; b < 3; ++b) G[(int64_t)I * 9 + a * 3 + b] += c * g[3 * (int64_t)I + a] * r[3 * (int64_t)I + b];
 }
 
-// dL/do from dL/dM: dDelta = S G S; diagonal outputs take dDelta_aa, the
-// off-diagonal ones dDelta_ab + dDelta_ba.
-__global__ void ldo_kernel(const double *__restrict__ G, const double *__restrict__ m, int nrows,
-                           float *__restrict__ dO)
+// dL/do from dL/dM: dK = S G S (K = L L^T), dL/dL = (dK + dK^T) L, and each
+// output takes the entry of dL/dL at its place in L.
+__global__ void ldo_kernel(const double *__restrict__ G, const double *__restrict__ m,
+                           const float *__restrict__ O, int nrows, float *__restrict__ dO)
 {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nrows) return;
     double S[3];
     for (int a = 0; a < 3; ++a) S[a] = sqrt(m[3 * (int64_t)I + a]);
+    const float *o = O + (int64_t)I * LOP;
+    const double L[3][3] = {{1.0 + o[0], 0.0, 0.0}, {o[3], 1.0 + o[1], 0.0}, {o[4], o[5], 1.0 + o[2]}};
     const double *gm = G + (int64_t)I * 9;
-    auto gd = [&](int a, int b) { return S[a] * gm[a * 3 + b] * S[b]; };
+    double Gs[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            Gs[a][b] = S[a] * gm[a * 3 + b] * S[b] + S[b] * gm[b * 3 + a] * S[a];
+    auto gl = [&](int a, int b) {
+        double v = 0.0;
+        for (int c = 0; c < 3; ++c) v += Gs[a][c] * L[c][b];
+        return v;
+    };
     float *d = dO + (int64_t)I * LOP;
-    d[0] = (float)gd(0, 0);
-    d[1] = (float)gd(1, 1);
-    d[2] = (float)gd(2, 2);
-    d[3] = (float)(gd(0, 1) + gd(1, 0));
-    d[4] = (float)(gd(0, 2) + gd(2, 0));
-    d[5] = (float)(gd(1, 2) + gd(2, 1));
+    d[0] = (float)gl(0, 0);
+    d[1] = (float)gl(1, 1);
+    d[2] = (float)gl(2, 2);
+    d[3] = (float)gl(1, 0);
+    d[4] = (float)gl(2, 0);
+    d[5] = (float)gl(2, 1);
     d[6] = d[7] = 0.0f;
 }
 
@@ -541,7 +553,7 @@ static int trainer_eval(amg_trainer t, cudaStream_t s)
             count_launch(2);
             AMG_TRY_CUDA(cudaGetLastError());
         }
-        ldo_kernel<<<(P.nrows + 255) / 256, 256, 0, s>>>(P.G, L0.M, P.nrows, P.dO);
+        ldo_kernel<<<(P.nrows + 255) / 256, 256, 0, s>>>(P.G, L0.M, P.O, P.nrows, P.dO);
         lbackward_kernel<<<t->nparts, BW_T, 0, s>>>(P.nrows, P.X, P.H, P.dO, t->net.W2, t->part);
         lreduce_kernel<<<(LNPARAM + 255) / 256, 256, 0, s>>>(t->part, t->nparts, t->grad);
         count_launch(3);
@@ -785,12 +797,30 @@ int amg_set_learned_smoother(amg_handle h, const float *params, int32_t *fell_ba
         st = AMG_ERR_CUDA;
     double lam = 0.0;
     if (st >= 0 && !hb) st = smoother_lambda_max(h, L0.Mb, tmp, s, &lam);
+    if (st >= 0 && !hb && h->spai0_lambda == 0.0) {
+        // the same estimate for SPAI0: blocks from a zero network output
+        float *O0 = nullptr;
+        double *M0 = nullptr;
+        st = tmp.alloc_n(&O0, (size_t)L0.A.nbr * LOP);
+        if (st >= 0) st = tmp.alloc_n(&M0, (size_t)L0.A.nbr * 9);
+        if (st >= 0 && cudaMemsetAsync(O0, 0, sizeof(float) * L0.A.nbr * LOP, s) != cudaSuccess)
+            st = AMG_ERR_CUDA;
+        if (st >= 0) {
+            mblocks_kernel<<<(L0.A.nbr + 255) / 256, 256, 0, s>>>(O0, L0.M, (int)L0.A.nbr, M0, bad);
+            count_launch(1);
+            if (cudaGetLastError() != cudaSuccess) st = AMG_ERR_CUDA;
+        }
+        double lam0 = 0.0;
+        if (st >= 0) st = smoother_lambda_max(h, M0, tmp, s, &lam0);
+        if (st >= 0) h->spai0_lambda = lam0;
+    }
     tmp.release_all();
     cudaStreamSynchronize(s);
     if (st < 0) return st;
-    // back to SPAI0 when a block is not positive definite (1) or when the
-    // smoothing iteration would not contract the energy norm (2)
-    const int fb = hb ? 1 : (lam >= 1.9 ? 2 : 0);
+    // back to SPAI0 when a block is singular (1) or when the learned smoother
+    // is less stable than both the bound 1.9 and SPAI0 itself (2): the
+    // smoothing step contracts the energy norm only while lambda_max(M A) < 2
+    const int fb = hb ? 1 : (lam >= std::max(1.9, h->spai0_lambda) ? 2 : 0);
     h->learned = fb ? 0 : 1;
     h->learned_lambda = lam;
     if (fell_back) *fell_back = fb;

@@ -22,6 +22,7 @@
 // bitwise reproducible for a fixed launch.
 #include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "amg_internal.cuh"
 
@@ -229,21 +230,6 @@ template int launch_sell<__nv_bfloat16, float>(const Sell<__nv_bfloat16> &, int,
                                                SellArgs<float>, const Geom &, cudaStream_t, int *);
 
 // ---------------------------------------------------------------- conversion
-__global__ void sell_width_kernel(const int *__restrict__ rp, int nrows, int nslices, int G,
-                                  const int *__restrict__ perm, int *__restrict__ width)
-{
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nslices) return;
-    const int rps = 32 / G;
-    int w = 0;
-    for (int t = 0; t < rps; ++t) {
-        const int slot = s * rps + t;
-        const int row = perm ? perm[slot] : slot;
-        if (row >= 0 && row < nrows) w = max(w, (rp[row + 1] - rp[row] + G - 1) / G);
-    }
-    width[s] = w;
-}
-
 template <class T>
 __global__ void sell_fill_kernel(const int *__restrict__ rp, const int *__restrict__ bcol,
                                  const double *__restrict__ bval, int nrows, int nslices, int bb,
@@ -272,6 +258,53 @@ __global__ void sell_fill_kernel(const int *__restrict__ rp, const int *__restri
     }
 }
 
+// Slot order of a sliced copy.  Slice widths follow the longest lane, so
+// rows of uneven length (P and R, whose length is the number of aggregates a
+// node's neighbourhood touches; coarse A) waste slots.  When the natural
+// order pads more than 5 %, rows are sorted by length, longest first, inside
+// windows of 32 slices (SELL-C-sigma); a window keeps rows that are close in
+// the numbering together, so the x gather keeps its locality.
+static void sell_order(const std::vector<int> &rp, int G, int nslices, std::vector<int> *perm,
+                       std::vector<int> *width)
+{
+    const int nrows = (int)rp.size() - 1, rps = 32 / G;
+    auto lanes = [&](int row) { return row < 0 ? 0 : (rp[row + 1] - rp[row] + G - 1) / G; };
+    auto widths = [&](const std::vector<int> *pm, std::vector<int> *w) {
+        int64_t slots = 0;
+        w->assign(nslices, 0);
+        for (int sl = 0; sl < nslices; ++sl) {
+            int m = 0;
+            for (int t = 0; t < rps; ++t) {
+                const int slot = sl * rps + t;
+                const int row = pm ? (*pm)[slot] : (slot < nrows ? slot : -1);
+                m = std::max(m, lanes(row));
+            }
+            (*w)[sl] = m;
+            slots += 32LL * m;
+        }
+        return slots;
+    };
+    perm->clear();
+    const int64_t nnzb = rp[nrows] - rp[0];
+    const int64_t natural = widths(nullptr, width);
+    if (nnzb == 0 || (double)(natural - nnzb) <= 0.05 * (double)nnzb) return;
+    perm->assign((size_t)nslices * rps, -1);
+    const int win = 32 * rps;
+    std::vector<int> idx;
+    for (int r0 = 0; r0 < nrows; r0 += win) {
+        const int r1 = std::min(nrows, r0 + win);
+        idx.resize(r1 - r0);
+        for (int r = r0; r < r1; ++r) idx[r - r0] = r;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+            return rp[a + 1] - rp[a] > rp[b + 1] - rp[b];
+        });
+        std::copy(idx.begin(), idx.end(), perm->begin() + r0);
+    }
+    std::vector<int> w2;
+    if (widths(perm, &w2) < natural) *width = w2;
+    else perm->clear();
+}
+
 template <class T>
 int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, double *padding)
 {
@@ -288,18 +321,14 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
     S.G = G;
     S.nslices = (B.nbr + 32 / G - 1) / (32 / G);
     const int bb = B.br * B.bc;
-    int *width = nullptr;
-    AMG_TRY_CUDA(cudaMallocAsync((void **)&width, sizeof(int) * std::max(S.nslices, 1), s));
-    if (S.nslices > 0) {
-        sell_width_kernel<<<(S.nslices + 255) / 256, 256, 0, s>>>(B.row_ptr, B.nbr, S.nslices,
-                                                                  G, nullptr, width);
-        count_launch(1);
-        AMG_TRY_CUDA(cudaGetLastError());
+    std::vector<int> rp(B.nbr + 1, 0);
+    if (B.nbr > 0) {
+        AMG_TRY_CUDA(cudaMemcpyAsync(rp.data(), B.row_ptr, sizeof(int) * (B.nbr + 1),
+                                     cudaMemcpyDeviceToHost, s));
+        AMG_TRY_CUDA(cudaStreamSynchronize(s));
     }
-    std::vector<int> wh(std::max(S.nslices, 1));
-    AMG_TRY_CUDA(cudaMemcpyAsync(wh.data(), width, sizeof(int) * S.nslices, cudaMemcpyDeviceToHost, s));
-    AMG_TRY_CUDA(cudaStreamSynchronize(s));
-    AMG_TRY_CUDA(cudaFreeAsync(width, s));
+    std::vector<int> perm, wh;
+    sell_order(rp, G, S.nslices, &perm, &wh);
     std::vector<int64_t> sp(S.nslices + 1, 0);
     for (int i = 0; i < S.nslices; ++i) sp[i + 1] = sp[i] + 32LL * wh[i];
     S.nslots = sp[S.nslices];
@@ -308,13 +337,18 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
     AMG_TRY(keep.alloc_n(&S.val, (size_t)std::max<int64_t>(S.nslots, 1) * bb));
     AMG_TRY_CUDA(cudaMemcpyAsync(S.slice_ptr, sp.data(), sizeof(int64_t) * (S.nslices + 1),
                                  cudaMemcpyHostToDevice, s));
+    if (!perm.empty()) {
+        AMG_TRY(keep.alloc_n(&S.perm, perm.size()));
+        AMG_TRY_CUDA(cudaMemcpyAsync(S.perm, perm.data(), sizeof(int) * perm.size(),
+                                     cudaMemcpyHostToDevice, s));
+    }
     if (S.nslices > 0) {
         sell_fill_kernel<T><<<(S.nslices * 32 + 127) / 128, 128, 0, s>>>(
-            B.row_ptr, B.col, B.val, B.nbr, S.nslices, bb, G, nullptr, S.slice_ptr, S.col, S.val);
+            B.row_ptr, B.col, B.val, B.nbr, S.nslices, bb, G, S.perm, S.slice_ptr, S.col, S.val);
         count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
     }
-    AMG_TRY_CUDA(cudaStreamSynchronize(s));  // sp is host memory
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));  // sp and perm are host memory
     if (padding) *padding = B.nnzb ? (double)(S.nslots - B.nnzb) / (double)B.nnzb : 0.0;
     *out = S;
     return AMG_OK;

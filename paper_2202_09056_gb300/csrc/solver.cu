@@ -990,6 +990,9 @@ int amg_get_stats(amg_handle h, amg_stats *out)
     out->bytes_matrices = bytes;
     out->bytes_total = (int64_t)h->mem.bytes;
     out->operator_complexity = nnz0 ? (double)nnz / (double)nnz0 : 0.0;
+    out->learned = h->learned;
+    out->learned_lambda = h->learned_lambda;
+    out->spai0_lambda = h->spai0_lambda;
     return AMG_OK;
 }
 

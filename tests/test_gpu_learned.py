@@ -5,7 +5,8 @@ accuracy; the device gradient of the training loss matches the oracle's
 analytic (finite-difference-pinned) gradient to BF16 accuracy; with a zero
 output layer the solve is the SPAI0 solve; a solve with learned blocks
 matches the oracle run with the same blocks (iterations +-1, solution 1e-7);
-a block that is not positive definite falls back to SPAI0; training lowers
+a singular block, or a smoother with lambda_max(M A) >= max(1.9, SPAI0's),
+falls back to SPAI0; training lowers
 the energy-norm loss, the result passes the stability check, and the CG
 iteration count drops on a mesh it has not seen.
 """
@@ -27,28 +28,30 @@ def _dev(p):
             torch.from_numpy(p.val).to(d), torch.from_numpy(p.B).to(d))
 
 
-def _params(seed=3, w2=0.08):
+def _params(seed=3, w2=0.08, bdiag=0.0):
     rng = np.random.default_rng(seed)
     w = amg.learned_init(seed)
     w[64 * 12:64 * 12 + 64] = 0.05 * rng.standard_normal(64)
     w[64 * 13:64 * 13 + 6 * 64] = w2 * rng.standard_normal(6 * 64)
     w[-6:] = 0.02 * rng.standard_normal(6)
+    w[-6:-3] += bdiag   # shrink the factor's diagonal: lambda_max(M A) below SPAI0's
     return w.astype(np.float32)
 
 
 def test_forward_matches_oracle_blocks():
     p = q.make_problem((7, 6, 8), traction=(0, 0, -1), inclusion_frac=0.2)
     G = amg.AMG(*_dev(p), coarse_enough=150)
-    w = _params()
+    w = _params(bdiag=-0.15)
     assert not G.set_learned_smoother(w)
     Mb = G.learned_blocks()
     m = G.export(0)["M"]
     X = lo.features(p.row_ptr, p.col, p.val)
     out, _, _ = lo.forward(lo.unflatten(w.astype(np.float64)), X)
     S = np.sqrt(m.reshape(-1, 3))
-    Dg = Mb / (S[:, :, None] * S[:, None, :]) - np.eye(3)
-    Do = lo.delta_from_output(out)
-    assert np.abs(Dg - Do).max() <= 3e-2 * np.abs(Do).max() + 1e-4
+    Kg = Mb / (S[:, :, None] * S[:, None, :])
+    Lo = lo.factor_from_output(out)
+    Ko = Lo @ np.transpose(Lo, (0, 2, 1))
+    assert np.abs(Kg - Ko).max() <= 3e-2 * np.abs(Ko - np.eye(3)).max() + 1e-4
     np.testing.assert_allclose(Mb, np.transpose(Mb, (0, 2, 1)), rtol=0, atol=0)
 
 
@@ -97,16 +100,22 @@ def test_learned_solve_matches_oracle_with_same_blocks():
     assert np.linalg.norm(z - H.vcycle(r)) <= 1e-9 * np.linalg.norm(z)
 
 
-def test_fallback_to_spai0_when_not_positive_definite():
+def test_fallback_to_spai0_when_singular_or_unstable():
     p = q.make_problem((6, 6, 6), traction=(0, 0, -1))
     G = amg.AMG(*_dev(p), coarse_enough=150)
     fb = torch.from_numpy(p.f).cuda()
     _, it0, _, _ = G.solve(fb)
-    w = amg.learned_init(2)
-    w[-6] = -5.0                      # 1 + o0 < 0 on every node
-    assert G.set_learned_smoother(w)  # fell back
+    w = amg.learned_init(2)           # W2 = 0: o = b2 on every node
+    w[-6] = -1.0                      # 1 + o0 = 0: every block singular
+    assert G.set_learned_smoother(w) == 1
+    assert G.stats()["learned"] == 0
     _, it1, _, st = G.solve(fb)
     assert st == amg.AMG_OK and it1 == it0
+    w[-6:-3] = 2.0                    # L = 3 I: M = 9 x SPAI0, lambda_max(M A) > 2
+    assert G.set_learned_smoother(w) == 2
+    assert G.stats()["learned_lambda"] > 2.0
+    _, it2, _, st = G.solve(fb)
+    assert st == amg.AMG_OK and it2 == it0
 
 
 def test_training_lowers_loss_and_iterations():
@@ -126,6 +135,10 @@ def test_training_lowers_loss_and_iterations():
     fb = torch.from_numpy(test.f).cuda()
     _, it_spai0, _, _ = G.solve(fb)
     assert not G.set_learned_smoother(T.params())
+    info = G.stats()
+    assert info["learned"] == 1 and 0.5 < info["learned_lambda"] < max(1.9, info["spai0_lambda"]), info
     _, it_learned, res, st = G.solve(fb)
     assert st == amg.AMG_OK and res <= 1e-8
     assert it_learned < it_spai0, (it_learned, it_spai0)
+    G.clear_learned_smoother()
+    assert G.stats()["learned"] == 0

@@ -5,7 +5,10 @@ oracle's block smoother.
 * dL/dM equals the derivative of the loss written densely;
 * a zero output layer reproduces SPAI0: same blocks, same V-cycle, same CG
   iterations as the scalar SPAI0 hierarchy;
-* features are unit-free (scaling A leaves them unchanged).
+* features are unit-free (scaling A leaves them unchanged);
+* the output-to-block map puts each output in its place of the lower
+  triangular factor (closed forms for single outputs) and gives symmetric
+  positive semidefinite blocks for any output.
 """
 import numpy as np
 import pytest
@@ -34,6 +37,30 @@ def test_features_are_unit_free():
     clamped = p.coords[:, 0] == 0.0
     np.testing.assert_allclose(X1[clamped, :9], np.tile(np.eye(3).ravel() / np.sqrt(3), (clamped.sum(), 1)))
     assert (X1[clamped, 9:11] == 0).all()
+
+
+def test_factor_mapping_and_definiteness():
+    m = np.array([4.0, 9.0, 16.0])          # S = diag(2, 3, 4)
+    S = np.diag([2.0, 3.0, 4.0])
+    t = 0.7
+    # o3 sits at L[1, 0]: K = [[1, t, 0], [t, 1 + t^2, 0], [0, 0, 1]]
+    o3 = np.zeros((1, 6))
+    o3[0, 3] = t
+    K = np.array([[1, t, 0], [t, 1 + t * t, 0], [0, 0, 1]])
+    np.testing.assert_allclose(lo.smoother_blocks(m, o3)[0], S @ K @ S, rtol=1e-15)
+    # o5 sits at L[2, 1] and o1 on L[1, 1]
+    o = np.zeros((1, 6))
+    o[0, 1], o[0, 5] = -0.5, t
+    K = np.array([[1, 0, 0], [0, 0.25, 0.5 * t], [0, 0.5 * t, t * t + 1]])
+    np.testing.assert_allclose(lo.smoother_blocks(m, o)[0], S @ K @ S, rtol=1e-15)
+    # any output: symmetric, eigenvalues >= 0; singular exactly when 1 + o_k = 0
+    rng = np.random.default_rng(1)
+    o = 3.0 * rng.standard_normal((200, 6))
+    M = lo.smoother_blocks(np.tile(m, 200), o)
+    np.testing.assert_array_equal(M, np.transpose(M, (0, 2, 1)))
+    assert np.linalg.eigvalsh(M).min() >= -1e-12 * np.abs(M).max()
+    o[0, :3] = [-1.0, 0.3, 0.2]
+    assert abs(np.linalg.det(lo.smoother_blocks(m, o[:1])[0])) == 0.0
 
 
 def test_gradient_matches_finite_differences():
