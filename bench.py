@@ -38,6 +38,7 @@ WORKLOADS = {
     "inclusions80": dict(n=80, desc="q1-hex-80^3-inclusions-20pct-E1000", tol=1e-8),
     "inclusions150": dict(n=150, desc="q1-hex-150^3-inclusions-20pct-E1000", tol=1e-8),
     "inclusions120": dict(n=120, desc="q1-hex-120^3-inclusions-20pct-E1000", tol=1e-8),
+    "inclusions64": dict(n=64, desc="q1-hex-64^3-inclusions-20pct-E1000", tol=1e-8),
     "inclusions48": dict(n=48, desc="q1-hex-48^3-inclusions-20pct-E1000", tol=1e-8),
     "inclusions40": dict(n=40, desc="q1-hex-40^3-inclusions-20pct-E1000", tol=1e-8),
     "cube10": dict(n=10, desc="q1-hex-10^3-cube-body-load", tol=1e-8),
@@ -344,6 +345,8 @@ def main():
     ap.add_argument("--profile-spmv", action="store_true",
                     help="only build the hierarchy and launch the fine SpMV kernel 8 times "
                          "(a short, fixed command for profilers)")
+    ap.add_argument("--profile-op", default="",
+                    help="LEVEL:OP (OP in A, P, R): like --profile-spmv for that level operator")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"],
                     help="V-cycle precision of the main line (CG stays FP64)")
     ap.add_argument("--no-forms", action="store_true",
@@ -404,14 +407,23 @@ def main():
                             it, res))
         return solver
 
-    if args.profile_spmv:
+    if args.profile_spmv or args.profile_op:
+        # a short, fixed sequence for profilers: 8 launches of one level
+        # operator's SpMV (PLAIN mode) on the benchmark hierarchy
         solver = amg.AMG(rp, cl, val, B)
-        x = torch.randn(p.ndof, dtype=torch.float64, device=dev)
-        y = torch.empty_like(x)
+        lvl, op = (0, "A") if not args.profile_op else args.profile_op.split(":")
+        lvl, which = int(lvl), "APR".index(op)
+        info = [solver.level_info(l) for l in range(solver.nlevels)]
+        nf = info[lvl]["nbrows"] * info[lvl]["bs"]
+        nc = info[lvl + 1]["nbrows"] * info[lvl + 1]["bs"] if which else nf
+        nx, ny = ((nf, nf), (nc, nf), (nf, nc))[which]
+        x = torch.randn(nx, dtype=torch.float64, device=dev)
+        y = torch.empty(ny, dtype=torch.float64, device=dev)
         for _ in range(8):
-            solver.level_spmv(0, 0, x, y)
+            solver.level_spmv(lvl, which, x, y)
         torch.cuda.synchronize()
-        print(json.dumps({"profile_spmv": args.workload, "nnzb": p.nnzb, "rows": p.nnodes}))
+        print(json.dumps({"profile_op": f"{lvl}:{op}", "workload": args.workload,
+                          "nnzb": info[lvl]["nnzb_P" if which else "nnzb_A"], "x": nx, "y": ny}))
         return 0
     for _ in range(args.warmup):
         solver = step()

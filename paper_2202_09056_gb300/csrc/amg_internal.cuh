@@ -139,12 +139,13 @@ int launch_coarse_gemv(const double *Ainv, int n, const TV *x, TV *y, const Geom
 // contiguous.
 template <class T> struct Sell {
     int nrows = 0, nbc = 0, br = 0, bc = 0, nslices = 0;
-    int G = 1;                   // lanes per block row (power of two); 32/G rows per slice
+    int G = 1;                   // lanes per block row (power of two, <= 128); 32/G rows
+                                 // per slice, or G/32 slices per row when G > 32
     int64_t nslots = 0;          // block slots including padding (multiple of 32)
     int64_t *slice_ptr = nullptr;// [nslices + 1] slot offsets
     int *col = nullptr;          // [nslots]
     T *val = nullptr;            // [nslots * br * bc]
-    int *perm = nullptr;         // optional row of each lane slot (-1 = padding lane)
+    int *perm = nullptr;         // optional row of each row slot (-1 = padding)
 };
 
 template <class TV> struct SellArgs {
@@ -169,7 +170,8 @@ template <class VT, class TV>
 int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom &g,
                 cudaStream_t s, int *grid_out = nullptr);
 template <class T>
-int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, double *padding);
+int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, double *padding,
+                int max_lanes = 128);
 
 // ---------------------------------------------------------------- setup (setup.cu)
 struct LevelBuild {
@@ -223,6 +225,7 @@ struct amg_handle_s {
     amg_params prm;
     cudaStream_t stream = nullptr;
     amg::Geom geom;
+    int max_lanes = 128;          // cap on lanes per row of the sliced copies
     amg::DevArena mem;
     std::vector<amg::Level> lv;
     double *Ainv = nullptr;

@@ -899,6 +899,7 @@ static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, co
         x->prm = h->prm;
         x->stream = s;
         x->mem.stream = s;
+        x->max_lanes = 32;  // the batched SpMM keeps each row within one warp
         h->inst.push_back(x);
         AMG_TRY(setup_impl(x, &A[i], B[i]));
         h->depth.push_back((int)x->lv.size());

@@ -6,9 +6,12 @@
 // (9 DFMA per 72 value bytes).  A kernel that splits a block row across all
 // lanes of a warp pays for cross-lane FP64 reductions and predicated
 // accumulations in that same pipe.  Here a row belongs to G lanes (G = 1 on
-// the fine level, where rows are many and short; up to 32 on the coarse
+// the fine level, where rows are many and short; up to 128 on the coarse
 // levels, where they are few and long): each lane does exactly br*bc DFMAs
-// per block it owns and the G partial sums meet in a log2(G)-step butterfly.
+// per block it owns and the G partial sums meet in a log2(G)-step butterfly
+// (G <= 32), or a full-warp butterfly followed by a fixed-order sum of the
+// G/32 warps' totals in shared memory (G = 64, 128: the row's slices are
+// consecutive and always handled by warps of one CTA).
 // To keep the loads coalesced, the 32 lanes of a slice store their blocks
 // interleaved: entry e of the block at depth d of lane t sits at
 // (slice_base + 32 d) * bb + 32 e + t, so every value load of a warp is one
@@ -59,19 +62,24 @@ __global__ void __launch_bounds__(SELL_THREADS) sell_spmv_kernel(SellArgs<TV> a)
 {
     using Acc = TV;
     constexpr int BB = BR * BC;
+    __shared__ Acc wsum[SELL_THREADS / 32][BR];
     if (a.stop && *a.stop) return;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int G = a.G;
-    const int sub = lane & (G - 1);
-    const int rows_per_slice = 32 / G;
+    const bool wide = G > 32;                  // a row spans G/32 slices
+    const int spr = wide ? G >> 5 : 1;
+    const int sub = wide ? 0 : lane & (G - 1);
+    const int rows_per_slice = wide ? 1 : 32 / G;
     const int nw = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
     const VT *__restrict__ val = static_cast<const VT *>(a.val);
     const int *__restrict__ col = a.col;
     const TV *__restrict__ x = a.x;
     double dot = 0.0;
+    // nslices is a multiple of 4 when wide, so every warp of a CTA runs the
+    // same number of iterations (the loop holds __syncthreads)
     for (int s = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5); s < a.nslices;
          s += nw) {
-        const int slot = s * rows_per_slice + lane / G;
+        const int slot = wide ? s / spr : s * rows_per_slice + lane / G;
         const int row = a.perm ? a.perm[slot] : slot;
         const int64_t base = a.slice_ptr[s];
         const int w = (int)((a.slice_ptr[s + 1] - base) >> 5);
@@ -96,10 +104,32 @@ __global__ void __launch_bounds__(SELL_THREADS) sell_spmv_kernel(SellArgs<TV> a)
                     acc[r] = fma((Acc)sldv(vb + (r * BC + c) * 32), xv[c], acc[r]);
         }
         // rows split over G lanes: fixed-order butterfly within the group
-        for (int m = G >> 1; m >= 1; m >>= 1)
+        bool owner;
+        if (!wide) {
+            for (int m = G >> 1; m >= 1; m >>= 1)
 #pragma unroll
-            for (int r = 0; r < BR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], m);
-        if (MODE == SPMV_SMOOTHB && sub == 0 && row >= 0 && row < a.nrows) {
+                for (int r = 0; r < BR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], m);
+            owner = sub == 0;
+        } else {
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1)
+#pragma unroll
+                for (int r = 0; r < BR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], m);
+            if (lane == 0)
+#pragma unroll
+                for (int r = 0; r < BR; ++r) wsum[warp][r] = acc[r];
+            __syncthreads();
+            owner = lane == 0 && warp % spr == 0;
+            if (owner)
+#pragma unroll
+                for (int r = 0; r < BR; ++r) {
+                    Acc t = wsum[warp][r];
+                    for (int q = 1; q < spr; ++q) t += wsum[warp + q][r];
+                    acc[r] = t;
+                }
+            __syncthreads();
+        }
+        if (MODE == SPMV_SMOOTHB && owner && row >= 0 && row < a.nrows) {
             // u + Mb (f - A u) with the row's 3x3 block (BR == 3)
             Acc res[BR];
 #pragma unroll
@@ -115,7 +145,7 @@ __global__ void __launch_bounds__(SELL_THREADS) sell_spmv_kernel(SellArgs<TV> a)
                 a.y[i] = out;
                 if (DOT == DOT_FY) dot += (double)a.f[i] * (double)out;
             }
-        } else if (sub == 0 && row >= 0 && row < a.nrows) {
+        } else if (owner && row >= 0 && row < a.nrows) {
 #pragma unroll
             for (int r = 0; r < BR; ++r) {
                 const int64_t i = (int64_t)row * BR + r;
@@ -239,8 +269,10 @@ __global__ void sell_fill_kernel(const int *__restrict__ rp, const int *__restri
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nslices * 32) return;
-    const int s = t >> 5, lane = t & 31, sub = lane & (G - 1);
-    const int slot = s * (32 / G) + lane / G;
+    const int s = t >> 5, lane = t & 31;
+    const bool wide = G > 32;
+    const int slot = wide ? s / (G >> 5) : s * (32 / G) + lane / G;
+    const int sub = wide ? (s % (G >> 5)) * 32 + lane : lane & (G - 1);
     const int row = perm ? perm[slot] : slot;
     const bool live = row >= 0 && row < nrows;
     const int len = live ? rp[row + 1] - rp[row] : 0;
@@ -258,68 +290,104 @@ __global__ void sell_fill_kernel(const int *__restrict__ rp, const int *__restri
     }
 }
 
-// Slot order of a sliced copy.  Slice widths follow the longest lane, so
-// rows of uneven length (P and R, whose length is the number of aggregates a
-// node's neighbourhood touches; coarse A) waste slots.  When the natural
-// order pads more than 5 %, rows are sorted by length, longest first, inside
-// windows of 32 slices (SELL-C-sigma); a window keeps rows that are close in
-// the numbering together, so the x gather keeps its locality.
-static void sell_order(const std::vector<int> &rp, int G, int nslices, std::vector<int> *perm,
-                       std::vector<int> *width)
+// Slot order of a sliced copy.  A row group is one slice of 32/G rows
+// (G <= 32) or the G/32 consecutive slices of one row (G > 32).  Slice
+// widths follow the longest lane, so rows of uneven length (P and R, whose
+// length is the number of aggregates a node's neighbourhood touches; coarse
+// A) waste slots.  When the natural order pads more than 5 %, rows are sorted
+// by length, longest first, inside windows of 32 groups (SELL-C-sigma); a
+// window keeps rows that are close in the numbering together, so the x
+// gather keeps its locality.  The groups are then ordered by width, widest
+// first: CTAs take them in that order (longest processing time first), so no
+// SM is left with a tail of long rows while the others idle.  Returns the
+// slice count (a multiple of 4 when G > 32).
+static int sell_order(const std::vector<int> &rp, int G, std::vector<int> *perm,
+                      std::vector<int> *width)
 {
-    const int nrows = (int)rp.size() - 1, rps = 32 / G;
-    auto lanes = [&](int row) { return row < 0 ? 0 : (rp[row + 1] - rp[row] + G - 1) / G; };
-    auto widths = [&](const std::vector<int> *pm, std::vector<int> *w) {
-        int64_t slots = 0;
-        w->assign(nslices, 0);
-        for (int sl = 0; sl < nslices; ++sl) {
+    const int nrows = (int)rp.size() - 1;
+    const bool wide = G > 32;
+    const int rpg = wide ? 1 : 32 / G, spg = wide ? G / 32 : 1;
+    int ngroups = (nrows + rpg - 1) / rpg;
+    while ((int64_t)ngroups * spg % 4 != 0 && wide) ++ngroups;
+    const int nslices = ngroups * spg, nslots = ngroups * rpg;
+    auto len = [&](int row) { return row < 0 || row >= nrows ? 0 : rp[row + 1] - rp[row]; };
+    // widths of group g's slices for slot -> row map `rowof`
+    auto group_widths = [&](int g, const int *rowof, int *w) {
+        if (wide) {
+            const int L = len(rowof[g]);
+            for (int q = 0; q < spg; ++q) w[q] = std::max(0, (L - 32 * q + G - 1) / G);
+        } else {
             int m = 0;
-            for (int t = 0; t < rps; ++t) {
-                const int slot = sl * rps + t;
-                const int row = pm ? (*pm)[slot] : (slot < nrows ? slot : -1);
-                m = std::max(m, lanes(row));
-            }
-            (*w)[sl] = m;
-            slots += 32LL * m;
+            for (int t = 0; t < rpg; ++t) m = std::max(m, (len(rowof[g * rpg + t]) + G - 1) / G);
+            w[0] = m;
+        }
+    };
+    auto all_widths = [&](const std::vector<int> &rowof, std::vector<int> *w) {
+        w->assign(nslices, 0);
+        int64_t slots = 0;
+        for (int g = 0; g < ngroups; ++g) {
+            group_widths(g, rowof.data(), w->data() + (size_t)g * spg);
+            for (int q = 0; q < spg; ++q) slots += 32LL * (*w)[(size_t)g * spg + q];
         }
         return slots;
     };
+    std::vector<int> natural(nslots);
+    for (int k = 0; k < nslots; ++k) natural[k] = k < nrows ? k : -1;
     perm->clear();
     const int64_t nnzb = rp[nrows] - rp[0];
-    const int64_t natural = widths(nullptr, width);
-    if (nnzb == 0 || (double)(natural - nnzb) <= 0.05 * (double)nnzb) return;
-    perm->assign((size_t)nslices * rps, -1);
-    const int win = 32 * rps;
+    const int64_t nat = all_widths(natural, width);
+    if (nnzb == 0 || (double)(nat - nnzb) <= 0.05 * (double)nnzb) return nslices;
+    std::vector<int> pw(nslots, -1);
+    const int win = 32 * rpg;
     std::vector<int> idx;
     for (int r0 = 0; r0 < nrows; r0 += win) {
         const int r1 = std::min(nrows, r0 + win);
         idx.resize(r1 - r0);
         for (int r = r0; r < r1; ++r) idx[r - r0] = r;
-        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
-            return rp[a + 1] - rp[a] > rp[b + 1] - rp[b];
-        });
-        std::copy(idx.begin(), idx.end(), perm->begin() + r0);
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return len(a) > len(b); });
+        std::copy(idx.begin(), idx.end(), pw.begin() + r0);
     }
     std::vector<int> w2;
-    if (widths(perm, &w2) < natural) *width = w2;
-    else perm->clear();
+    if (all_widths(pw, &w2) >= nat) return nslices;
+    // widest groups first
+    std::vector<int64_t> cost(ngroups, 0);
+    for (int g = 0; g < ngroups; ++g)
+        for (int q = 0; q < spg; ++q) cost[g] += w2[(size_t)g * spg + q];
+    std::vector<int> order(ngroups);
+    for (int g = 0; g < ngroups; ++g) order[g] = g;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    perm->assign(nslots, -1);
+    width->assign(nslices, 0);
+    for (int k = 0; k < ngroups; ++k) {
+        const int g = order[k];
+        std::copy(pw.begin() + (size_t)g * rpg, pw.begin() + (size_t)(g + 1) * rpg,
+                  perm->begin() + (size_t)k * rpg);
+        std::copy(w2.begin() + (size_t)g * spg, w2.begin() + (size_t)(g + 1) * spg,
+                  width->begin() + (size_t)k * spg);
+    }
+    return nslices;
 }
 
 template <class T>
-int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, double *padding)
+int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, double *padding,
+                int max_lanes)
 {
     Sell<T> S;
     S.nrows = B.nbr;
     S.nbc = B.nbc;
     S.br = B.br;
     S.bc = B.bc;
-    // lanes per row: enough threads to fill the GPU (rows x G >= 160k), but
-    // keep at least two blocks per lane on average
+    // lanes per row: enough threads to fill the GPU (rows x G >= 160k, about
+    // 32 warps per SM) while every lane keeps two blocks on average (one
+    // when the operator has so few rows that fewer than 40k threads would
+    // work on it); measured on the 80^3 hierarchy, each choice is within a
+    // few percent of the best power of two
     const double avg = B.nbr ? (double)B.nnzb / B.nbr : 0.0;
     int G = 1;
-    while (G < 32 && (int64_t)B.nbr * G < 160000 && avg / (2 * G) >= 2.0) G <<= 1;
+    while (G < max_lanes && (int64_t)B.nbr * G < 160000 &&
+           avg / (2 * G) >= ((int64_t)B.nbr * G < 40000 ? 1.0 : 2.0))
+        G <<= 1;
     S.G = G;
-    S.nslices = (B.nbr + 32 / G - 1) / (32 / G);
     const int bb = B.br * B.bc;
     std::vector<int> rp(B.nbr + 1, 0);
     if (B.nbr > 0) {
@@ -328,7 +396,7 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
         AMG_TRY_CUDA(cudaStreamSynchronize(s));
     }
     std::vector<int> perm, wh;
-    sell_order(rp, G, S.nslices, &perm, &wh);
+    S.nslices = B.nbr > 0 ? sell_order(rp, G, &perm, &wh) : 0;
     std::vector<int64_t> sp(S.nslices + 1, 0);
     for (int i = 0; i < S.nslices; ++i) sp[i + 1] = sp[i] + 32LL * wh[i];
     S.nslots = sp[S.nslices];
@@ -354,9 +422,11 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
     return AMG_OK;
 }
 
-template int bsr_to_sell<double>(const BsrD &, DevArena &, cudaStream_t, Sell<double> *, double *);
-template int bsr_to_sell<float>(const BsrD &, DevArena &, cudaStream_t, Sell<float> *, double *);
+template int bsr_to_sell<double>(const BsrD &, DevArena &, cudaStream_t, Sell<double> *, double *,
+                                 int);
+template int bsr_to_sell<float>(const BsrD &, DevArena &, cudaStream_t, Sell<float> *, double *,
+                                int);
 template int bsr_to_sell<__nv_bfloat16>(const BsrD &, DevArena &, cudaStream_t,
-                                        Sell<__nv_bfloat16> *, double *);
+                                        Sell<__nv_bfloat16> *, double *, int);
 
 }  // namespace amg

@@ -718,20 +718,20 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         Level &L = h->lv[l];
         const bool vc = !L.coarsest;
         if (l == 0 || (vc && prec == AMG_PREC_FP64))
-            AMG_TRY(bsr_to_sell<double>(L.A, h->mem, s, &L.sA, &L.pad_A));
+            AMG_TRY(bsr_to_sell<double>(L.A, h->mem, s, &L.sA, &L.pad_A, h->max_lanes));
         if (vc && prec == AMG_PREC_FP64) {
-            AMG_TRY(bsr_to_sell<double>(L.P, h->mem, s, &L.sP, &L.pad_P));
-            AMG_TRY(bsr_to_sell<double>(L.R, h->mem, s, &L.sR, &L.pad_R));
+            AMG_TRY(bsr_to_sell<double>(L.P, h->mem, s, &L.sP, &L.pad_P, h->max_lanes));
+            AMG_TRY(bsr_to_sell<double>(L.R, h->mem, s, &L.sR, &L.pad_R, h->max_lanes));
         }
         if (vc && prec == AMG_PREC_FP32) {
-            AMG_TRY(bsr_to_sell<float>(L.A, h->mem, s, &L.fA, &L.pad_A));
-            AMG_TRY(bsr_to_sell<float>(L.P, h->mem, s, &L.fP, &L.pad_P));
-            AMG_TRY(bsr_to_sell<float>(L.R, h->mem, s, &L.fR, &L.pad_R));
+            AMG_TRY(bsr_to_sell<float>(L.A, h->mem, s, &L.fA, &L.pad_A, h->max_lanes));
+            AMG_TRY(bsr_to_sell<float>(L.P, h->mem, s, &L.fP, &L.pad_P, h->max_lanes));
+            AMG_TRY(bsr_to_sell<float>(L.R, h->mem, s, &L.fR, &L.pad_R, h->max_lanes));
         }
         if (vc && prec == AMG_PREC_BF16) {
-            AMG_TRY(bsr_to_sell<__nv_bfloat16>(L.A, h->mem, s, &L.bA, &L.pad_A));
-            AMG_TRY(bsr_to_sell<__nv_bfloat16>(L.P, h->mem, s, &L.bP, &L.pad_P));
-            AMG_TRY(bsr_to_sell<__nv_bfloat16>(L.R, h->mem, s, &L.bR, &L.pad_R));
+            AMG_TRY(bsr_to_sell<__nv_bfloat16>(L.A, h->mem, s, &L.bA, &L.pad_A, h->max_lanes));
+            AMG_TRY(bsr_to_sell<__nv_bfloat16>(L.P, h->mem, s, &L.bP, &L.pad_P, h->max_lanes));
+            AMG_TRY(bsr_to_sell<__nv_bfloat16>(L.R, h->mem, s, &L.bR, &L.pad_R, h->max_lanes));
         }
     }
     for (size_t l = 0; l < h->lv.size(); ++l) {
