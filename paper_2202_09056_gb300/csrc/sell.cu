@@ -57,16 +57,16 @@ template <int NT> __device__ __forceinline__ double cta_sum_d(double v)
 
 constexpr int SELL_THREADS = 128;
 
-template <int BR, int BC, class VT, class TV, int MODE, int DOT>
+template <int BR, int BC, class VT, class TV, int MODE, int DOT, bool WIDE>
 __global__ void __launch_bounds__(SELL_THREADS) sell_spmv_kernel(SellArgs<TV> a)
 {
     using Acc = TV;
     constexpr int BB = BR * BC;
-    __shared__ Acc wsum[SELL_THREADS / 32][BR];
+    __shared__ Acc wsum[WIDE ? SELL_THREADS / 32 : 1][BR];
     if (a.stop && *a.stop) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int G = a.G;
-    const bool wide = G > 32;                  // a row spans G/32 slices
+    constexpr bool wide = WIDE;                // a row spans G/32 slices (G > 32)
     const int spr = wide ? G >> 5 : 1;
     const int sub = wide ? 0 : lane & (G - 1);
     const int rows_per_slice = wide ? 1 : 32 / G;
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(SELL_THREADS) sell_spmv_kernel(SellArgs<TV> a)
         }
         // rows split over G lanes: fixed-order butterfly within the group
         bool owner;
-        if (!wide) {
+        if constexpr (!wide) {
             for (int m = G >> 1; m >= 1; m >>= 1)
 #pragma unroll
                 for (int r = 0; r < BR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], m);
@@ -181,7 +181,14 @@ int sell_grid(int nslices, const Geom &g)
 template <int BR, int BC, class VT, class TV, int MODE, int DOT>
 static int sell_go(const SellArgs<TV> &a, int grid, cudaStream_t s)
 {
-    sell_spmv_kernel<BR, BC, VT, TV, MODE, DOT><<<grid, SELL_THREADS, 0, s>>>(a);
+    if (a.G <= 32) {
+        sell_spmv_kernel<BR, BC, VT, TV, MODE, DOT, false><<<grid, SELL_THREADS, 0, s>>>(a);
+    } else if constexpr (BR == 6) {
+        sell_spmv_kernel<BR, BC, VT, TV, MODE, DOT, true><<<grid, SELL_THREADS, 0, s>>>(a);
+    } else {
+        set_error("rows over several warps need 6-row blocks");
+        return AMG_ERR_ARG;
+    }
     count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     return AMG_OK;
@@ -383,6 +390,7 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
     // work on it); measured on the 80^3 hierarchy, each choice is within a
     // few percent of the best power of two
     const double avg = B.nbr ? (double)B.nnzb / B.nbr : 0.0;
+    if (B.br != 6) max_lanes = std::min(max_lanes, 32);  // wide rows: 6-row blocks only
     int G = 1;
     while (G < max_lanes && (int64_t)B.nbr * G < 160000 &&
            avg / (2 * G) >= ((int64_t)B.nbr * G < 40000 ? 1.0 : 2.0))
