@@ -165,7 +165,7 @@ template <class TV> struct SellArgs {
     const int *stop;
 };
 
-int sell_grid(int nslices, const Geom &g);
+int sell_grid(int nslices, int br, int bc, const Geom &g);
 template <class VT, class TV>
 int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom &g,
                 cudaStream_t s, int *grid_out = nullptr);

@@ -75,7 +75,7 @@ int query_geom(Geom *g)
     g->max_ctas = g->num_sms * 8;  // 8 CTAs of 256 threads fill an SM's 2048 thread slots
     // the sliced SpMV runs up to 16 CTAs of 128 threads per SM; every kernel
     // that leaves one partial sum per CTA stays within this many
-    g->max_partials = g->num_sms * 16;
+    g->max_partials = g->num_sms * 32;  // largest SELL grid (sell_cap)
     return AMG_OK;
 }
 

@@ -57,8 +57,18 @@ template <int NT> __device__ __forceinline__ double cta_sum_d(double v)
 
 constexpr int SELL_THREADS = 128;
 
+// Register budget: the kernel is compiled for minb resident CTAs per SM
+// (65536 / (128 x minb) registers per thread).  Grid: up to cap CTAs per SM,
+// measured on the 80^3 hierarchy.  The fine-level shapes (3-row blocks, one
+// lane per row, uniform slices) run fastest oversubscribed, one slice group
+// per CTA with the hardware scheduler balancing; the 6x6 coarse operators
+// (few, long rows in widest-first order) fastest as exactly one resident
+// wave with the warp-strided loop balancing.
+__host__ __device__ constexpr int sell_minb(int br, int bc) { return br == 6 ? (bc == 6 ? 8 : 10) : 12; }
+__host__ __device__ constexpr int sell_cap(int br, int bc) { return br == 6 ? (bc == 6 ? 8 : 16) : 32; }
+
 template <int BR, int BC, class VT, class TV, int MODE, int DOT, bool WIDE>
-__global__ void __launch_bounds__(SELL_THREADS) sell_spmv_kernel(SellArgs<TV> a)
+__global__ void __launch_bounds__(SELL_THREADS, sell_minb(BR, BC)) sell_spmv_kernel(SellArgs<TV> a)
 {
     using Acc = TV;
     constexpr int BB = BR * BC;
@@ -169,11 +179,11 @@ __global__ void __launch_bounds__(SELL_THREADS) sell_spmv_kernel(SellArgs<TV> a)
     }
 }
 
-int sell_grid(int nslices, const Geom &g)
+int sell_grid(int nslices, int br, int bc, const Geom &g)
 {
     const int per_cta = SELL_THREADS / 32;
     int grid = (nslices + per_cta - 1) / per_cta;
-    const int cap = g.num_sms * 16;  // = Geom::max_partials
+    const int cap = g.num_sms * sell_cap(br, bc);  // <= Geom::max_partials
     if (grid > cap) grid = cap;
     return std::max(grid, 1);
 }
@@ -240,7 +250,7 @@ int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom
     a.col = A.col;
     a.val = A.val;
     a.perm = A.perm;
-    const int grid = sell_grid(A.nslices, g);
+    const int grid = sell_grid(A.nslices, A.br, A.bc, g);
     if (grid_out) *grid_out = grid;
     if (dot != DOT_NONE && grid > g.max_partials) {
         set_error("fused dot needs %d partial sums, the buffer holds %d", grid, g.max_partials);

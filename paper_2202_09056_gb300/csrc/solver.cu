@@ -393,7 +393,7 @@ static int rz_parts(amg_handle h)
     const Level &L0 = h->lv[0];
     if (h->lv.size() == 1) return vgrid(h, h->nc);
     if (h->prm.npost == 0) return vgrid(h, L0.n());
-    return sell_grid(L0.sA.nslices, h->geom);
+    return sell_grid(L0.sA.nslices, L0.sA.br, L0.sA.bc, h->geom);
 }
 
 // One CG iteration, as recorded into the body of the graph.  The outer
