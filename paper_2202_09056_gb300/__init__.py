@@ -21,6 +21,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
 
 AMG_OK, AMG_NOT_CONVERGED = 0, 1
+AMG_ERR_ARG, AMG_ERR_CUDA, AMG_ERR_BREAKDOWN, AMG_ERR_COARSE, AMG_ERR_LIMIT, AMG_ERR_STATE = \
+    -1, -2, -3, -4, -5, -6
 _ERRORS = {-1: "bad argument", -2: "CUDA error", -3: "CG breakdown",
            -4: "coarsest matrix not positive definite", -5: "size limit", -6: "bad state"}
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2

@@ -301,28 +301,51 @@ __device__ __forceinline__ int find_sorted(const int *a, int lo, int hi, int x)
     return lo;
 }
 
-// Symbolic C = X Y, first pass: one thread per row keeps the row's distinct
-// columns in a sorted local set.  Count mode writes the row length, or -1
-// and appends the row to `overflow` when the row has more than SYM_CAP
-// distinct columns; write mode fills the rows that fit.
+// Symbolic C = X Y, routing: a row whose candidate products (the sum of the
+// lengths of the Y rows it touches) are many goes straight to the bitmap
+// pass: more than 4 SYM_CAP candidates, or more than SYM_CAP when C has at
+// most 4096 columns (the bitmap is then at most 512 bytes).  The per-thread
+// sorted set costs a binary search per candidate and a shift per new column,
+// in local memory, which dominated the symbolic products on the coarse levels.
+__global__ void sym_route_kernel(const int *__restrict__ xrp, const int *__restrict__ xcol,
+                                 const int *__restrict__ yrp, int nrows, int ncols,
+                                 uint8_t *__restrict__ islong, int *__restrict__ longrows,
+                                 int *__restrict__ nlong)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows) return;
+    int64_t cand = 0;
+    for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
+        const int k = xcol[p];
+        cand += yrp[k + 1] - yrp[k];
+    }
+    const bool lng = cand > 4 * SYM_CAP || (cand > SYM_CAP && ncols <= 4096);
+    islong[i] = lng ? 1 : 0;
+    if (lng) longrows[atomicAdd(nlong, 1)] = i;
+}
+
+// Symbolic C = X Y, first pass for the other rows: one thread per row keeps
+// the row's distinct columns in a sorted local set.  Count mode writes the
+// row length, or marks the row long and appends it to `longrows` when it has
+// more than SYM_CAP distinct columns; write mode fills the short rows.
 template <bool WRITE>
 __global__ void sym_small_kernel(const int *__restrict__ xrp, const int *__restrict__ xcol,
                                  const int *__restrict__ yrp, const int *__restrict__ ycol,
                                  int nrows, int *__restrict__ cnt, const int *__restrict__ crp,
-                                 int *__restrict__ ccol, int *__restrict__ overflow,
-                                 int *__restrict__ noverflow)
+                                 int *__restrict__ ccol, uint8_t *__restrict__ islong,
+                                 int *__restrict__ longrows, int *__restrict__ nlong)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nrows) return;
-    if (WRITE && cnt[i] < 0) return;
+    if (islong[i]) return;
     SortedSet<SYM_CAP> S;
     for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
         const int k = xcol[p];
         for (int q = yrp[k]; q < yrp[k + 1]; ++q)
             if (!S.insert(ycol[q])) {
                 if (!WRITE) {
-                    cnt[i] = -1;
-                    overflow[atomicAdd(noverflow, 1)] = i;
+                    islong[i] = 1;
+                    longrows[atomicAdd(nlong, 1)] = i;
                 }
                 return;
             }
@@ -395,15 +418,19 @@ static int spgemm_symbolic(const int *xrp, const int *xcol, int nrows, const int
                            cudaStream_t s, int **crp_out, int **ccol_out, int *nnz_out)
 {
     int *cnt = nullptr, *ovf = nullptr, *novf = nullptr, *crp = nullptr, *ccol = nullptr;
+    uint8_t *islong = nullptr;
     AMG_TRY(tmp.alloc_n(&cnt, (size_t)nrows + 1));
     AMG_TRY(tmp.alloc_n(&ovf, (size_t)std::max(nrows, 1)));
+    AMG_TRY(tmp.alloc_n(&islong, (size_t)std::max(nrows, 1)));
     AMG_TRY(tmp.alloc_n(&novf, 1));
     AMG_TRY(keep.alloc_n(&crp, (size_t)nrows + 1));
     AMG_TRY_CUDA(cudaMemsetAsync(novf, 0, sizeof(int), s));
     if (nrows > 0) {
+        sym_route_kernel<<<nblk(nrows), T1D, 0, s>>>(xrp, xcol, yrp, nrows, ncols, islong, ovf,
+                                                     novf);
         sym_small_kernel<false><<<nblk(nrows), T1D, 0, s>>>(xrp, xcol, yrp, ycol, nrows, cnt,
-                                                            nullptr, nullptr, ovf, novf);
-        ::amg::count_launch(1);
+                                                            nullptr, nullptr, islong, ovf, novf);
+        ::amg::count_launch(2);
         AMG_TRY_CUDA(cudaGetLastError());
     }
     int nlong = 0;
@@ -421,7 +448,7 @@ static int spgemm_symbolic(const int *xrp, const int *xcol, int nrows, const int
             AMG_TRY_CUDA(cudaFuncSetAttribute(sym_bitmap_kernel<true>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         }
-        sym_bitmap_kernel<false><<<std::min(nlong, 4096), SYM_T, smem, s>>>(
+        sym_bitmap_kernel<false><<<std::min(nlong, 8192), SYM_T, smem, s>>>(
             xrp, xcol, yrp, ycol, ncols, ovf, nlong, cnt, nullptr, nullptr);
         ::amg::count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
@@ -431,18 +458,19 @@ static int spgemm_symbolic(const int *xrp, const int *xcol, int nrows, const int
     AMG_TRY(keep.alloc_n(&ccol, (size_t)std::max(total, 1)));
     if (nrows > 0) {
         sym_small_kernel<true><<<nblk(nrows), T1D, 0, s>>>(xrp, xcol, yrp, ycol, nrows, cnt, crp,
-                                                           ccol, nullptr, nullptr);
+                                                           ccol, islong, nullptr, nullptr);
         ::amg::count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
     }
     if (nlong > 0) {
-        sym_bitmap_kernel<true><<<std::min(nlong, 4096), SYM_T, smem, s>>>(
+        sym_bitmap_kernel<true><<<std::min(nlong, 8192), SYM_T, smem, s>>>(
             xrp, xcol, yrp, ycol, ncols, ovf, nlong, cnt, crp, ccol);
         ::amg::count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
     }
     tmp.release(cnt);
     tmp.release(ovf);
+    tmp.release(islong);
     tmp.release(novf);
     *crp_out = crp;
     *ccol_out = ccol;
@@ -632,6 +660,96 @@ __global__ void spgemm_values_kernel(const int *__restrict__ xrp, const int *__r
         for (int c = 0; c < YC; ++c) cval[q * XR * YC + r * YC + c] = acc[r][c];
 }
 
+// C = X Y by rows (Gustavson), L lanes per output row.  The row's columns
+// (from the symbolic pass) and its block accumulators sit in shared memory;
+// X row i is walked in ascending order, and for each X_ik the lanes take the
+// entries of Y row k (distinct columns, so no two lanes touch the same
+// accumulator) and add X_ik Y_kj into the block of column j, found by a
+// binary search in the shared column list.  Every accumulator entry sees
+// the same FMA sequence as in spgemm_values_kernel (k ascending, then the
+// inner index), so both kernels give the same bits; this one does no search
+// in Y's rows and no work for the (k, j) pairs that do not exist.
+template <int XR, int XC, int YC, int L>
+__global__ void __launch_bounds__(128) spgemm_rows_kernel(
+    const int *__restrict__ xrp, const int *__restrict__ xcol, const double *__restrict__ xval,
+    const int *__restrict__ yrp, const int *__restrict__ ycol, const double *__restrict__ yval,
+    const int *__restrict__ crp, const int *__restrict__ ccol, int nrows, int cmax,
+    double *__restrict__ cval)
+{
+    constexpr int CB = XR * YC;
+    extern __shared__ double sm[];
+    const int GROUPS = blockDim.x / L;
+    const int g = threadIdx.x / L, lane = threadIdx.x % L;
+    const unsigned mask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) / L * L));
+    double *acc = sm + (size_t)g * cmax * CB;
+    int *cols = reinterpret_cast<int *>(sm + (size_t)GROUPS * cmax * CB) + (size_t)g * cmax;
+    for (int i = blockIdx.x * GROUPS + g; i < nrows; i += gridDim.x * GROUPS) {
+        const int c0 = crp[i], len = crp[i + 1] - c0;
+        for (int t = lane; t < len; t += L) cols[t] = ccol[c0 + t];
+        for (int t = lane; t < len * CB; t += L) acc[t] = 0.0;
+        __syncwarp(mask);
+        for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
+            const int k = xcol[p];
+            double xb[XR * XC];
+#pragma unroll
+            for (int e = 0; e < XR * XC; ++e) xb[e] = xval[(int64_t)p * XR * XC + e];
+            const int hi = yrp[k + 1];
+            for (int t = yrp[k] + lane; t < hi; t += L) {
+                const int j = ycol[t];
+                const int pos = find_sorted(cols, 0, len, j);
+                if (pos >= len || cols[pos] != j) continue;  // cannot happen: C holds every product
+                const double *yb = yval + (int64_t)t * XC * YC;
+                double *a = acc + (size_t)pos * CB;
+#pragma unroll
+                for (int r = 0; r < XR; ++r)
+#pragma unroll
+                    for (int c = 0; c < YC; ++c) {
+                        double v = a[r * YC + c];
+#pragma unroll
+                        for (int m = 0; m < XC; ++m) v += xb[r * XC + m] * yb[m * YC + c];
+                        a[r * YC + c] = v;
+                    }
+            }
+            __syncwarp(mask);
+        }
+        for (int t = lane; t < len * CB; t += L) cval[(int64_t)c0 * CB + t] = acc[t];
+        __syncwarp(mask);
+    }
+}
+
+__global__ void row_max_kernel(const int *__restrict__ rp, int n, int *__restrict__ mx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(mx, rp[i + 1] - rp[i]);
+}
+
+template <int XR, int XC, int YC>
+static int spgemm_rows(const BsrD &X, const BsrD &Y, BsrD *C, int cmax, int lanes, cudaStream_t s,
+                       bool *done)
+{
+    constexpr int CB = XR * YC;
+    *done = false;
+    const size_t per = (size_t)cmax * (CB * sizeof(double) + sizeof(int));
+    auto go = [&](auto kern, int L) -> int {
+        const int groups = (int)std::min<size_t>(128 / L, (200 * 1024) / std::max<size_t>(per, 1));
+        if (groups < 1) return AMG_OK;  // rows too long for shared memory: the per-block kernel
+        const size_t smem = per * groups;
+        if (smem > 48 * 1024)
+            AMG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        const int grid = std::max(1, std::min((X.nbr + groups - 1) / groups, 1 << 20));
+        kern<<<grid, groups * L, smem, s>>>(X.row_ptr, X.col, X.val, Y.row_ptr, Y.col, Y.val, C->row_ptr,
+                                     C->col, X.nbr, cmax, C->val);
+        ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+        *done = true;
+        return AMG_OK;
+    };
+    if (lanes <= 8) return go(spgemm_rows_kernel<XR, XC, YC, 8>, 8);
+    if (lanes <= 16) return go(spgemm_rows_kernel<XR, XC, YC, 16>, 16);
+    return go(spgemm_rows_kernel<XR, XC, YC, 32>, 32);
+}
+
 static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, cudaStream_t s,
                   BsrD *C)
 {
@@ -644,6 +762,36 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
                             &C->row_ptr, &C->col, &total));
     C->nnzb = total;
     AMG_TRY(keep.alloc_n(&C->val, (size_t)std::max(total, 1) * C->br * C->bc));
+    if (total == 0) return AMG_OK;
+    const int xr = X.br, xc = X.bc, yc = Y.bc;
+    if (!((xr == 3 && xc == 3 && yc == 6) || (xr == 6 && xc == 6 && yc == 6) ||
+          (xr == 6 && xc == 3 && yc == 6))) {
+        set_error("unsupported block product %dx%d * %dx%d", xr, xc, X.bc, yc);
+        return AMG_ERR_ARG;
+    }
+    // rows of C in shared memory, lanes per row ~ the mean length of Y's rows;
+    // only when there are rows enough to fill the GPU (on the 80^3 hierarchy
+    // the row kernel took 12 / 30 / 18 ms for the three products with 22k+
+    // rows against 20 / 36 / 28 ms, and lost on the ones with 1694 and 141)
+    bool done = false;
+    if (X.nbr < 16384) goto per_block;
+    {
+    int *mx = nullptr, cmax = 0;
+    AMG_TRY(tmp.alloc_n(&mx, 1));
+    AMG_TRY_CUDA(cudaMemsetAsync(mx, 0, sizeof(int), s));
+    row_max_kernel<<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, X.nbr, mx);
+    ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaMemcpyAsync(&cmax, mx, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    tmp.release(mx);
+    const double ylen = Y.nbr ? (double)Y.nnzb / Y.nbr : 0.0;
+    const int lanes = ylen <= 8.0 ? 8 : (ylen <= 16.0 ? 16 : 32);
+    if (xr == 3) AMG_TRY((spgemm_rows<3, 3, 6>(X, Y, C, cmax, lanes, s, &done)));
+    else if (xc == 6) AMG_TRY((spgemm_rows<6, 6, 6>(X, Y, C, cmax, lanes, s, &done)));
+    else AMG_TRY((spgemm_rows<6, 3, 6>(X, Y, C, cmax, lanes, s, &done)));
+    if (done) return AMG_OK;
+    }
+per_block:
     int *cbrow = nullptr;
     AMG_TRY(tmp.alloc_n(&cbrow, (size_t)std::max(total, 1)));
     if (X.nbr > 0) {
@@ -651,24 +799,17 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
         ::amg::count_launch(1);
     }
     AMG_TRY_CUDA(cudaGetLastError());
-    if (total > 0) {
-        const int g = nblk(total, 128);
-        const int xr = X.br, xc = X.bc, yc = Y.bc;
+    const int g = nblk(total, 128);
 #define AMG_SPGEMM_VALS(XR_, XC_, YC_)                                                       \
     spgemm_values_kernel<XR_, XC_, YC_><<<g, 128, 0, s>>>(X.row_ptr, X.col, X.val, Y.row_ptr, \
                                                           Y.col, Y.val, cbrow, C->col, total, \
                                                           C->val)
-        if (xr == 3 && xc == 3 && yc == 6) AMG_SPGEMM_VALS(3, 3, 6);
-        else if (xr == 6 && xc == 6 && yc == 6) AMG_SPGEMM_VALS(6, 6, 6);
-        else if (xr == 6 && xc == 3 && yc == 6) AMG_SPGEMM_VALS(6, 3, 6);
-        else {
-            set_error("unsupported block product %dx%d * %dx%d", xr, xc, X.bc, yc);
-            return AMG_ERR_ARG;
-        }
-        ::amg::count_launch(1);
+    if (xr == 3) AMG_SPGEMM_VALS(3, 3, 6);
+    else if (xc == 6) AMG_SPGEMM_VALS(6, 6, 6);
+    else AMG_SPGEMM_VALS(6, 3, 6);
+    ::amg::count_launch(1);
 #undef AMG_SPGEMM_VALS
-        AMG_TRY_CUDA(cudaGetLastError());
-    }
+    AMG_TRY_CUDA(cudaGetLastError());
     tmp.release(cbrow);
     return AMG_OK;
 }

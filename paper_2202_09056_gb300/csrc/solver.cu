@@ -610,6 +610,36 @@ void amg::destroy_handle(amg_handle h)
     delete h;
 }
 
+// Input pattern check, one thread per block row: bad[0] |= 1 (row pointers),
+// 2 (columns not ascending or out of range), 4 (no diagonal block); bad[1] =
+// the lowest offending row.
+__global__ void validate_pattern_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                                        int nbr, int nbc, int64_t nnzb, int *__restrict__ bad)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nbr) return;
+    const int64_t a = rp[I], b = rp[I + 1];
+    int code = 0;
+    if (a < 0 || b < a || b > nnzb || (I == 0 && a != 0) || (I == nbr - 1 && b != nnzb)) {
+        code = 1;
+    } else {
+        bool diag = false;
+        for (int64_t k = a; k < b; ++k) {
+            const int c = col[k];
+            if (c < 0 || c >= nbc || (k > a && c <= col[k - 1])) {
+                code = 2;
+                break;
+            }
+            diag |= c == I;
+        }
+        if (!code && !diag) code = 4;
+    }
+    if (code) {
+        atomicOr(bad, code);
+        atomicMin(bad + 1, I);
+    }
+}
+
 int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
 {
     cudaStream_t s = h->stream;
@@ -642,34 +672,34 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         AMG_TRY_CUDA(cudaMemcpyAsync(L0.B, B, sizeof(double) * 18 * A.nbr,
                                      cudaMemcpyDeviceToDevice, s));
         L0.eps = prm.eps_strong;
-        // validate the pattern on the host before any kernel indexes with it
-        std::vector<int> rp(A.nbr + 1), cl(std::max<int64_t>(A.nnzb, 1));
-        AMG_TRY_CUDA(cudaMemcpyAsync(rp.data(), A.row_ptr, sizeof(int) * (A.nbr + 1),
-                                     cudaMemcpyDeviceToHost, s));
-        AMG_TRY_CUDA(cudaMemcpyAsync(cl.data(), A.col, sizeof(int) * A.nnzb,
-                                     cudaMemcpyDeviceToHost, s));
+        // validate the pattern before any other kernel indexes with it: the
+        // checking kernel reads a row's columns only after its own row
+        // pointers were found inside [0, nnzb]
+        int *bad = nullptr;
+        AMG_TRY(tmp.alloc_n(&bad, 2));
+        const int init[2] = {0, INT32_MAX};
+        AMG_TRY_CUDA(cudaMemcpyAsync(bad, init, sizeof(init), cudaMemcpyHostToDevice, s));
+        if (A.nbr > 0) {
+            validate_pattern_kernel<<<(A.nbr + 255) / 256, 256, 0, s>>>(A.row_ptr, A.col, A.nbr,
+                                                                        A.nbc, A.nnzb, bad);
+            ::amg::count_launch(1);
+            AMG_TRY_CUDA(cudaGetLastError());
+        }
+        int hb[2] = {0, 0};
+        AMG_TRY_CUDA(cudaMemcpyAsync(hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, s));
         AMG_TRY_CUDA(cudaStreamSynchronize(s));
-        if (rp[0] != 0 || rp[A.nbr] != A.nnzb) {
-            set_error("row_ptr must start at 0 and end at nnzb");
+        tmp.release(bad);
+        if (hb[0] & 1) {
+            set_error("row_ptr must start at 0, end at nnzb and not decrease (block row %d)", hb[1]);
             return AMG_ERR_ARG;
         }
-        for (int I = 0; I < A.nbr; ++I) {
-            if (rp[I + 1] < rp[I]) {
-                set_error("row_ptr decreases at block row %d", I);
-                return AMG_ERR_ARG;
-            }
-            bool diag = false;
-            for (int k = rp[I]; k < rp[I + 1]; ++k) {
-                if (cl[k] < 0 || cl[k] >= A.nbc || (k > rp[I] && cl[k] <= cl[k - 1])) {
-                    set_error("block row %d: columns must be ascending and in range", I);
-                    return AMG_ERR_ARG;
-                }
-                diag |= cl[k] == I;
-            }
-            if (!diag) {
-                set_error("block row %d has no diagonal block", I);
-                return AMG_ERR_ARG;
-            }
+        if (hb[0] & 2) {
+            set_error("block row %d: columns must be ascending and in range", hb[1]);
+            return AMG_ERR_ARG;
+        }
+        if (hb[0] & 4) {
+            set_error("block row %d has no diagonal block", hb[1]);
+            return AMG_ERR_ARG;
         }
         h->lv.push_back(L0);
     }

@@ -267,3 +267,48 @@ def test_reduced_precision_vcycle_solves_to_fp64_accuracy(prec):
     zo = H.vcycle(r)
     tol = 1e-4 if prec == amg.PREC_FP32 else 5e-2
     assert np.linalg.norm(z - zo) <= tol * np.linalg.norm(zo)
+
+
+def test_setup_rejects_malformed_patterns():
+    """The input pattern is checked on the device before any kernel indexes
+    with it; every malformed case returns AMG_ERR_ARG and names the row."""
+    p = q.cube(3)
+    rp0, cl0, val0, B0 = p.row_ptr.copy(), p.col.copy(), p.val, p.B
+
+    def setup(rp, cl):
+        d = torch.device("cuda:0")
+        return amg.AMG(torch.from_numpy(rp).to(d), torch.from_numpy(cl).to(d),
+                       torch.from_numpy(val0).to(d), torch.from_numpy(B0).to(d))
+
+    # a valid pattern passes
+    setup(rp0, cl0)
+    # decreasing row pointer (row 5 ends before it starts); columns stay in range
+    rp = rp0.copy()
+    rp[6] = rp[5] - 1
+    with pytest.raises(amg.AmgError) as e:
+        setup(rp, cl0)
+    assert e.value.status == amg.AMG_ERR_ARG and "row_ptr" in str(e.value)
+    # unsorted columns in row 7
+    cl = cl0.copy()
+    a, b = rp0[7], rp0[8]
+    cl[a], cl[a + 1] = cl[a + 1], cl[a]
+    with pytest.raises(amg.AmgError) as e:
+        setup(rp0, cl)
+    assert "block row 7" in str(e.value) and "ascending" in str(e.value)
+    # a column out of range in the last row
+    cl = cl0.copy()
+    cl[rp0[-1] - 1] = p.nnodes + 3
+    with pytest.raises(amg.AmgError) as e:
+        setup(rp0, cl)
+    assert f"block row {p.nnodes - 1}" in str(e.value)
+    # a row without its diagonal block: row 0's diagonal entry points at a
+    # column absent from the row instead (columns kept ascending)
+    cl = cl0.copy()
+    row0 = list(cl0[rp0[0]:rp0[1]])
+    free = next(c for c in range(p.nnodes) if c not in row0)
+    d0 = rp0[0] + row0.index(0)
+    cl[d0] = free
+    cl[rp0[0]:rp0[1]] = np.sort(cl[rp0[0]:rp0[1]])
+    with pytest.raises(amg.AmgError) as e:
+        setup(rp0, cl)
+    assert "block row 0 has no diagonal block" in str(e.value)
