@@ -552,12 +552,16 @@ __global__ void transpose_scatter_kernel(const int *__restrict__ brow, const int
 
 // Sort each transposed row by column (the scatter order is arbitrary): the
 // result does not depend on the order of the atomics.
+constexpr int RSORT_MAX = 32;        // rows up to this length: insertion sort per thread
+constexpr int RSORT_CTA_MAX = 4096;  // longer rows up to this: rank sort per CTA
+
 __global__ void row_sort_kernel(const int *__restrict__ trp, int nrows, int *__restrict__ tcol,
                                 int *__restrict__ tsrc)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
     const int lo = trp[r], hi = trp[r + 1];
+    if (hi - lo > RSORT_MAX && hi - lo <= RSORT_CTA_MAX) return;  // row_rank_sort_kernel
     for (int i = lo + 1; i < hi; ++i) {
         const int c = tcol[i], s = tsrc[i];
         int j = i - 1;
@@ -568,6 +572,32 @@ __global__ void row_sort_kernel(const int *__restrict__ trp, int nrows, int *__r
         }
         tcol[j + 1] = c;
         tsrc[j + 1] = s;
+    }
+}
+
+// Long rows: one CTA per row, keys staged in shared memory, every entry's
+// rank = the number of smaller keys (the keys of a row are distinct).
+__global__ void __launch_bounds__(256) row_rank_sort_kernel(const int *__restrict__ trp, int nrows,
+                                                            int *__restrict__ tcol,
+                                                            int *__restrict__ tsrc)
+{
+    __shared__ int kc[RSORT_CTA_MAX], ks[RSORT_CTA_MAX];
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int lo = trp[r], n = trp[r + 1] - lo;
+        if (n <= RSORT_MAX || n > RSORT_CTA_MAX) continue;  // block-uniform
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            kc[i] = tcol[lo + i];
+            ks[i] = tsrc[lo + i];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int c = kc[i];
+            int rank = 0;
+            for (int j = 0; j < n; ++j) rank += kc[j] < c;
+            tcol[lo + rank] = c;
+            tsrc[lo + rank] = ks[i];
+        }
+        __syncthreads();
     }
 }
 
@@ -610,6 +640,7 @@ static int transpose_bsr(const BsrD &P, const int *pbrow, DevArena &keep, DevAre
         transpose_scatter_kernel<<<nblk(P.nnzb), T1D, 0, s>>>(pbrow, P.col, P.nnzb, R->row_ptr,
                                                                fill, R->col, tsrc); ::amg::count_launch(1);
         row_sort_kernel<<<nblk(R->nbr), T1D, 0, s>>>(R->row_ptr, R->nbr, R->col, tsrc); ::amg::count_launch(1);
+        row_rank_sort_kernel<<<std::max(1, std::min(R->nbr, 8192)), 256, 0, s>>>(R->row_ptr, R->nbr, R->col, tsrc); ::amg::count_launch(1);
         transpose_values_kernel<<<nblk(P.nnzb), T1D, 0, s>>>(tsrc, P.nnzb, P.br, P.bc, P.val,
                                                               R->val); ::amg::count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
@@ -628,11 +659,16 @@ __global__ void spgemm_values_kernel(const int *__restrict__ xrp, const int *__r
                                      const double *__restrict__ xval, const int *__restrict__ yrp,
                                      const int *__restrict__ ycol, const double *__restrict__ yval,
                                      const int *__restrict__ cbrow, const int *__restrict__ ccol,
-                                     int64_t nnzc, double *__restrict__ cval)
+                                     int64_t nnzc, int upper, double *__restrict__ cval)
 {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= nnzc) return;
     const int i = cbrow[q], j = ccol[q];
+    if (upper && j < i) {  // filled from block (j, i) by mirror_lower_kernel
+#pragma unroll
+        for (int e = 0; e < XR * YC; ++e) cval[q * XR * YC + e] = 0.0;
+        return;
+    }
     double acc[XR][YC];
 #pragma unroll
     for (int r = 0; r < XR; ++r)
@@ -673,7 +709,7 @@ template <int XR, int XC, int YC, int L>
 __global__ void __launch_bounds__(128) spgemm_rows_kernel(
     const int *__restrict__ xrp, const int *__restrict__ xcol, const double *__restrict__ xval,
     const int *__restrict__ yrp, const int *__restrict__ ycol, const double *__restrict__ yval,
-    const int *__restrict__ crp, const int *__restrict__ ccol, int nrows, int cmax,
+    const int *__restrict__ crp, const int *__restrict__ ccol, int nrows, int cmax, int upper,
     double *__restrict__ cval)
 {
     constexpr int CB = XR * YC;
@@ -696,6 +732,7 @@ __global__ void __launch_bounds__(128) spgemm_rows_kernel(
             const int hi = yrp[k + 1];
             for (int t = yrp[k] + lane; t < hi; t += L) {
                 const int j = ycol[t];
+                if (upper && j < i) continue;  // lower blocks: mirror_lower_kernel
                 const int pos = find_sorted(cols, 0, len, j);
                 if (pos >= len || cols[pos] != j) continue;  // cannot happen: C holds every product
                 const double *yb = yval + (int64_t)t * XC * YC;
@@ -724,8 +761,8 @@ __global__ void row_max_kernel(const int *__restrict__ rp, int n, int *__restric
 }
 
 template <int XR, int XC, int YC>
-static int spgemm_rows(const BsrD &X, const BsrD &Y, BsrD *C, int cmax, int lanes, cudaStream_t s,
-                       bool *done)
+static int spgemm_rows(const BsrD &X, const BsrD &Y, BsrD *C, int cmax, int lanes, int upper,
+                       cudaStream_t s, bool *done)
 {
     constexpr int CB = XR * YC;
     *done = false;
@@ -739,7 +776,7 @@ static int spgemm_rows(const BsrD &X, const BsrD &Y, BsrD *C, int cmax, int lane
                                               (int)smem));
         const int grid = std::max(1, std::min((X.nbr + groups - 1) / groups, 1 << 20));
         kern<<<grid, groups * L, smem, s>>>(X.row_ptr, X.col, X.val, Y.row_ptr, Y.col, Y.val, C->row_ptr,
-                                     C->col, X.nbr, cmax, C->val);
+                                     C->col, X.nbr, cmax, upper, C->val);
         ::amg::count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
         *done = true;
@@ -750,8 +787,34 @@ static int spgemm_rows(const BsrD &X, const BsrD &Y, BsrD *C, int cmax, int lane
     return go(spgemm_rows_kernel<XR, XC, YC, 32>, 32);
 }
 
+// Lower blocks of a product known to be symmetric: C_ij = C_ji^T, one
+// thread per block row.
+template <int BS>
+__global__ void mirror_lower_kernel(const int *__restrict__ crp, const int *__restrict__ ccol,
+                                    int nrows, double *__restrict__ cval)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows) return;
+    for (int q = crp[i]; q < crp[i + 1]; ++q) {
+        const int j = ccol[q];
+        if (j >= i) break;
+        const int lo = crp[j], hi = crp[j + 1];
+        const int t = find_sorted(ccol, lo, hi, i);
+        if (t >= hi || ccol[t] != i) continue;  // cannot happen for a symmetric pattern
+        const double *src = cval + (int64_t)t * BS * BS;
+        double *dst = cval + (int64_t)q * BS * BS;
+#pragma unroll
+        for (int r = 0; r < BS; ++r)
+#pragma unroll
+            for (int c = 0; c < BS; ++c) dst[r * BS + c] = src[c * BS + r];
+    }
+}
+
+// C = X Y.  symmetric: C is known to be symmetric (the Galerkin product
+// R (A P) with R = P^T and A symmetric): only the blocks on and above the
+// diagonal are computed, the others are their transposes.
 static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, cudaStream_t s,
-                  BsrD *C)
+                  BsrD *C, bool symmetric = false)
 {
     C->nbr = X.nbr;
     C->nbc = Y.nbc;
@@ -773,6 +836,7 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
     // only when there are rows enough to fill the GPU (on the 80^3 hierarchy
     // the row kernel took 12 / 30 / 18 ms for the three products with 22k+
     // rows against 20 / 36 / 28 ms, and lost on the ones with 1694 and 141)
+    const int upper = (symmetric && xr == yc && X.nbr == Y.nbc) ? 1 : 0;
     bool done = false;
     if (X.nbr < 16384) goto per_block;
     {
@@ -786,12 +850,13 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
     tmp.release(mx);
     const double ylen = Y.nbr ? (double)Y.nnzb / Y.nbr : 0.0;
     const int lanes = ylen <= 8.0 ? 8 : (ylen <= 16.0 ? 16 : 32);
-    if (xr == 3) AMG_TRY((spgemm_rows<3, 3, 6>(X, Y, C, cmax, lanes, s, &done)));
-    else if (xc == 6) AMG_TRY((spgemm_rows<6, 6, 6>(X, Y, C, cmax, lanes, s, &done)));
-    else AMG_TRY((spgemm_rows<6, 3, 6>(X, Y, C, cmax, lanes, s, &done)));
-    if (done) return AMG_OK;
+    if (xr == 3) AMG_TRY((spgemm_rows<3, 3, 6>(X, Y, C, cmax, lanes, upper, s, &done)));
+    else if (xc == 6) AMG_TRY((spgemm_rows<6, 6, 6>(X, Y, C, cmax, lanes, upper, s, &done)));
+    else AMG_TRY((spgemm_rows<6, 3, 6>(X, Y, C, cmax, lanes, upper, s, &done)));
+    if (done) goto mirror;
     }
 per_block:
+    {
     int *cbrow = nullptr;
     AMG_TRY(tmp.alloc_n(&cbrow, (size_t)std::max(total, 1)));
     if (X.nbr > 0) {
@@ -803,7 +868,7 @@ per_block:
 #define AMG_SPGEMM_VALS(XR_, XC_, YC_)                                                       \
     spgemm_values_kernel<XR_, XC_, YC_><<<g, 128, 0, s>>>(X.row_ptr, X.col, X.val, Y.row_ptr, \
                                                           Y.col, Y.val, cbrow, C->col, total, \
-                                                          C->val)
+                                                          upper, C->val)
     if (xr == 3) AMG_SPGEMM_VALS(3, 3, 6);
     else if (xc == 6) AMG_SPGEMM_VALS(6, 6, 6);
     else AMG_SPGEMM_VALS(6, 3, 6);
@@ -811,6 +876,13 @@ per_block:
 #undef AMG_SPGEMM_VALS
     AMG_TRY_CUDA(cudaGetLastError());
     tmp.release(cbrow);
+    }
+mirror:
+    if (upper) {
+        mirror_lower_kernel<6><<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, C->col, X.nbr, C->val);
+        ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
     return AMG_OK;
 }
 
@@ -822,7 +894,7 @@ int galerkin(const BsrD &A, const BsrD &P, const BsrD &R, DevArena &keep, DevAre
     DevArena apmem;
     apmem.stream = s;
     int st = spgemm(A, P, apmem, tmp, s, &AP);
-    if (st >= 0) st = spgemm(R, AP, keep, tmp, s, Ac);
+    if (st >= 0) st = spgemm(R, AP, keep, tmp, s, Ac, true);
     apmem.release_all();
     return st;
 }
