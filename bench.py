@@ -482,8 +482,13 @@ def main():
         # storage (FP32 accumulation), CG recurrences and dots in FP64
         u_ref, it_ref, _, _ = solver.solve(f, tol=tol, maxiter=5000)
         forms = {}
-        for name in ("fp64", "fp32", "bf16"):
-            sol = amg.AMG(rp, cl, val, B, precision=PRECS[name])
+        for name in ("fp64", "fp32", "bf16", "scalar_fp64", "scalar_fp32", "scalar_bf16"):
+            # scalar_*: the same hierarchy with every solve operator in scalar
+            # CSR rows (the scalar solver of Sec. 4) instead of blocks
+            scalar = name.startswith("scalar_")
+            pname = name.split("_")[-1]
+            sol = amg.AMG(rp, cl, val, B, precision=PRECS[pname],
+                          storage=amg.STORAGE_SCALAR if scalar else amg.STORAGE_BLOCK)
             sol.solve(f, tol=tol, maxiter=5000)  # warm-up (graph capture)
             times = []
             for _ in range(args.steps):
@@ -496,12 +501,18 @@ def main():
             err = float(torch.linalg.norm(u_p - u_ref) / torch.linalg.norm(u_ref))
             forms[name] = {"value": float(np.mean(times)), "iterations": it_p, "rel_resid": res_p,
                            "status": st_p, "err_vs_fp64_solution": err,
+                           "operator_bytes": int(sol.stats()["bytes_solve"]),
+                           "storage": "scalar CSR rows" if scalar else "blocks",
                            "vcycle": {"fp64": "FP64 matrices and vectors",
                                       "fp32": "FP32 matrices and vectors, FP32 accumulation",
-                                      "bf16": "BF16-stored matrices, FP32 vectors and accumulation"}[name]}
+                                      "bf16": "BF16-stored matrices, FP32 vectors and accumulation"}[pname]}
             del sol
         for name in ("fp32", "bf16"):
             forms[name]["speedup_vs_fp64"] = forms["fp64"]["value"] / forms[name]["value"]
+        for name in ("fp64", "fp32", "bf16"):
+            sc, bl = forms["scalar_" + name], forms[name]
+            sc["block_speedup"] = sc["value"] / bl["value"]
+            sc["block_memory_ratio"] = bl["operator_bytes"] / sc["operator_bytes"]
         if args.precision == "fp64":
             forms["learned"] = learned_form(amg, torch, solver, f, tol, u_ref,
                                             forms["fp64"]["value"], forms["fp64"]["iterations"],

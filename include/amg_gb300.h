@@ -52,6 +52,15 @@ extern "C" {
 #define AMG_PREC_FP32 1           /* V-cycle in FP32 storage, FP32 accumulation */
 #define AMG_PREC_BF16 2           /* V-cycle matrices stored BF16, FP32 accumulation */
 
+/* Storage of the solve's operators (amg_params.storage).  Sec. 4 compares
+ * the block-valued solver with a scalar one ("NS Scalar"): the same
+ * hierarchy, every operator in scalar CSR.  AMG_STORAGE_SCALAR keeps the
+ * block setup and stores the V-cycle's A_l, P_l, R_l and the CG's fine A
+ * unblocked (one scalar row per DOF, the blocks' explicit zeros kept), so
+ * the two storages run the same arithmetic and differ only in layout. */
+#define AMG_STORAGE_BLOCK 0       /* b x b blocks (3x3 fine, 6x6 coarse) */
+#define AMG_STORAGE_SCALAR 1      /* scalar CSR rows */
+
 /* Block CSR matrix, borrowed for the duration of a call.
  * row_ptr[nbrows+1] and col[nnzb] are int32 with columns strictly ascending
  * within each block row; val holds nnzb blocks of bs_r x bs_c doubles, each
@@ -80,7 +89,8 @@ typedef struct {
                               node); 1: the host launches one captured iteration graph
                               per CG step (for profilers that cannot look inside
                               conditional graphs).  Same kernels, same results. */
-    int32_t reserved[6];   /* must be zero */
+    int32_t storage;       /* AMG_STORAGE_* of the solve's operators (AMG_STORAGE_BLOCK) */
+    int32_t reserved[5];   /* must be zero */
 } amg_params;
 
 typedef struct amg_handle_s *amg_handle;
@@ -109,6 +119,9 @@ typedef struct {
     double learned_lambda;     /* lambda_max(M A) estimate of the last learned smoother
                                   offered to amg_set_learned_smoother (0 if none) */
     double spai0_lambda;       /* the same estimate for SPAI0 (0 until one was offered) */
+    int64_t bytes_solve;       /* the solve's operator copies (sliced A_l, P_l, R_l in the
+                                  V-cycle's precision and storage, plus the fine FP64 A):
+                                  values, column indices, slice pointers, row maps */
 } amg_stats;
 
 /* Fill *prm with the defaults listed above.  Returns AMG_OK. */

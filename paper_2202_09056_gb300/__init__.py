@@ -26,6 +26,7 @@ AMG_ERR_ARG, AMG_ERR_CUDA, AMG_ERR_BREAKDOWN, AMG_ERR_COARSE, AMG_ERR_LIMIT, AMG
 _ERRORS = {-1: "bad argument", -2: "CUDA error", -3: "CG breakdown",
            -4: "coarsest matrix not positive definite", -5: "size limit", -6: "bad state"}
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
+STORAGE_BLOCK, STORAGE_SCALAR = 0, 1
 
 
 class AmgError(RuntimeError):
@@ -45,7 +46,8 @@ class Params(ctypes.Structure):
                 ("smooth_relax", ctypes.c_double), ("coarse_enough", ctypes.c_int32),
                 ("max_levels", ctypes.c_int32), ("npre", ctypes.c_int32),
                 ("npost", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("loop_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("loop_mode", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class LevelDesc(ctypes.Structure):
@@ -60,7 +62,8 @@ class Stats(ctypes.Structure):
                 ("setup_seconds", ctypes.c_double), ("bytes_matrices", ctypes.c_int64),
                 ("bytes_total", ctypes.c_int64), ("operator_complexity", ctypes.c_double),
                 ("learned", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("learned_lambda", ctypes.c_double), ("spai0_lambda", ctypes.c_double)]
+                ("learned_lambda", ctypes.c_double), ("spai0_lambda", ctypes.c_double),
+                ("bytes_solve", ctypes.c_int64)]
 
 
 class BatchDesc(ctypes.Structure):

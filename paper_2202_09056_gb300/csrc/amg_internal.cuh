@@ -166,6 +166,8 @@ template <class TV> struct SellArgs {
 };
 
 int sell_grid(int nslices, int br, int bc, const Geom &g);
+// bytes a sliced copy holds on the device
+template <class T> int64_t sell_bytes(const Sell<T> &S);
 template <class VT, class TV>
 int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom &g,
                 cudaStream_t s, int *grid_out = nullptr);
@@ -191,6 +193,8 @@ int aggregate_host(int nn, const int *row_ptr, const int *col, const uint8_t *st
 int build_transfer(const BsrD &A, const double *B, const uint8_t *strong, const int *agg_h,
                    int nagg, double relax, DevArena &keep, DevArena &tmp, cudaStream_t s,
                    LevelBuild *out);
+// scalar CSR (1x1 blocks) copy of a BSR matrix, allocated in mem
+int unblock_bsr(const BsrD &B, DevArena &mem, cudaStream_t s, BsrD *out);
 int galerkin(const BsrD &A, const BsrD &P, const BsrD &R, DevArena &keep, DevArena &tmp,
              cudaStream_t s, BsrD *Ac);
 int spai0_diag(const BsrD &A, double scale, double *M, cudaStream_t s);

@@ -886,6 +886,10 @@ static void bdestroy(amg_batch h)
 
 static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, const int32_t *nrhs)
 {
+    if (h->prm.storage != AMG_STORAGE_BLOCK) {
+        set_error("the batched solve uses block storage");
+        return AMG_ERR_ARG;
+    }
     cudaStream_t s = h->stream;
     AMG_TRY(query_geom(&h->geom));
     const int ni = h->ninst;

@@ -774,8 +774,9 @@ int amg_set_learned_smoother(amg_handle h, const float *params, int32_t *fell_ba
         return AMG_ERR_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->lv.size() < 2 || h->prm.precision != AMG_PREC_FP64 || h->lv[0].A.br != 3) {
-        set_error("the learned smoother needs a multi-level FP64 hierarchy");
+    if (h->lv.size() < 2 || h->prm.precision != AMG_PREC_FP64 || h->lv[0].A.br != 3 ||
+        h->prm.storage != AMG_STORAGE_BLOCK) {
+        set_error("the learned smoother needs a multi-level FP64 hierarchy in block storage");
         return AMG_ERR_ARG;
     }
     DevArena tmp;

@@ -261,6 +261,7 @@ int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom
         return AMG_OK;
     }
     const int br = A.br, bc = A.bc;
+    if (br == 1 && bc == 1) return sell_mode<1, 1, VT, TV>(mode, dot, a, grid, s);
     if (br == 3 && bc == 3) return sell_mode<3, 3, VT, TV>(mode, dot, a, grid, s);
     if (br == 6 && bc == 6) return sell_mode<6, 6, VT, TV>(mode, dot, a, grid, s);
     if (br == 3 && bc == 6) return sell_mode<3, 6, VT, TV>(mode, dot, a, grid, s);
@@ -439,6 +440,18 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
     *out = S;
     return AMG_OK;
 }
+
+template <class T> int64_t sell_bytes(const Sell<T> &S)
+{
+    if (!S.slice_ptr) return 0;
+    const int rslots = S.G > 32 ? S.nslices / (S.G / 32) : S.nslices * (32 / S.G);
+    return S.nslots * (int64_t)(S.br * S.bc * sizeof(T) + sizeof(int)) +
+           (int64_t)(S.nslices + 1) * (int64_t)sizeof(int64_t) +
+           (S.perm ? (int64_t)rslots * (int64_t)sizeof(int) : 0);
+}
+template int64_t sell_bytes<double>(const Sell<double> &);
+template int64_t sell_bytes<float>(const Sell<float> &);
+template int64_t sell_bytes<__nv_bfloat16>(const Sell<__nv_bfloat16> &);
 
 template int bsr_to_sell<double>(const BsrD &, DevArena &, cudaStream_t, Sell<double> *, double *,
                                  int);

@@ -15,6 +15,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <climits>
+
 #include "amg_internal.cuh"
 
 namespace amg {
@@ -1171,6 +1173,76 @@ int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
     tmp.release(brow);
     tmp.release(err);
     *Ainv_out = X;
+    return AMG_OK;
+}
+
+
+// ---------------------------------------------------------------- scalar storage
+// Scalar CSR of a BSR matrix: block row I becomes rows I br .. I br + br - 1,
+// each holding the row's blocks' entries in block order (columns J bc + c,
+// ascending); explicit zeros inside blocks are kept.
+__global__ void unblock_rows_kernel(const int *__restrict__ rp, int nbr, int br, int bc,
+                                    int *__restrict__ srp)
+{
+    const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (row > (int64_t)nbr * br) return;
+    if (row == (int64_t)nbr * br) {
+        srp[row] = rp[nbr] * br * bc;
+        return;
+    }
+    const int I = (int)(row / br), r = (int)(row % br);
+    srp[row] = rp[I] * br * bc + r * (rp[I + 1] - rp[I]) * bc;
+}
+
+__global__ void unblock_vals_kernel(const int *__restrict__ rp, const int *__restrict__ brow,
+                                    const int *__restrict__ col, const double *__restrict__ val,
+                                    int64_t nnzb, int br, int bc, const int *__restrict__ srp,
+                                    int *__restrict__ scol, double *__restrict__ sval)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nnzb * br) return;
+    const int64_t k = t / br;
+    const int r = (int)(t % br);
+    const int I = brow[k];
+    const int64_t dst = srp[(int64_t)I * br + r] + (k - rp[I]) * bc;
+    for (int c = 0; c < bc; ++c) {
+        scol[dst + c] = col[k] * bc + c;
+        sval[dst + c] = val[k * br * bc + r * bc + c];
+    }
+}
+
+int unblock_bsr(const BsrD &B, DevArena &mem, cudaStream_t s, BsrD *out)
+{
+    const int64_t nnz = B.nnzb * B.br * B.bc;
+    const int64_t nrows = (int64_t)B.nbr * B.br;
+    if (nnz > INT32_MAX || nrows >= INT32_MAX || (int64_t)B.nbc * B.bc >= INT32_MAX) {
+        set_error("scalar storage: %lld entries exceed 32-bit indices", (long long)nnz);
+        return AMG_ERR_LIMIT;
+    }
+    BsrD U;
+    U.nbr = (int)nrows;
+    U.nbc = B.nbc * B.bc;
+    U.br = U.bc = 1;
+    U.nnzb = nnz;
+    AMG_TRY(mem.alloc_n(&U.row_ptr, (size_t)nrows + 1));
+    AMG_TRY(mem.alloc_n(&U.col, (size_t)std::max<int64_t>(nnz, 1)));
+    AMG_TRY(mem.alloc_n(&U.val, (size_t)std::max<int64_t>(nnz, 1)));
+    unblock_rows_kernel<<<nblk(nrows + 1), T1D, 0, s>>>(B.row_ptr, B.nbr, B.br, B.bc, U.row_ptr);
+    ::amg::count_launch(1);
+    if (B.nnzb > 0) {
+        int *brow = nullptr;
+        AMG_TRY(mem.alloc_n(&brow, (size_t)B.nnzb));
+        block_rows_kernel<<<nblk(B.nbr), T1D, 0, s>>>(B.row_ptr, B.nbr, brow);
+        unblock_vals_kernel<<<nblk(B.nnzb * B.br), T1D, 0, s>>>(B.row_ptr, brow, B.col, B.val,
+                                                                 B.nnzb, B.br, B.bc, U.row_ptr,
+                                                                 U.col, U.val);
+        ::amg::count_launch(2);
+        AMG_TRY_CUDA(cudaGetLastError());
+        AMG_TRY_CUDA(cudaStreamSynchronize(s));
+        mem.release(brow);
+    }
+    AMG_TRY_CUDA(cudaGetLastError());
+    *out = U;
     return AMG_OK;
 }
 

@@ -744,24 +744,49 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
     // V-cycle operators in the sliced layout, in the V-cycle's precision; the
     // fine A is also kept in FP64 for the CG products.
     const int prec = prm.precision;
+    const bool scalar = prm.storage == AMG_STORAGE_SCALAR;
     for (size_t l = 0; l < h->lv.size(); ++l) {
         Level &L = h->lv[l];
         const bool vc = !L.coarsest;
+        // the operators as stored for the solve: the block BSR itself, or its
+        // scalar unblocking (temporary; only the sliced copies are kept)
+        BsrD uA, uP, uR;
+        const BsrD *oA = &L.A, *oP = &L.P, *oR = &L.R;
+        if (scalar) {
+            if (l == 0 || vc) {
+                AMG_TRY(unblock_bsr(L.A, tmp, s, &uA));
+                oA = &uA;
+            }
+            if (vc) {
+                AMG_TRY(unblock_bsr(L.P, tmp, s, &uP));
+                AMG_TRY(unblock_bsr(L.R, tmp, s, &uR));
+                oP = &uP;
+                oR = &uR;
+            }
+        }
         if (l == 0 || (vc && prec == AMG_PREC_FP64))
-            AMG_TRY(bsr_to_sell<double>(L.A, h->mem, s, &L.sA, &L.pad_A, h->max_lanes));
+            AMG_TRY(bsr_to_sell<double>(*oA, h->mem, s, &L.sA, &L.pad_A, h->max_lanes));
         if (vc && prec == AMG_PREC_FP64) {
-            AMG_TRY(bsr_to_sell<double>(L.P, h->mem, s, &L.sP, &L.pad_P, h->max_lanes));
-            AMG_TRY(bsr_to_sell<double>(L.R, h->mem, s, &L.sR, &L.pad_R, h->max_lanes));
+            AMG_TRY(bsr_to_sell<double>(*oP, h->mem, s, &L.sP, &L.pad_P, h->max_lanes));
+            AMG_TRY(bsr_to_sell<double>(*oR, h->mem, s, &L.sR, &L.pad_R, h->max_lanes));
         }
         if (vc && prec == AMG_PREC_FP32) {
-            AMG_TRY(bsr_to_sell<float>(L.A, h->mem, s, &L.fA, &L.pad_A, h->max_lanes));
-            AMG_TRY(bsr_to_sell<float>(L.P, h->mem, s, &L.fP, &L.pad_P, h->max_lanes));
-            AMG_TRY(bsr_to_sell<float>(L.R, h->mem, s, &L.fR, &L.pad_R, h->max_lanes));
+            AMG_TRY(bsr_to_sell<float>(*oA, h->mem, s, &L.fA, &L.pad_A, h->max_lanes));
+            AMG_TRY(bsr_to_sell<float>(*oP, h->mem, s, &L.fP, &L.pad_P, h->max_lanes));
+            AMG_TRY(bsr_to_sell<float>(*oR, h->mem, s, &L.fR, &L.pad_R, h->max_lanes));
         }
         if (vc && prec == AMG_PREC_BF16) {
-            AMG_TRY(bsr_to_sell<__nv_bfloat16>(L.A, h->mem, s, &L.bA, &L.pad_A, h->max_lanes));
-            AMG_TRY(bsr_to_sell<__nv_bfloat16>(L.P, h->mem, s, &L.bP, &L.pad_P, h->max_lanes));
-            AMG_TRY(bsr_to_sell<__nv_bfloat16>(L.R, h->mem, s, &L.bR, &L.pad_R, h->max_lanes));
+            AMG_TRY(bsr_to_sell<__nv_bfloat16>(*oA, h->mem, s, &L.bA, &L.pad_A, h->max_lanes));
+            AMG_TRY(bsr_to_sell<__nv_bfloat16>(*oP, h->mem, s, &L.bP, &L.pad_P, h->max_lanes));
+            AMG_TRY(bsr_to_sell<__nv_bfloat16>(*oR, h->mem, s, &L.bR, &L.pad_R, h->max_lanes));
+        }
+        if (scalar) {
+            AMG_TRY_CUDA(cudaStreamSynchronize(s));
+            for (BsrD *u : {&uA, &uP, &uR}) {
+                if (u->row_ptr) tmp.release(u->row_ptr);
+                if (u->col) tmp.release(u->col);
+                if (u->val) tmp.release(u->val);
+            }
         }
     }
     for (size_t l = 0; l < h->lv.size(); ++l) {
@@ -834,8 +859,8 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
     if (prm) p = *prm;
     if (p.npre < 0 || p.npost < 0 || p.max_levels < 1 || p.coarse_enough < 0 ||
         !(p.eps_strong >= 0.0) || p.precision < AMG_PREC_FP64 || p.precision > AMG_PREC_BF16 ||
-        p.loop_mode < 0 ||
-        p.loop_mode > 1) {
+        p.loop_mode < 0 || p.loop_mode > 1 || p.storage < AMG_STORAGE_BLOCK ||
+        p.storage > AMG_STORAGE_SCALAR) {
         set_error("bad parameters");
         return AMG_ERR_ARG;
     }
@@ -1022,6 +1047,12 @@ int amg_get_stats(amg_handle h, amg_stats *out)
     out->operator_complexity = nnz0 ? (double)nnz / (double)nnz0 : 0.0;
     out->learned = h->learned;
     out->learned_lambda = h->learned_lambda;
+    int64_t sb = 0;
+    for (const Level &L : h->lv)
+        sb += sell_bytes(L.sA) + sell_bytes(L.sP) + sell_bytes(L.sR) + sell_bytes(L.fA) +
+              sell_bytes(L.fP) + sell_bytes(L.fR) + sell_bytes(L.bA) + sell_bytes(L.bP) +
+              sell_bytes(L.bR);
+    out->bytes_solve = sb;
     out->spai0_lambda = h->spai0_lambda;
     return AMG_OK;
 }
