@@ -41,7 +41,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("eps_strong", ctypes.c_double), ("coarse_enough", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("npre", ctypes.c_int),
                 ("npost", ctypes.c_int), ("relax", ctypes.c_double),
-                ("smooth_relax", ctypes.c_double)]
+                ("smooth_relax", ctypes.c_double), ("ns", ctypes.c_int)]
 
 
 def _load():
@@ -62,7 +62,7 @@ def _load():
         "orc_graph_copy": ([P, P, P, P, P], None),
         "orc_strength": ([P, i, d], P),
         "orc_aggregate": ([P, P], i64),
-        "orc_tentative": ([i64, i, P, i64, P, P], P),
+        "orc_tentative": ([i64, i, P, i64, P, i, P], P),
         "orc_jacobi_rho": ([P, P, P], None),
         "orc_spgemm": ([P, P], P),
         "orc_transpose": ([P], P),
@@ -202,8 +202,9 @@ def tentative(nnodes: int, b: int, agg: np.ndarray, nagg: int, B: np.ndarray):
     """(P_tent, B_c) from the aggregates and the near-nullspace."""
     agg = np.ascontiguousarray(agg, dtype=np.int32)
     B = np.ascontiguousarray(B, dtype=np.float64)
-    Bc = np.empty((nagg * 6, 6))
-    h = _load().orc_tentative(nnodes, b, _p(agg), nagg, _p(B), _p(Bc))
+    ns = B.shape[1]
+    Bc = np.empty((nagg * ns, ns))
+    h = _load().orc_tentative(nnodes, b, _p(agg), nagg, _p(B), ns, _p(Bc))
     return CSR._from_handle(h), Bc
 
 
@@ -262,9 +263,11 @@ class Hierarchy:
     def __init__(self, A: CSR, bs: int, B: np.ndarray, *, eps_strong=0.08, coarse_enough=3000,
                  max_levels=15, npre=1, npost=1, relax=1.0, smooth_relax=0.8):
         lib = _load()
-        prm = _Params(eps_strong, coarse_enough, max_levels, npre, npost, relax, smooth_relax)
-        self._A = _Owned(A)
         B = np.ascontiguousarray(B, dtype=np.float64)
+        self.ns = B.shape[1]
+        prm = _Params(eps_strong, coarse_enough, max_levels, npre, npost, relax, smooth_relax,
+                      self.ns)
+        self._A = _Owned(A)
         st = ctypes.c_int(0)
         self.h = lib.orc_setup(self._A.h, bs, _p(B), ctypes.byref(prm), ctypes.byref(st))
         if not self.h:
@@ -289,7 +292,7 @@ class Hierarchy:
         out["A"] = CSR._from_handle(lib.orc_level_matrix(self.h, l, 0), free=False)
         agg = np.empty(n // b, dtype=np.int32) if hasP else None
         M = np.empty(n) if hasP else None
-        B = np.empty((n, 6))
+        B = np.empty((n, self.ns))
         d = np.empty(n) if hasP else None
         lib.orc_level_vectors(self.h, l, _p(agg), _p(M), _p(B), _p(d))
         out.update(agg=agg, M=M, B=B, d=d)

@@ -325,15 +325,17 @@ int64_t orc_aggregate(const orc_graph *G, int32_t *agg)
 }
 
 /* Tentative prolongation from the near-nullspace (Sec. 2; Sec. 3 notes this
- * step is scalar).  B is n x 6 (n = nnodes * b), row-major.  For aggregate a
- * the member rows of B are stacked in ascending node order and factored by
- * modified Gram-Schmidt with re-orthogonalisation.  P_tent row (b I + r) holds
- * the matching Q row in columns 6a..6a+5 (all six stored, zeros included);
- * Bc rows 6a..6a+5 are R.  Isolated nodes get empty rows. */
+ * step is scalar).  B is n x ns (n = nnodes * b, ns <= 6), row-major: the six
+ * rigid-body modes, or the three translations (the block solver of Sec. 4
+ * without a near-nullspace, whose tentative prolongation is the block
+ * identity per aggregate).  For aggregate a the member rows of B are stacked
+ * in ascending node order and factored by modified Gram-Schmidt with
+ * re-orthogonalisation.  P_tent row (b I + r) holds the matching Q row in
+ * columns ns a .. ns a + ns - 1 (all stored, zeros included); Bc rows
+ * ns a .. ns a + ns - 1 are R.  Isolated nodes get empty rows. */
 orc_csr *orc_tentative(int64_t nnodes, int b, const int32_t *agg, int64_t nagg, const double *B,
-                       double *Bc)
+                       int ns, double *Bc)
 {
-    const int ns = 6;
     int64_t n = nnodes * b;
     int64_t *cnt = (int64_t *)calloc((size_t)nagg + 1, sizeof(int64_t));
     for (int64_t I = 0; I < nnodes; ++I)
@@ -358,7 +360,7 @@ orc_csr *orc_tentative(int64_t nnodes, int b, const int32_t *agg, int64_t nagg, 
 
     for (int64_t a = 0; a < nagg; ++a) {
         int64_t na = cnt[a + 1] - cnt[a], m = na * b;
-        double *Q = (double *)calloc((size_t)(m * ns), sizeof(double)); /* column-major m x 6 */
+        double *Q = (double *)calloc((size_t)(m * ns), sizeof(double)); /* column-major m x ns */
         double R[6][6];
         memset(R, 0, sizeof R);
         for (int64_t t = 0; t < na; ++t)
@@ -610,7 +612,7 @@ typedef struct {
     double eps, omega, rho;
     double *M;  /* SPAI0 diagonal */
     double *Mb; /* optional block smoother (3x3 per node, row-major), replaces M */
-    double *B;  /* near-nullspace of this level, n x 6 */
+    double *B;  /* near-nullspace of this level, n x ns */
     double *d;  /* filtered diagonal */
 } orc_level;
 
@@ -621,6 +623,7 @@ typedef struct {
     uint8_t *zrow;
     int64_t nc;
     int npre, npost;
+    int ns;           /* near-nullspace columns (6 or 3) = DOFs of a coarse node */
     double *work;     /* scratch, 3 vectors per level */
 } orc_hier;
 
@@ -631,6 +634,7 @@ typedef struct {
     int npre, npost;     /* 1, 1 */
     double relax;        /* omega multiplier, 1.0 */
     double smooth_relax; /* smoother damping w_s, 0.8 */
+    int ns;              /* near-nullspace columns of B: 6 (rigid-body modes) or 3 */
 } orc_params;
 
 void orc_params_default(orc_params *p)
@@ -642,6 +646,7 @@ void orc_params_default(orc_params *p)
     p->npost = 1;
     p->relax = 1.0;
     p->smooth_relax = 0.8;
+    p->ns = 6;
 }
 
 void orc_free(orc_hier *H)
@@ -665,19 +670,27 @@ void orc_free(orc_hier *H)
     free(H);
 }
 
-/* Alg. 1.  A is scalar CSR (n = nnodes * bs rows), B is n x 6.  The hierarchy
- * takes a copy of A.  Returns NULL on failure, with *status < 0. */
+/* Alg. 1.  A is scalar CSR (n = nnodes * bs rows), B is n x prm->ns; coarse
+ * nodes carry ns DOFs.  The hierarchy takes a copy of A.  Returns NULL on
+ * failure, with *status < 0. */
 orc_hier *orc_setup(const orc_csr *A0, int bs, const double *B0, const orc_params *prm,
                     int *status)
 {
     orc_hier *H = (orc_hier *)calloc(1, sizeof(orc_hier));
     H->npre = prm->npre;
     H->npost = prm->npost;
+    const int ns = prm->ns;
+    if (ns != 3 && ns != 6) {
+        *status = -1;
+        free(H);
+        return NULL;
+    }
+    H->ns = ns;
     orc_level *L0 = &H->lv[0];
     L0->A = orc_csr_from(A0->nrows, A0->ncols, A0->ptr, A0->col, A0->val);
     L0->b = bs;
-    L0->B = (double *)malloc(sizeof(double) * (size_t)(A0->nrows * 6));
-    memcpy(L0->B, B0, sizeof(double) * (size_t)(A0->nrows * 6));
+    L0->B = (double *)malloc(sizeof(double) * (size_t)(A0->nrows * ns));
+    memcpy(L0->B, B0, sizeof(double) * (size_t)(A0->nrows * ns));
     L0->eps = prm->eps_strong;
     H->nlev = 1;
     *status = 0;
@@ -698,8 +711,8 @@ orc_hier *orc_setup(const orc_csr *A0, int bs, const double *B0, const orc_param
             break;
         }
         orc_level *N = &H->lv[H->nlev];
-        N->B = (double *)malloc(sizeof(double) * (size_t)(C->nagg * 36));
-        orc_csr *Pt = orc_tentative(nn, C->b, C->agg, C->nagg, C->B, N->B);
+        N->B = (double *)malloc(sizeof(double) * (size_t)(C->nagg * ns * ns));
+        orc_csr *Pt = orc_tentative(nn, C->b, C->agg, C->nagg, C->B, ns, N->B);
         C->d = (double *)malloc(sizeof(double) * (size_t)n);
         orc_jacobi_rho(C->A, C->d, &C->rho);
         C->omega = (C->rho > 0.0) ? prm->relax * (4.0 / 3.0) / C->rho : 0.0;
@@ -712,7 +725,7 @@ orc_hier *orc_setup(const orc_csr *A0, int bs, const double *B0, const orc_param
         C->M = (double *)malloc(sizeof(double) * (size_t)n);
         orc_spai0(C->A, C->M);
         for (int64_t i = 0; i < n; ++i) C->M[i] = prm->smooth_relax * C->M[i];
-        N->b = 6;
+        N->b = ns;
         N->eps = C->eps * 0.5;
         H->nlev++;
     }
@@ -905,7 +918,7 @@ void orc_level_vectors(const orc_hier *H, int l, int32_t *agg, double *M, double
     int64_t n = L->A->nrows;
     if (agg && L->agg) memcpy(agg, L->agg, sizeof(int32_t) * (size_t)(n / L->b));
     if (M && L->M) memcpy(M, L->M, sizeof(double) * (size_t)n);
-    if (B && L->B) memcpy(B, L->B, sizeof(double) * (size_t)(n * 6));
+    if (B && L->B) memcpy(B, L->B, sizeof(double) * (size_t)(n * H->ns));
     if (d && L->d) memcpy(d, L->d, sizeof(double) * (size_t)n);
 }
 

@@ -151,6 +151,73 @@ def test_tentative_single_node_aggregate_is_rank_three():
     assert np.count_nonzero(np.abs(Bc).sum(1)) == 3
 
 
+def _translations(ndof):
+    T = np.zeros((ndof, 3))
+    for c in range(3):
+        T[c::3, c] = 1.0
+    return T
+
+
+def test_tentative_translations_is_normalised_block_identity():
+    # Without rotations (the block solver with no near-nullspace) the stacked
+    # member rows of an aggregate of n_a nodes are n_a identity blocks: Q is
+    # the block identity over sqrt(n_a) and R = sqrt(n_a) I, in closed form.
+    p = q.make_problem((4, 3, 3), clamp=False, body=(0, 0, -1))
+    A = o.from_problem(p)
+    agg, nagg = o.aggregate(A, 3, 0.08)
+    Pt, Bc = o.tentative(p.nnodes, 3, agg, nagg, _translations(p.ndof))
+    Pd = Pt.to_dense()
+    assert Pd.shape == (p.ndof, 3 * nagg) and Bc.shape == (3 * nagg, 3)
+    for a in range(nagg):
+        na = int((agg == a).sum())
+        np.testing.assert_allclose(Bc[3 * a:3 * a + 3], np.sqrt(na) * np.eye(3), rtol=1e-15)
+        for I in np.nonzero(agg == a)[0]:
+            np.testing.assert_allclose(Pd[3 * I:3 * I + 3, 3 * a:3 * a + 3], np.eye(3) / np.sqrt(na),
+                                       rtol=1e-15, atol=0)
+    assert np.count_nonzero(Pd) == 3 * int((agg >= 0).sum())
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.08])
+def test_smoothed_prolongation_keeps_translations(eps):
+    # The same chain as for the rigid modes with B = the three translations
+    # (A T = 0 on the unconstrained operator too); coarse nodes carry 3 DOFs.
+    p = q.make_problem((6, 5, 4), clamp=False, body=(0, 0, -1))
+    A, B, b = o.from_problem(p), _translations(p.ndof), 3
+    for level in range(3):
+        nn = A.shape[0] // b
+        agg, nagg = o.aggregate(A, b, eps * 0.5 ** level)
+        assert nagg < nn
+        rows = np.repeat(agg >= 0, b)
+        Pt, Bc = o.tentative(nn, b, agg, nagg, B)
+        assert Bc.shape == (3 * nagg, 3)
+        d, rho = o.jacobi_rho(A)
+        P = o.smooth_prolongation(A, d, (4.0 / 3.0) / rho, Pt)
+        assert np.abs((P.to_scipy() @ Bc - B)[rows]).max() <= 1e-10
+        Ac = o.spgemm(o.transpose(P), o.spgemm(A, P))
+        As = Ac.to_scipy()
+        scale = max(abs(As).max(), abs(A.to_scipy()).max())
+        assert np.abs(As @ Bc).max() <= 1e-10 * scale * np.abs(Bc).max()
+        A, B = Ac, Bc
+        if nagg < 2:
+            break
+
+
+def test_translations_only_hierarchy_solves_and_is_weaker():
+    # The block solver without a near-nullspace: 3-DOF coarse nodes, PCG to a
+    # dense direct solve's answer; the rigid-body modes cut the iterations.
+    p = q.make_problem((5, 4, 6), traction=(0, 0, -1), inclusion_frac=0.2)
+    H3 = o.Hierarchy(o.from_problem(p), 3, _translations(p.ndof), coarse_enough=150)
+    H6 = o.Hierarchy(o.from_problem(p), 3, p.B, coarse_enough=150)
+    assert H3.nlevels >= 2 and all(H3.level(l)["b"] == 3 for l in range(H3.nlevels))
+    assert H3.level(1)["n"] == 3 * H3.level(0)["nagg"]
+    u3, it3, res3 = H3.solve(p.f, tol=1e-8, maxiter=3000)
+    u6, it6, _ = H6.solve(p.f, tol=1e-8)
+    ud = np.linalg.solve(q.bsr_to_dense(p), p.f)
+    assert res3 <= 1e-8
+    assert np.linalg.norm(u3 - ud) <= 1e-7 * np.linalg.norm(ud)
+    assert it6 < it3
+
+
 # ---------------------------------------------------------------- Jacobi rho, omega, P
 def test_jacobi_diagonal_and_gershgorin_bound():
     p = q.inclusions(5)
