@@ -128,8 +128,10 @@ typedef struct {
 int amg_params_default(amg_params *prm);
 
 /* Alg. 1: build the hierarchy for A (3x3 BSR, square, symmetric positive
- * definite) with near-nullspace B (device, row-major [nbrows*3][nb_ns],
- * nb_ns = 6: three translations and three rotations).  prm may be NULL for
+ * definite) with near-nullspace B (device, row-major [nbrows*3][nb_ns]:
+ * nb_ns = 6, the three translations and three rotations, or nb_ns = 3, the
+ * translations only, which is the block solver of Sec. 4 without a
+ * near-nullspace; coarse nodes carry nb_ns DOFs).  prm may be NULL for
  * the defaults.  On success *out owns every level on the device (allocated
  * stream-ordered on `stream`).  A and B are only read. */
 int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params *prm,

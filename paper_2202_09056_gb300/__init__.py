@@ -218,6 +218,7 @@ class AMG:
         self.params = params if params is not None else default_params(**kw)
         A = make_bsr(row_ptr, col, val)
         self.n = A.nbrows * A.bs_r
+        self.ns = int(B.shape[1])
         self.device = val.device
         h = ctypes.c_void_p()
         _check(self._lib.amg_setup(ctypes.byref(A), _dptr(B, torch.float64, "B"),
@@ -319,8 +320,8 @@ class AMG:
 
         out["A"] = bsr(0, nbr, info["nnzb_A"], bs, bs)
         if not info["is_coarsest"]:
-            out["P"] = bsr(1, nbr, info["nnzb_P"], bs, 6)
-            out["R"] = bsr(2, info["nagg"], info["nnzb_P"], 6, bs)
+            out["P"] = bsr(1, nbr, info["nnzb_P"], bs, self.ns)
+            out["R"] = bsr(2, info["nagg"], info["nnzb_P"], self.ns, bs)
             agg = np.empty(nbr, np.int32)
             _check(self._lib.amg_level_export(self._h, l, 3, agg.ctypes.data, None, None))
             out["agg"] = agg
@@ -330,7 +331,7 @@ class AMG:
             strong = np.empty(max(info["nnzb_A"], 1), np.uint8)
             _check(self._lib.amg_level_export(self._h, l, 6, strong.ctypes.data, None, None))
             out["strong"] = strong[:info["nnzb_A"]]
-        B = np.empty((nbr * bs, 6))
+        B = np.empty((nbr * bs, self.ns))
         _check(self._lib.amg_level_export(self._h, l, 5, None, None, B.ctypes.data))
         out["B"] = B
         return out

@@ -190,9 +190,9 @@ int exclusive_scan_i32(const int *in, int *out, int n, int *total_host, DevArena
 int compute_strength(const BsrD &A, double eps, uint8_t *strong, cudaStream_t s);
 int aggregate_host(int nn, const int *row_ptr, const int *col, const uint8_t *strong,
                    int *agg, int *nagg);   // host arrays
-int build_transfer(const BsrD &A, const double *B, const uint8_t *strong, const int *agg_h,
-                   int nagg, double relax, DevArena &keep, DevArena &tmp, cudaStream_t s,
-                   LevelBuild *out);
+int build_transfer(const BsrD &A, const double *B, int ns, const uint8_t *strong,
+                   const int *agg_h, int nagg, double relax, DevArena &keep, DevArena &tmp,
+                   cudaStream_t s, LevelBuild *out);
 // scalar CSR (1x1 blocks) copy of a BSR matrix, allocated in mem
 int unblock_bsr(const BsrD &B, DevArena &mem, cudaStream_t s, BsrD *out);
 int galerkin(const BsrD &A, const BsrD &P, const BsrD &R, DevArena &keep, DevArena &tmp,
@@ -230,6 +230,7 @@ struct amg_handle_s {
     cudaStream_t stream = nullptr;
     amg::Geom geom;
     int max_lanes = 128;          // cap on lanes per row of the sliced copies
+    int ns = 6;                   // near-nullspace columns = DOFs of a coarse node (6 or 3)
     amg::DevArena mem;
     std::vector<amg::Level> lv;
     double *Ainv = nullptr;

@@ -174,11 +174,13 @@ template <class T> __device__ __forceinline__ T wsum(T v)
 }
 
 // One warp per aggregate.  The member rows of B (ascending node order, b rows
-// per node) are stacked into Qs (row-major, 6 columns) and orthonormalised by
+// per node) are stacked into Qs (row-major, NS columns: NS rigid-body modes or
+// 3 translations) and orthonormalised by
 // modified Gram-Schmidt with one re-orthogonalisation pass; a column whose
 // norm drops to <= 1e-10 of its original norm is dropped (zero Q column and
 // zero R row).  Every lane owns rows lane, lane+32, ... of the stack, so only
 // the reductions cross lanes.
+template <int NS>
 __global__ void tentative_kernel(int nagg, int b, const int *__restrict__ agg_ptr,
                                  const int *__restrict__ members, const double *__restrict__ B,
                                  double *__restrict__ Qs, double *__restrict__ ptent,
@@ -188,57 +190,59 @@ __global__ void tentative_kernel(int nagg, int b, const int *__restrict__ agg_pt
     const int a = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (a >= nagg) return;
     const int m0 = agg_ptr[a], m = (agg_ptr[a + 1] - m0) * b;
-    double *Q = Qs + (int64_t)m0 * b * 6;
+    double *Q = Qs + (int64_t)m0 * b * NS;
     for (int i = lane; i < m; i += 32) {
         const int node = members[m0 + i / b], r = i % b;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) Q[i * 6 + k] = B[((int64_t)node * b + r) * 6 + k];
+        for (int k = 0; k < NS; ++k) Q[i * NS + k] = B[((int64_t)node * b + r) * NS + k];
     }
-    double R[6][6];
+    double R[NS][NS];
 #pragma unroll
-    for (int j = 0; j < 6; ++j)
+    for (int j = 0; j < NS; ++j)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) R[j][k] = 0.0;
-    bool dropped[6] = {false, false, false, false, false, false};
+        for (int k = 0; k < NS; ++k) R[j][k] = 0.0;
+    bool dropped[NS];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < NS; ++k) dropped[k] = false;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
         double s = 0.0;
-        for (int i = lane; i < m; i += 32) s += Q[i * 6 + k] * Q[i * 6 + k];
+        for (int i = lane; i < m; i += 32) s += Q[i * NS + k] * Q[i * NS + k];
         const double pre = sqrt(wsum(s));
         for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll
             for (int j = 0; j < k; ++j) {
                 if (dropped[j]) continue;
                 double t = 0.0;
-                for (int i = lane; i < m; i += 32) t += Q[i * 6 + j] * Q[i * 6 + k];
+                for (int i = lane; i < m; i += 32) t += Q[i * NS + j] * Q[i * NS + k];
                 const double d = wsum(t);
                 R[j][k] += d;
-                for (int i = lane; i < m; i += 32) Q[i * 6 + k] -= d * Q[i * 6 + j];
+                for (int i = lane; i < m; i += 32) Q[i * NS + k] -= d * Q[i * NS + j];
             }
         }
         s = 0.0;
-        for (int i = lane; i < m; i += 32) s += Q[i * 6 + k] * Q[i * 6 + k];
+        for (int i = lane; i < m; i += 32) s += Q[i * NS + k] * Q[i * NS + k];
         const double post = sqrt(wsum(s));
         if (post <= 1e-10 * pre) {
             dropped[k] = true;
-            for (int i = lane; i < m; i += 32) Q[i * 6 + k] = 0.0;
+            for (int i = lane; i < m; i += 32) Q[i * NS + k] = 0.0;
 #pragma unroll
-            for (int j = 0; j < 6; ++j) R[k][j] = 0.0;
+            for (int j = 0; j < NS; ++j) R[k][j] = 0.0;
         } else {
-            for (int i = lane; i < m; i += 32) Q[i * 6 + k] /= post;
+            for (int i = lane; i < m; i += 32) Q[i * NS + k] /= post;
             R[k][k] = post;
         }
     }
     if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k)
+        for (int k = 0; k < NS; ++k)
 #pragma unroll
-            for (int j = 0; j < 6; ++j) Bc[(int64_t)a * 36 + k * 6 + j] = R[k][j];
+            for (int j = 0; j < NS; ++j) Bc[(int64_t)a * NS * NS + k * NS + j] = R[k][j];
     }
     for (int i = lane; i < m; i += 32) {
         const int node = members[m0 + i / b], r = i % b;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) ptent[((int64_t)node * b + r) * 6 + k] = Q[i * 6 + k];
+        for (int k = 0; k < NS; ++k) ptent[((int64_t)node * b + r) * NS + k] = Q[i * NS + k];
     }
 }
 
@@ -489,7 +493,7 @@ __global__ void block_rows_kernel(const int *__restrict__ rp, int nbr, int *__re
 
 // P block (I, a) = [a == agg(I)] Pt_I - diag(omega / d) sum_{J: agg(J) = a}
 // A_IJ Pt_J, sums over J ascending then the inner index.
-template <int B>
+template <int B, int NS>
 __global__ void p_values_kernel(const int *__restrict__ rp, const int *__restrict__ col,
                                 const double *__restrict__ val, const uint8_t *__restrict__ strong,
                                 const int *__restrict__ agg, const double *__restrict__ ptent,
@@ -500,23 +504,23 @@ __global__ void p_values_kernel(const int *__restrict__ rp, const int *__restric
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= nnzp) return;
     const int I = pbrow[k], a = pcol[k];
-    double acc[B][6];
+    double acc[B][NS];
 #pragma unroll
     for (int r = 0; r < B; ++r)
 #pragma unroll
-        for (int q = 0; q < 6; ++q) acc[r][q] = 0.0;
+        for (int q = 0; q < NS; ++q) acc[r][q] = 0.0;
     for (int p = rp[I]; p < rp[I + 1]; ++p) {
         const int J = col[p];
         if (agg[J] != a) continue;
         const double *blk = val + (int64_t)p * B * B;
-        const double *pt = ptent + (int64_t)J * B * 6;
+        const double *pt = ptent + (int64_t)J * B * NS;
 #pragma unroll
         for (int r = 0; r < B; ++r)
 #pragma unroll
             for (int c = 0; c < B; ++c) {
                 const double af = blk[r * B + c];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) acc[r][q] += af * pt[c * 6 + q];
+                for (int q = 0; q < NS; ++q) acc[r][q] += af * pt[c * NS + q];
             }
     }
     const bool own = agg[I] == a;
@@ -525,9 +529,9 @@ __global__ void p_values_kernel(const int *__restrict__ rp, const int *__restric
         const double dr = d[(int64_t)I * B + r];
         const double sc = (dr != 0.0) ? omega / dr : 0.0;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const double pt = own ? ptent[((int64_t)I * B + r) * 6 + q] : 0.0;
-            pval[k * B * 6 + r * 6 + q] = pt - sc * acc[r][q];
+        for (int q = 0; q < NS; ++q) {
+            const double pt = own ? ptent[((int64_t)I * B + r) * NS + q] : 0.0;
+            pval[k * B * NS + r * NS + q] = pt - sc * acc[r][q];
         }
     }
 }
@@ -830,7 +834,7 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
     if (total == 0) return AMG_OK;
     const int xr = X.br, xc = X.bc, yc = Y.bc;
     if (!((xr == 3 && xc == 3 && yc == 6) || (xr == 6 && xc == 6 && yc == 6) ||
-          (xr == 6 && xc == 3 && yc == 6))) {
+          (xr == 6 && xc == 3 && yc == 6) || (xr == 3 && xc == 3 && yc == 3))) {
         set_error("unsupported block product %dx%d * %dx%d", xr, xc, X.bc, yc);
         return AMG_ERR_ARG;
     }
@@ -852,7 +856,8 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
     tmp.release(mx);
     const double ylen = Y.nbr ? (double)Y.nnzb / Y.nbr : 0.0;
     const int lanes = ylen <= 8.0 ? 8 : (ylen <= 16.0 ? 16 : 32);
-    if (xr == 3) AMG_TRY((spgemm_rows<3, 3, 6>(X, Y, C, cmax, lanes, upper, s, &done)));
+    if (xr == 3 && yc == 3) AMG_TRY((spgemm_rows<3, 3, 3>(X, Y, C, cmax, lanes, upper, s, &done)));
+    else if (xr == 3) AMG_TRY((spgemm_rows<3, 3, 6>(X, Y, C, cmax, lanes, upper, s, &done)));
     else if (xc == 6) AMG_TRY((spgemm_rows<6, 6, 6>(X, Y, C, cmax, lanes, upper, s, &done)));
     else AMG_TRY((spgemm_rows<6, 3, 6>(X, Y, C, cmax, lanes, upper, s, &done)));
     if (done) goto mirror;
@@ -871,7 +876,8 @@ per_block:
     spgemm_values_kernel<XR_, XC_, YC_><<<g, 128, 0, s>>>(X.row_ptr, X.col, X.val, Y.row_ptr, \
                                                           Y.col, Y.val, cbrow, C->col, total, \
                                                           upper, C->val)
-    if (xr == 3) AMG_SPGEMM_VALS(3, 3, 6);
+    if (xr == 3 && yc == 3) AMG_SPGEMM_VALS(3, 3, 3);
+    else if (xr == 3) AMG_SPGEMM_VALS(3, 3, 6);
     else if (xc == 6) AMG_SPGEMM_VALS(6, 6, 6);
     else AMG_SPGEMM_VALS(6, 3, 6);
     ::amg::count_launch(1);
@@ -881,7 +887,10 @@ per_block:
     }
 mirror:
     if (upper) {
-        mirror_lower_kernel<6><<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, C->col, X.nbr, C->val);
+        if (yc == 3)
+            mirror_lower_kernel<3><<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, C->col, X.nbr, C->val);
+        else
+            mirror_lower_kernel<6><<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, C->col, X.nbr, C->val);
         ::amg::count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
     }
@@ -902,9 +911,9 @@ int galerkin(const BsrD &A, const BsrD &P, const BsrD &R, DevArena &keep, DevAre
 }
 
 // ---------------------------------------------------------------- transfer operators
-int build_transfer(const BsrD &A, const double *B, const uint8_t *strong, const int *agg_h,
-                   int nagg, double relax, DevArena &keep, DevArena &tmp, cudaStream_t s,
-                   LevelBuild *out)
+int build_transfer(const BsrD &A, const double *B, int ns, const uint8_t *strong,
+                   const int *agg_h, int nagg, double relax, DevArena &keep, DevArena &tmp,
+                   cudaStream_t s, LevelBuild *out)
 {
     const int nn = A.nbr, b = A.br;
     // aggregate membership lists (ascending node order) from the host aggregation
@@ -924,22 +933,27 @@ int build_transfer(const BsrD &A, const double *B, const uint8_t *strong, const 
     AMG_TRY(tmp.alloc_n(&d_aptr, nagg + 1));
     AMG_TRY(tmp.alloc_n(&d_mem, mem.size()));
     AMG_TRY(keep.alloc_n(&out->agg, std::max(nn, 1)));
-    AMG_TRY(tmp.alloc_n(&Qs, (size_t)std::max(aptr[nagg], 1) * b * 6));
-    AMG_TRY(tmp.alloc_n(&ptent, (size_t)std::max(nn, 1) * b * 6));
+    AMG_TRY(tmp.alloc_n(&Qs, (size_t)std::max(aptr[nagg], 1) * b * ns));
+    AMG_TRY(tmp.alloc_n(&ptent, (size_t)std::max(nn, 1) * b * ns));
     AMG_TRY(tmp.alloc_n(&d, (size_t)std::max(nn, 1) * b));
     AMG_TRY(tmp.alloc_n(&rho_bits, 1));
-    AMG_TRY(keep.alloc_n(&out->Bc, (size_t)std::max(nagg, 1) * 36));
+    AMG_TRY(keep.alloc_n(&out->Bc, (size_t)std::max(nagg, 1) * ns * ns));
     AMG_TRY_CUDA(cudaMemcpyAsync(d_aptr, aptr.data(), sizeof(int) * (nagg + 1),
                                  cudaMemcpyHostToDevice, s));
     AMG_TRY_CUDA(cudaMemcpyAsync(d_mem, mem.data(), sizeof(int) * mem.size(),
                                  cudaMemcpyHostToDevice, s));
     AMG_TRY_CUDA(cudaMemcpyAsync(out->agg, agg_h, sizeof(int) * nn, cudaMemcpyHostToDevice, s));
-    AMG_TRY_CUDA(cudaMemsetAsync(ptent, 0, sizeof(double) * (size_t)nn * b * 6, s));
+    AMG_TRY_CUDA(cudaMemsetAsync(ptent, 0, sizeof(double) * (size_t)nn * b * ns, s));
     AMG_TRY_CUDA(cudaMemsetAsync(rho_bits, 0, sizeof(unsigned long long), s));
     out->nagg = nagg;
     if (nagg > 0) {
-        tentative_kernel<<<nblk((int64_t)nagg * 32), T1D, 0, s>>>(nagg, b, d_aptr, d_mem, B, Qs,
-                                                                   ptent, out->Bc); ::amg::count_launch(1);
+        if (ns == 6)
+            tentative_kernel<6><<<nblk((int64_t)nagg * 32), T1D, 0, s>>>(nagg, b, d_aptr, d_mem, B,
+                                                                          Qs, ptent, out->Bc);
+        else
+            tentative_kernel<3><<<nblk((int64_t)nagg * 32), T1D, 0, s>>>(nagg, b, d_aptr, d_mem, B,
+                                                                          Qs, ptent, out->Bc);
+        ::amg::count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
     }
     jacobi_rho_kernel<<<nblk(nn), T1D, 0, s>>>(A.row_ptr, A.col, A.val, nn, b, d, rho_bits); ::amg::count_launch(1);
@@ -958,7 +972,7 @@ int build_transfer(const BsrD &A, const double *B, const uint8_t *strong, const 
     P.nbr = nn;
     P.nbc = nagg;
     P.br = b;
-    P.bc = 6;
+    P.bc = ns;
     std::vector<int> trp(nn + 1, 0), tcl;
     for (int J = 0; J < nn; ++J) {
         trp[J + 1] = trp[J] + (agg_h[J] >= 0 ? 1 : 0);
@@ -975,23 +989,23 @@ int build_transfer(const BsrD &A, const double *B, const uint8_t *strong, const 
                             &P.col, &nnzp));  // synchronises: trp/tcl may go out of scope
     P.nnzb = nnzp;
     int *pbrow = nullptr;
-    AMG_TRY(keep.alloc_n(&P.val, (size_t)std::max(nnzp, 1) * b * 6));
+    AMG_TRY(keep.alloc_n(&P.val, (size_t)std::max(nnzp, 1) * b * ns));
     AMG_TRY(tmp.alloc_n(&pbrow, (size_t)std::max(nnzp, 1)));
     block_rows_kernel<<<nblk(nn), T1D, 0, s>>>(P.row_ptr, nn, pbrow); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     if (nnzp > 0) {
-        if (b == 3)
-            p_values_kernel<3><<<nblk(nnzp, 128), 128, 0, s>>>(A.row_ptr, A.col, A.val, strong,
-                                                               out->agg, ptent, d, out->omega,
-                                                               pbrow, P.col, nnzp, P.val);
-        else if (b == 6)
-            p_values_kernel<6><<<nblk(nnzp, 128), 128, 0, s>>>(A.row_ptr, A.col, A.val, strong,
-                                                               out->agg, ptent, d, out->omega,
-                                                               pbrow, P.col, nnzp, P.val);
+#define AMG_PVALS(B_, NS_)                                                                   \
+    p_values_kernel<B_, NS_><<<nblk(nnzp, 128), 128, 0, s>>>(A.row_ptr, A.col, A.val, strong,  \
+                                                            out->agg, ptent, d, out->omega,    \
+                                                            pbrow, P.col, nnzp, P.val)
+        if (b == 3 && ns == 6) AMG_PVALS(3, 6);
+        else if (b == 6 && ns == 6) AMG_PVALS(6, 6);
+        else if (b == 3 && ns == 3) AMG_PVALS(3, 3);
         else {
-            set_error("unsupported node block size %d", b);
+            set_error("unsupported node block size %d with %d near-nullspace vectors", b, ns);
             return AMG_ERR_ARG;
         }
+#undef AMG_PVALS
         ::amg::count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
     }

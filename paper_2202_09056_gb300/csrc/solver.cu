@@ -662,14 +662,14 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         AMG_TRY(h->mem.alloc_n(&A.row_ptr, (size_t)A.nbr + 1));
         AMG_TRY(h->mem.alloc_n(&A.col, (size_t)std::max<int64_t>(A.nnzb, 1)));
         AMG_TRY(h->mem.alloc_n(&A.val, (size_t)std::max<int64_t>(A.nnzb, 1) * 9));
-        AMG_TRY(h->mem.alloc_n(&L0.B, (size_t)A.nbr * 3 * 6));
+        AMG_TRY(h->mem.alloc_n(&L0.B, (size_t)A.nbr * 3 * h->ns));
         AMG_TRY_CUDA(cudaMemcpyAsync(A.row_ptr, Ain->row_ptr, sizeof(int) * (A.nbr + 1),
                                      cudaMemcpyDeviceToDevice, s));
         AMG_TRY_CUDA(cudaMemcpyAsync(A.col, Ain->col, sizeof(int) * A.nnzb,
                                      cudaMemcpyDeviceToDevice, s));
         AMG_TRY_CUDA(cudaMemcpyAsync(A.val, Ain->val, sizeof(double) * 9 * A.nnzb,
                                      cudaMemcpyDeviceToDevice, s));
-        AMG_TRY_CUDA(cudaMemcpyAsync(L0.B, B, sizeof(double) * 18 * A.nbr,
+        AMG_TRY_CUDA(cudaMemcpyAsync(L0.B, B, sizeof(double) * 3 * h->ns * A.nbr,
                                      cudaMemcpyDeviceToDevice, s));
         L0.eps = prm.eps_strong;
         // validate the pattern before any other kernel indexes with it: the
@@ -721,7 +721,7 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         AMG_TRY(aggregate_host(nn, rp.data(), cl.data(), sf.data(), agg.data(), &nagg));
         if (nagg == 0 || (double)nagg >= 0.9 * (double)nn) break;
         LevelBuild lb;
-        AMG_TRY(build_transfer(C.A, C.B, C.strong, agg.data(), nagg, prm.relax, h->mem, tmp, s,
+        AMG_TRY(build_transfer(C.A, C.B, h->ns, C.strong, agg.data(), nagg, prm.relax, h->mem, tmp, s,
                                &lb));
         C.P = lb.P;
         C.R = lb.R;
@@ -850,8 +850,8 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
         set_error("amg_setup expects a non-empty 3x3 block matrix");
         return AMG_ERR_ARG;
     }
-    if (nb_ns != 6 || !B) {
-        set_error("amg_setup expects the six rigid-body modes (nb_ns = 6)");
+    if ((nb_ns != 6 && nb_ns != 3) || !B) {
+        set_error("amg_setup expects the six rigid-body modes (nb_ns = 6) or three translations (3)");
         return AMG_ERR_ARG;
     }
     amg_params p;
@@ -867,6 +867,7 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
     auto t0 = std::chrono::steady_clock::now();
     amg_handle h = new amg_handle_s();
     h->prm = p;
+    h->ns = nb_ns;
     h->stream = (cudaStream_t)stream;
     h->mem.stream = h->stream;
     int st = setup_impl(h, A, B);
@@ -1114,7 +1115,7 @@ int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_pt
         if (val) AMG_TRY_CUDA(cudaMemcpyAsync(val, L.M, sizeof(double) * L.n(), cudaMemcpyDeviceToHost, s));
         break;
     case 5:
-        if (val) AMG_TRY_CUDA(cudaMemcpyAsync(val, L.B, sizeof(double) * L.n() * 6, cudaMemcpyDeviceToHost, s));
+        if (val) AMG_TRY_CUDA(cudaMemcpyAsync(val, L.B, sizeof(double) * L.n() * h->ns, cudaMemcpyDeviceToHost, s));
         break;
     case 7:
         if (!L.Mb || !h->learned) { set_error("no learned smoother blocks on this level"); return AMG_ERR_STATE; }

@@ -73,10 +73,12 @@ def test_spmv_empty_matrix():
     assert y.numel() == 0
 
 
-def _compare_hierarchy(p, coarse_enough, tol_val=1e-12):
-    H = o.Hierarchy(o.from_problem(p), 3, p.B, coarse_enough=coarse_enough)
-    rp, cl, val, B = _dev(p)
-    G = amg.AMG(rp, cl, val, B, coarse_enough=coarse_enough)
+def _compare_hierarchy(p, coarse_enough, tol_val=1e-12, Bns=None):
+    Bns = p.B if Bns is None else Bns
+    ns = Bns.shape[1]
+    H = o.Hierarchy(o.from_problem(p), 3, Bns, coarse_enough=coarse_enough)
+    rp, cl, val, _ = _dev(p)
+    G = amg.AMG(rp, cl, val, torch.from_numpy(Bns).cuda(), coarse_enough=coarse_enough)
     assert G.nlevels == H.nlevels
     for l in range(H.nlevels):
         ol, gl = H.level(l), G.export(l)
@@ -99,8 +101,8 @@ def _compare_hierarchy(p, coarse_enough, tol_val=1e-12):
         assert abs(info["rho"] - ol["rho"]) <= rtol * ol["rho"], l
         assert abs(info["omega"] - ol["omega"]) <= rtol * ol["omega"], l
         gP, gR = gl["P"], gl["R"]
-        cP = o.unblock(gP[0], gP[1], gP[2].reshape(len(gP[1]), -1), b, 6, nbcols=info["nagg"])
-        cR = o.unblock(gR[0], gR[1], gR[2].reshape(len(gR[1]), -1), 6, b, nbcols=info["nbrows"])
+        cP = o.unblock(gP[0], gP[1], gP[2].reshape(len(gP[1]), -1), b, ns, nbcols=info["nagg"])
+        cR = o.unblock(gR[0], gR[1], gR[2].reshape(len(gR[1]), -1), ns, b, nbcols=info["nbrows"])
         assert np.array_equal(cP.ptr, ol["P"].ptr) and np.array_equal(cP.col, ol["P"].col), l
         assert np.array_equal(cR.ptr, ol["R"].ptr) and np.array_equal(cR.col, ol["R"].col), l
         assert _rel(cP.val, ol["P"].val) <= tol_val, l
@@ -117,6 +119,34 @@ def _compare_hierarchy(p, coarse_enough, tol_val=1e-12):
 def test_setup_matches_oracle(shape, kw, ce):
     p = q.make_problem(shape, **kw)
     _compare_hierarchy(p, ce)
+
+
+def _translations(ndof):
+    T = np.zeros((ndof, 3))
+    for c in range(3):
+        T[c::3, c] = 1.0
+    return T
+
+
+@pytest.mark.parametrize("shape,kw,ce", [
+    ((10, 10, 10), {"body": (0, 0, -1)}, 500),
+    ((12, 11, 13), {"traction": (0, 0, -1), "inclusion_frac": 0.2}, 300),
+])
+def test_translations_only_setup_and_solve_match_oracle(shape, kw, ce):
+    """The block solver without rotations (near-nullspace = the three
+    translations, 3-DOF coarse nodes): hierarchy, then PCG, against the
+    oracle; the rigid-body modes need fewer iterations."""
+    p = q.make_problem(shape, **kw)
+    T = _translations(p.ndof)
+    H, G = _compare_hierarchy(p, ce, Bns=T)
+    assert all(G.level_info(l)["bs"] == 3 for l in range(G.nlevels))
+    uo, ito, _ = H.solve(p.f, tol=1e-8, maxiter=3000)
+    fb = torch.from_numpy(p.f).cuda()
+    u, it, res, st = G.solve(fb, tol=1e-8, maxiter=3000)
+    assert st == amg.AMG_OK and res <= 1e-8 and abs(it - ito) <= 1, (it, ito)
+    assert np.linalg.norm(u.cpu().numpy() - uo) <= 1e-7 * np.linalg.norm(uo)
+    _, it6, _, _ = amg.AMG(*_dev(p), coarse_enough=ce).solve(fb)
+    assert it6 < it
 
 
 def test_vcycle_matches_oracle():
