@@ -40,6 +40,7 @@ struct BSell {
     int *s_inst = nullptr, *s_local = nullptr, *s_G = nullptr;
     int *perm = nullptr;         // concatenated slot -> row maps of the sorted parts
     int64_t *s_pbase = nullptr;  // per slice: its first slot in perm, or -1 (natural order)
+    int *order = nullptr;        // slices widest first over all instances
 };
 
 struct BArgs {
@@ -50,6 +51,7 @@ struct BArgs {
     const int *s_inst, *s_local, *s_G;
     const int *perm;
     const int64_t *s_pbase;
+    const int *order;
     const int *K;           // right-hand sides per instance
     const int *nrows;       // block rows of the output space per instance
     const int64_t *xoff;    // instance offsets of x's space
@@ -66,8 +68,9 @@ __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
     constexpr int BB = BR * BC;
     const int lane = threadIdx.x & 31;
     const int nw = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
-    for (int s = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5); s < a.nslices;
-         s += nw) {
+    for (int k = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5); k < a.nslices;
+         k += nw) {
+        const int s = a.order[k];
         const int inst = a.s_inst[s];
         if (!a.enable[inst]) continue;
         const int G = a.s_G[s], sub = lane & (G - 1);
@@ -178,8 +181,11 @@ static int launch_bspmm(const BSell &S, int kt, int mode, BArgs a, const Geom &g
     a.s_G = S.s_G;
     a.perm = S.perm;
     a.s_pbase = S.s_pbase;
+    a.order = S.order;
+    // one slice group per CTA up to 32 CTAs per SM, widest slices first: the
+    // hardware scheduler balances the instances' uneven rows
     int grid = (S.nslices + BT / 32 - 1) / (BT / 32);
-    grid = std::min(grid, g.num_sms * 16);
+    grid = std::min(grid, g.num_sms * 32);
     if (S.br == 3 && S.bc == 3) return bspmm_mode<3, 3>(S, kt, mode, a, grid, s);
     if (S.br == 6 && S.bc == 6) return bspmm_mode<6, 6>(S, kt, mode, a, grid, s);
     if (S.br == 3 && S.bc == 6) return bspmm_mode<3, 6>(S, kt, mode, a, grid, s);
@@ -809,6 +815,14 @@ static int concat_sell(amg_batch h, int l, int which, BSell *out)
     AMG_TRY(upload(h->mem, s_local, &S.s_local, s));
     AMG_TRY(upload(h->mem, s_G, &S.s_G, s));
     AMG_TRY(upload(h->mem, s_pbase, &S.s_pbase, s));
+    {
+        std::vector<int> order(S.nslices);
+        for (int k = 0; k < S.nslices; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return sp[x + 1] - sp[x] > sp[y + 1] - sp[y];
+        });
+        AMG_TRY(upload(h->mem, order, &S.order, s));
+    }
     AMG_TRY(h->mem.alloc_n(&S.perm, (size_t)std::max<int64_t>(nperm, 1)));
     AMG_TRY(h->mem.alloc_n(&S.col, (size_t)nslots));
     AMG_TRY(h->mem.alloc_n(&S.val, (size_t)nslots * bb));

@@ -726,7 +726,10 @@ __global__ void __launch_bounds__(128) spgemm_rows_kernel(
     double *acc = sm + (size_t)g * cmax * CB;
     int *cols = reinterpret_cast<int *>(sm + (size_t)GROUPS * cmax * CB) + (size_t)g * cmax;
     for (int i = blockIdx.x * GROUPS + g; i < nrows; i += gridDim.x * GROUPS) {
-        const int c0 = crp[i], len = crp[i + 1] - c0;
+        // upper: only the blocks on and above the diagonal, columns >= i (the
+        // row's tail) are kept; cmax is then the longest such tail
+        const int r0 = crp[i], r1 = crp[i + 1];
+        const int c0 = upper ? find_sorted(ccol, r0, r1, i) : r0, len = r1 - c0;
         for (int t = lane; t < len; t += L) cols[t] = ccol[c0 + t];
         for (int t = lane; t < len * CB; t += L) acc[t] = 0.0;
         __syncwarp(mask);
@@ -736,9 +739,9 @@ __global__ void __launch_bounds__(128) spgemm_rows_kernel(
 #pragma unroll
             for (int e = 0; e < XR * XC; ++e) xb[e] = xval[(int64_t)p * XR * XC + e];
             const int hi = yrp[k + 1];
-            for (int t = yrp[k] + lane; t < hi; t += L) {
+            const int lo = upper ? find_sorted(ycol, yrp[k], hi, i) : yrp[k];
+            for (int t = lo + lane; t < hi; t += L) {
                 const int j = ycol[t];
-                if (upper && j < i) continue;  // lower blocks: mirror_lower_kernel
                 const int pos = find_sorted(cols, 0, len, j);
                 if (pos >= len || cols[pos] != j) continue;  // cannot happen: C holds every product
                 const double *yb = yval + (int64_t)t * XC * YC;
@@ -756,8 +759,18 @@ __global__ void __launch_bounds__(128) spgemm_rows_kernel(
             __syncwarp(mask);
         }
         for (int t = lane; t < len * CB; t += L) cval[(int64_t)c0 * CB + t] = acc[t];
+        if (upper)  // lower blocks: zero here, mirror_lower_kernel fills them
+            for (int t = lane; t < (c0 - r0) * CB; t += L) cval[(int64_t)r0 * CB + t] = 0.0;
         __syncwarp(mask);
     }
+}
+
+// longest tail (columns >= row) of a row: the upper part of a symmetric product
+__global__ void row_max_upper_kernel(const int *__restrict__ rp, const int *__restrict__ col, int n,
+                                     int *__restrict__ mx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(mx, rp[i + 1] - find_sorted(col, rp[i], rp[i + 1], i));
 }
 
 __global__ void row_max_kernel(const int *__restrict__ rp, int n, int *__restrict__ mx)
@@ -849,12 +862,16 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
     int *mx = nullptr, cmax = 0;
     AMG_TRY(tmp.alloc_n(&mx, 1));
     AMG_TRY_CUDA(cudaMemsetAsync(mx, 0, sizeof(int), s));
-    row_max_kernel<<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, X.nbr, mx);
+    if (upper)
+        row_max_upper_kernel<<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, C->col, X.nbr, mx);
+    else
+        row_max_kernel<<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, X.nbr, mx);
     ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaMemcpyAsync(&cmax, mx, sizeof(int), cudaMemcpyDeviceToHost, s));
     AMG_TRY_CUDA(cudaStreamSynchronize(s));
     tmp.release(mx);
-    const double ylen = Y.nbr ? (double)Y.nnzb / Y.nbr : 0.0;
+    // an upper product uses about half of each Y row
+    const double ylen = (Y.nbr ? (double)Y.nnzb / Y.nbr : 0.0) * (upper ? 0.5 : 1.0);
     const int lanes = ylen <= 8.0 ? 8 : (ylen <= 16.0 ? 16 : 32);
     if (xr == 3 && yc == 3) AMG_TRY((spgemm_rows<3, 3, 3>(X, Y, C, cmax, lanes, upper, s, &done)));
     else if (xr == 3) AMG_TRY((spgemm_rows<3, 3, 6>(X, Y, C, cmax, lanes, upper, s, &done)));
