@@ -313,77 +313,67 @@ __global__ void sell_fill_kernel(const int *__restrict__ rp, const int *__restri
 // widths follow the longest lane, so rows of uneven length (P and R, whose
 // length is the number of aggregates a node's neighbourhood touches; coarse
 // A) waste slots.  When the natural order pads more than 5 %, rows are sorted
-// by length, longest first, inside windows of 32 groups (SELL-C-sigma); a
-// window keeps rows that are close in the numbering together, so the x
-// gather keeps its locality.  The groups are then ordered by width, widest
-// first: CTAs take them in that order (longest processing time first), so no
-// SM is left with a tail of long rows while the others idle.  Returns the
-// slice count (a multiple of 4 when G > 32).
-static int sell_order(const std::vector<int> &rp, int G, std::vector<int> *perm,
-                      std::vector<int> *width)
+// by length, longest first (ties: ascending row), inside windows of 32 groups
+// (SELL-C-sigma); a window keeps rows that are close in the numbering
+// together, so the x gather keeps its locality.  The groups are then ordered
+// by width, widest first (ties: ascending group): CTAs take them in that
+// order (longest processing time first), so no SM is left with a tail of long
+// rows while the others idle.  The sorting runs on the device; only the
+// slice widths and group costs cross to the host.
+
+// widths of every group's slices for the slot -> row map rowof (null: the
+// natural order); total += the slots they take
+__global__ void sell_group_width_kernel(const int *__restrict__ rp, int nrows, int G, int rpg,
+                                        int spg, int ngroups, const int *__restrict__ rowof,
+                                        int *__restrict__ w, unsigned long long *__restrict__ total)
 {
-    const int nrows = (int)rp.size() - 1;
-    const bool wide = G > 32;
-    const int rpg = wide ? 1 : 32 / G, spg = wide ? G / 32 : 1;
-    int ngroups = (nrows + rpg - 1) / rpg;
-    while ((int64_t)ngroups * spg % 4 != 0 && wide) ++ngroups;
-    const int nslices = ngroups * spg, nslots = ngroups * rpg;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    auto row_of = [&](int slot) { return rowof ? rowof[slot] : (slot < nrows ? slot : -1); };
     auto len = [&](int row) { return row < 0 || row >= nrows ? 0 : rp[row + 1] - rp[row]; };
-    // widths of group g's slices for slot -> row map `rowof`
-    auto group_widths = [&](int g, const int *rowof, int *w) {
-        if (wide) {
-            const int L = len(rowof[g]);
-            for (int q = 0; q < spg; ++q) w[q] = std::max(0, (L - 32 * q + G - 1) / G);
-        } else {
-            int m = 0;
-            for (int t = 0; t < rpg; ++t) m = std::max(m, (len(rowof[g * rpg + t]) + G - 1) / G);
-            w[0] = m;
+    unsigned long long slots = 0;
+    if (G > 32) {
+        const int L = len(row_of(g));
+        for (int q = 0; q < spg; ++q) {
+            const int wq = max(0, (L - 32 * q + G - 1) / G);
+            w[g * spg + q] = wq;
+            slots += 32ull * wq;
         }
-    };
-    auto all_widths = [&](const std::vector<int> &rowof, std::vector<int> *w) {
-        w->assign(nslices, 0);
-        int64_t slots = 0;
-        for (int g = 0; g < ngroups; ++g) {
-            group_widths(g, rowof.data(), w->data() + (size_t)g * spg);
-            for (int q = 0; q < spg; ++q) slots += 32LL * (*w)[(size_t)g * spg + q];
-        }
-        return slots;
-    };
-    std::vector<int> natural(nslots);
-    for (int k = 0; k < nslots; ++k) natural[k] = k < nrows ? k : -1;
-    perm->clear();
-    const int64_t nnzb = rp[nrows] - rp[0];
-    const int64_t nat = all_widths(natural, width);
-    if (nnzb == 0 || (double)(nat - nnzb) <= 0.05 * (double)nnzb) return nslices;
-    std::vector<int> pw(nslots, -1);
-    const int win = 32 * rpg;
-    std::vector<int> idx;
-    for (int r0 = 0; r0 < nrows; r0 += win) {
-        const int r1 = std::min(nrows, r0 + win);
-        idx.resize(r1 - r0);
-        for (int r = r0; r < r1; ++r) idx[r - r0] = r;
-        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return len(a) > len(b); });
-        std::copy(idx.begin(), idx.end(), pw.begin() + r0);
+    } else {
+        int m = 0;
+        for (int t = 0; t < rpg; ++t) m = max(m, (len(row_of(g * rpg + t)) + G - 1) / G);
+        w[g] = m;
+        slots = 32ull * m;
     }
-    std::vector<int> w2;
-    if (all_widths(pw, &w2) >= nat) return nslices;
-    // widest groups first
-    std::vector<int64_t> cost(ngroups, 0);
-    for (int g = 0; g < ngroups; ++g)
-        for (int q = 0; q < spg; ++q) cost[g] += w2[(size_t)g * spg + q];
-    std::vector<int> order(ngroups);
-    for (int g = 0; g < ngroups; ++g) order[g] = g;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    perm->assign(nslots, -1);
-    width->assign(nslices, 0);
-    for (int k = 0; k < ngroups; ++k) {
-        const int g = order[k];
-        std::copy(pw.begin() + (size_t)g * rpg, pw.begin() + (size_t)(g + 1) * rpg,
-                  perm->begin() + (size_t)k * rpg);
-        std::copy(w2.begin() + (size_t)g * spg, w2.begin() + (size_t)(g + 1) * spg,
-                  width->begin() + (size_t)k * spg);
+    atomicAdd(total, slots);
+}
+
+// one CTA per window of `win` rows: every row's rank by (length descending,
+// row ascending) among the window's rows, pw[window start + rank] = row
+constexpr int SELL_WIN_MAX = 1024;
+__global__ void __launch_bounds__(256) sell_window_rank_kernel(const int *__restrict__ rp, int nrows,
+                                                               int win, int *__restrict__ pw)
+{
+    __shared__ int ln[SELL_WIN_MAX];
+    const int r0 = blockIdx.x * win, n = min(win, nrows - r0);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ln[i] = rp[r0 + i + 1] - rp[r0 + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int li = ln[i];
+        int rank = 0;
+        for (int j = 0; j < n; ++j) rank += (ln[j] > li) || (ln[j] == li && j < i);
+        pw[r0 + rank] = r0 + i;
     }
-    return nslices;
+}
+
+// perm[k rpg + t] = pw[order[k] rpg + t]
+__global__ void sell_gather_groups_kernel(const int *__restrict__ order, const int *__restrict__ pw,
+                                          int ngroups, int rpg, int *__restrict__ perm)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ngroups) return;
+    const int g = order[k];
+    for (int t = 0; t < rpg; ++t) perm[(int64_t)k * rpg + t] = pw[(int64_t)g * rpg + t];
 }
 
 template <class T>
@@ -408,14 +398,82 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
         G <<= 1;
     S.G = G;
     const int bb = B.br * B.bc;
-    std::vector<int> rp(B.nbr + 1, 0);
-    if (B.nbr > 0) {
-        AMG_TRY_CUDA(cudaMemcpyAsync(rp.data(), B.row_ptr, sizeof(int) * (B.nbr + 1),
-                                     cudaMemcpyDeviceToHost, s));
+    const bool wide = G > 32;
+    const int nrows = B.nbr, rpg = wide ? 1 : 32 / G, spg = wide ? G / 32 : 1;
+    int ngroups = (nrows + rpg - 1) / rpg;
+    while (wide && (int64_t)ngroups * spg % 4 != 0) ++ngroups;
+    S.nslices = nrows > 0 ? ngroups * spg : 0;
+    const int nslots = ngroups * rpg;
+    std::vector<int> wh(std::max(S.nslices, 1), 0);
+    if (S.nslices > 0) {
+        int *w = nullptr, *pw = nullptr;
+        unsigned long long *tot = nullptr;
+        AMG_TRY_CUDA(cudaMallocAsync((void **)&w, sizeof(int) * S.nslices, s));
+        AMG_TRY_CUDA(cudaMallocAsync((void **)&tot, sizeof(unsigned long long) * 2, s));
+        AMG_TRY_CUDA(cudaMemsetAsync(tot, 0, sizeof(unsigned long long) * 2, s));
+        sell_group_width_kernel<<<(ngroups + 255) / 256, 256, 0, s>>>(B.row_ptr, nrows, G, rpg, spg,
+                                                                      ngroups, nullptr, w, tot);
+        count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+        unsigned long long ht[2] = {0, 0};
+        AMG_TRY_CUDA(cudaMemcpyAsync(ht, tot, sizeof(ht[0]), cudaMemcpyDeviceToHost, s));
         AMG_TRY_CUDA(cudaStreamSynchronize(s));
+        const int64_t nat = (int64_t)ht[0];
+        bool sorted = false;
+        if (B.nnzb > 0 && (double)(nat - B.nnzb) > 0.05 * (double)B.nnzb) {
+            const int win = 32 * rpg;
+            AMG_TRY_CUDA(cudaMallocAsync((void **)&pw, sizeof(int) * nslots, s));
+            AMG_TRY_CUDA(cudaMemsetAsync(pw, 0xff, sizeof(int) * nslots, s));  // -1: padding slots
+            sell_window_rank_kernel<<<(nrows + win - 1) / win, 256, 0, s>>>(B.row_ptr, nrows, win, pw);
+            sell_group_width_kernel<<<(ngroups + 255) / 256, 256, 0, s>>>(
+                B.row_ptr, nrows, G, rpg, spg, ngroups, pw, w, tot + 1);
+            count_launch(2);
+            AMG_TRY_CUDA(cudaGetLastError());
+            AMG_TRY_CUDA(cudaMemcpyAsync(ht + 1, tot + 1, sizeof(ht[1]), cudaMemcpyDeviceToHost, s));
+            AMG_TRY_CUDA(cudaStreamSynchronize(s));
+            sorted = (int64_t)ht[1] < nat;
+        }
+        if (!sorted && pw) {  // the sort does not pay: natural widths again
+            AMG_TRY_CUDA(cudaMemsetAsync(tot, 0, sizeof(unsigned long long), s));
+            sell_group_width_kernel<<<(ngroups + 255) / 256, 256, 0, s>>>(
+                B.row_ptr, nrows, G, rpg, spg, ngroups, nullptr, w, tot);
+            count_launch(1);
+            AMG_TRY_CUDA(cudaGetLastError());
+        }
+        AMG_TRY_CUDA(cudaMemcpyAsync(wh.data(), w, sizeof(int) * S.nslices, cudaMemcpyDeviceToHost, s));
+        AMG_TRY_CUDA(cudaStreamSynchronize(s));
+        if (sorted) {
+            // widest groups first, ties in ascending group order (a stable
+            // counting sort on the group widths)
+            std::vector<int> cost(ngroups, 0);
+            int cmax = 0;
+            for (int g = 0; g < ngroups; ++g) {
+                for (int q = 0; q < spg; ++q) cost[g] += wh[(size_t)g * spg + q];
+                cmax = std::max(cmax, cost[g]);
+            }
+            std::vector<int> start(cmax + 2, 0), order(ngroups);
+            for (int g = 0; g < ngroups; ++g) start[cmax - cost[g] + 1]++;
+            for (int c = 0; c <= cmax; ++c) start[c + 1] += start[c];
+            for (int g = 0; g < ngroups; ++g) order[start[cmax - cost[g]]++] = g;
+            std::vector<int> w2(wh);
+            for (int k = 0; k < ngroups; ++k)
+                for (int q = 0; q < spg; ++q) wh[(size_t)k * spg + q] = w2[(size_t)order[k] * spg + q];
+            int *dorder = nullptr;
+            AMG_TRY_CUDA(cudaMallocAsync((void **)&dorder, sizeof(int) * ngroups, s));
+            AMG_TRY_CUDA(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * ngroups,
+                                         cudaMemcpyHostToDevice, s));
+            AMG_TRY(keep.alloc_n(&S.perm, (size_t)nslots));
+            sell_gather_groups_kernel<<<(ngroups + 255) / 256, 256, 0, s>>>(dorder, pw, ngroups, rpg,
+                                                                            S.perm);
+            count_launch(1);
+            AMG_TRY_CUDA(cudaGetLastError());
+            AMG_TRY_CUDA(cudaStreamSynchronize(s));  // order is host memory
+            AMG_TRY_CUDA(cudaFreeAsync(dorder, s));
+        }
+        if (pw) AMG_TRY_CUDA(cudaFreeAsync(pw, s));
+        AMG_TRY_CUDA(cudaFreeAsync(w, s));
+        AMG_TRY_CUDA(cudaFreeAsync(tot, s));
     }
-    std::vector<int> perm, wh;
-    S.nslices = B.nbr > 0 ? sell_order(rp, G, &perm, &wh) : 0;
     std::vector<int64_t> sp(S.nslices + 1, 0);
     for (int i = 0; i < S.nslices; ++i) sp[i + 1] = sp[i] + 32LL * wh[i];
     S.nslots = sp[S.nslices];
@@ -424,18 +482,13 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
     AMG_TRY(keep.alloc_n(&S.val, (size_t)std::max<int64_t>(S.nslots, 1) * bb));
     AMG_TRY_CUDA(cudaMemcpyAsync(S.slice_ptr, sp.data(), sizeof(int64_t) * (S.nslices + 1),
                                  cudaMemcpyHostToDevice, s));
-    if (!perm.empty()) {
-        AMG_TRY(keep.alloc_n(&S.perm, perm.size()));
-        AMG_TRY_CUDA(cudaMemcpyAsync(S.perm, perm.data(), sizeof(int) * perm.size(),
-                                     cudaMemcpyHostToDevice, s));
-    }
     if (S.nslices > 0) {
         sell_fill_kernel<T><<<(S.nslices * 32 + 127) / 128, 128, 0, s>>>(
             B.row_ptr, B.col, B.val, B.nbr, S.nslices, bb, G, S.perm, S.slice_ptr, S.col, S.val);
         count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
     }
-    AMG_TRY_CUDA(cudaStreamSynchronize(s));  // sp and perm are host memory
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));  // sp is host memory
     if (padding) *padding = B.nnzb ? (double)(S.nslots - B.nnzb) / (double)B.nnzb : 0.0;
     *out = S;
     return AMG_OK;
