@@ -255,7 +255,31 @@ def learned_form(amg, torch, solver, f, tol, u_ref, t_spai0, it_spai0, steps):
     out.update(value=float(np.mean(times)), iterations=it_l, rel_resid=res_l, status=st_l,
                err_vs_fp64_solution=float(torch.linalg.norm(u_l - u_ref) / torch.linalg.norm(u_ref)),
                speedup_vs_fp64=t_spai0 / float(np.mean(times)))
+    out["weights"] = w
     return out
+
+
+def learned_fp32_form(amg, torch, args_dev, w, f, tol, u_ref, t_fp64, fp32_form, steps):
+    """The same trained network in the FP32 V-cycle (blocks applied in FP32),
+    against SPAI0 in the FP32 V-cycle and the plain FP64 path."""
+    s = torch.cuda.current_stream()
+    sol = amg.AMG(*args_dev, precision=amg.PREC_FP32)
+    fb = sol.set_learned_smoother(w)
+    sol.solve(f, tol=tol, maxiter=5000)  # warm-up (graph capture)
+    times = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        u_l, it_l, res_l, st_l = sol.solve(f, tol=tol, maxiter=5000)
+        e1.record(s)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    v = float(np.mean(times))
+    return {"value": v, "iterations": it_l, "rel_resid": res_l, "status": st_l, "fallback": fb,
+            "err_vs_fp64_solution": float(torch.linalg.norm(u_l - u_ref) / torch.linalg.norm(u_ref)),
+            "speedup_vs_fp64": t_fp64 / v, "speedup_vs_spai0_fp32": fp32_form["value"] / v,
+            "spai0_fp32_iterations": fp32_form["iterations"],
+            "vcycle": "FP32 matrices and vectors; level 0 smoothed with the learned blocks in FP32"}
 
 
 def run_batch(args, amg, torch):
@@ -543,6 +567,10 @@ def main():
             forms["learned"] = learned_form(amg, torch, solver, f, tol, u_ref,
                                             forms["fp64"]["value"], forms["fp64"]["iterations"],
                                             args.steps)
+            w_learned = forms["learned"].pop("weights")
+            forms["learned_fp32"] = learned_fp32_form(amg, torch, (rp, cl, val, B), w_learned, f,
+                                                      tol, u_ref, forms["fp64"]["value"],
+                                                      forms["fp32"], args.steps)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()

@@ -149,7 +149,7 @@ template <class T> struct Sell {
 };
 
 template <class TV> struct SellArgs {
-    const double *Mb;    // 3x3 smoother blocks (SPMV_SMOOTHB)
+    const TV *Mb;        // 3x3 smoother blocks (SPMV_SMOOTHB), in the vectors' precision
     int nrows, nslices, G;
     const int64_t *slice_ptr;
     const int *col;
@@ -219,6 +219,7 @@ struct Level {
     double eps = 0, omega = 0, rho = 0;
     double *f = nullptr, *u = nullptr, *e = nullptr, *z = nullptr, *t = nullptr;
     double *Mb = nullptr;     // learned 3x3 smoother blocks (level 0), replaces M when set
+    float *Mbf = nullptr;     // FP32 copy of Mb for the FP32 / BF16 V-cycles
     int n() const { return A.nbr * A.br; }
 };
 
@@ -254,6 +255,6 @@ namespace amg {
 int setup_impl(amg_handle h, const amg_bsr *Ain, const double *B);
 void destroy_handle(amg_handle h);
 // out_I = Mb_I r_I for every 3-row node (learned smoother, learned.cu)
-int launch_block_apply(const double *Mb, const double *r, double *out, int nrows, const Geom &g,
-                       cudaStream_t s);
+template <class T>
+int launch_block_apply(const T *Mb, const T *r, T *out, int nrows, const Geom &g, cudaStream_t s);
 }  // namespace amg

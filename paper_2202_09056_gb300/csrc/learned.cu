@@ -34,26 +34,38 @@ constexpr int LF = 12, LFP = 16, LH = 64, LO = 6, LOP = 8;
 constexpr int LNPARAM = LH * LF + LH + LO * LH + LO;  // 1222, order W1 b1 W2 b2
 
 // ---------------------------------------------------------------- block apply
-__global__ void block_apply_kernel(const double *__restrict__ Mb, const double *__restrict__ r,
-                                   double *__restrict__ out, int nrows)
+template <class T>
+__global__ void block_apply_kernel(const T *__restrict__ Mb, const T *__restrict__ r,
+                                   T *__restrict__ out, int nrows)
 {
     for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nrows; I += gridDim.x * blockDim.x) {
-        const double *m = Mb + (int64_t)I * 9;
-        const double r0 = r[3 * (int64_t)I], r1 = r[3 * (int64_t)I + 1], r2 = r[3 * (int64_t)I + 2];
+        const T *m = Mb + (int64_t)I * 9;
+        const T r0 = r[3 * (int64_t)I], r1 = r[3 * (int64_t)I + 1], r2 = r[3 * (int64_t)I + 2];
 #pragma unroll
         for (int a = 0; a < 3; ++a) out[3 * (int64_t)I + a] = m[3 * a] * r0 + m[3 * a + 1] * r1 + m[3 * a + 2] * r2;
     }
 }
 
-int launch_block_apply(const double *Mb, const double *r, double *out, int nrows, const Geom &g,
-                       cudaStream_t s)
+template <class T>
+int launch_block_apply(const T *Mb, const T *r, T *out, int nrows, const Geom &g, cudaStream_t s)
 {
     if (nrows == 0) return AMG_OK;
     int grid = std::min((nrows + 255) / 256, g.max_ctas);
-    block_apply_kernel<<<grid, 256, 0, s>>>(Mb, r, out, nrows);
+    block_apply_kernel<T><<<grid, 256, 0, s>>>(Mb, r, out, nrows);
     count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     return AMG_OK;
+}
+template int launch_block_apply<double>(const double *, const double *, double *, int, const Geom &,
+                                        cudaStream_t);
+template int launch_block_apply<float>(const float *, const float *, float *, int, const Geom &,
+                                       cudaStream_t);
+
+__global__ void narrow9_kernel(const double *__restrict__ a, float *__restrict__ b, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
 }
 
 // ---------------------------------------------------------------- features
@@ -774,9 +786,8 @@ int amg_set_learned_smoother(amg_handle h, const float *params, int32_t *fell_ba
         return AMG_ERR_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->lv.size() < 2 || h->prm.precision != AMG_PREC_FP64 || h->lv[0].A.br != 3 ||
-        h->prm.storage != AMG_STORAGE_BLOCK) {
-        set_error("the learned smoother needs a multi-level FP64 hierarchy in block storage");
+    if (h->lv.size() < 2 || h->lv[0].A.br != 3 || h->prm.storage != AMG_STORAGE_BLOCK) {
+        set_error("the learned smoother needs a multi-level hierarchy in block storage");
         return AMG_ERR_ARG;
     }
     DevArena tmp;
@@ -822,6 +833,16 @@ int amg_set_learned_smoother(amg_handle h, const float *params, int32_t *fell_ba
     // is less stable than both the bound 1.9 and SPAI0 itself (2): the
     // smoothing step contracts the energy norm only while lambda_max(M A) < 2
     const int fb = hb ? 1 : (lam >= std::max(1.9, h->spai0_lambda) ? 2 : 0);
+    if (!fb && h->prm.precision != AMG_PREC_FP64) {
+        // the FP32 / BF16 V-cycles apply the blocks in FP32
+        if (!L0.Mbf) AMG_TRY(h->mem.alloc_n(&L0.Mbf, (size_t)L0.A.nbr * 9));
+        const int64_t n9 = (int64_t)L0.A.nbr * 9;
+        narrow9_kernel<<<(int)std::min<int64_t>((n9 + 255) / 256, h->geom.max_ctas), 256, 0, s>>>(
+            L0.Mb, L0.Mbf, n9);
+        count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+        AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    }
     h->learned = fb ? 0 : 1;
     h->learned_lambda = lam;
     if (fell_back) *fell_back = fb;

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(SELL_THREADS, sell_minb(BR, BC)) sell_spmv_ker
             Acc res[BR];
 #pragma unroll
             for (int r = 0; r < BR; ++r) res[r] = a.f[(int64_t)row * BR + r] - acc[r];
-            const double *mb = a.Mb + (int64_t)row * BR * BR;
+            const TV *mb = a.Mb + (int64_t)row * BR * BR;
 #pragma unroll
             for (int r = 0; r < BR; ++r) {
                 const int64_t i = (int64_t)row * BR + r;
@@ -231,9 +231,9 @@ static int sell_mode(int mode, int dot, const SellArgs<TV> &a, int grid, cudaStr
     case SPMV_AXPY: return sell_dot<BR, BC, VT, TV, SPMV_AXPY>(dot, a, grid, s);
     case SPMV_RESTRICT: return sell_dot<BR, BC, VT, TV, SPMV_RESTRICT>(dot, a, grid, s);
     case SPMV_SMOOTHB:
-        if constexpr (BR == 3 && BC == 3 && std::is_same<TV, double>::value)
+        if constexpr (BR == 3 && BC == 3)
             return sell_dot<BR, BC, VT, TV, SPMV_SMOOTHB>(dot, a, grid, s);
-        set_error("block smoothing needs 3x3 FP64 blocks");
+        set_error("block smoothing needs 3x3 blocks");
         return AMG_ERR_ARG;
     default: set_error("bad spmv mode %d", mode); return AMG_ERR_ARG;
     }

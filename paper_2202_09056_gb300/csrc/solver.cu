@@ -296,6 +296,11 @@ static int launch_vec_dot(amg_handle h, const TV *x, const TV *y, int64_t n, dou
 // pre-smoothing sweep M_0 f0 (or zero without pre-smoothing).  With
 // rz_partials, the last level-0 kernel also leaves the per-CTA partial sums
 // of f0 . z0 (accumulated in FP64).
+// The learned blocks in the V-cycle's vector precision.
+template <class TV> static const TV *learned_blocks_ptr(const amg_handle h);
+template <> const double *learned_blocks_ptr<double>(const amg_handle h) { return h->lv[0].Mb; }
+template <> const float *learned_blocks_ptr<float>(const amg_handle h) { return h->lv[0].Mbf; }
+
 template <class VT, class TV>
 static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials, cudaStream_t s)
 {
@@ -311,12 +316,12 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
         const TV *f = (l == 0) ? f0 : C.f;
         TV *u = C.u, *t = C.t;
         for (int sweep = 1; sweep < npre; ++sweep) {  // further pre-smoothing sweeps
-            const bool blocks = std::is_same<TV, double>::value && l == 0 && h->learned;
+            const bool blocks = l == 0 && h->learned;
             SellArgs<TV> a{};
             a.x = u;
             a.f = f;
             a.M = C.M;
-            a.Mb = h->lv[0].Mb;
+            a.Mb = learned_blocks_ptr<TV>(h);
             a.y = t;
             AMG_TRY((launch_sell<VT, TV>(*C.A, blocks ? SPMV_SMOOTHB : SPMV_SMOOTH, DOT_NONE, a, g,
                                          s)));
@@ -362,7 +367,7 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
             AMG_TRY((launch_sell<VT, TV>(*C.P, SPMV_AXPY, DOT_NONE, a, g, s)));
         }
         const TV *w = u;
-        const bool blocks = std::is_same<TV, double>::value && l == 0 && h->learned;
+        const bool blocks = l == 0 && h->learned;
         for (int sweep = 0; sweep < npost; ++sweep) {  // u += M (f - A u)
             const bool last = (sweep == npost - 1);
             TV *out = last ? zl : t;
@@ -370,7 +375,7 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
             a.x = w;
             a.f = f;
             a.M = C.M;
-            a.Mb = h->lv[0].Mb;
+            a.Mb = learned_blocks_ptr<TV>(h);
             a.y = out;
             a.partials = rz_partials;
             const int dot = (l == 0 && last && rz_partials) ? DOT_FY : DOT_NONE;
@@ -429,7 +434,7 @@ static int record_cg_iteration_t(amg_handle h, cudaStream_t s, cudaGraphConditio
         AMG_TRY((launch_sell<double, double>(L0.sA, SPMV_PLAIN, DOT_XY, a, g, s, &grid)));
     }
     cg_alpha_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, grid); ::amg::count_launch(1);
-    const bool blocks = f64 && h->learned && multi && npre > 0;
+    const bool blocks = h->learned && multi && npre > 0;
     cg_update_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(h->uu, h->r, h->p, h->q, V0.M,
                                                      (multi && !blocks) ? V0.u : nullptr, rv, h->st,
                                                      n, npre > 0, h->partials); ::amg::count_launch(1);
@@ -450,7 +455,7 @@ static int record_cg_iteration_t(amg_handle h, cudaStream_t s, cudaGraphConditio
                                                       n, npre > 0); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     if (blocks)  // next pre-smoothing with the learned blocks: u0 = Mb r
-        AMG_TRY(launch_block_apply(L0.Mb, h->r, (double *)V0.u, L0.A.nbr, g, s));
+        AMG_TRY(launch_block_apply<TV>(learned_blocks_ptr<TV>(h), f0, V0.u, L0.A.nbr, g, s));
     return AMG_OK;
 }
 
@@ -907,10 +912,12 @@ int amg_apply_vcycle(amg_handle h, const double *r, double *z, void *stream)
         }
         return record_vcycle<double, double>(h, r, z, nullptr, s);
     }
-    scale_kernel<float><<<vgrid(h, n), 256, 0, s>>>(L0.Mf, r, multi ? L0.vu : nullptr, h->rv, n,
-                                                    zero);
+    const bool lb = multi && h->learned && !zero;
+    scale_kernel<float><<<vgrid(h, n), 256, 0, s>>>(L0.Mf, r, (multi && !lb) ? L0.vu : nullptr,
+                                                    h->rv, n, zero);
     count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
+    if (lb) AMG_TRY(launch_block_apply<float>(L0.Mbf, h->rv, L0.vu, L0.A.nbr, h->geom, s));
     if (h->prm.precision == AMG_PREC_FP32)
         AMG_TRY((record_vcycle<float, float>(h, h->rv, h->zv, nullptr, s)));
     else
@@ -961,9 +968,12 @@ int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxi
             count_launch(1);
         }
     } else {
-        scale_kernel<float><<<vgrid(h, n), 256, 0, s>>>(L0.Mf, h->r, multi ? L0.vu : nullptr,
-                                                        h->rv, n, h->prm.npre == 0);
+        const bool lb = multi && h->learned && h->prm.npre > 0;
+        scale_kernel<float><<<vgrid(h, n), 256, 0, s>>>(L0.Mf, h->r,
+                                                        (multi && !lb) ? L0.vu : nullptr, h->rv,
+                                                        n, h->prm.npre == 0);
         count_launch(1);
+        if (lb) AMG_TRY(launch_block_apply<float>(L0.Mbf, h->rv, L0.vu, L0.A.nbr, h->geom, s));
     }
     AMG_TRY_CUDA(cudaGetLastError());
     AMG_TRY_CUDA(cudaMemcpyAsync(h->st_h, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));

@@ -142,3 +142,28 @@ def test_training_lowers_loss_and_iterations():
     assert it_learned < it_spai0, (it_learned, it_spai0)
     G.clear_learned_smoother()
     assert G.stats()["learned"] == 0
+
+
+@pytest.mark.parametrize("prec", [amg.PREC_FP32, amg.PREC_BF16])
+def test_learned_blocks_in_reduced_precision_vcycle(prec):
+    """The FP32 / BF16 V-cycles apply the learned blocks in FP32: a zero
+    output layer gives the SPAI0 solve of that precision, and blocks from a
+    random network solve to 1e-8 with iterations close to the FP64 V-cycle
+    with the same blocks."""
+    p = q.make_problem((10, 9, 8), traction=(0, 0, -1), inclusion_frac=0.2)
+    fb = torch.from_numpy(p.f).cuda()
+    G = amg.AMG(*_dev(p), coarse_enough=200, precision=prec)
+    u0, it0, _, _ = G.solve(fb)
+    assert not G.set_learned_smoother(amg.learned_init(1))
+    u1, it1, _, st = G.solve(fb)
+    assert st == amg.AMG_OK and abs(it1 - it0) <= 1
+    assert torch.linalg.norm(u1 - u0) <= 1e-7 * torch.linalg.norm(u0)
+    w = _params(seed=7, w2=0.05)
+    assert not G.set_learned_smoother(w)
+    u2, it2, res2, st2 = G.solve(fb)
+    G64 = amg.AMG(*_dev(p), coarse_enough=200)
+    assert not G64.set_learned_smoother(w)
+    u3, it3, _, _ = G64.solve(fb)
+    assert st2 == amg.AMG_OK and res2 <= 1e-8
+    assert abs(it2 - it3) <= max(2, it3 // 10), (it2, it3)
+    assert torch.linalg.norm(u2 - u3) <= 1e-6 * torch.linalg.norm(u3)
