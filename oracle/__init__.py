@@ -41,7 +41,8 @@ class _Params(ctypes.Structure):
     _fields_ = [("eps_strong", ctypes.c_double), ("coarse_enough", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("npre", ctypes.c_int),
                 ("npost", ctypes.c_int), ("relax", ctypes.c_double),
-                ("smooth_relax", ctypes.c_double), ("ns", ctypes.c_int)]
+                ("smooth_relax", ctypes.c_double), ("ns", ctypes.c_int),
+                ("smoother", ctypes.c_int), ("ilu_sweeps", ctypes.c_int)]
 
 
 def _load():
@@ -72,6 +73,11 @@ def _load():
         "orc_cholesky_solve": ([i64, P, P, P, P], None),
         "orc_params_default": ([P], None),
         "orc_setup": ([P, i, P, P, P], P),
+        "orc_ilu0": ([P, i], P),
+        "orc_ilu_apply": ([P, i, P, P, P], None),
+        "orc_ilu_shape": ([P, P], None),
+        "orc_ilu_copy": ([P, P, P, P, P], None),
+        "orc_ilu_free": ([P], None),
         "orc_free": ([P], None),
         "orc_vcycle": ([P, P, P], None),
         "orc_pcg": ([P, P, P, d, i, P], i),
@@ -257,16 +263,54 @@ def cholesky_solve(L, zrow, f):
     return u
 
 
+class ILU0:
+    """Block ILU(0) of a scalar CSR matrix in b x b blocks (the level smoother
+    of Sec. 4's experiments); apply() solves with `sweeps` Jacobi sweeps per
+    triangular factor."""
+
+    def __init__(self, A: CSR, b: int):
+        self._A = _Owned(A)
+        self.h = _load().orc_ilu0(self._A.h, b)
+        if not self.h:
+            raise RuntimeError("block ILU(0) breakdown")
+        sh = np.zeros(3, dtype=np.int64)
+        _load().orc_ilu_shape(self.h, _p(sh))
+        self.nb, self.b, self.nnzb = (int(x) for x in sh)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _load().orc_ilu_free(self.h)
+            self.h = None
+
+    def factors(self):
+        """(ptr, col, val [nnzb, b, b], dinv [nb, b, b]): L strictly below and
+        U on and above the block diagonal; dinv = U_II^-1."""
+        ptr = np.empty(self.nb + 1, dtype=np.int64)
+        col = np.empty(max(self.nnzb, 1), dtype=np.int32)
+        val = np.empty((max(self.nnzb, 1), self.b, self.b))
+        dinv = np.empty((self.nb, self.b, self.b))
+        _load().orc_ilu_copy(self.h, _p(ptr), _p(col), _p(val), _p(dinv))
+        return ptr, col[:self.nnzb], val[:self.nnzb], dinv
+
+    def apply(self, r: np.ndarray, sweeps: int) -> np.ndarray:
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        out = np.empty_like(r)
+        work = np.empty(2 * len(r))
+        _load().orc_ilu_apply(self.h, sweeps, _p(r), _p(out), _p(work))
+        return out
+
+
 class Hierarchy:
     """Alg. 1 on a scalar CSR matrix; V-cycle (Alg. 2) and PCG on top."""
 
     def __init__(self, A: CSR, bs: int, B: np.ndarray, *, eps_strong=0.08, coarse_enough=3000,
-                 max_levels=15, npre=1, npost=1, relax=1.0, smooth_relax=0.8):
+                 max_levels=15, npre=1, npost=1, relax=1.0, smooth_relax=0.8, smoother="spai0",
+                 ilu_sweeps=2):
         lib = _load()
         B = np.ascontiguousarray(B, dtype=np.float64)
         self.ns = B.shape[1]
         prm = _Params(eps_strong, coarse_enough, max_levels, npre, npost, relax, smooth_relax,
-                      self.ns)
+                      self.ns, {"spai0": 0, "ilu0": 1}[smoother], ilu_sweeps)
         self._A = _Owned(A)
         st = ctypes.c_int(0)
         self.h = lib.orc_setup(self._A.h, bs, _p(B), ctypes.byref(prm), ctypes.byref(st))

@@ -614,7 +614,11 @@ typedef struct {
     double *Mb; /* optional block smoother (3x3 per node, row-major), replaces M */
     double *B;  /* near-nullspace of this level, n x ns */
     double *d;  /* filtered diagonal */
+    struct orc_ilu *ilu; /* block ILU(0) smoother, when selected */
 } orc_level;
+
+struct orc_ilu;
+static void ilu_free(struct orc_ilu *F);
 
 typedef struct {
     int nlev;
@@ -624,7 +628,9 @@ typedef struct {
     int64_t nc;
     int npre, npost;
     int ns;           /* near-nullspace columns (6 or 3) = DOFs of a coarse node */
+    int ilu_sweeps;   /* Jacobi sweeps per triangular solve of the ILU(0) smoother */
     double *work;     /* scratch, 3 vectors per level */
+    double *iwork;    /* scratch of the ILU(0) smoother, 3 vectors of the finest size */
 } orc_hier;
 
 typedef struct {
@@ -635,6 +641,8 @@ typedef struct {
     double relax;        /* omega multiplier, 1.0 */
     double smooth_relax; /* smoother damping w_s, 0.8 */
     int ns;              /* near-nullspace columns of B: 6 (rigid-body modes) or 3 */
+    int smoother;        /* 0: damped SPAI0; 1: block ILU(0) */
+    int ilu_sweeps;      /* Jacobi sweeps per triangular solve of ILU(0) (2) */
 } orc_params;
 
 void orc_params_default(orc_params *p)
@@ -647,6 +655,8 @@ void orc_params_default(orc_params *p)
     p->relax = 1.0;
     p->smooth_relax = 0.8;
     p->ns = 6;
+    p->smoother = 0;
+    p->ilu_sweeps = 2;
 }
 
 void orc_free(orc_hier *H)
@@ -663,12 +673,217 @@ void orc_free(orc_hier *H)
         free(L->Mb);
         free(L->B);
         free(L->d);
+        ilu_free(L->ilu);
     }
     free(H->L);
     free(H->zrow);
     free(H->work);
+    free(H->iwork);
     free(H);
 }
+
+/* ---------------------------------------------------------------------- */
+/* Block ILU(0) smoother (Sec. 4 uses ILU(0) smoothing).                   */
+/* The level matrix in b x b blocks (dense blocks, explicit zeros kept) is  */
+/* factored as L U on its own block pattern: for every block row I and its  */
+/* blocks K < I in ascending order, L_IK = A_IK U_KK^-1, then A_IJ -=       */
+/* L_IK A_KJ for the blocks J > K of row I that row K also holds; what is   */
+/* left on and above the diagonal is U, and U_II is inverted.  A block      */
+/* triangular solve is approximated by a fixed number of Jacobi sweeps, as  */
+/* a data-parallel machine does it: L y = r by y <- r - (L - I) y from      */
+/* y = r, U x = y by x <- U_D^-1 (y - (U - U_D) x) from x = U_D^-1 y.       */
+
+typedef struct orc_ilu {
+    int64_t nb;
+    int b;
+    int64_t *ptr;    /* block rows */
+    int32_t *col;    /* block columns, ascending */
+    int64_t *diag;   /* position of the diagonal block of each row */
+    double *val;     /* L below, U on and above the diagonal, b x b row-major */
+    double *dinv;    /* U_II^-1 */
+} orc_ilu;
+
+static void ilu_free(orc_ilu *F)
+{
+    if (!F) return;
+    free(F->ptr);
+    free(F->col);
+    free(F->diag);
+    free(F->val);
+    free(F->dinv);
+    free(F);
+}
+
+/* Gauss-Jordan inverse of a b x b block without pivoting; -1 on a zero or
+ * non-finite pivot.  A row of the block that is exactly zero (a DOF whose
+ * near-nullspace column was dropped: its whole matrix row and column are
+ * zero) gets a unit pivot and a zero row and column in the inverse, so that
+ * DOF stays zero, as in the coarse solve. */
+static int block_inverse(int b, const double *a, double *inv)
+{
+    double m[6][12];
+    int zero[6];
+    for (int r = 0; r < b; ++r) {
+        zero[r] = 1;
+        for (int c = 0; c < b; ++c) zero[r] &= a[r * b + c] == 0.0;
+    }
+    for (int r = 0; r < b; ++r)
+        for (int c = 0; c < 2 * b; ++c)
+            m[r][c] = c < b ? (zero[r] ? (c == r ? 1.0 : 0.0) : a[r * b + c]) : (c - b == r ? 1.0 : 0.0);
+    for (int p = 0; p < b; ++p) {
+        const double piv = m[p][p];
+        if (!(fabs(piv) > 0.0) || !isfinite(piv)) return -1;
+        for (int c = 0; c < 2 * b; ++c) m[p][c] /= piv;
+        for (int r = 0; r < b; ++r) {
+            if (r == p) continue;
+            const double f = m[r][p];
+            for (int c = 0; c < 2 * b; ++c) m[r][c] -= f * m[p][c];
+        }
+    }
+    for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) inv[r * b + c] = (zero[r] || zero[c]) ? 0.0 : m[r][b + c];
+    return 0;
+}
+
+/* C (b x b) = X Y, both b x b row-major */
+static void block_mul(int b, const double *X, const double *Y, double *C)
+{
+    for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) {
+            double v = 0.0;
+            for (int k = 0; k < b; ++k) v += X[r * b + k] * Y[k * b + c];
+            C[r * b + c] = v;
+        }
+}
+
+/* Block ILU(0) of A (scalar CSR whose pattern is a union of dense b x b
+ * blocks).  Returns NULL if a diagonal block cannot be inverted. */
+orc_ilu *orc_ilu0(const orc_csr *A, int b)
+{
+    const int64_t nb = A->nrows / b, bb = b * b;
+    orc_ilu *F = (orc_ilu *)calloc(1, sizeof(orc_ilu));
+    F->nb = nb;
+    F->b = b;
+    F->ptr = (int64_t *)calloc((size_t)nb + 1, sizeof(int64_t));
+    /* block pattern from the first scalar row of each block row */
+    for (int64_t I = 0; I < nb; ++I) {
+        int64_t cnt = 0, last = -1;
+        for (int64_t p = A->ptr[I * b]; p < A->ptr[I * b + 1]; ++p)
+            if (A->col[p] / b != last) {
+                last = A->col[p] / b;
+                ++cnt;
+            }
+        F->ptr[I + 1] = F->ptr[I] + cnt;
+    }
+    const int64_t nnzb = F->ptr[nb];
+    F->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnzb > 0 ? nnzb : 1));
+    F->val = (double *)calloc((size_t)(nnzb > 0 ? nnzb : 1) * bb, sizeof(double));
+    F->diag = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb > 0 ? nb : 1));
+    F->dinv = (double *)calloc((size_t)(nb > 0 ? nb : 1) * bb, sizeof(double));
+    for (int64_t I = 0; I < nb; ++I) {
+        int64_t q = F->ptr[I] - 1, last = -1;
+        for (int64_t p = A->ptr[I * b]; p < A->ptr[I * b + 1]; ++p)
+            if (A->col[p] / b != last) {
+                last = A->col[p] / b;
+                F->col[++q] = (int32_t)last;
+            }
+        F->diag[I] = -1;
+        for (int64_t q2 = F->ptr[I]; q2 < F->ptr[I + 1]; ++q2)
+            if (F->col[q2] == I) F->diag[I] = q2;
+        for (int r = 0; r < b; ++r) {
+            int64_t q2 = F->ptr[I];
+            for (int64_t p = A->ptr[I * b + r]; p < A->ptr[I * b + r + 1]; ++p) {
+                const int32_t J = A->col[p] / b, c = A->col[p] % b;
+                while (F->col[q2] != J) ++q2;
+                F->val[q2 * bb + r * b + c] = A->val[p];
+            }
+        }
+    }
+    double T[36];
+    for (int64_t I = 0; I < nb; ++I) {
+        for (int64_t pk = F->ptr[I]; pk < F->ptr[I + 1] && F->col[pk] < I; ++pk) {
+            const int32_t K = F->col[pk];
+            block_mul(b, F->val + pk * bb, F->dinv + K * bb, T); /* L_IK = A_IK U_KK^-1 */
+            memcpy(F->val + pk * bb, T, sizeof(double) * (size_t)bb);
+            int64_t pkj = F->diag[K] + 1;
+            for (int64_t pj = pk + 1; pj < F->ptr[I + 1]; ++pj) {
+                const int32_t J = F->col[pj];
+                while (pkj < F->ptr[K + 1] && F->col[pkj] < J) ++pkj;
+                if (pkj >= F->ptr[K + 1] || F->col[pkj] != J) continue;
+                block_mul(b, F->val + pk * bb, F->val + pkj * bb, T); /* A_IJ -= L_IK A_KJ */
+                for (int e = 0; e < bb; ++e) F->val[pj * bb + e] -= T[e];
+            }
+        }
+        if (F->diag[I] < 0 || block_inverse(b, F->val + F->diag[I] * bb, F->dinv + I * bb) != 0) {
+            ilu_free(F);
+            return NULL;
+        }
+    }
+    return F;
+}
+
+/* out = ILU^-1 r, approximately: `sweeps` Jacobi sweeps per triangular
+ * solve (work: 2 vectors of the level's size). */
+void orc_ilu_apply(const orc_ilu *F, int sweeps, const double *r, double *out, double *work)
+{
+    const int b = F->b, bb = b * b;
+    const int64_t nb = F->nb, n = nb * b;
+    double *y = work, *t = work + n;
+    memcpy(y, r, sizeof(double) * (size_t)n);
+    for (int s = 0; s < sweeps; ++s) {
+        for (int64_t I = 0; I < nb; ++I)
+            for (int rr = 0; rr < b; ++rr) {
+                double v = 0.0;
+                for (int64_t p = F->ptr[I]; p < F->diag[I]; ++p)
+                    for (int c = 0; c < b; ++c) v += F->val[p * bb + rr * b + c] * y[F->col[p] * b + c];
+                t[I * b + rr] = r[I * b + rr] - v;
+            }
+        memcpy(y, t, sizeof(double) * (size_t)n);
+    }
+    for (int64_t I = 0; I < nb; ++I)
+        for (int rr = 0; rr < b; ++rr) {
+            double v = 0.0;
+            for (int c = 0; c < b; ++c) v += F->dinv[I * bb + rr * b + c] * y[I * b + c];
+            out[I * b + rr] = v;
+        }
+    for (int s = 0; s < sweeps; ++s) {
+        for (int64_t I = 0; I < nb; ++I) {
+            double res[6];
+            for (int rr = 0; rr < b; ++rr) {
+                double v = 0.0;
+                for (int64_t p = F->diag[I] + 1; p < F->ptr[I + 1]; ++p)
+                    for (int c = 0; c < b; ++c) v += F->val[p * bb + rr * b + c] * out[F->col[p] * b + c];
+                res[rr] = y[I * b + rr] - v;
+            }
+            for (int rr = 0; rr < b; ++rr) {
+                double v = 0.0;
+                for (int c = 0; c < b; ++c) v += F->dinv[I * bb + rr * b + c] * res[c];
+                t[I * b + rr] = v;
+            }
+        }
+        memcpy(out, t, sizeof(double) * (size_t)n);
+    }
+}
+
+/* Factor copies for tests: the blocks (nnzb x b x b) and the diagonal
+ * inverses (nb x b x b); NULL pointers skip. */
+void orc_ilu_shape(const orc_ilu *F, int64_t *out3)
+{
+    out3[0] = F->nb;
+    out3[1] = F->b;
+    out3[2] = F->ptr[F->nb];
+}
+
+void orc_ilu_copy(const orc_ilu *F, int64_t *ptr, int32_t *col, double *val, double *dinv)
+{
+    const int64_t bb = (int64_t)F->b * F->b;
+    if (ptr) memcpy(ptr, F->ptr, sizeof(int64_t) * (size_t)(F->nb + 1));
+    if (col) memcpy(col, F->col, sizeof(int32_t) * (size_t)F->ptr[F->nb]);
+    if (val) memcpy(val, F->val, sizeof(double) * (size_t)(F->ptr[F->nb] * bb));
+    if (dinv) memcpy(dinv, F->dinv, sizeof(double) * (size_t)(F->nb * bb));
+}
+
+void orc_ilu_free(orc_ilu *F) { ilu_free(F); }
 
 /* Alg. 1.  A is scalar CSR (n = nnodes * bs rows), B is n x prm->ns; coarse
  * nodes carry ns DOFs.  The hierarchy takes a copy of A.  Returns NULL on
@@ -686,6 +901,7 @@ orc_hier *orc_setup(const orc_csr *A0, int bs, const double *B0, const orc_param
         return NULL;
     }
     H->ns = ns;
+    H->ilu_sweeps = prm->ilu_sweeps;
     orc_level *L0 = &H->lv[0];
     L0->A = orc_csr_from(A0->nrows, A0->ncols, A0->ptr, A0->col, A0->val);
     L0->b = bs;
@@ -725,6 +941,14 @@ orc_hier *orc_setup(const orc_csr *A0, int bs, const double *B0, const orc_param
         C->M = (double *)malloc(sizeof(double) * (size_t)n);
         orc_spai0(C->A, C->M);
         for (int64_t i = 0; i < n; ++i) C->M[i] = prm->smooth_relax * C->M[i];
+        if (prm->smoother == 1) {
+            C->ilu = orc_ilu0(C->A, C->b);
+            if (!C->ilu) {
+                *status = -4;
+                orc_free(H);
+                return NULL;
+            }
+        }
         N->b = ns;
         N->eps = C->eps * 0.5;
         H->nlev++;
@@ -751,14 +975,20 @@ orc_hier *orc_setup(const orc_csr *A0, int bs, const double *B0, const orc_param
     int64_t tot = 0;
     for (int l = 0; l < H->nlev; ++l) tot += 3 * H->lv[l].A->nrows;
     H->work = (double *)calloc((size_t)tot, sizeof(double));
+    H->iwork = (double *)calloc((size_t)(3 * H->lv[0].A->nrows + 1), sizeof(double));
     return H;
 }
 
-/* out = M x (diagonal SPAI0) or the 3x3 block smoother when one is set;
- * with add != 0, out += M x. */
-static void apply_smoother(const orc_level *L, int64_t n, const double *x, double *out, int add)
+/* out = M x (diagonal SPAI0), the 3x3 block smoother when one is set, or the
+ * block ILU(0) smoother; with add != 0, out += M x. */
+static void apply_smoother(const orc_hier *H, const orc_level *L, int64_t n, const double *x,
+                           double *out, int add)
 {
-    if (L->Mb) {
+    if (L->ilu) {
+        double *z = H->iwork + 2 * n;
+        orc_ilu_apply(L->ilu, H->ilu_sweeps, x, z, H->iwork);
+        for (int64_t i = 0; i < n; ++i) out[i] = add ? out[i] + z[i] : z[i];
+    } else if (L->Mb) {
         for (int64_t I = 0; I < n / 3; ++I)
             for (int a = 0; a < 3; ++a) {
                 double v = 0.0;
@@ -794,13 +1024,13 @@ static void vcycle_level(orc_hier *H, int l, const double *f, double *u, double 
     }
     double *e = work, *fc = work + n, *uc = fc + L->R->nrows, *next = uc + L->R->nrows;
     /* pre-smoothing from u = 0: the first sweep gives u = M f */
-    if (H->npre > 0) apply_smoother(L, n, f, u, 0);
+    if (H->npre > 0) apply_smoother(H, L, n, f, u, 0);
     else
         for (int64_t i = 0; i < n; ++i) u[i] = 0.0;
     for (int s = 1; s < H->npre; ++s) {
         orc_spmv(L->A, u, e);
         for (int64_t i = 0; i < n; ++i) e[i] = f[i] - e[i];
-        apply_smoother(L, n, e, u, 1);
+        apply_smoother(H, L, n, e, u, 1);
     }
     /* residual and restriction: f_{l+1} = R (f - A u) */
     orc_spmv(L->A, u, e);
@@ -814,7 +1044,7 @@ static void vcycle_level(orc_hier *H, int l, const double *f, double *u, double 
     for (int s = 0; s < H->npost; ++s) {
         orc_spmv(L->A, u, e);
         for (int64_t i = 0; i < n; ++i) e[i] = f[i] - e[i];
-        apply_smoother(L, n, e, u, 1);
+        apply_smoother(H, L, n, e, u, 1);
     }
 }
 
