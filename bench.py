@@ -282,13 +282,32 @@ def learned_fp32_form(amg, torch, args_dev, w, f, tol, u_ref, t_fp64, fp32_form,
             "vcycle": "FP32 matrices and vectors; level 0 smoothed with the learned blocks in FP32"}
 
 
-def run_batch(args, amg, torch):
+def reduce_max(dist, values, device):
+    """Element-wise maximum over ranks (the slowest rank sets the time);
+    the values themselves when there is one rank."""
+    import torch
+    if dist is None:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def batch_seed(rank):
+    """Each rank solves its own batch of 64 boxes (weak scaling: independent
+    problems, no collective on the data path); rank 0's is the 1-GPU batch."""
+    return 2202 + 1000 * rank
+
+
+def run_batch(args, amg, torch, rank=0, world=1, dist=None, local=0):
     """64 independent boxes (seeded sizes 20^3-60^3, nu in [0.2, 0.45], 1-16
     random unit body loads each): one batched solve of every right-hand side
-    against a loop of single FP64 solves of the same systems."""
+    against a loop of single FP64 solves of the same systems.  Under N ranks
+    every rank solves its own seeded batch and the step time is the maximum
+    over ranks."""
     import q1elasticity as q
-    dev = torch.device("cuda", 0)
-    specs = q.batch_specs(64)
+    dev = torch.device("cuda", local)
+    specs = q.batch_specs(64, seed=batch_seed(rank))
     mats, Bs, F, nrhs = [], [], [], []
     for sp in specs:
         p = q.make_problem(sp["n"], nu=sp["nu"], body=sp["body"])
@@ -299,6 +318,8 @@ def run_batch(args, amg, torch):
         nrhs.append(sp["nrhs"])
     s = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     bat = amg.AMGBatch(mats, Bs, nrhs)
     torch.cuda.synchronize()
@@ -309,6 +330,9 @@ def run_batch(args, amg, torch):
     launches0 = amg.kernel_launches()
     with ClockSampler(_gpu_id(torch)) as clk:
         for _ in range(args.steps):
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
             e0, e1 = ev(), ev()
             e0.record(s)
             U, its, res, st = bat.solve(F)
@@ -316,6 +340,7 @@ def run_batch(args, amg, torch):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
     launches = amg.kernel_launches() - launches0
+    times = reduce_max(dist, times, dev)
     assert st == amg.AMG_OK, st
     info = bat.info()
     del bat
@@ -337,14 +362,17 @@ def run_batch(args, amg, torch):
             its_single.append(it1)
             errs.append(float(torch.linalg.norm(U[i][j] - u1) / torch.linalg.norm(u1)))
         del one
+    loop_solve, loop_setup, setup_t = reduce_max(dist, [loop_solve, loop_setup, setup_t], dev)
     v = float(np.mean(times))
     return {
-        "metric": METRIC, "value": v, "unit": "s", "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS["batch64"]["desc"], "instances": 64,
-                   "rhs_total": int(sum(nrhs)), "dofs_total": int(info["dofs_total"]),
-                   "l2": "inputs larger than L2", "parallelism": "single"},
+        "config": {"workload": WORKLOADS["batch64"]["desc"], "instances": 64 * world,
+                   "rhs_rank0": int(sum(nrhs)), "dofs_rank0": int(info["dofs_total"]),
+                   "l2": "inputs larger than L2",
+                   "parallelism": (f"dp{world}: every rank its own seeded batch of 64"
+                                   if world > 1 else "single")},
         "batch": {"setup_s": setup_t, "rhs_tile_per_level_A_P_R": info["rhs_tile"],
                   "iterations_max": int(max(max(x) for x in its)),
                   "iterations_mean": float(np.mean([y for x in its for y in x])),
@@ -401,8 +429,11 @@ def main():
 
     amg.load()
     if args.workload == "batch64":
-        line = run_batch(args, amg, torch)
-        print(json.dumps(line), flush=True)
+        line = run_batch(args, amg, torch, rank, world, dist, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
         return 0
     p = _problem(args.workload)
     dev = torch.device("cuda", local)
@@ -467,10 +498,7 @@ def main():
     its = timings[-1][2]
     res = timings[-1][3]
     step_t = setup_t + solve_t
-    if dist is not None:
-        tt = torch.tensor([solve_t, step_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        solve_t, step_t = float(tt[0]), float(tt[1])
+    solve_t, step_t = reduce_max(dist, [solve_t, step_t], dev)
 
     # end to end through the public API: pinned host f -> device, solve, u -> host
     fh = torch.from_numpy(p.f).pin_memory()
