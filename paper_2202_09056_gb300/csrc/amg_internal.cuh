@@ -168,9 +168,11 @@ template <class TV> struct SellArgs {
 int sell_grid(int nslices, int br, int bc, const Geom &g);
 // bytes a sliced copy holds on the device
 template <class T> int64_t sell_bytes(const Sell<T> &S);
+// max_grid > 0 caps the grid (the warp-strided loop covers every slice): for
+// launches that usually exit at once on their stop flag
 template <class VT, class TV>
 int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom &g,
-                cudaStream_t s, int *grid_out = nullptr);
+                cudaStream_t s, int *grid_out = nullptr, int max_grid = 0);
 template <class T>
 int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, double *padding,
                 int max_lanes = 128);

@@ -241,7 +241,7 @@ static int sell_mode(int mode, int dot, const SellArgs<TV> &a, int grid, cudaStr
 
 template <class VT, class TV>
 int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom &g,
-                cudaStream_t s, int *grid_out)
+                cudaStream_t s, int *grid_out, int max_grid)
 {
     a.nrows = A.nrows;
     a.nslices = A.nslices;
@@ -250,7 +250,8 @@ int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom
     a.col = A.col;
     a.val = A.val;
     a.perm = A.perm;
-    const int grid = sell_grid(A.nslices, A.br, A.bc, g);
+    int grid = sell_grid(A.nslices, A.br, A.bc, g);
+    if (max_grid > 0 && grid > max_grid) grid = max_grid;
     if (grid_out) *grid_out = grid;
     if (dot != DOT_NONE && grid > g.max_partials) {
         set_error("fused dot needs %d partial sums, the buffer holds %d", grid, g.max_partials);
@@ -271,11 +272,12 @@ int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom
 }
 
 template int launch_sell<double, double>(const Sell<double> &, int, int, SellArgs<double>,
-                                         const Geom &, cudaStream_t, int *);
+                                         const Geom &, cudaStream_t, int *, int);
 template int launch_sell<float, float>(const Sell<float> &, int, int, SellArgs<float>,
-                                       const Geom &, cudaStream_t, int *);
+                                       const Geom &, cudaStream_t, int *, int);
 template int launch_sell<__nv_bfloat16, float>(const Sell<__nv_bfloat16> &, int, int,
-                                               SellArgs<float>, const Geom &, cudaStream_t, int *);
+                                               SellArgs<float>, const Geom &, cudaStream_t, int *,
+                                               int);
 
 // ---------------------------------------------------------------- conversion
 template <class T>

@@ -440,14 +440,17 @@ static int record_cg_iteration_t(amg_handle h, cudaStream_t s, cudaGraphConditio
                                                      n, npre > 0, h->partials); ::amg::count_launch(1);
     cg_resnorm_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, vgrid(h, n)); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
-    {  // true residual, only when the recurrence residual reached tol
+    {  // true residual, only when the recurrence residual reached tol: every
+       // other iteration the launch exits at once, so a small grid (4 CTAs
+       // per SM, warp-strided over the slices) keeps that cheap
         SellArgs<double> a{};
         a.x = h->uu;
         a.f = h->ff;
         a.y = h->rt;
         a.partials = h->partials;
         a.stop = &h->st->no_check;
-        AMG_TRY((launch_sell<double, double>(L0.sA, SPMV_RESID, DOT_YY, a, g, s, &grid)));
+        AMG_TRY((launch_sell<double, double>(L0.sA, SPMV_RESID, DOT_YY, a, g, s, &grid,
+                                             g.num_sms * 4)));
     }
     cg_decide_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, grid, cond, use_cond); ::amg::count_launch(1);
     cg_replace_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(h->r, h->rt, V0.M,
