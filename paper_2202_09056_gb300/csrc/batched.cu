@@ -98,12 +98,17 @@ __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
 #pragma unroll
                     for (int t = 0; t < KT; ++t)
                         xv[c][t] = (k0 + t < K) ? __ldg(xb + ((int64_t)j * BC + c) * K + k0 + t) : 0.0;
-                const double *vb = vp + (int64_t)d * 32 * BB;
+                // FP64 sliced values: entries 2p, 2p+1 of a lane side by
+                // side, an odd last entry after the pairs (as in sell.cu)
+                const double *vg = vp - lane + (int64_t)d * 32 * BB;
 #pragma unroll
                 for (int r = 0; r < BR; ++r)
 #pragma unroll
                     for (int c = 0; c < BC; ++c) {
-                        const double v = __ldg(vb + (r * BC + c) * 32);
+                        constexpr int PAIRED = BB & ~1;
+                        const int e = r * BC + c;
+                        const double v = __ldg(vg + (e < PAIRED ? (e >> 1) * 64 + 2 * lane + (e & 1)
+                                                                : (BB >> 1) * 64 + lane));
 #pragma unroll
                         for (int t = 0; t < KT; ++t) acc[r][t] = fma(v, xv[c][t], acc[r][t]);
                     }

@@ -15,7 +15,9 @@
 // To keep the loads coalesced, the 32 lanes of a slice store their blocks
 // interleaved: entry e of the block at depth d of lane t sits at
 // (slice_base + 32 d) * bb + 32 e + t, so every value load of a warp is one
-// contiguous 256-byte segment.  A slice is as deep as its longest lane;
+// contiguous 256-byte segment; FP64 values go in lane pairs instead (entries
+// 2p and 2p+1 of lane t at (slice_base + 32 d) * bb + 64 p + 2 t, an odd last
+// entry after the pairs), one contiguous 512-byte segment per 16-byte load.  A slice is as deep as its longest lane;
 // shorter lanes are padded with zero blocks pointing at column 0 (the padding
 // is overhead, not algorithmic bytes).
 //
@@ -106,12 +108,31 @@ __global__ void __launch_bounds__(SELL_THREADS, sell_minb(BR, BC)) sell_spmv_ker
             Acc xv[BC];
 #pragma unroll
             for (int c = 0; c < BC; ++c) xv[c] = (Acc)__ldg(x + (int64_t)j * BC + c);
-            const VT *vb = vp + (int64_t)k * 32 * BB;
+            if constexpr (std::is_same<VT, double>::value) {
+                // FP64 values are stored in lane pairs: one 16-byte load
+                // brings two entries of a lane's block (half the load
+                // instructions of the per-entry layout)
+                const double *vg = val + (base + (int64_t)k * 32) * BB;
+                double v[BB];
 #pragma unroll
-            for (int r = 0; r < BR; ++r)
+                for (int p = 0; p < BB / 2; ++p) {
+                    const double2 t2 = __ldcs(reinterpret_cast<const double2 *>(vg + p * 64) + lane);
+                    v[2 * p] = t2.x;
+                    v[2 * p + 1] = t2.y;
+                }
+                if constexpr (BB % 2 == 1) v[BB - 1] = __ldcs(vg + (BB / 2) * 64 + lane);
 #pragma unroll
-                for (int c = 0; c < BC; ++c)
-                    acc[r] = fma((Acc)sldv(vb + (r * BC + c) * 32), xv[c], acc[r]);
+                for (int r = 0; r < BR; ++r)
+#pragma unroll
+                    for (int c = 0; c < BC; ++c) acc[r] = fma(v[r * BC + c], xv[c], acc[r]);
+            } else {
+                const VT *vb = vp + (int64_t)k * 32 * BB;
+#pragma unroll
+                for (int r = 0; r < BR; ++r)
+#pragma unroll
+                    for (int c = 0; c < BC; ++c)
+                        acc[r] = fma((Acc)sldv(vb + (r * BC + c) * 32), xv[c], acc[r]);
+            }
         }
         // rows split over G lanes: fixed-order butterfly within the group
         bool owner;
@@ -304,9 +325,16 @@ __global__ void sell_fill_kernel(const int *__restrict__ rp, const int *__restri
         const bool have = k < len;
         const int64_t src = have ? (int64_t)rp[row] + k : 0;
         col[q] = have ? bcol[src] : 0;
-        for (int e = 0; e < bb; ++e)
-            val[(base + (int64_t)d * 32) * bb + (int64_t)e * 32 + lane] =
-                have ? (T)bval[src * bb + e] : (T)0.0;
+        T *vg = val + (base + (int64_t)d * 32) * bb;
+        for (int e = 0; e < bb; ++e) {
+            // FP64: entries 2p, 2p + 1 of a lane side by side (pair p of the
+            // 32 lanes is one 512-byte run), an odd last entry per lane after
+            // the pairs; other types: entry e of the 32 lanes is one run
+            const int64_t off = sizeof(T) == 8 ? (e < (bb & ~1) ? (int64_t)(e >> 1) * 64 + 2 * lane + (e & 1)
+                                                                 : (int64_t)(bb >> 1) * 64 + lane)
+                                               : (int64_t)e * 32 + lane;
+            vg[off] = have ? (T)bval[src * bb + e] : (T)0.0;
+        }
     }
 }
 
