@@ -60,13 +60,15 @@ template <int NT> __device__ __forceinline__ double cta_sum_d(double v)
 constexpr int SELL_THREADS = 128;
 
 // Register budget: the kernel is compiled for minb resident CTAs per SM
-// (65536 / (128 x minb) registers per thread).  Grid: up to cap CTAs per SM,
+// (65536 / (128 x minb) registers per thread): 12 (40 registers) for 3x3
+// blocks, 8 (64) for the others, whose paired FP64 loads hold 18-36 values
+// (at 10 CTAs the 6x3 restriction spilled and ran 7 % slower).  Grid: up to cap CTAs per SM,
 // measured on the 80^3 hierarchy.  The fine-level shapes (3-row blocks, one
 // lane per row, uniform slices) run fastest oversubscribed, one slice group
 // per CTA with the hardware scheduler balancing; the 6x6 coarse operators
 // (few, long rows in widest-first order) fastest as exactly one resident
 // wave with the warp-strided loop balancing.
-__host__ __device__ constexpr int sell_minb(int br, int bc) { return br == 6 ? (bc == 6 ? 8 : 10) : 12; }
+__host__ __device__ constexpr int sell_minb(int br, int bc) { return br == 6 ? 8 : (bc == 6 ? 8 : 12); }
 __host__ __device__ constexpr int sell_cap(int br, int bc) { return br == 6 ? (bc == 6 ? 8 : 16) : 32; }
 
 template <int BR, int BC, class VT, class TV, int MODE, int DOT, bool WIDE>
