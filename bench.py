@@ -629,6 +629,7 @@ def main():
                      "algorithmic_flops": flops, "launch_ms": 1e3 * t_spmv,
                      "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_kind,
+                             "frac_of_nominal_8tbs": achieved / 8000.0,
                              "algorithmic_bytes": algo}},
         "wall_s": wall,
         "precision": args.precision,

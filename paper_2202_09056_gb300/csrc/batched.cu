@@ -99,19 +99,24 @@ __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
                     for (int t = 0; t < KT; ++t)
                         xv[c][t] = (k0 + t < K) ? __ldg(xb + ((int64_t)j * BC + c) * K + k0 + t) : 0.0;
                 // FP64 sliced values: entries 2p, 2p+1 of a lane side by
-                // side, an odd last entry after the pairs (as in sell.cu)
+                // side (one 16-byte load), an odd last entry after the pairs
+                // (the layout of sell.cu)
                 const double *vg = vp - lane + (int64_t)d * 32 * BB;
+                double v[BB];
+#pragma unroll
+                for (int pr = 0; pr < BB / 2; ++pr) {
+                    const double2 t2 = __ldg(reinterpret_cast<const double2 *>(vg + pr * 64) + lane);
+                    v[2 * pr] = t2.x;
+                    v[2 * pr + 1] = t2.y;
+                }
+                if constexpr (BB % 2 == 1) v[BB - 1] = __ldg(vg + (BB / 2) * 64 + lane);
 #pragma unroll
                 for (int r = 0; r < BR; ++r)
 #pragma unroll
-                    for (int c = 0; c < BC; ++c) {
-                        constexpr int PAIRED = BB & ~1;
-                        const int e = r * BC + c;
-                        const double v = __ldg(vg + (e < PAIRED ? (e >> 1) * 64 + 2 * lane + (e & 1)
-                                                                : (BB >> 1) * 64 + lane));
+                    for (int c = 0; c < BC; ++c)
 #pragma unroll
-                        for (int t = 0; t < KT; ++t) acc[r][t] = fma(v, xv[c][t], acc[r][t]);
-                    }
+                        for (int t = 0; t < KT; ++t)
+                            acc[r][t] = fma(v[r * BC + c], xv[c][t], acc[r][t]);
             }
             for (int m = G >> 1; m >= 1; m >>= 1)
 #pragma unroll
