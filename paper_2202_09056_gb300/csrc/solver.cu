@@ -619,8 +619,32 @@ void amg::destroy_handle(amg_handle h)
 }
 
 // Input pattern check, one thread per block row: bad[0] |= 1 (row pointers),
-// 2 (columns not ascending or out of range), 4 (no diagonal block); bad[1] =
-// the lowest offending row.
+// 2 (columns not ascending or out of range), 4 (no diagonal block), 8 (the
+// pattern is not symmetric: block (I, J) without (J, I); A is SPD, and the
+// Galerkin products rely on it); bad[1] = the lowest offending row.  Rows are
+// first checked on their own (codes 1, 2, 4); only a fully valid pattern is
+// searched for the transposed blocks, so no search reads a bad row.
+__global__ void validate_symmetry_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                                         int nbr, int *__restrict__ bad)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nbr || bad[0] != 0) return;
+    for (int k = rp[I]; k < rp[I + 1]; ++k) {
+        const int J = col[k];
+        int lo = rp[J], hi = rp[J + 1];
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (col[mid] < I) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo >= rp[J + 1] || col[lo] != I) {
+            atomicOr(bad + 2, 8);
+            atomicMin(bad + 1, I);
+            return;
+        }
+    }
+}
+
 __global__ void validate_pattern_kernel(const int *__restrict__ rp, const int *__restrict__ col,
                                         int nbr, int nbc, int64_t nnzb, int *__restrict__ bad)
 {
@@ -684,16 +708,20 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         // checking kernel reads a row's columns only after its own row
         // pointers were found inside [0, nnzb]
         int *bad = nullptr;
-        AMG_TRY(tmp.alloc_n(&bad, 2));
-        const int init[2] = {0, INT32_MAX};
+        AMG_TRY(tmp.alloc_n(&bad, 3));
+        const int init[3] = {0, INT32_MAX, 0};
         AMG_TRY_CUDA(cudaMemcpyAsync(bad, init, sizeof(init), cudaMemcpyHostToDevice, s));
         if (A.nbr > 0) {
             validate_pattern_kernel<<<(A.nbr + 255) / 256, 256, 0, s>>>(A.row_ptr, A.col, A.nbr,
                                                                         A.nbc, A.nnzb, bad);
-            ::amg::count_launch(1);
+            // square matrices only reach here (nbc == nbr); runs only when
+            // every row passed (each thread reads bad[0] first)
+            validate_symmetry_kernel<<<(A.nbr + 255) / 256, 256, 0, s>>>(A.row_ptr, A.col, A.nbr,
+                                                                         bad);
+            ::amg::count_launch(2);
             AMG_TRY_CUDA(cudaGetLastError());
         }
-        int hb[2] = {0, 0};
+        int hb[3] = {0, 0, 0};
         AMG_TRY_CUDA(cudaMemcpyAsync(hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, s));
         AMG_TRY_CUDA(cudaStreamSynchronize(s));
         tmp.release(bad);
@@ -707,6 +735,10 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         }
         if (hb[0] & 4) {
             set_error("block row %d has no diagonal block", hb[1]);
+            return AMG_ERR_ARG;
+        }
+        if (hb[2] & 8) {
+            set_error("the block pattern is not symmetric (block row %d)", hb[1]);
             return AMG_ERR_ARG;
         }
         h->lv.push_back(L0);

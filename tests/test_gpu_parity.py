@@ -342,3 +342,15 @@ def test_setup_rejects_malformed_patterns():
     with pytest.raises(amg.AmgError) as e:
         setup(rp0, cl)
     assert "block row 0 has no diagonal block" in str(e.value)
+    # a non-symmetric pattern: row 7 loses its first block (column 2), row 2
+    # keeps its block (2, 7)
+    a = rp0[7]
+    assert cl0[a] == 2 and 7 in cl0[rp0[2]:rp0[3]]
+    cl = np.delete(cl0, a)
+    rp = rp0.copy()
+    rp[8:] -= 1
+    d = torch.device("cuda:0")
+    with pytest.raises(amg.AmgError) as e:
+        amg.AMG(torch.from_numpy(rp).to(d), torch.from_numpy(cl).to(d),
+                torch.from_numpy(np.delete(val0, a, axis=0)).to(d), torch.from_numpy(B0).to(d))
+    assert "not symmetric" in str(e.value) and "block row 2" in str(e.value)
