@@ -335,7 +335,7 @@ def run_batch(args, amg, torch, rank=0, world=1, dist=None, local=0):
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
-    bat = amg.AMGBatch(mats, Bs, nrhs)
+    bat = amg.AMGBatch(mats, Bs, nrhs, loop_mode=args.loop_mode)
     torch.cuda.synchronize()
     setup_t = time.perf_counter() - t0
     for _ in range(args.warmup):

@@ -560,6 +560,7 @@ struct amg_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long body_kernels = 0;
+    int host_loop = 0;  // exec is one iteration, launched by the host (loop_mode 1)
     int tol_maxiter_key = 0;
     double tol = 0;
     int maxiter = 0;
@@ -733,6 +734,38 @@ static int build_bgraph(amg_batch h)
         h->exec = nullptr;
         h->graph = nullptr;
     }
+    if (h->prm.loop_mode == 1) {
+        // one captured iteration, launched by the host until no pair is
+        // active (for profilers that cannot look inside conditional graphs;
+        // same kernels, same results)
+        cudaStream_t cs;
+        AMG_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        AMG_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        long long nbody = 0;
+        begin_launch_capture(&nbody);
+        int st = record_biteration(h, cs, cudaGraphConditionalHandle{}, 0);
+        end_launch_capture();
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        cudaStreamDestroy(cs);
+        if (st < 0 || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            if (st >= 0) set_error("graph capture: %s", cudaGetErrorString(e));
+            return st < 0 ? st : AMG_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&h->exec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            h->exec = nullptr;
+            set_error("graph instantiate: %s", cudaGetErrorString(e));
+            return AMG_ERR_CUDA;
+        }
+        h->graph = graph;
+        h->body_kernels = nbody;
+        h->host_loop = 1;
+        return AMG_OK;
+    }
+    h->host_loop = 0;
     cudaGraph_t graph = nullptr;
     AMG_TRY_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle cond;
@@ -1192,7 +1225,16 @@ int amg_batch_solve(amg_batch h, const double *const *F, double *const *U, doubl
             h->maxiter = maxiter;
             AMG_TRY(build_bgraph(h));
         }
-        AMG_TRY_CUDA(cudaGraphLaunch(h->exec, s));
+        if (!h->host_loop) {
+            AMG_TRY_CUDA(cudaGraphLaunch(h->exec, s));
+        } else {
+            for (int k = 0; k <= maxiter && any; ++k) {
+                AMG_TRY_CUDA(cudaGraphLaunch(h->exec, s));
+                AMG_TRY_CUDA(cudaMemcpyAsync(&any, st.any_active, sizeof(int),
+                                             cudaMemcpyDeviceToHost, s));
+                AMG_TRY_CUDA(cudaStreamSynchronize(s));
+            }
+        }
     }
     // u of a zero right-hand side is zero
     std::vector<double> nf(h->ngl), res(h->ngl), rest(h->ngl);

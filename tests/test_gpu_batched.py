@@ -90,3 +90,22 @@ def test_batch_zero_rhs_and_cap():
     assert its[0][1] == 0 and not U[0][1].any()
     U, its, res, st = bat.solve([F], tol=1e-14, maxiter=2)
     assert st == amg.AMG_NOT_CONVERGED and its[0][0] == 2
+
+
+def test_host_loop_mode_gives_identical_batch_results():
+    """loop_mode 1 (one captured iteration per host launch, for profilers)
+    runs the same kernels: the same bits as the device-side loop."""
+    specs = q.batch_specs(3, seed=11, nmin=5, nmax=8, rhs_max=3)
+    d = torch.device("cuda:0")
+    mats, Bs, F, nrhs = [], [], [], []
+    for sp in specs:
+        p = q.make_problem(sp["n"], nu=sp["nu"], body=sp["body"])
+        mats.append((torch.from_numpy(p.row_ptr).to(d), torch.from_numpy(p.col).to(d),
+                     torch.from_numpy(p.val).to(d)))
+        Bs.append(torch.from_numpy(p.B).to(d))
+        F.append(torch.from_numpy(np.atleast_2d(p.f).copy()).to(d))
+        nrhs.append(sp["nrhs"])
+    U0, it0, r0, s0 = amg.AMGBatch(mats, Bs, nrhs, coarse_enough=150).solve(F)
+    U1, it1, r1, s1 = amg.AMGBatch(mats, Bs, nrhs, coarse_enough=150, loop_mode=1).solve(F)
+    assert s0 == s1 == amg.AMG_OK and it0 == it1 and r0 == r1
+    assert all(torch.equal(a, b) for a, b in zip(U0, U1))
