@@ -11,7 +11,8 @@
  *     coarsest A_L.
  *   - Alg. 2 (Sec. 2): V-cycle, applied once per preconditioning step.
  *   - Sec. 2/3: every matrix of the hierarchy is held in block CSR (BSR):
- *     3x3 blocks on the finest level, 6x6 below it (six rigid-body modes);
+ *     3x3 blocks on the finest level, 6x6 below it (six rigid-body modes;
+ *     3x3 when B holds only the three translations);
  *     only the tentative prolongation is built from B in scalar terms, and
  *     here it is built per aggregate inside block-structured kernels (the
  *     paper's "NS Block" route, Sec. 3, Listing 2 semantics).
@@ -98,7 +99,7 @@ typedef struct amg_handle_s *amg_handle;
 /* Per-level description filled by amg_level_info (host struct). */
 typedef struct {
     int32_t nbrows;        /* block rows of A on this level */
-    int32_t bs;            /* block size of A (3 on level 0, 6 below) */
+    int32_t bs;            /* block size of A (3 on level 0, nb_ns below) */
     int64_t nnzb_A;
     int64_t nnzb_P;        /* 0 on the coarsest level */
     int32_t nagg;          /* aggregates = block rows of the next level (0 on the coarsest) */
@@ -133,7 +134,11 @@ int amg_params_default(amg_params *prm);
  * translations only, which is the block solver of Sec. 4 without a
  * near-nullspace; coarse nodes carry nb_ns DOFs).  prm may be NULL for
  * the defaults.  On success *out owns every level on the device (allocated
- * stream-ordered on `stream`).  A and B are only read. */
+ * stream-ordered on `stream`).  A and B are only read.  The block pattern is
+ * checked on the device before any other kernel reads it: row pointers
+ * within [0, nnzb] and non-decreasing, columns ascending and in range, a
+ * diagonal block in every row, and a symmetric pattern; a violation returns
+ * AMG_ERR_ARG naming the lowest offending block row. */
 int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params *prm,
               void *stream, amg_handle *out);
 
@@ -160,12 +165,12 @@ int amg_get_stats(amg_handle h, amg_stats *out);
 int amg_level_info(amg_handle h, int32_t level, amg_level_desc *out);
 
 /* Copy one operator of a level to HOST buffers sized from amg_level_info:
- * which = 0: A (nbrows+1, nnzb_A, nnzb_A*bs*bs), 1: P (bs x 6 blocks),
- * 2: R (6 x bs blocks, nagg+1 row pointers).  Any pointer may be NULL.
+ * which = 0: A (nbrows+1, nnzb_A, nnzb_A*bs*bs), 1: P (bs x nb_ns blocks),
+ * 2: R (nb_ns x bs blocks, nagg+1 row pointers).  Any pointer may be NULL.
  * which = 3: the aggregate of every node (row_ptr receives nbrows int32,
  * -1 for an isolated node); which = 4: the smoother diagonal (val receives
  * nbrows*bs doubles); which = 5: the near-nullspace of the level (val
- * receives nbrows*bs*6 doubles); which = 6: the strong-connection flags of A
+ * receives nbrows*bs*nb_ns doubles); which = 6: the strong-connection flags of A
  * (row_ptr receives nnzb_A bytes); which = 7: the learned smoother blocks of
  * level 0 (val receives nbrows*9 doubles).  Synchronises the stream it was set
  * up on. */
@@ -231,7 +236,10 @@ typedef struct {
  * instance in one concatenated sliced operator, right-hand sides interleaved
  * so the SpMM reads each block once per tile of right-hand sides, and the
  * tile chosen per operator by timing the candidates (1, 2, 4).
- * A[i] (3x3 BSR) and B[i] (n_i x 6) are device arrays, read only. */
+ * A[i] (3x3 BSR) and B[i] (n_i x 6) are device arrays, read only.  FP64 and
+ * block storage only (prm->precision and prm->storage at their defaults;
+ * prm->loop_mode 1 launches one captured iteration per host step, for
+ * profilers, with the same results). */
 int amg_batch_setup(int32_t ninst, const amg_bsr *A, const double *const *B, const int32_t *nrhs,
                     const amg_params *prm, void *stream, amg_batch *out);
 
@@ -270,7 +278,9 @@ void amg_batch_free(amg_batch h);
  * estimate for SPAI0) it keeps SPAI0 and sets *fell_back to 2 (the smoothing
  * step contracts the energy norm only while lambda_max(M A) < 2, and beyond
  * that the V-cycle can stop being positive definite).  params is host memory.
- * Later amg_solve / amg_apply_vcycle calls use the blocks (FP64 V-cycle). */
+ * Later amg_solve / amg_apply_vcycle calls use the blocks, in every V-cycle
+ * precision (the FP32 and BF16 V-cycles apply an FP32 copy); block storage
+ * only (AMG_ERR_ARG for AMG_STORAGE_SCALAR). */
 int amg_set_learned_smoother(amg_handle h, const float *params, int32_t *fell_back, void *stream);
 
 /* Back to the SPAI0 smoother. */
