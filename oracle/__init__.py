@@ -42,7 +42,8 @@ class _Params(ctypes.Structure):
                 ("max_levels", ctypes.c_int), ("npre", ctypes.c_int),
                 ("npost", ctypes.c_int), ("relax", ctypes.c_double),
                 ("smooth_relax", ctypes.c_double), ("ns", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("ilu_sweeps", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("ilu_sweeps", ctypes.c_int),
+                ("aggregation", ctypes.c_int)]
 
 
 def _load():
@@ -63,6 +64,8 @@ def _load():
         "orc_graph_copy": ([P, P, P, P, P], None),
         "orc_strength": ([P, i, d], P),
         "orc_aggregate": ([P, P], i64),
+        "orc_aggregate_mis2": ([P, P], i64),
+        "orc_fmix32": ([ctypes.c_uint32], ctypes.c_uint32),
         "orc_tentative": ([i64, i, P, i64, P, i, P], P),
         "orc_jacobi_rho": ([P, P, P], None),
         "orc_spgemm": ([P, P], P),
@@ -204,6 +207,28 @@ def aggregate(A: CSR, b: int, eps: float):
     return agg, int(nagg)
 
 
+def aggregate_mis2(A: CSR, b: int, eps: float):
+    """Strength + MIS-2 aggregation (greedy distance-2 independent set in
+    descending fmix32 priority on the undirected strong graph); returns
+    (agg, nagg)."""
+    lib = _load()
+    o = _Owned(A)
+    g = lib.orc_strength(o.h, b, eps)
+    s = np.zeros(2, dtype=np.int64)
+    lib.orc_graph_shape(g, _p(s))
+    agg = np.empty(s[0], dtype=np.int32)
+    nagg = lib.orc_aggregate_mis2(g, _p(agg))
+    lib.orc_graph_free(g)
+    if nagg < 0:
+        raise RuntimeError("MIS-2 aggregation: roots are not a maximal distance-2 set")
+    return agg, int(nagg)
+
+
+def fmix32(x: int) -> int:
+    """MurmurHash3's 32-bit finaliser, the MIS-2 node priority."""
+    return int(_load().orc_fmix32(x & 0xFFFFFFFF))
+
+
 def tentative(nnodes: int, b: int, agg: np.ndarray, nagg: int, B: np.ndarray):
     """(P_tent, B_c) from the aggregates and the near-nullspace."""
     agg = np.ascontiguousarray(agg, dtype=np.int32)
@@ -305,12 +330,13 @@ class Hierarchy:
 
     def __init__(self, A: CSR, bs: int, B: np.ndarray, *, eps_strong=0.08, coarse_enough=3000,
                  max_levels=15, npre=1, npost=1, relax=1.0, smooth_relax=0.8, smoother="spai0",
-                 ilu_sweeps=2):
+                 ilu_sweeps=2, aggregation="greedy"):
         lib = _load()
         B = np.ascontiguousarray(B, dtype=np.float64)
         self.ns = B.shape[1]
         prm = _Params(eps_strong, coarse_enough, max_levels, npre, npost, relax, smooth_relax,
-                      self.ns, {"spai0": 0, "ilu0": 1}[smoother], ilu_sweeps)
+                      self.ns, {"spai0": 0, "ilu0": 1}[smoother], ilu_sweeps,
+                      {"greedy": 0, "mis2": 1}[aggregation])
         self._A = _Owned(A)
         st = ctypes.c_int(0)
         self.h = lib.orc_setup(self._A.h, bs, _p(B), ctypes.byref(prm), ctypes.byref(st))

@@ -26,7 +26,9 @@
  *               squares summed in row-major block order; eps_1 = 0.08,
  *               eps_{l+1} = eps_l / 2.  A node without strong neighbours is
  *               isolated: never aggregated, zero prolongation row.
- *   aggregation: three greedy passes in ascending node order (see aggregate()).
+ *   aggregation: three greedy passes in ascending node order (see
+ *               orc_aggregate()), or the distance-2 maximal independent set
+ *               of orc_aggregate_mis2() (the parallel variant).
  *   P_tent:     per aggregate, stacked B rows, modified Gram-Schmidt with one
  *               re-orthogonalisation pass; a column whose norm after
  *               orthogonalisation is <= 1e-10 x its norm before is dropped
@@ -322,6 +324,148 @@ int64_t orc_aggregate(const orc_graph *G, int32_t *agg)
         if (agg[I] == ISOLATED) agg[I] = -1;
     free(p1);
     return nagg;
+}
+
+/* MurmurHash3's 32-bit finaliser (Appleby, public domain): two xor-shift /
+ * odd-multiply rounds and a last xor-shift, each a bijection of the 32-bit
+ * integers, so distinct nodes get distinct priorities. */
+uint32_t orc_fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+/* The strong connections made undirected: J is a neighbour of I when either
+ * direction is strong (I != J).  Sorted, duplicate-free lists. */
+typedef struct {
+    int64_t n;
+    int64_t *ptr;
+    int32_t *adj;
+} orc_undirected;
+
+static orc_undirected undirected_strong(const orc_graph *G)
+{
+    orc_undirected U;
+    int64_t nn = G->nnodes, m = 0;
+    U.n = nn;
+    for (int64_t p = 0; p < G->nnz; ++p) m += G->strong[p] ? 2 : 0;
+    int32_t *pi = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    int32_t *pj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    int64_t k = 0;
+    for (int64_t I = 0; I < nn; ++I)
+        for (int64_t p = G->ptr[I]; p < G->ptr[I + 1]; ++p)
+            if (G->strong[p]) {
+                pi[k] = (int32_t)I; pj[k] = G->col[p]; ++k;
+                pi[k] = G->col[p]; pj[k] = (int32_t)I; ++k;
+            }
+    /* bucket by the first node, then sort and deduplicate each bucket */
+    int64_t *cnt = (int64_t *)calloc((size_t)nn + 1, sizeof(int64_t));
+    for (int64_t t = 0; t < m; ++t) cnt[pi[t] + 1]++;
+    for (int64_t I = 0; I < nn; ++I) cnt[I + 1] += cnt[I];
+    int32_t *tmp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nn > 0 ? nn : 1));
+    for (int64_t I = 0; I < nn; ++I) fill[I] = cnt[I];
+    for (int64_t t = 0; t < m; ++t) tmp[fill[pi[t]]++] = pj[t];
+    U.ptr = (int64_t *)calloc((size_t)nn + 1, sizeof(int64_t));
+    U.adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    int64_t w = 0;
+    for (int64_t I = 0; I < nn; ++I) {
+        int64_t a = cnt[I], b = cnt[I + 1];
+        qsort(tmp + a, (size_t)(b - a), sizeof(int32_t), cmp_i32);
+        for (int64_t t = a; t < b; ++t)
+            if (t == a || tmp[t] != tmp[t - 1]) U.adj[w++] = tmp[t];
+        U.ptr[I + 1] = w;
+    }
+    free(pi);
+    free(pj);
+    free(cnt);
+    free(tmp);
+    free(fill);
+    return U;
+}
+
+static const uint32_t *g_prio_sort;
+static int cmp_prio_desc(const void *a, const void *b)
+{
+    uint32_t x = g_prio_sort[*(const int32_t *)a], y = g_prio_sort[*(const int32_t *)b];
+    return (x < y) - (x > y);
+}
+
+/* Aggregation by a distance-2 maximal independent set (MIS-2), the
+ * parallel alternative to the greedy passes above; the rest of Alg. 1 is
+ * unchanged.  On the undirected strong graph:
+ *  roots:  visit the nodes that have a neighbour in descending priority
+ *          orc_fmix32(I); a node that no earlier root reaches in at most
+ *          two edges becomes a root (the greedy MIS of the squared graph);
+ *  step 1: a root and its neighbours form an aggregate (roots are at least
+ *          three edges apart, so no node neighbours two roots); aggregates
+ *          are numbered in ascending root index;
+ *  step 2: every other node with a neighbour joins the step-1 aggregate of
+ *          its lowest-index neighbour that has one (one exists: the set is
+ *          maximal, so some root is two edges away).
+ * A node without neighbours stays unaggregated (-1).  Returns the number of
+ * aggregates, or -1 if a step-1 conflict or an unplaced node shows the
+ * roots are not a maximal distance-2 independent set. */
+int64_t orc_aggregate_mis2(const orc_graph *G, int32_t *agg)
+{
+    int64_t nn = G->nnodes, nagg = 0, bad = 0;
+    orc_undirected U = undirected_strong(G);
+    uint32_t *prio = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(nn > 0 ? nn : 1));
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nn > 0 ? nn : 1));
+    uint8_t *reached = (uint8_t *)calloc((size_t)nn + 1, 1);
+    uint8_t *root = (uint8_t *)calloc((size_t)nn + 1, 1);
+    int32_t *id = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nn > 0 ? nn : 1));
+    int32_t *step1 = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nn > 0 ? nn : 1));
+    for (int64_t I = 0; I < nn; ++I) {
+        prio[I] = orc_fmix32((uint32_t)I);
+        order[I] = (int32_t)I;
+    }
+    g_prio_sort = prio;
+    qsort(order, (size_t)nn, sizeof(int32_t), cmp_prio_desc);
+    for (int64_t t = 0; t < nn; ++t) {
+        int32_t v = order[t];
+        if (U.ptr[v] == U.ptr[v + 1] || reached[v]) continue;
+        root[v] = 1;
+        reached[v] = 1;
+        for (int64_t p = U.ptr[v]; p < U.ptr[v + 1]; ++p) {
+            int32_t u = U.adj[p];
+            reached[u] = 1;
+            for (int64_t q = U.ptr[u]; q < U.ptr[u + 1]; ++q) reached[U.adj[q]] = 1;
+        }
+    }
+    for (int64_t I = 0; I < nn; ++I) id[I] = root[I] ? (int32_t)nagg++ : -1;
+    for (int64_t I = 0; I < nn; ++I) {
+        step1[I] = id[I];
+        if (root[I]) continue;
+        for (int64_t p = U.ptr[I]; p < U.ptr[I + 1]; ++p)
+            if (root[U.adj[p]]) {
+                if (step1[I] >= 0) bad = 1;
+                step1[I] = id[U.adj[p]];
+            }
+    }
+    for (int64_t I = 0; I < nn; ++I) {
+        agg[I] = step1[I];
+        if (agg[I] >= 0 || U.ptr[I] == U.ptr[I + 1]) continue;
+        for (int64_t p = U.ptr[I]; p < U.ptr[I + 1]; ++p)
+            if (step1[U.adj[p]] >= 0) {
+                agg[I] = step1[U.adj[p]];
+                break;
+            }
+        if (agg[I] < 0) bad = 1;
+    }
+    free(U.ptr);
+    free(U.adj);
+    free(prio);
+    free(order);
+    free(reached);
+    free(root);
+    free(id);
+    free(step1);
+    return bad ? -1 : nagg;
 }
 
 /* Tentative prolongation from the near-nullspace (Sec. 2; Sec. 3 notes this
@@ -643,6 +787,7 @@ typedef struct {
     int ns;              /* near-nullspace columns of B: 6 (rigid-body modes) or 3 */
     int smoother;        /* 0: damped SPAI0; 1: block ILU(0) */
     int ilu_sweeps;      /* Jacobi sweeps per triangular solve of ILU(0) (2) */
+    int aggregation;     /* 0: three greedy passes; 1: MIS-2 (orc_aggregate_mis2) */
 } orc_params;
 
 void orc_params_default(orc_params *p)
@@ -657,6 +802,7 @@ void orc_params_default(orc_params *p)
     p->ns = 6;
     p->smoother = 0;
     p->ilu_sweeps = 2;
+    p->aggregation = 0;
 }
 
 void orc_free(orc_hier *H)
@@ -917,7 +1063,13 @@ orc_hier *orc_setup(const orc_csr *A0, int bs, const double *B0, const orc_param
         C->G = orc_strength(C->A, C->b, C->eps);
         int64_t nn = n / C->b;
         C->agg = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nn > 0 ? nn : 1));
-        C->nagg = orc_aggregate(C->G, C->agg);
+        C->nagg = prm->aggregation == 1 ? orc_aggregate_mis2(C->G, C->agg)
+                                        : orc_aggregate(C->G, C->agg);
+        if (C->nagg < 0) {
+            *status = -5;
+            orc_free(H);
+            return NULL;
+        }
         if (C->nagg == 0 || (double)C->nagg >= 0.9 * (double)nn) {
             orc_graph_free(C->G);
             C->G = NULL;
