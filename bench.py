@@ -601,6 +601,35 @@ def main():
             "operator_bytes": int(sol.stats()["bytes_solve"]),
             "vcycle": "FP64; near-nullspace = 3 translations (no rotations), 3x3 blocks on every level"}
         del sol
+        # aggregation on the device (MIS-2) against the host's greedy passes:
+        # setup times side by side, then the MIS-2 hierarchy's FP64 solve
+        setups = {"greedy": [], "mis2": []}
+        for _ in range(3):
+            for agg_name, code in (("greedy", amg.AGG_GREEDY), ("mis2", amg.AGG_MIS2)):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sol = amg.AMG(rp, cl, val, B, aggregation=code)
+                torch.cuda.synchronize()
+                setups[agg_name].append(time.perf_counter() - t0)
+                if agg_name == "greedy":
+                    del sol
+        sol.solve(f, tol=tol, maxiter=5000)
+        times = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            u_p, it_p, res_p, st_p = sol.solve(f, tol=tol, maxiter=5000)
+            e1.record(s)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        forms["mis2_fp64"] = {
+            "value": float(np.mean(times)), "iterations": it_p, "rel_resid": res_p, "status": st_p,
+            "setup_s": float(np.median(setups["mis2"])),
+            "greedy_setup_s": float(np.median(setups["greedy"])), "levels": sol.nlevels,
+            "err_vs_fp64_solution": float(torch.linalg.norm(u_p - u_ref) / torch.linalg.norm(u_ref)),
+            "operator_bytes": int(sol.stats()["bytes_solve"]),
+            "vcycle": "FP64; aggregates from a distance-2 maximal independent set on the device"}
+        del sol
         for name in ("fp64", "fp32", "bf16"):
             sc, bl = forms["scalar_" + name], forms[name]
             sc["block_speedup"] = sc["value"] / bl["value"]

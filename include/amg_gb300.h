@@ -62,6 +62,25 @@ extern "C" {
 #define AMG_STORAGE_BLOCK 0       /* b x b blocks (3x3 fine, 6x6 coarse) */
 #define AMG_STORAGE_SCALAR 1      /* scalar CSR rows */
 
+/* Aggregation (the coarsening step of Alg. 1, point-wise on block rows as in
+ * Sec. 4; the paper does not specify the algorithm).  Both run on the strong
+ * connections of the level's block matrix and give every aggregated node
+ * exactly one aggregate; nodes without strong neighbours stay unaggregated.
+ *   AMG_AGG_GREEDY: three sequential passes in ascending node order on the
+ *     host (a node whose strong neighbours are all free roots an aggregate;
+ *     leftovers join the lowest-index neighbour placed in the first pass;
+ *     the rest start new aggregates).
+ *   AMG_AGG_MIS2: on the device, aggregates grown around a distance-2
+ *     maximal independent set of the strong graph made undirected: the roots
+ *     are those of a visit in descending priority fmix32(node index)
+ *     (MurmurHash3's 32-bit finaliser), found by synchronous rounds of
+ *     two-hop key maxima; a root with its neighbours forms an aggregate
+ *     (numbered by ascending root index), every other node joins the
+ *     aggregate of its lowest-index neighbour that has one.  The hierarchy
+ *     differs from the greedy one (other aggregates), not the method. */
+#define AMG_AGG_GREEDY 0
+#define AMG_AGG_MIS2 1
+
 /* Block CSR matrix, borrowed for the duration of a call.
  * row_ptr[nbrows+1] and col[nnzb] are int32 with columns strictly ascending
  * within each block row; val holds nnzb blocks of bs_r x bs_c doubles, each
@@ -91,7 +110,8 @@ typedef struct {
                               per CG step (for profilers that cannot look inside
                               conditional graphs).  Same kernels, same results. */
     int32_t storage;       /* AMG_STORAGE_* of the solve's operators (AMG_STORAGE_BLOCK) */
-    int32_t reserved[5];   /* must be zero */
+    int32_t aggregation;   /* AMG_AGG_* (AMG_AGG_GREEDY) */
+    int32_t reserved[4];   /* must be zero */
 } amg_params;
 
 typedef struct amg_handle_s *amg_handle;

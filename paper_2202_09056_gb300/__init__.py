@@ -27,6 +27,7 @@ _ERRORS = {-1: "bad argument", -2: "CUDA error", -3: "CG breakdown",
            -4: "coarsest matrix not positive definite", -5: "size limit", -6: "bad state"}
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
 STORAGE_BLOCK, STORAGE_SCALAR = 0, 1
+AGG_GREEDY, AGG_MIS2 = 0, 1
 
 
 class AmgError(RuntimeError):
@@ -47,7 +48,7 @@ class Params(ctypes.Structure):
                 ("max_levels", ctypes.c_int32), ("npre", ctypes.c_int32),
                 ("npost", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("loop_mode", ctypes.c_int32), ("storage", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("aggregation", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class LevelDesc(ctypes.Structure):

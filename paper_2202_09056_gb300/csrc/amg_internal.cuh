@@ -190,6 +190,10 @@ struct LevelBuild {
 int exclusive_scan_i32(const int *in, int *out, int n, int *total_host, DevArena &tmp,
                        cudaStream_t s);
 int compute_strength(const BsrD &A, double eps, uint8_t *strong, cudaStream_t s);
+// Parallel MIS-2 aggregation on the device (mis2.cu): agg[nbr] device, the
+// aggregate count (and, if asked, the number of rounds) to the host.
+int aggregate_mis2(const BsrD &A, const uint8_t *strong, int *agg, int *nagg_host, int *rounds_host,
+                   DevArena &tmp, cudaStream_t s);
 int aggregate_host(int nn, const int *row_ptr, const int *col, const uint8_t *strong,
                    int *agg, int *nagg);   // host arrays
 int build_transfer(const BsrD &A, const double *B, int ns, const uint8_t *strong,

@@ -749,16 +749,28 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         if (n <= prm.coarse_enough || (int)h->lv.size() >= prm.max_levels) break;
         AMG_TRY(h->mem.alloc_n(&C.strong, (size_t)std::max<int64_t>(C.A.nnzb, 1)));
         AMG_TRY(compute_strength(C.A, C.eps, C.strong, s));
-        std::vector<int> rp(nn + 1), cl(std::max<int64_t>(C.A.nnzb, 1)), agg(std::max(nn, 1));
-        std::vector<uint8_t> sf(std::max<int64_t>(C.A.nnzb, 1));
-        AMG_TRY_CUDA(cudaMemcpyAsync(rp.data(), C.A.row_ptr, sizeof(int) * (nn + 1),
-                                     cudaMemcpyDeviceToHost, s));
-        AMG_TRY_CUDA(cudaMemcpyAsync(cl.data(), C.A.col, sizeof(int) * C.A.nnzb,
-                                     cudaMemcpyDeviceToHost, s));
-        AMG_TRY_CUDA(cudaMemcpyAsync(sf.data(), C.strong, C.A.nnzb, cudaMemcpyDeviceToHost, s));
-        AMG_TRY_CUDA(cudaStreamSynchronize(s));
+        std::vector<int> agg(std::max(nn, 1));
         int nagg = 0;
-        AMG_TRY(aggregate_host(nn, rp.data(), cl.data(), sf.data(), agg.data(), &nagg));
+        if (prm.aggregation == AMG_AGG_MIS2) {
+            // parallel aggregation on the device; only the map comes back
+            int *dagg = nullptr;
+            AMG_TRY(tmp.alloc_n(&dagg, (size_t)nn));
+            AMG_TRY(aggregate_mis2(C.A, C.strong, dagg, &nagg, nullptr, tmp, s));
+            AMG_TRY_CUDA(cudaMemcpyAsync(agg.data(), dagg, sizeof(int) * nn,
+                                         cudaMemcpyDeviceToHost, s));
+            AMG_TRY_CUDA(cudaStreamSynchronize(s));
+            tmp.release(dagg);
+        } else {
+            std::vector<int> rp(nn + 1), cl(std::max<int64_t>(C.A.nnzb, 1));
+            std::vector<uint8_t> sf(std::max<int64_t>(C.A.nnzb, 1));
+            AMG_TRY_CUDA(cudaMemcpyAsync(rp.data(), C.A.row_ptr, sizeof(int) * (nn + 1),
+                                         cudaMemcpyDeviceToHost, s));
+            AMG_TRY_CUDA(cudaMemcpyAsync(cl.data(), C.A.col, sizeof(int) * C.A.nnzb,
+                                         cudaMemcpyDeviceToHost, s));
+            AMG_TRY_CUDA(cudaMemcpyAsync(sf.data(), C.strong, C.A.nnzb, cudaMemcpyDeviceToHost, s));
+            AMG_TRY_CUDA(cudaStreamSynchronize(s));
+            AMG_TRY(aggregate_host(nn, rp.data(), cl.data(), sf.data(), agg.data(), &nagg));
+        }
         if (nagg == 0 || (double)nagg >= 0.9 * (double)nn) break;
         LevelBuild lb;
         AMG_TRY(build_transfer(C.A, C.B, h->ns, C.strong, agg.data(), nagg, prm.relax, h->mem, tmp, s,
@@ -900,7 +912,8 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
     if (p.npre < 0 || p.npost < 0 || p.max_levels < 1 || p.coarse_enough < 0 ||
         !(p.eps_strong >= 0.0) || p.precision < AMG_PREC_FP64 || p.precision > AMG_PREC_BF16 ||
         p.loop_mode < 0 || p.loop_mode > 1 || p.storage < AMG_STORAGE_BLOCK ||
-        p.storage > AMG_STORAGE_SCALAR) {
+        p.storage > AMG_STORAGE_SCALAR || p.aggregation < AMG_AGG_GREEDY ||
+        p.aggregation > AMG_AGG_MIS2) {
         set_error("bad parameters");
         return AMG_ERR_ARG;
     }

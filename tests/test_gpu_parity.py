@@ -73,12 +73,14 @@ def test_spmv_empty_matrix():
     assert y.numel() == 0
 
 
-def _compare_hierarchy(p, coarse_enough, tol_val=1e-12, Bns=None):
+def _compare_hierarchy(p, coarse_enough, tol_val=1e-12, Bns=None, aggregation="greedy", **kw):
     Bns = p.B if Bns is None else Bns
     ns = Bns.shape[1]
-    H = o.Hierarchy(o.from_problem(p), 3, Bns, coarse_enough=coarse_enough)
+    H = o.Hierarchy(o.from_problem(p), 3, Bns, coarse_enough=coarse_enough,
+                    aggregation=aggregation, **kw)
     rp, cl, val, _ = _dev(p)
-    G = amg.AMG(rp, cl, val, torch.from_numpy(Bns).cuda(), coarse_enough=coarse_enough)
+    G = amg.AMG(rp, cl, val, torch.from_numpy(Bns).cuda(), coarse_enough=coarse_enough,
+                aggregation={"greedy": amg.AGG_GREEDY, "mis2": amg.AGG_MIS2}[aggregation], **kw)
     assert G.nlevels == H.nlevels
     for l in range(H.nlevels):
         ol, gl = H.level(l), G.export(l)
@@ -215,6 +217,68 @@ def test_solve_is_bitwise_reproducible():
     u1, it1, r1, _ = G.solve(fb)
     u2, it2, r2, _ = G.solve(fb)
     assert it1 == it2 and r1 == r2 and torch.equal(u1, u2)
+
+
+# ------------------------------------------------ MIS-2 aggregation on the device
+@pytest.mark.parametrize("shape,kw,ce", [
+    ((10, 10, 10), {"body": (0, 0, -1)}, 3000),
+    ((7, 5, 9), {"traction": (0, 0, -1), "inclusion_frac": 0.2}, 200),
+    ((12, 12, 12), {"traction": (0, 0, -1), "inclusion_frac": 0.2}, 300),
+    ((21, 9, 14), {"traction": (0, 0, -1), "inclusion_frac": 0.2}, 100),
+])
+def test_mis2_setup_matches_oracle(shape, kw, ce):
+    """Device MIS-2 aggregation: aggregates bit-exact with the oracle's
+    sequential visit on every level (fine 3x3 graphs and coarse 6x6 ones,
+    several CTAs of rows and ragged tails), then the whole hierarchy."""
+    p = q.make_problem(shape, **kw)
+    H, G = _compare_hierarchy(p, ce, aggregation="mis2")
+    assert G.nlevels >= 2
+
+
+@pytest.mark.parametrize("eps,levels", [(0.0, None), (10.0, 1)])
+def test_mis2_degenerate_strength(eps, levels):
+    """Every block strong (eps = 0) and no block strong (every node isolated:
+    no aggregate, so the hierarchy keeps one level)."""
+    p = q.make_problem((5, 4, 6), traction=(0, 0, -1), inclusion_frac=0.2)
+    H, G = _compare_hierarchy(p, 40, aggregation="mis2", eps_strong=eps)
+    if levels is not None:
+        assert G.nlevels == levels
+
+
+@pytest.mark.parametrize("shape,kw,ce", [
+    ((10, 10, 10), {"body": (0, 0, -1)}, 3000),
+    ((16, 16, 16), {"traction": (0, 0, -1), "inclusion_frac": 0.2}, 3000),
+    ((11, 6, 8), {"traction": (0, 0, -1), "inclusion_frac": 0.2}, 150),
+])
+def test_mis2_pcg_matches_oracle(shape, kw, ce):
+    p = q.make_problem(shape, **kw)
+    H = o.Hierarchy(o.from_problem(p), 3, p.B, coarse_enough=ce, aggregation="mis2")
+    uo, ito, _ = H.solve(p.f, tol=1e-8, maxiter=1000)
+    G = amg.AMG(*_dev(p), coarse_enough=ce, aggregation=amg.AGG_MIS2)
+    u, it, res, st = G.solve(torch.from_numpy(p.f).cuda(), tol=1e-8, maxiter=1000)
+    assert st == amg.AMG_OK and res <= 1e-8
+    assert abs(it - ito) <= 1, (it, ito)
+    assert np.linalg.norm(u.cpu().numpy() - uo) <= 1e-7 * np.linalg.norm(uo)
+
+
+@pytest.mark.slow
+def test_mis2_full_size_inclusions_80():
+    """80^3 elements: the fine-level aggregates of the device MIS-2 equal the
+    oracle's (its strength and sequential visit on the scalar matrix), and
+    the MIS-2 hierarchy solves to a host-checked 1e-8."""
+    p = q.inclusions(80)
+    rp, cl, val, B = _dev(p)
+    G = amg.AMG(rp, cl, val, B, aggregation=amg.AGG_MIS2)
+    agg = np.empty(p.nnodes, np.int32)
+    amg._check(G._lib.amg_level_export(G._h, 0, 3, agg.ctypes.data, None, None))
+    ago, nago = o.aggregate_mis2(o.from_problem(p), 3, 0.08)
+    assert np.array_equal(agg, ago) and G.level_info(0)["nagg"] == nago
+    u, it, res, st = G.solve(torch.from_numpy(p.f).cuda(), tol=1e-8, maxiter=2000)
+    assert st == amg.AMG_OK
+    import scipy.sparse as sp
+    A = sp.bsr_matrix((p.val, p.col, p.row_ptr), shape=(p.ndof, p.ndof))
+    un = u.cpu().numpy()
+    assert np.linalg.norm(p.f - A @ un) / np.linalg.norm(p.f) <= 1.0001e-8
 
 
 @pytest.mark.slow
