@@ -296,6 +296,64 @@ def learned_fp32_form(amg, torch, args_dev, w, f, tol, u_ref, t_fp64, fp32_form,
             "vcycle": "FP32 matrices and vectors; level 0 smoothed with the learned blocks in FP32"}
 
 
+def _timed_solves(torch, sol, f, tol, steps, maxiter, stream):
+    """(mean CUDA-event time, iterations, residual, status, u) of `steps`
+    solves after one untimed solve (graph capture)."""
+    sol.solve(f, tol=tol, maxiter=maxiter)
+    times = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u, it, res, st = sol.solve(f, tol=tol, maxiter=maxiter)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return float(np.mean(times)), it, res, st, u
+
+
+def ilu0_form(amg, torch, dev_args, f, tol, u_ref, fp64, p, stream, steps, sweeps=3):
+    """Block ILU(0) smoothing (the relaxation of Sec. 4's experiments), FP64,
+    `sweeps` Jacobi sweeps per triangle: on the workload, and on the same
+    cube and load without inclusions against SPAI0 there."""
+    import q1elasticity as q
+    rp, cl, val, B = dev_args
+    out = {"sweeps_per_triangle": sweeps,
+           "vcycle": "FP64; block ILU(0) on every smoothing level, Jacobi-swept triangles"}
+    t0 = time.perf_counter()
+    try:
+        sol = amg.AMG(rp, cl, val, B, smoother=amg.SMOOTH_ILU0, ilu_sweeps=sweeps)
+        torch.cuda.synchronize()
+        out["setup_s"] = time.perf_counter() - t0
+        t, it, res, st, u = _timed_solves(torch, sol, f, tol, steps, 5000, stream)
+        out.update({"value": t, "iterations": it, "rel_resid": res, "status": st,
+                    "err_vs_fp64_solution": float(torch.linalg.norm(u - u_ref) /
+                                                  torch.linalg.norm(u_ref))})
+        del sol
+    except amg.AmgError as e:
+        out.update({"value": None, "status": e.status, "error": str(e)})
+    # the same cube and traction without inclusions (E = 1 everywhere)
+    n = round(len(p.row_ptr) ** (1.0 / 3.0)) - 1
+    ph = q.make_problem(n, traction=(0.0, 0.0, -1.0))
+    d = val.device
+    hargs = (torch.from_numpy(ph.row_ptr).to(d), torch.from_numpy(ph.col).to(d),
+             torch.from_numpy(ph.val).to(d), torch.from_numpy(ph.B).to(d))
+    fh = torch.from_numpy(ph.f).to(d)
+    homog = {"workload": f"q1-hex-{n}^3-homogeneous", "dofs": ph.ndof}
+    for name, kw in (("spai0", {}), ("ilu0", {"smoother": amg.SMOOTH_ILU0, "ilu_sweeps": sweeps})):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sol = amg.AMG(*hargs, **kw)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        t, it, res, st, _ = _timed_solves(torch, sol, fh, tol, steps, 5000, stream)
+        homog[name] = {"value": t, "iterations": it, "rel_resid": res, "status": st,
+                       "setup_s": setup}
+        del sol
+    homog["ilu0_speedup"] = homog["spai0"]["value"] / homog["ilu0"]["value"]
+    out["homogeneous"] = homog
+    return out
+
+
 def reduce_max(dist, values, device):
     """Element-wise maximum over ranks (the slowest rank sets the time);
     the values themselves when there is one rank."""
@@ -630,6 +688,8 @@ def main():
             "operator_bytes": int(sol.stats()["bytes_solve"]),
             "vcycle": "FP64; aggregates from a distance-2 maximal independent set on the device"}
         del sol
+        forms["ilu0_fp64"] = ilu0_form(amg, torch, (rp, cl, val, B), f, tol, u_ref,
+                                       forms["fp64"], p, s, args.steps)
         for name in ("fp64", "fp32", "bf16"):
             sc, bl = forms["scalar_" + name], forms[name]
             sc["block_speedup"] = sc["value"] / bl["value"]

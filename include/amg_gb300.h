@@ -81,6 +81,19 @@ extern "C" {
 #define AMG_AGG_GREEDY 0
 #define AMG_AGG_MIS2 1
 
+/* Level smoother.  AMG_SMOOTH_SPAI0: damped SPAI0 diagonal (the default).
+ * AMG_SMOOTH_ILU0: block ILU(0), the relaxation of the paper's experiments
+ * (Sec. 4), factored on each level's own block pattern (b x b blocks,
+ * explicit zeros kept: L_IK = A_IK U_KK^-1, A_IJ -= L_IK U_KJ for the blocks
+ * J > K that row K holds) and applied with `ilu_sweeps` Jacobi sweeps per
+ * triangular factor (y <- r - L_s y from y = r; x <- U_D^-1 (y - U_s x)
+ * from x = U_D^-1 y), before and after the coarse correction.  FP64 V-cycle
+ * and block storage only.  The sweeps make the preconditioner slightly
+ * non-symmetric; on matrices where ILU(0) itself is indefinite (stiff
+ * inclusions) CG can break down (AMG_ERR_BREAKDOWN). */
+#define AMG_SMOOTH_SPAI0 0
+#define AMG_SMOOTH_ILU0 1
+
 /* Block CSR matrix, borrowed for the duration of a call.
  * row_ptr[nbrows+1] and col[nnzb] are int32 with columns strictly ascending
  * within each block row; val holds nnzb blocks of bs_r x bs_c doubles, each
@@ -111,7 +124,9 @@ typedef struct {
                               conditional graphs).  Same kernels, same results. */
     int32_t storage;       /* AMG_STORAGE_* of the solve's operators (AMG_STORAGE_BLOCK) */
     int32_t aggregation;   /* AMG_AGG_* (AMG_AGG_GREEDY) */
-    int32_t reserved[4];   /* must be zero */
+    int32_t smoother;      /* AMG_SMOOTH_* (AMG_SMOOTH_SPAI0) */
+    int32_t ilu_sweeps;    /* Jacobi sweeps per triangle of AMG_SMOOTH_ILU0, 0..64 (2) */
+    int32_t reserved[2];   /* must be zero */
 } amg_params;
 
 typedef struct amg_handle_s *amg_handle;
@@ -192,8 +207,11 @@ int amg_level_info(amg_handle h, int32_t level, amg_level_desc *out);
  * nbrows*bs doubles); which = 5: the near-nullspace of the level (val
  * receives nbrows*bs*nb_ns doubles); which = 6: the strong-connection flags of A
  * (row_ptr receives nnzb_A bytes); which = 7: the learned smoother blocks of
- * level 0 (val receives nbrows*9 doubles).  Synchronises the stream it was set
- * up on. */
+ * level 0 (val receives nbrows*9 doubles); with AMG_SMOOTH_ILU0, which = 8:
+ * the block ILU(0) factor on A's block pattern (val receives nnzb_A*bs*bs
+ * doubles: L below the diagonal, U on and above it) and which = 9: the
+ * inverses of U's diagonal blocks (val receives nbrows*bs*bs doubles).
+ * Synchronises the stream it was set up on. */
 int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_ptr,
                      int32_t *col, double *val);
 

@@ -28,6 +28,7 @@ _ERRORS = {-1: "bad argument", -2: "CUDA error", -3: "CG breakdown",
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
 STORAGE_BLOCK, STORAGE_SCALAR = 0, 1
 AGG_GREEDY, AGG_MIS2 = 0, 1
+SMOOTH_SPAI0, SMOOTH_ILU0 = 0, 1
 
 
 class AmgError(RuntimeError):
@@ -48,7 +49,8 @@ class Params(ctypes.Structure):
                 ("max_levels", ctypes.c_int32), ("npre", ctypes.c_int32),
                 ("npost", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("loop_mode", ctypes.c_int32), ("storage", ctypes.c_int32),
-                ("aggregation", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("aggregation", ctypes.c_int32), ("smoother", ctypes.c_int32),
+                ("ilu_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class LevelDesc(ctypes.Structure):
@@ -304,6 +306,18 @@ class AMG:
     @property
     def nlevels(self) -> int:
         return self.stats()["nlevels"]
+
+    def ilu_factor(self, l: int):
+        """Host copies of level l's block ILU(0): (factor values on A's block
+        pattern [nnzb, b, b], L below and U on/above the diagonal; inverses of
+        U's diagonal blocks [nbrows, b, b])."""
+        info = self.level_info(l)
+        nbr, bs, nnz = info["nbrows"], info["bs"], info["nnzb_A"]
+        F = np.empty((max(nnz, 1), bs, bs))
+        D = np.empty((max(nbr, 1), bs, bs))
+        _check(self._lib.amg_level_export(self._h, l, 8, None, None, F.ctypes.data))
+        _check(self._lib.amg_level_export(self._h, l, 9, None, None, D.ctypes.data))
+        return F[:nnz], D[:nbr]
 
     def export(self, l: int) -> dict:
         """Host copies of level l: A, P, R (BSR), aggregates, smoother, B, strength flags."""

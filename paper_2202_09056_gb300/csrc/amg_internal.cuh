@@ -207,6 +207,21 @@ int spai0_diag(const BsrD &A, double scale, double *M, cudaStream_t s);
 int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
                    double **Ainv_out);
 
+// ---------------------------------------------------------------- block ILU(0) (ilu.cu)
+struct Ilu {
+    int nbr = 0, b = 0, depth = 0;  // depth = dependency levels of the factorisation
+    double *F = nullptr;            // factor on A's block pattern: L below, U on/above the diagonal
+    double *Dinv = nullptr;         // [nbr][b][b] inverses of U's diagonal blocks
+    Sell<double> sL, sU;            // strict lower / strict upper parts, sliced
+    bool has_L = false, has_U = false;
+    double *y0 = nullptr, *y1 = nullptr;  // sweep vectors
+};
+int ilu0_factor(const BsrD &A, int max_lanes, DevArena &keep, DevArena &tmp, cudaStream_t s,
+                Ilu *out);
+// x = ILU^-1 r with `sweeps` Jacobi sweeps per triangle (x must not alias r)
+int ilu0_apply(const Ilu &F, int sweeps, const double *r, double *x, const Geom &g, cudaStream_t s);
+int launch_vec_add(const double *a, const double *b, double *y, int64_t n, cudaStream_t s);
+
 // ---------------------------------------------------------------- hierarchy (solver.cu)
 struct Level {
     BsrD A, P, R;
@@ -226,6 +241,7 @@ struct Level {
     double *f = nullptr, *u = nullptr, *e = nullptr, *z = nullptr, *t = nullptr;
     double *Mb = nullptr;     // learned 3x3 smoother blocks (level 0), replaces M when set
     float *Mbf = nullptr;     // FP32 copy of Mb for the FP32 / BF16 V-cycles
+    Ilu ilu;                  // block ILU(0) smoother (when selected), replaces M
     int n() const { return A.nbr * A.br; }
 };
 
@@ -252,6 +268,7 @@ struct amg_handle_s {
     long long body_kernels = 0;   // kernels in one iteration of the graph body
     double setup_seconds = 0.0;
     int learned = 0;              // level 0 smooths with the learned blocks
+    int ilu = 0;                  // every smoothing level uses its block ILU(0)
     double learned_lambda = 0.0;  // estimated lambda_max(M A) of the learned smoother
     double spai0_lambda = 0.0;    // the same estimate for SPAI0 (0 until first needed)
 };

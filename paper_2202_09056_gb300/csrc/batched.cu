@@ -1130,8 +1130,9 @@ int amg_batch_setup(int32_t ninst, const amg_bsr *A, const double *const *B, con
     amg_params p;
     amg_params_default(&p);
     if (prm) p = *prm;
-    if (p.precision != AMG_PREC_FP64 || p.npre != 1 || p.npost != 1) {
-        set_error("the batched solve runs FP64 V(1,1) cycles");
+    if (p.precision != AMG_PREC_FP64 || p.npre != 1 || p.npost != 1 ||
+        p.smoother != AMG_SMOOTH_SPAI0) {
+        set_error("the batched solve runs FP64 V(1,1) cycles with the SPAI0 smoother");
         return AMG_ERR_ARG;
     }
     auto t0 = std::chrono::steady_clock::now();

@@ -790,6 +790,10 @@ int amg_set_learned_smoother(amg_handle h, const float *params, int32_t *fell_ba
         set_error("the learned smoother needs a multi-level hierarchy in block storage");
         return AMG_ERR_ARG;
     }
+    if (h->ilu) {
+        set_error("the hierarchy smooths with ILU(0); the learned smoother replaces SPAI0 only");
+        return AMG_ERR_STATE;
+    }
     DevArena tmp;
     tmp.stream = s;
     Net net;

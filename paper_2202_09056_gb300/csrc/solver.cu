@@ -291,6 +291,29 @@ template <class TV>
 static int launch_vec_dot(amg_handle h, const TV *x, const TV *y, int64_t n, double *part,
                           cudaStream_t s);
 
+// Block ILU(0) smoothing step x = ILU_l^-1 r and y = a + b (FP64 V-cycle only).
+template <class TV> static int ilu_smooth(amg_handle h, int l, const TV *r, TV *x, cudaStream_t s);
+template <> int ilu_smooth<double>(amg_handle h, int l, const double *r, double *x, cudaStream_t s)
+{
+    return ilu0_apply(h->lv[l].ilu, h->prm.ilu_sweeps, r, x, h->geom, s);
+}
+template <> int ilu_smooth<float>(amg_handle, int, const float *, float *, cudaStream_t)
+{
+    set_error("the ILU(0) smoother runs in the FP64 V-cycle only");
+    return AMG_ERR_STATE;
+}
+template <class TV> static int vec_add(const TV *a, const TV *b, TV *y, int64_t n, cudaStream_t s);
+template <> int vec_add<double>(const double *a, const double *b, double *y, int64_t n,
+                                cudaStream_t s)
+{
+    return launch_vec_add(a, b, y, n, s);
+}
+template <> int vec_add<float>(const float *, const float *, float *, int64_t, cudaStream_t)
+{
+    set_error("the ILU(0) smoother runs in the FP64 V-cycle only");
+    return AMG_ERR_STATE;
+}
+
 // One V-cycle (Alg. 2) from a zero initial guess: z0 = V(f0), matrices stored
 // in VT and vectors in TV.  Level 0's u must already hold the first
 // pre-smoothing sweep M_0 f0 (or zero without pre-smoothing).  With
@@ -310,12 +333,26 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
     std::vector<VLevel<VT, TV>> V;
     for (auto &lev : h->lv) V.push_back(view<VT, TV>(lev));
     std::vector<TV *> ucur(L + 1, nullptr), spare(L + 1, nullptr);
+    const bool ilu = h->ilu != 0;  // FP64 V-cycle only (checked at setup)
+    const bool ilu_pre = ilu && npre > 0;
     for (int l = 0; l < L; ++l) {
         VLevel<VT, TV> &C = V[l];
         VLevel<VT, TV> &N = V[l + 1];
         const TV *f = (l == 0) ? f0 : C.f;
         TV *u = C.u, *t = C.t;
-        for (int sweep = 1; sweep < npre; ++sweep) {  // further pre-smoothing sweeps
+        if (ilu_pre) {  // first pre-smoothing sweep from zero: u = ILU^-1 f
+            AMG_TRY(ilu_smooth<TV>(h, l, f, u, s));
+            for (int sweep = 1; sweep < npre; ++sweep) {  // u += ILU^-1 (f - A u)
+                SellArgs<TV> a{};
+                a.x = u;
+                a.f = f;
+                a.y = C.e;
+                AMG_TRY((launch_sell<VT, TV>(*C.A, SPMV_RESID, DOT_NONE, a, g, s)));
+                AMG_TRY(ilu_smooth<TV>(h, l, C.e, t, s));
+                AMG_TRY(vec_add<TV>(u, t, u, C.n, s));
+            }
+        }
+        for (int sweep = 1; sweep < npre && !ilu; ++sweep) {  // further pre-smoothing sweeps
             const bool blocks = l == 0 && h->learned;
             SellArgs<TV> a{};
             a.x = u;
@@ -341,7 +378,8 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
             a.x = C.e;
             a.y = N.f;
             const bool next_smooths = (l + 1 < L);
-            a.y2 = next_smooths ? N.u : nullptr;
+            // with ILU(0) the next level pre-smooths itself (npre = 0: zero u)
+            a.y2 = (next_smooths && !ilu_pre) ? N.u : nullptr;
             a.M = (next_smooths && npre > 0) ? N.M : nullptr;
             AMG_TRY((launch_sell<VT, TV>(*C.R, SPMV_RESTRICT, DOT_NONE, a, g, s)));
         }
@@ -366,9 +404,22 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
             a.y = u;
             AMG_TRY((launch_sell<VT, TV>(*C.P, SPMV_AXPY, DOT_NONE, a, g, s)));
         }
+        if (ilu) {  // u += ILU^-1 (f - A u), the last sweep written to z_l
+            for (int sweep = 0; sweep < npost; ++sweep) {
+                SellArgs<TV> a{};
+                a.x = u;
+                a.f = f;
+                a.y = C.e;
+                AMG_TRY((launch_sell<VT, TV>(*C.A, SPMV_RESID, DOT_NONE, a, g, s)));
+                AMG_TRY(ilu_smooth<TV>(h, l, C.e, t, s));
+                AMG_TRY(vec_add<TV>(u, t, sweep == npost - 1 ? zl : u, C.n, s));
+            }
+            if (npost > 0 && l == 0 && rz_partials)
+                AMG_TRY(launch_vec_dot<TV>(h, f0, z0, C.n, rz_partials, s));
+        }
         const TV *w = u;
         const bool blocks = l == 0 && h->learned;
-        for (int sweep = 0; sweep < npost; ++sweep) {  // u += M (f - A u)
+        for (int sweep = 0; sweep < npost && !ilu; ++sweep) {  // u += M (f - A u)
             const bool last = (sweep == npost - 1);
             TV *out = last ? zl : t;
             SellArgs<TV> a{};
@@ -397,7 +448,7 @@ static int rz_parts(amg_handle h)
 {
     const Level &L0 = h->lv[0];
     if (h->lv.size() == 1) return vgrid(h, h->nc);
-    if (h->prm.npost == 0) return vgrid(h, L0.n());
+    if (h->prm.npost == 0 || h->ilu) return vgrid(h, L0.n());
     return sell_grid(L0.sA.nslices, L0.sA.br, L0.sA.bc, h->geom);
 }
 
@@ -435,8 +486,10 @@ static int record_cg_iteration_t(amg_handle h, cudaStream_t s, cudaGraphConditio
     }
     cg_alpha_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, grid); ::amg::count_launch(1);
     const bool blocks = h->learned && multi && npre > 0;
+    // the next pre-smoothing M r fused into the update (ILU(0) smooths inside the V-cycle)
+    const bool fuse_pre = multi && !blocks && !(h->ilu && npre > 0);
     cg_update_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(h->uu, h->r, h->p, h->q, V0.M,
-                                                     (multi && !blocks) ? V0.u : nullptr, rv, h->st,
+                                                     fuse_pre ? V0.u : nullptr, rv, h->st,
                                                      n, npre > 0, h->partials); ::amg::count_launch(1);
     cg_resnorm_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, vgrid(h, n)); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
@@ -454,7 +507,7 @@ static int record_cg_iteration_t(amg_handle h, cudaStream_t s, cudaGraphConditio
     }
     cg_decide_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, grid, cond, use_cond); ::amg::count_launch(1);
     cg_replace_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(h->r, h->rt, V0.M,
-                                                      (multi && !blocks) ? V0.u : nullptr, rv, h->st,
+                                                      fuse_pre ? V0.u : nullptr, rv, h->st,
                                                       n, npre > 0); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     if (blocks)  // next pre-smoothing with the learned blocks: u0 = Mb r
@@ -578,6 +631,7 @@ int amg_params_default(amg_params *prm)
     prm->npre = 1;
     prm->npost = 1;
     prm->precision = AMG_PREC_FP64;
+    prm->ilu_sweeps = 2;
     return AMG_OK;
 }
 
@@ -793,6 +847,11 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
     Cc.coarsest = true;
     AMG_TRY(coarse_inverse(Cc.A, h->mem, tmp, s, &h->Ainv));
     h->nc = Cc.n();
+    if (prm.smoother == AMG_SMOOTH_ILU0) {  // block ILU(0) of every smoothing level
+        for (size_t l = 0; l + 1 < h->lv.size(); ++l)
+            AMG_TRY(ilu0_factor(h->lv[l].A, h->max_lanes, h->mem, tmp, s, &h->lv[l].ilu));
+        h->ilu = 1;
+    }
     // V-cycle operators in the sliced layout, in the V-cycle's precision; the
     // fine A is also kept in FP64 for the CG products.
     const int prec = prm.precision;
@@ -913,8 +972,14 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
         !(p.eps_strong >= 0.0) || p.precision < AMG_PREC_FP64 || p.precision > AMG_PREC_BF16 ||
         p.loop_mode < 0 || p.loop_mode > 1 || p.storage < AMG_STORAGE_BLOCK ||
         p.storage > AMG_STORAGE_SCALAR || p.aggregation < AMG_AGG_GREEDY ||
-        p.aggregation > AMG_AGG_MIS2) {
+        p.aggregation > AMG_AGG_MIS2 || p.smoother < AMG_SMOOTH_SPAI0 ||
+        p.smoother > AMG_SMOOTH_ILU0 || p.ilu_sweeps < 0 || p.ilu_sweeps > 64) {
         set_error("bad parameters");
+        return AMG_ERR_ARG;
+    }
+    if (p.smoother == AMG_SMOOTH_ILU0 &&
+        (p.precision != AMG_PREC_FP64 || p.storage != AMG_STORAGE_BLOCK)) {
+        set_error("the ILU(0) smoother runs in the FP64 V-cycle with block storage");
         return AMG_ERR_ARG;
     }
     auto t0 = std::chrono::steady_clock::now();
@@ -953,7 +1018,7 @@ int amg_apply_vcycle(amg_handle h, const double *r, double *z, void *stream)
     if (h->prm.precision == AMG_PREC_FP64) {
         if (multi && h->learned && !zero) {
             AMG_TRY(launch_block_apply(L0.Mb, r, L0.u, L0.A.nbr, h->geom, s));
-        } else if (multi) {
+        } else if (multi && !(h->ilu && !zero)) {  // ILU(0) pre-smooths inside the V-cycle
             scale_kernel<double><<<vgrid(h, n), 256, 0, s>>>(L0.M, r, L0.u, nullptr, n, zero);
             count_launch(1);
             AMG_TRY_CUDA(cudaGetLastError());
@@ -1010,7 +1075,7 @@ int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxi
     if (h->prm.precision == AMG_PREC_FP64) {
         if (multi && h->learned && h->prm.npre > 0) {
             AMG_TRY(launch_block_apply(L0.Mb, h->r, L0.u, L0.A.nbr, h->geom, s));
-        } else if (multi) {
+        } else if (multi && !(h->ilu && h->prm.npre > 0)) {  // ILU(0) pre-smooths in the V-cycle
             scale_kernel<double><<<vgrid(h, n), 256, 0, s>>>(L0.M, h->r, L0.u, nullptr, n,
                                                              h->prm.npre == 0);
             count_launch(1);
@@ -1178,6 +1243,16 @@ int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_pt
     case 7:
         if (!L.Mb || !h->learned) { set_error("no learned smoother blocks on this level"); return AMG_ERR_STATE; }
         if (val) AMG_TRY_CUDA(cudaMemcpyAsync(val, L.Mb, sizeof(double) * L.A.nbr * 9, cudaMemcpyDeviceToHost, s));
+        break;
+    case 8:
+    case 9:
+        if (!L.ilu.F) { set_error("no ILU(0) factor on this level"); return AMG_ERR_STATE; }
+        if (val && which == 8)
+            AMG_TRY_CUDA(cudaMemcpyAsync(val, L.ilu.F, sizeof(double) * L.A.nnzb * L.A.br * L.A.br,
+                                         cudaMemcpyDeviceToHost, s));
+        if (val && which == 9)
+            AMG_TRY_CUDA(cudaMemcpyAsync(val, L.ilu.Dinv, sizeof(double) * L.A.nbr * L.A.br * L.A.br,
+                                         cudaMemcpyDeviceToHost, s));
         break;
     case 6:
         if (!L.strong) { set_error("no strength flags on this level"); return AMG_ERR_STATE; }
