@@ -130,15 +130,17 @@ __global__ void diag_norm_kernel(const int *__restrict__ rp, const int *__restri
     dn[I] = v;
 }
 
-// J != I is strong iff ||A_IJ||^2 > (eps^2 ||A_II||) ||A_JJ||.
+// J != I is strong iff ||A_IJ||^2 > (eps^2 ||A_II||) ||A_JJ||.  One warp per
+// block row, the lanes over its blocks (each test is independent).
 __global__ void strength_kernel(const int *__restrict__ rp, const int *__restrict__ col,
                                 const double *__restrict__ val, int nbr, int b, double e2,
                                 const double *__restrict__ dn, uint8_t *__restrict__ strong)
 {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int I = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (I >= nbr) return;
     const double dI = dn[I];
-    for (int p = rp[I]; p < rp[I + 1]; ++p) {
+    for (int p = rp[I] + lane; p < rp[I + 1]; p += 32) {
         const int J = col[p];
         uint8_t st = 0;
         if (J != I) {
@@ -158,8 +160,9 @@ int compute_strength(const BsrD &A, double eps, uint8_t *strong, cudaStream_t s)
     AMG_TRY_CUDA(cudaMallocAsync((void **)&dn, sizeof(double) * A.nbr, s));
     diag_norm_kernel<<<nblk(A.nbr), T1D, 0, s>>>(A.row_ptr, A.col, A.val, A.nbr, A.br, dn); ::amg::count_launch(1);
     const double e2 = eps * eps;
-    strength_kernel<<<nblk(A.nbr), T1D, 0, s>>>(A.row_ptr, A.col, A.val, A.nbr, A.br, e2, dn,
-                                                strong); ::amg::count_launch(1);
+    strength_kernel<<<nblk((int64_t)A.nbr * 32), T1D, 0, s>>>(A.row_ptr, A.col, A.val, A.nbr, A.br,
+                                                              e2, dn, strong);
+    ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     AMG_TRY_CUDA(cudaFreeAsync(dn, s));
     return AMG_OK;
@@ -255,22 +258,22 @@ __global__ void jacobi_rho_kernel(const int *__restrict__ rp, const int *__restr
                                   const double *__restrict__ val, int nbr, int b,
                                   double *__restrict__ d, unsigned long long *__restrict__ rho_bits)
 {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nbr) return;
+    // one thread per scalar row (b per block row)
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)nbr * b) return;
+    const int I = (int)(i / b), r = (int)(i % b);
     const int bb = b * b;
-    for (int r = 0; r < b; ++r) {
-        double dia = 0.0, s = 0.0;
-        for (int p = rp[I]; p < rp[I + 1]; ++p)
-            for (int c = 0; c < b; ++c) {
-                const double v = val[(int64_t)p * bb + r * b + c];
-                if (col[p] == I && c == r) dia = v;
-                s = __dadd_rn(s, fabs(v));
-            }
-        d[(int64_t)I * b + r] = dia;
-        if (dia != 0.0) {
-            const double g = __ddiv_rn(s, fabs(dia));
-            atomicMax(rho_bits, (unsigned long long)__double_as_longlong(g));
+    double dia = 0.0, s = 0.0;
+    for (int p = rp[I]; p < rp[I + 1]; ++p)
+        for (int c = 0; c < b; ++c) {
+            const double v = val[(int64_t)p * bb + r * b + c];
+            if (col[p] == I && c == r) dia = v;
+            s = __dadd_rn(s, fabs(v));
         }
+    d[i] = dia;
+    if (dia != 0.0) {
+        const double g = __ddiv_rn(s, fabs(dia));
+        atomicMax(rho_bits, (unsigned long long)__double_as_longlong(g));
     }
 }
 
@@ -765,6 +768,83 @@ __global__ void __launch_bounds__(128) spgemm_rows_kernel(
     }
 }
 
+// C = X Y for few, long rows (the coarse levels): one CTA per output row,
+// the row's block accumulators in shared memory.  For each X_ik, k
+// ascending, the threads first locate the columns of Y row k in C's row,
+// then take its (block, entry) pairs, so every accumulator entry sees the
+// same FMA sequence as in the kernels above (k ascending, then the inner
+// index) and gets the same bits, with the whole CTA on one row.
+constexpr int SPG_CT = 256;
+template <int XR, int XC, int YC>
+__global__ void __launch_bounds__(SPG_CT) spgemm_cta_kernel(
+    const int *__restrict__ xrp, const int *__restrict__ xcol, const double *__restrict__ xval,
+    const int *__restrict__ yrp, const int *__restrict__ ycol, const double *__restrict__ yval,
+    const int *__restrict__ crp, const int *__restrict__ ccol, int cmax, int ymax, int upper,
+    double *__restrict__ cval)
+{
+    constexpr int CB = XR * YC, XB = XR * XC, YB = XC * YC;
+    extern __shared__ double sm[];
+    double *acc = sm;                                     // [cmax * CB]
+    double *xb = sm + (size_t)cmax * CB;                  // [XB]
+    int *cols = reinterpret_cast<int *>(xb + XB);         // [cmax]
+    int *ypos = cols + cmax;                              // [ymax]
+    const int i = blockIdx.x, tid = threadIdx.x;
+    const int r0 = crp[i], r1 = crp[i + 1];
+    const int c0 = upper ? find_sorted(ccol, r0, r1, i) : r0, len = r1 - c0;
+    for (int t = tid; t < len; t += SPG_CT) cols[t] = ccol[c0 + t];
+    for (int t = tid; t < len * CB; t += SPG_CT) acc[t] = 0.0;
+    __syncthreads();
+    for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
+        const int k = xcol[p];
+        if (tid < XB) xb[tid] = xval[(int64_t)p * XB + tid];
+        const int hi = yrp[k + 1];
+        const int lo = upper ? find_sorted(ycol, yrp[k], hi, i) : yrp[k];
+        const int ny = hi - lo;  // <= ymax
+        for (int t = tid; t < ny; t += SPG_CT) {
+            const int j = ycol[lo + t];
+            const int pos = find_sorted(cols, 0, len, j);
+            ypos[t] = (pos < len && cols[pos] == j) ? pos : -1;  // -1 cannot happen
+        }
+        __syncthreads();
+        for (int task = tid; task < ny * CB; task += SPG_CT) {
+            const int t = task / CB, e = task % CB;
+            const int pos = ypos[t];
+            if (pos < 0) continue;
+            const int r = e / YC, c = e % YC;
+            const double *yb = yval + (int64_t)(lo + t) * YB;
+            double v = acc[(size_t)pos * CB + e];
+#pragma unroll
+            for (int m = 0; m < XC; ++m) v += xb[r * XC + m] * yb[m * YC + c];
+            acc[(size_t)pos * CB + e] = v;
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < len * CB; t += SPG_CT) cval[(int64_t)c0 * CB + t] = acc[t];
+    if (upper)  // lower blocks: zero here, mirror_lower_kernel fills them
+        for (int t = tid; t < (c0 - r0) * CB; t += SPG_CT) cval[(int64_t)r0 * CB + t] = 0.0;
+}
+
+template <int XR, int XC, int YC>
+static int spgemm_cta(const BsrD &X, const BsrD &Y, BsrD *C, int cmax, int ymax, int upper,
+                      cudaStream_t s, bool *done)
+{
+    constexpr int CB = XR * YC, XB = XR * XC;
+    *done = false;
+    const size_t smem = (size_t)cmax * CB * sizeof(double) + XB * sizeof(double) +
+                        (size_t)(cmax + ymax) * sizeof(int);
+    if (smem > 200 * 1024) return AMG_OK;  // rows too long: the per-block kernel
+    auto kern = spgemm_cta_kernel<XR, XC, YC>;
+    if (smem > 48 * 1024)
+        AMG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+    kern<<<X.nbr, SPG_CT, smem, s>>>(X.row_ptr, X.col, X.val, Y.row_ptr, Y.col, Y.val, C->row_ptr,
+                                     C->col, cmax, ymax, upper, C->val);
+    ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    *done = true;
+    return AMG_OK;
+}
+
 // longest tail (columns >= row) of a row: the upper part of a symmetric product
 __global__ void row_max_upper_kernel(const int *__restrict__ rp, const int *__restrict__ col, int n,
                                      int *__restrict__ mx)
@@ -857,7 +937,27 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
     // rows against 20 / 36 / 28 ms, and lost on the ones with 1694 and 141)
     const int upper = (symmetric && xr == yc && X.nbr == Y.nbc) ? 1 : 0;
     bool done = false;
-    if (X.nbr < 16384) goto per_block;
+    if (X.nbr < 16384) {
+        // few rows: one CTA per output row (the shared-memory row must fit)
+        int *mx = nullptr, hm[2] = {0, 0};
+        AMG_TRY(tmp.alloc_n(&mx, 2));
+        AMG_TRY_CUDA(cudaMemsetAsync(mx, 0, 2 * sizeof(int), s));
+        if (upper)
+            row_max_upper_kernel<<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, C->col, X.nbr, mx);
+        else
+            row_max_kernel<<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, X.nbr, mx);
+        if (Y.nbr > 0) row_max_kernel<<<nblk(Y.nbr), T1D, 0, s>>>(Y.row_ptr, Y.nbr, mx + 1);
+        ::amg::count_launch(Y.nbr > 0 ? 2 : 1);
+        AMG_TRY_CUDA(cudaMemcpyAsync(hm, mx, sizeof(hm), cudaMemcpyDeviceToHost, s));
+        AMG_TRY_CUDA(cudaStreamSynchronize(s));
+        tmp.release(mx);
+        if (xr == 3 && yc == 3) AMG_TRY((spgemm_cta<3, 3, 3>(X, Y, C, hm[0], hm[1], upper, s, &done)));
+        else if (xr == 3) AMG_TRY((spgemm_cta<3, 3, 6>(X, Y, C, hm[0], hm[1], upper, s, &done)));
+        else if (xc == 6) AMG_TRY((spgemm_cta<6, 6, 6>(X, Y, C, hm[0], hm[1], upper, s, &done)));
+        else AMG_TRY((spgemm_cta<6, 3, 6>(X, Y, C, hm[0], hm[1], upper, s, &done)));
+        if (done) goto mirror;
+        goto per_block;
+    }
     {
     int *mx = nullptr, cmax = 0;
     AMG_TRY(tmp.alloc_n(&mx, 1));
@@ -973,7 +1073,9 @@ int build_transfer(const BsrD &A, const double *B, int ns, const uint8_t *strong
         ::amg::count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
     }
-    jacobi_rho_kernel<<<nblk(nn), T1D, 0, s>>>(A.row_ptr, A.col, A.val, nn, b, d, rho_bits); ::amg::count_launch(1);
+    jacobi_rho_kernel<<<nblk((int64_t)nn * b), T1D, 0, s>>>(A.row_ptr, A.col, A.val, nn, b, d,
+                                                            rho_bits);
+    ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     unsigned long long rb = 0;
     AMG_TRY_CUDA(cudaMemcpyAsync(&rb, rho_bits, sizeof(rb), cudaMemcpyDeviceToHost, s));
@@ -1045,26 +1147,28 @@ __global__ void spai0_kernel(const int *__restrict__ rp, const int *__restrict__
                              const double *__restrict__ val, int nbr, int b, double scale,
                              double *__restrict__ M)
 {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nbr) return;
+    // one thread per scalar row (b per block row)
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)nbr * b) return;
+    const int I = (int)(i / b), r = (int)(i % b);
     const int bb = b * b;
-    for (int r = 0; r < b; ++r) {
-        double dia = 0.0, s = 0.0;
-        for (int p = rp[I]; p < rp[I + 1]; ++p)
-            for (int c = 0; c < b; ++c) {
-                const double v = val[(int64_t)p * bb + r * b + c];
-                if (col[p] == I && c == r) dia = v;
-                s += v * v;
-            }
-        const double m = (s != 0.0) ? dia / s : 0.0;
-        M[(int64_t)I * b + r] = scale * m;
-    }
+    double dia = 0.0, s = 0.0;
+    for (int p = rp[I]; p < rp[I + 1]; ++p)
+        for (int c = 0; c < b; ++c) {
+            const double v = val[(int64_t)p * bb + r * b + c];
+            if (col[p] == I && c == r) dia = v;
+            s += v * v;
+        }
+    const double m = (s != 0.0) ? dia / s : 0.0;
+    M[i] = scale * m;
 }
 
 int spai0_diag(const BsrD &A, double scale, double *M, cudaStream_t s)
 {
     if (A.nbr == 0) return AMG_OK;
-    spai0_kernel<<<nblk(A.nbr), T1D, 0, s>>>(A.row_ptr, A.col, A.val, A.nbr, A.br, scale, M); ::amg::count_launch(1);
+    spai0_kernel<<<nblk((int64_t)A.nbr * A.br), T1D, 0, s>>>(A.row_ptr, A.col, A.val, A.nbr, A.br,
+                                                             scale, M);
+    ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     return AMG_OK;
 }
