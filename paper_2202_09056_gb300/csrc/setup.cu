@@ -539,6 +539,47 @@ __global__ void p_values_kernel(const int *__restrict__ rp, const int *__restric
     }
 }
 
+// The same values with one CTA per block row I: the slot of agg(J) among the
+// columns of P's row I is found once per block of A's row (in shared
+// memory), then the threads take the (P block, r, q) entries of the row and
+// walk the staged slots; every entry sees the same FMA sequence as above
+// (blocks of A's row ascending, then c), so the bits are the same.
+constexpr int PV_CT = 128;
+template <int B, int NS>
+__global__ void __launch_bounds__(PV_CT) p_values_cta_kernel(
+    const int *__restrict__ rp, const int *__restrict__ col, const double *__restrict__ val,
+    const int *__restrict__ agg, const double *__restrict__ ptent, const double *__restrict__ d,
+    double omega, const int *__restrict__ prp, const int *__restrict__ pcol,
+    double *__restrict__ pval)
+{
+    extern __shared__ int slot[];  // [longest row of A]
+    const int I = blockIdx.x, tid = threadIdx.x;
+    const int a0 = rp[I], na = rp[I + 1] - a0;
+    const int p0 = prp[I], np = prp[I + 1] - p0;
+    for (int t = tid; t < na; t += PV_CT) {
+        const int g = agg[col[a0 + t]];
+        const int pos = g >= 0 ? find_sorted(pcol, p0, p0 + np, g) : p0 + np;
+        slot[t] = (pos < p0 + np && pcol[pos] == g) ? pos - p0 : -1;
+    }
+    __syncthreads();
+    const int gI = agg[I];
+    for (int task = tid; task < np * B * NS; task += PV_CT) {
+        const int sl = task / (B * NS), e = task % (B * NS), r = e / NS, q = e % NS;
+        double acc = 0.0;
+        for (int t = 0; t < na; ++t) {
+            if (slot[t] != sl) continue;
+            const double *blk = val + (int64_t)(a0 + t) * B * B + r * B;
+            const double *pt = ptent + (int64_t)col[a0 + t] * B * NS + q;
+#pragma unroll
+            for (int c = 0; c < B; ++c) acc += blk[c] * pt[c * NS];
+        }
+        const double dr = d[(int64_t)I * B + r];
+        const double sc = (dr != 0.0) ? omega / dr : 0.0;
+        const double own = (gI == pcol[p0 + sl]) ? ptent[((int64_t)I * B + r) * NS + q] : 0.0;
+        pval[(int64_t)(p0 + sl) * B * NS + e] = own - sc * acc;
+    }
+}
+
 // ---------------------------------------------------------------- transpose
 __global__ void col_count_kernel(const int *__restrict__ col, int64_t nnz, int *__restrict__ cnt)
 {
@@ -886,17 +927,18 @@ static int spgemm_rows(const BsrD &X, const BsrD &Y, BsrD *C, int cmax, int lane
     return go(spgemm_rows_kernel<XR, XC, YC, 32>, 32);
 }
 
-// Lower blocks of a product known to be symmetric: C_ij = C_ji^T, one
-// thread per block row.
+// Lower blocks of a product known to be symmetric: C_ij = C_ji^T, one warp
+// per block row, the lanes over its lower blocks.
 template <int BS>
 __global__ void mirror_lower_kernel(const int *__restrict__ crp, const int *__restrict__ ccol,
                                     int nrows, double *__restrict__ cval)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (i >= nrows) return;
-    for (int q = crp[i]; q < crp[i + 1]; ++q) {
+    for (int q = crp[i] + lane; q < crp[i + 1]; q += 32) {
         const int j = ccol[q];
-        if (j >= i) break;
+        if (j >= i) break;  // columns ascend: the rest of this lane's blocks are upper
         const int lo = crp[j], hi = crp[j + 1];
         const int t = find_sorted(ccol, lo, hi, i);
         if (t >= hi || ccol[t] != i) continue;  // cannot happen for a symmetric pattern
@@ -937,8 +979,10 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
     // rows against 20 / 36 / 28 ms, and lost on the ones with 1694 and 141)
     const int upper = (symmetric && xr == yc && X.nbr == Y.nbc) ? 1 : 0;
     bool done = false;
-    if (X.nbr < 16384) {
-        // few rows: one CTA per output row (the shared-memory row must fit)
+    const double xlen = X.nbr ? (double)X.nnzb / X.nbr : 0.0;
+    if (X.nbr < 16384 || xlen >= 32.0) {
+        // few rows, or long X rows (the restrictions and the coarse A P):
+        // one CTA per output row (the shared-memory row must fit)
         int *mx = nullptr, hm[2] = {0, 0};
         AMG_TRY(tmp.alloc_n(&mx, 2));
         AMG_TRY_CUDA(cudaMemsetAsync(mx, 0, 2 * sizeof(int), s));
@@ -956,7 +1000,7 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
         else if (xc == 6) AMG_TRY((spgemm_cta<6, 6, 6>(X, Y, C, hm[0], hm[1], upper, s, &done)));
         else AMG_TRY((spgemm_cta<6, 3, 6>(X, Y, C, hm[0], hm[1], upper, s, &done)));
         if (done) goto mirror;
-        goto per_block;
+        if (X.nbr < 16384) goto per_block;
     }
     {
     int *mx = nullptr, cmax = 0;
@@ -1004,10 +1048,11 @@ per_block:
     }
 mirror:
     if (upper) {
+        const int mg = nblk((int64_t)X.nbr * 32);
         if (yc == 3)
-            mirror_lower_kernel<3><<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, C->col, X.nbr, C->val);
+            mirror_lower_kernel<3><<<mg, T1D, 0, s>>>(C->row_ptr, C->col, X.nbr, C->val);
         else
-            mirror_lower_kernel<6><<<nblk(X.nbr), T1D, 0, s>>>(C->row_ptr, C->col, X.nbr, C->val);
+            mirror_lower_kernel<6><<<mg, T1D, 0, s>>>(C->row_ptr, C->col, X.nbr, C->val);
         ::amg::count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
     }
@@ -1112,7 +1157,32 @@ int build_transfer(const BsrD &A, const double *B, int ns, const uint8_t *strong
     AMG_TRY(tmp.alloc_n(&pbrow, (size_t)std::max(nnzp, 1)));
     block_rows_kernel<<<nblk(nn), T1D, 0, s>>>(P.row_ptr, nn, pbrow); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
+    int amax = 0;  // longest row of A: the per-row kernel's staged slots
     if (nnzp > 0) {
+        int *mx = nullptr;
+        AMG_TRY(tmp.alloc_n(&mx, 1));
+        AMG_TRY_CUDA(cudaMemsetAsync(mx, 0, sizeof(int), s));
+        row_max_kernel<<<nblk(nn), T1D, 0, s>>>(A.row_ptr, nn, mx);
+        ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaMemcpyAsync(&amax, mx, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_TRY_CUDA(cudaStreamSynchronize(s));
+        tmp.release(mx);
+    }
+    if (nnzp > 0 && amax <= 12 * 1024) {
+#define AMG_PVALS(B_, NS_)                                                                   \
+    p_values_cta_kernel<B_, NS_><<<nn, PV_CT, sizeof(int) * amax, s>>>(                       \
+        A.row_ptr, A.col, A.val, out->agg, ptent, d, out->omega, P.row_ptr, P.col, P.val)
+        if (b == 3 && ns == 6) AMG_PVALS(3, 6);
+        else if (b == 6 && ns == 6) AMG_PVALS(6, 6);
+        else if (b == 3 && ns == 3) AMG_PVALS(3, 3);
+        else {
+            set_error("unsupported node block size %d with %d near-nullspace vectors", b, ns);
+            return AMG_ERR_ARG;
+        }
+#undef AMG_PVALS
+        ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    } else if (nnzp > 0) {
 #define AMG_PVALS(B_, NS_)                                                                   \
     p_values_kernel<B_, NS_><<<nblk(nnzp, 128), 128, 0, s>>>(A.row_ptr, A.col, A.val, strong,  \
                                                             out->agg, ptent, d, out->omega,    \
