@@ -129,19 +129,20 @@ def _gpu_id(torch):
         return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
 
 
-def _spmv_roofline(solver, torch, n, nbr, nnzb, reps=40):
-    """Average duration of the solve's fine-level 3x3 FP64 SpMV kernel (the
-    dominant kernel of the PCG iteration) on the launch stream."""
+def _spmv_roofline(solver, torch, n, nbr, nnzb, reps=40, which=0):
+    """Average duration of the solve's fine-level 3x3 SpMV kernel (the
+    dominant kernel of the PCG iteration) on the launch stream: which = 0 the
+    FP64 copy, 3 the FP32-pair copy of a PREC_DF64 hierarchy (same bytes)."""
     x = torch.randn(n, dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
     for _ in range(5):
-        solver.level_spmv(0, 0, x, y)
+        solver.level_spmv(0, which, x, y)
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(s)
     for _ in range(reps):
-        solver.level_spmv(0, 0, x, y)  # 1 GB of values per launch: larger than L2
+        solver.level_spmv(0, which, x, y)  # 1 GB of values per launch: larger than L2
     e1.record(s)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / reps
@@ -687,6 +688,22 @@ def main():
             "err_vs_fp64_solution": float(torch.linalg.norm(u_p - u_ref) / torch.linalg.norm(u_ref)),
             "operator_bytes": int(sol.stats()["bytes_solve"]),
             "vcycle": "FP64; aggregates from a distance-2 maximal independent set on the device"}
+        del sol
+        # FP64 emulated on FP32 pairs: the whole solve phase's matrices as
+        # hi + lo floats, FP64 vectors and CG; its fine SpMV against HBM
+        sol = amg.AMG(rp, cl, val, B, precision=amg.PREC_DF64)
+        t_df, it_df, res_df, st_df, u_df = _timed_solves(torch, sol, f, tol, args.steps, 5000, s)
+        t_sp, algo_sp = _spmv_roofline(sol, torch, p.ndof, p.nnodes, p.nnzb, which=3)
+        forms["df64"] = {
+            "value": t_df, "iterations": it_df, "rel_resid": res_df, "status": st_df,
+            "speedup_vs_fp64": forms["fp64"]["value"] / t_df,
+            "err_vs_fp64_solution": float(torch.linalg.norm(u_df - u_ref) / torch.linalg.norm(u_ref)),
+            "operator_bytes": int(sol.stats()["bytes_solve"]),
+            "fine_spmv": {"launch_ms": t_sp * 1e3, "achieved_gbs": algo_sp / t_sp / 1e9,
+                          "frac_of_measured_hbm": algo_sp / t_sp / 1e9 / peak,
+                          "frac_of_nominal_8tbs": algo_sp / t_sp / 8e12},
+            "vcycle": "V-cycle in FP64 emulated on FP32 pairs (hi + lo floats, ~2^-45 per "
+                      "product), FP64 vectors; CG's A p, dots and true residual in FP64"}
         del sol
         forms["ilu0_fp64"] = ilu0_form(amg, torch, (rp, cl, val, B), f, tol, u_ref,
                                        forms["fp64"], p, s, args.steps)

@@ -52,6 +52,11 @@ extern "C" {
 #define AMG_PREC_FP64 0           /* V-cycle matrices and vectors in FP64 */
 #define AMG_PREC_FP32 1           /* V-cycle in FP32 storage, FP32 accumulation */
 #define AMG_PREC_BF16 2           /* V-cycle matrices stored BF16, FP32 accumulation */
+#define AMG_PREC_DF64 3           /* V-cycle in FP64 emulated on FP32 pairs: A, P, R stored
+                                     as hi + lo floats (the FP64 value truncated to ~48 bits),
+                                     products and sums in FP32-pair arithmetic (about 2^-45
+                                     relative per product), FP64 vectors; the CG's A p, dots
+                                     and true residual stay FP64 */
 
 /* Storage of the solve's operators (amg_params.storage).  Sec. 4 compares
  * the block-valued solver with a scalar one ("NS Scalar"): the same
@@ -217,8 +222,10 @@ int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_pt
 
 /* y = op x with the hierarchy's own V-cycle kernel for operator `which` of
  * level `level` (0: A, 1: P, 2: R), in the sliced block-ELL layout the solve
- * uses.  x has (columns x block columns) and y (rows x block rows) doubles,
- * device, not overlapping.  Asynchronous on `stream`. */
+ * uses.  which = 3, 4, 5: the same operators in the FP32-pair copies of an
+ * AMG_PREC_DF64 hierarchy (AMG_ERR_STATE otherwise).  x has (columns x block
+ * columns) and y (rows x block rows) doubles, device, not overlapping.
+ * Asynchronous on `stream`. */
 int amg_level_spmv(amg_handle h, int32_t level, int32_t which, const double *x, double *y,
                    void *stream);
 

@@ -25,7 +25,7 @@ AMG_ERR_ARG, AMG_ERR_CUDA, AMG_ERR_BREAKDOWN, AMG_ERR_COARSE, AMG_ERR_LIMIT, AMG
     -1, -2, -3, -4, -5, -6
 _ERRORS = {-1: "bad argument", -2: "CUDA error", -3: "CG breakdown",
            -4: "coarsest matrix not positive definite", -5: "size limit", -6: "bad state"}
-PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_BF16, PREC_DF64 = 0, 1, 2, 3
 STORAGE_BLOCK, STORAGE_SCALAR = 0, 1
 AGG_GREEDY, AGG_MIS2 = 0, 1
 SMOOTH_SPAI0, SMOOTH_ILU0 = 0, 1
@@ -292,7 +292,8 @@ class AMG:
         return out
 
     def level_spmv(self, l: int, which: int, x, y, stream=None):
-        """y = op x with the solve's own kernel; which = 0 (A), 1 (P), 2 (R)."""
+        """y = op x with the solve's own kernel; which = 0 (A), 1 (P), 2 (R);
+        3, 4, 5: the same in the FP32-pair copies of a PREC_DF64 hierarchy."""
         import torch
         _check(self._lib.amg_level_spmv(self._h, l, which, _dptr(x, torch.float64, "x"),
                                         _dptr(y, torch.float64, "y"), _stream(stream)))

@@ -132,6 +132,63 @@ template <class TV>
 int launch_coarse_gemv(const double *Ainv, int n, const TV *x, TV *y, const Geom &g,
                        cudaStream_t s);
 
+// ---------------------------------------------------------------- FP64 on FP32 pairs
+// A double held as the unevaluated sum of two floats, hi + lo (about 48
+// significant bits).  GB300 issues FP32 at 64x its FP64 rate, so products of
+// such pairs computed with FP32 operations (an error-free product plus a
+// compensated sum) move the FP64-bound SpMV onto the FP32 pipe.  The
+// conversions are done on the bits (integer operations), so that no step
+// runs on the FP64 pipe.
+//
+// split: hi = x with its significand truncated to 24 bits, lo = the next 24
+// of the 29 bits below (truncated); |x - (hi + lo)| < 2^-47 |x|.  Values
+// outside FP32's normal range (|x| < 2^-126 or > 2^128) are flushed to zero
+// or infinity; a lo part below that range is dropped.
+__device__ __forceinline__ void split_f64(double x, float &h, float &l)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sgn = (unsigned int)(u >> 63) << 31;
+    const int e = (int)((u >> 52) & 0x7ff);
+    const unsigned long long m = u & 0xfffffffffffffull;
+    const int fe = e - 1023 + 127;  // FP32 biased exponent of x
+    l = __uint_as_float(sgn);
+    if (e == 0 || fe <= 0) {
+        h = __uint_as_float(sgn);
+        return;
+    }
+    if (fe >= 255) {
+        h = __uint_as_float(sgn | 0x7f800000u | ((e == 0x7ff && m) ? 0x400000u : 0u));
+        return;
+    }
+    h = __uint_as_float(sgn | ((unsigned int)fe << 23) | (unsigned int)(m >> 29));
+    const unsigned long long rem = m & 0x1fffffffull;  // x - hi = rem * 2^(e - 1075)
+    if (rem == 0) return;
+    const int top = 63 - __clzll((long long)rem);  // rem in [2^top, 2^(top+1)), top <= 28
+    const int le = e - 1075 + top + 127;
+    if (le <= 0) return;
+    const unsigned int mant =
+        top >= 23 ? (unsigned int)(rem >> (top - 23)) : (unsigned int)(rem << (23 - top));
+    l = __uint_as_float(sgn | ((unsigned int)le << 23) | (mant & 0x7fffffu));
+}
+
+// exact float -> double on the bits (subnormal floats flushed to zero)
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
+    const unsigned int e = (u >> 23) & 0xff;
+    const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
+    if (e == 0) return __longlong_as_double((long long)sgn);
+    if (e == 0xff) return __longlong_as_double((long long)(sgn | 0x7ff0000000000000ull | m));
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 896) << 52) | m));
+}
+
+struct __align__(8) df32 {
+    float h, l;
+    __host__ __device__ df32() : h(0.0f), l(0.0f) {}
+    __device__ explicit df32(double v) { split_f64(v, h, l); }
+};
+
 // ---------------------------------------------------------------- SELL-32 (sell.cu)
 // Sliced block-ELL: 32 lanes per slice, G lanes per block row (32/G rows per
 // slice); block k of a row belongs to lane k % G of its group at depth k / G,
@@ -228,6 +285,7 @@ struct Level {
     Sell<double> sA, sP, sR;  // V-cycle copies of A, P, R in the SELL layout (FP64)
     Sell<float> fA, fP, fR;   // FP32 copies (precision form)
     Sell<__nv_bfloat16> bA, bP, bR;  // BF16-stored copies (precision form)
+    Sell<df32> eA, eP, eR;    // FP64 values as FP32 pairs (AMG_PREC_DF64)
     double pad_A = 0, pad_P = 0, pad_R = 0;
     float *Mf = nullptr;      // smoother diagonal for the reduced-precision V-cycle
     float *vf = nullptr, *vu = nullptr, *ve = nullptr, *vz = nullptr, *vt = nullptr;

@@ -837,7 +837,7 @@ int amg_set_learned_smoother(amg_handle h, const float *params, int32_t *fell_ba
     // is less stable than both the bound 1.9 and SPAI0 itself (2): the
     // smoothing step contracts the energy norm only while lambda_max(M A) < 2
     const int fb = hb ? 1 : (lam >= std::max(1.9, h->spai0_lambda) ? 2 : 0);
-    if (!fb && h->prm.precision != AMG_PREC_FP64) {
+    if (!fb && (h->prm.precision == AMG_PREC_FP32 || h->prm.precision == AMG_PREC_BF16)) {
         // the FP32 / BF16 V-cycles apply the blocks in FP32
         if (!L0.Mbf) AMG_TRY(h->mem.alloc_n(&L0.Mbf, (size_t)L0.A.nbr * 9));
         const int64_t n9 = (int64_t)L0.A.nbr * 9;

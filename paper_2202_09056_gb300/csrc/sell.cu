@@ -70,9 +70,21 @@ constexpr int SELL_THREADS = 128;
 // wave with the warp-strided loop balancing.
 __host__ __device__ constexpr int sell_minb(int br, int bc) { return br == 6 ? 8 : (bc == 6 ? 8 : 12); }
 __host__ __device__ constexpr int sell_cap(int br, int bc) { return br == 6 ? (bc == 6 ? 8 : 16) : 32; }
+// FP32-pair values hold hi and lo of every entry plus the pair accumulators:
+// 64 registers for 3x3 (8 CTAs), 80 for 3x6 / 6x3 (6), 128 for 6x6 (4, and
+// one resident wave of 4 CTAs per SM)
+template <class VT> __host__ __device__ constexpr int sell_minb_t(int br, int bc)
+{
+    return std::is_same<VT, df32>::value ? (br == 6 && bc == 6 ? 4 : (br == 6 || bc == 6 ? 6 : 8))
+                                         : sell_minb(br, bc);
+}
+template <class VT> __host__ __device__ constexpr int sell_cap_t(int br, int bc)
+{
+    return std::is_same<VT, df32>::value && br == 6 && bc == 6 ? 4 : sell_cap(br, bc);
+}
 
 template <int BR, int BC, class VT, class TV, int MODE, int DOT, bool WIDE>
-__global__ void __launch_bounds__(SELL_THREADS, sell_minb(BR, BC)) sell_spmv_kernel(SellArgs<TV> a)
+__global__ void __launch_bounds__(SELL_THREADS, sell_minb_t<VT>(BR, BC)) sell_spmv_kernel(SellArgs<TV> a)
 {
     using Acc = TV;
     constexpr int BB = BR * BC;
@@ -102,8 +114,11 @@ __global__ void __launch_bounds__(SELL_THREADS, sell_minb(BR, BC)) sell_spmv_ker
         Acc acc[BR];
 #pragma unroll
         for (int r = 0; r < BR; ++r) acc[r] = Acc(0);
+        float sh[BR], sl[BR];  // FP32-pair accumulators (VT = df32)
+#pragma unroll
+        for (int r = 0; r < BR; ++r) sh[r] = sl[r] = 0.0f;
         int jn = (w > 0) ? __ldg(cp) : 0;
-#pragma unroll 2
+#pragma unroll(std::is_same<VT, df32>::value ? 1 : 2)
         for (int k = 0; k < w; ++k) {
             const int j = jn;
             if (k + 1 < w) jn = __ldg(cp + (k + 1) * 32);
@@ -127,6 +142,49 @@ __global__ void __launch_bounds__(SELL_THREADS, sell_minb(BR, BC)) sell_spmv_ker
                 for (int r = 0; r < BR; ++r)
 #pragma unroll
                     for (int c = 0; c < BC; ++c) acc[r] = fma(v[r * BC + c], xv[c], acc[r]);
+            } else if constexpr (std::is_same<VT, df32>::value) {
+                // FP64 on FP32 pairs, stored like the FP64 lane pairs (one
+                // 16-byte load brings two entries, hi and lo each); x split
+                // on the bits.  Per entry: the error-free FP32 product of the
+                // his with the cross terms added to its error, then the
+                // double-float sum: two-sum of the his, the los added to its
+                // error, a fast two-sum to renormalise (|sl| <= ulp(sh) / 2)
+                // -- every rounded operation written out, nothing contracted
+                const df32 *vg = val + (base + (int64_t)k * 32) * BB;
+                float vh[BB], vl[BB];
+#pragma unroll
+                for (int p = 0; p < BB / 2; ++p) {
+                    const float4 t4 = __ldcs(reinterpret_cast<const float4 *>(vg + p * 64) + lane);
+                    vh[2 * p] = t4.x;
+                    vl[2 * p] = t4.y;
+                    vh[2 * p + 1] = t4.z;
+                    vl[2 * p + 1] = t4.w;
+                }
+                if constexpr (BB % 2 == 1) {
+                    const float2 t2 = __ldcs(reinterpret_cast<const float2 *>(vg + (BB / 2) * 64) + lane);
+                    vh[BB - 1] = t2.x;
+                    vl[BB - 1] = t2.y;
+                }
+                float xh[BC], xl[BC];
+#pragma unroll
+                for (int c = 0; c < BC; ++c) split_f64((double)xv[c], xh[c], xl[c]);
+#pragma unroll
+                for (int r = 0; r < BR; ++r)
+#pragma unroll
+                    for (int c = 0; c < BC; ++c) {
+                        const float ah = vh[r * BC + c], al = vl[r * BC + c];
+                        const float pr = __fmul_rn(ah, xh[c]);
+                        float er = __fmaf_rn(ah, xh[c], -pr);
+                        er = __fmaf_rn(ah, xl[c], er);
+                        er = __fmaf_rn(al, xh[c], er);
+                        const float sn = __fadd_rn(sh[r], pr);
+                        const float bv = __fsub_rn(sn, sh[r]);
+                        float te = __fadd_rn(__fsub_rn(sh[r], __fsub_rn(sn, bv)),
+                                             __fsub_rn(pr, bv));
+                        te = __fadd_rn(te, __fadd_rn(sl[r], er));
+                        sh[r] = __fadd_rn(sn, te);
+                        sl[r] = __fsub_rn(te, __fsub_rn(sh[r], sn));
+                    }
             } else {
                 const VT *vb = vp + (int64_t)k * 32 * BB;
 #pragma unroll
@@ -136,6 +194,9 @@ __global__ void __launch_bounds__(SELL_THREADS, sell_minb(BR, BC)) sell_spmv_ker
                         acc[r] = fma((Acc)sldv(vb + (r * BC + c) * 32), xv[c], acc[r]);
             }
         }
+        if constexpr (std::is_same<VT, df32>::value)
+#pragma unroll
+            for (int r = 0; r < BR; ++r) acc[r] = f32_to_f64(sh[r]) + f32_to_f64(sl[r]);
         // rows split over G lanes: fixed-order butterfly within the group
         bool owner;
         if constexpr (!wide) {
@@ -200,6 +261,15 @@ __global__ void __launch_bounds__(SELL_THREADS, sell_minb(BR, BC)) sell_spmv_ker
         const double t = cta_sum_d<SELL_THREADS>(dot);
         if (threadIdx.x == 0) a.partials[blockIdx.x] = t;
     }
+}
+
+static int sell_grid_cap(int nslices, int cap_per_sm, const Geom &g)
+{
+    const int per_cta = SELL_THREADS / 32;
+    int grid = (nslices + per_cta - 1) / per_cta;
+    const int cap = g.num_sms * cap_per_sm;  // <= Geom::max_partials
+    if (grid > cap) grid = cap;
+    return std::max(grid, 1);
 }
 
 int sell_grid(int nslices, int br, int bc, const Geom &g)
@@ -273,7 +343,7 @@ int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom
     a.col = A.col;
     a.val = A.val;
     a.perm = A.perm;
-    int grid = sell_grid(A.nslices, A.br, A.bc, g);
+    int grid = sell_grid_cap(A.nslices, sell_cap_t<VT>(A.br, A.bc), g);
     if (max_grid > 0 && grid > max_grid) grid = max_grid;
     if (grid_out) *grid_out = grid;
     if (dot != DOT_NONE && grid > g.max_partials) {
@@ -301,6 +371,8 @@ template int launch_sell<float, float>(const Sell<float> &, int, int, SellArgs<f
 template int launch_sell<__nv_bfloat16, float>(const Sell<__nv_bfloat16> &, int, int,
                                                SellArgs<float>, const Geom &, cudaStream_t, int *,
                                                int);
+template int launch_sell<df32, double>(const Sell<df32> &, int, int, SellArgs<double>,
+                                       const Geom &, cudaStream_t, int *, int);
 
 // ---------------------------------------------------------------- conversion
 template <class T>
@@ -537,6 +609,7 @@ template <class T> int64_t sell_bytes(const Sell<T> &S)
 template int64_t sell_bytes<double>(const Sell<double> &);
 template int64_t sell_bytes<float>(const Sell<float> &);
 template int64_t sell_bytes<__nv_bfloat16>(const Sell<__nv_bfloat16> &);
+template int64_t sell_bytes<df32>(const Sell<df32> &);
 
 template int bsr_to_sell<double>(const BsrD &, DevArena &, cudaStream_t, Sell<double> *, double *,
                                  int);
@@ -544,5 +617,7 @@ template int bsr_to_sell<float>(const BsrD &, DevArena &, cudaStream_t, Sell<flo
                                 int);
 template int bsr_to_sell<__nv_bfloat16>(const BsrD &, DevArena &, cudaStream_t,
                                         Sell<__nv_bfloat16> *, double *, int);
+template int bsr_to_sell<df32>(const BsrD &, DevArena &, cudaStream_t, Sell<df32> *, double *,
+                               int);
 
 }  // namespace amg

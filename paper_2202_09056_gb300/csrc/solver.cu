@@ -272,6 +272,13 @@ template <> VLevel<double, double> view<double, double>(Level &L)
     v.f = L.f; v.u = L.u; v.e = L.e; v.z = L.z; v.t = L.t; v.n = L.n();
     return v;
 }
+template <> VLevel<df32, double> view<df32, double>(Level &L)
+{
+    VLevel<df32, double> v;
+    v.A = &L.eA; v.P = &L.eP; v.R = &L.eR; v.M = L.M;
+    v.f = L.f; v.u = L.u; v.e = L.e; v.z = L.z; v.t = L.t; v.n = L.n();
+    return v;
+}
 template <> VLevel<float, float> view<float, float>(Level &L)
 {
     VLevel<float, float> v;
@@ -476,7 +483,8 @@ static int record_cg_iteration_t(amg_handle h, cudaStream_t s, cudaGraphConditio
     cg_direction_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(z0, h->p, h->st, n); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     int grid = 0;
-    {  // q = A p, partial p.q (FP64)
+    {  // q = A p, partial p.q (FP64 in every precision form: the CG's attainable
+       // accuracy follows the error of A p relative to |A| |p|)
         SellArgs<double> a{};
         a.x = h->p;
         a.y = h->q;
@@ -520,6 +528,7 @@ static int record_cg_iteration(amg_handle h, cudaStream_t s, cudaGraphConditiona
 {
     switch (h->prm.precision) {
     case AMG_PREC_FP32: return record_cg_iteration_t<float, float>(h, s, cond, use_cond);
+    case AMG_PREC_DF64: return record_cg_iteration_t<df32, double>(h, s, cond, use_cond);
     case AMG_PREC_BF16: return record_cg_iteration_t<__nv_bfloat16, float>(h, s, cond, use_cond);
     default: return record_cg_iteration_t<double, double>(h, s, cond, use_cond);
     }
@@ -881,6 +890,12 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
             AMG_TRY(bsr_to_sell<double>(*oP, h->mem, s, &L.sP, &L.pad_P, h->max_lanes));
             AMG_TRY(bsr_to_sell<double>(*oR, h->mem, s, &L.sR, &L.pad_R, h->max_lanes));
         }
+        if (prec == AMG_PREC_DF64 && (l == 0 || vc))
+            AMG_TRY(bsr_to_sell<df32>(*oA, h->mem, s, &L.eA, &L.pad_A, h->max_lanes));
+        if (vc && prec == AMG_PREC_DF64) {
+            AMG_TRY(bsr_to_sell<df32>(*oP, h->mem, s, &L.eP, &L.pad_P, h->max_lanes));
+            AMG_TRY(bsr_to_sell<df32>(*oR, h->mem, s, &L.eR, &L.pad_R, h->max_lanes));
+        }
         if (vc && prec == AMG_PREC_FP32) {
             AMG_TRY(bsr_to_sell<float>(*oA, h->mem, s, &L.fA, &L.pad_A, h->max_lanes));
             AMG_TRY(bsr_to_sell<float>(*oP, h->mem, s, &L.fP, &L.pad_P, h->max_lanes));
@@ -903,7 +918,7 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
     for (size_t l = 0; l < h->lv.size(); ++l) {
         Level &L = h->lv[l];
         const size_t n = (size_t)std::max(L.n(), 1);
-        if (prec == AMG_PREC_FP64) {
+        if (prec == AMG_PREC_FP64 || prec == AMG_PREC_DF64) {
             if (l > 0) AMG_TRY(h->mem.alloc_n(&L.f, n));
             AMG_TRY(h->mem.alloc_n(&L.u, n));
             AMG_TRY(h->mem.alloc_n(&L.e, n));
@@ -923,7 +938,7 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
             }
         }
     }
-    if (prec != AMG_PREC_FP64) {
+    if (prec == AMG_PREC_FP32 || prec == AMG_PREC_BF16) {
         const size_t n0 = (size_t)std::max(h->lv[0].n(), 1);
         AMG_TRY(h->mem.alloc_n(&h->rv, n0));
         AMG_TRY(h->mem.alloc_n(&h->zv, n0));
@@ -969,7 +984,7 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
     amg_params_default(&p);
     if (prm) p = *prm;
     if (p.npre < 0 || p.npost < 0 || p.max_levels < 1 || p.coarse_enough < 0 ||
-        !(p.eps_strong >= 0.0) || p.precision < AMG_PREC_FP64 || p.precision > AMG_PREC_BF16 ||
+        !(p.eps_strong >= 0.0) || p.precision < AMG_PREC_FP64 || p.precision > AMG_PREC_DF64 ||
         p.loop_mode < 0 || p.loop_mode > 1 || p.storage < AMG_STORAGE_BLOCK ||
         p.storage > AMG_STORAGE_SCALAR || p.aggregation < AMG_AGG_GREEDY ||
         p.aggregation > AMG_AGG_MIS2 || p.smoother < AMG_SMOOTH_SPAI0 ||
@@ -1015,7 +1030,7 @@ int amg_apply_vcycle(amg_handle h, const double *r, double *z, void *stream)
     const int64_t n = L0.n();
     const bool multi = h->lv.size() > 1;
     const int zero = h->prm.npre == 0;
-    if (h->prm.precision == AMG_PREC_FP64) {
+    if (h->prm.precision == AMG_PREC_FP64 || h->prm.precision == AMG_PREC_DF64) {
         if (multi && h->learned && !zero) {
             AMG_TRY(launch_block_apply(L0.Mb, r, L0.u, L0.A.nbr, h->geom, s));
         } else if (multi && !(h->ilu && !zero)) {  // ILU(0) pre-smooths inside the V-cycle
@@ -1023,6 +1038,7 @@ int amg_apply_vcycle(amg_handle h, const double *r, double *z, void *stream)
             count_launch(1);
             AMG_TRY_CUDA(cudaGetLastError());
         }
+        if (h->prm.precision == AMG_PREC_DF64) return record_vcycle<df32, double>(h, r, z, nullptr, s);
         return record_vcycle<double, double>(h, r, z, nullptr, s);
     }
     const bool lb = multi && h->learned && !zero;
@@ -1072,7 +1088,7 @@ int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxi
     }
     AMG_TRY(launch_reduce_sum(h->partials, grid, h->scal + 1, s));
     cg_start_kernel<<<1, 1, 0, s>>>(h->st, h->scal, tol, maxiter); ::amg::count_launch(1);
-    if (h->prm.precision == AMG_PREC_FP64) {
+    if (h->prm.precision == AMG_PREC_FP64 || h->prm.precision == AMG_PREC_DF64) {
         if (multi && h->learned && h->prm.npre > 0) {
             AMG_TRY(launch_block_apply(L0.Mb, h->r, L0.u, L0.A.nbr, h->geom, s));
         } else if (multi && !(h->ilu && h->prm.npre > 0)) {  // ILU(0) pre-smooths in the V-cycle
@@ -1175,7 +1191,7 @@ int amg_get_stats(amg_handle h, amg_stats *out)
     for (const Level &L : h->lv)
         sb += sell_bytes(L.sA) + sell_bytes(L.sP) + sell_bytes(L.sR) + sell_bytes(L.fA) +
               sell_bytes(L.fP) + sell_bytes(L.fR) + sell_bytes(L.bA) + sell_bytes(L.bP) +
-              sell_bytes(L.bR);
+              sell_bytes(L.bR) + sell_bytes(L.eA) + sell_bytes(L.eP) + sell_bytes(L.eR);
     out->bytes_solve = sb;
     out->spai0_lambda = h->spai0_lambda;
     return AMG_OK;
@@ -1268,11 +1284,22 @@ int amg_level_spmv(amg_handle h, int32_t level, int32_t which, const double *x, 
                    void *stream)
 {
     clear_error();
-    if (!h || level < 0 || level >= (int)h->lv.size() || which < 0 || which > 2 || !x || !y) {
+    if (!h || level < 0 || level >= (int)h->lv.size() || which < 0 || which > 5 || !x || !y) {
         set_error("bad argument");
         return AMG_ERR_ARG;
     }
     const Level &L = h->lv[level];
+    if (which >= 3) {  // the FP32-pair copies of an AMG_PREC_DF64 hierarchy
+        const Sell<df32> &E = which == 3 ? L.eA : which == 4 ? L.eP : L.eR;
+        if (!E.slice_ptr) {
+            set_error("no FP32-pair copy of this operator (AMG_PREC_DF64 only)");
+            return AMG_ERR_STATE;
+        }
+        SellArgs<double> a{};
+        a.x = x;
+        a.y = y;
+        return launch_sell<df32, double>(E, SPMV_PLAIN, DOT_NONE, a, h->geom, (cudaStream_t)stream);
+    }
     const Sell<double> &S = which == 0 ? L.sA : which == 1 ? L.sP : L.sR;
     if (!S.slice_ptr) {
         set_error("operator not present on this level");
