@@ -472,8 +472,9 @@ def main():
                          "(a short, fixed command for profilers)")
     ap.add_argument("--profile-op", default="",
                     help="LEVEL:OP (OP in A, P, R): like --profile-spmv for that level operator")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"],
-                    help="V-cycle precision of the main line (CG stays FP64)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16", "df64"],
+                    help="V-cycle precision of the main line (CG stays FP64); with "
+                         "--profile-spmv / --profile-op, df64 profiles the FP32-pair copies")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32/BF16 V-cycle and learned-smoother comparisons "
                          "on the same workload")
@@ -517,7 +518,8 @@ def main():
     f = torch.from_numpy(p.f).to(dev)
     tol = WORKLOADS[args.workload]["tol"]
     s = torch.cuda.current_stream()
-    PRECS = {"fp64": amg.PREC_FP64, "fp32": amg.PREC_FP32, "bf16": amg.PREC_BF16}
+    PRECS = {"fp64": amg.PREC_FP64, "fp32": amg.PREC_FP32, "bf16": amg.PREC_BF16,
+             "df64": amg.PREC_DF64}
     prec = PRECS[args.precision]
 
     def step(timings=None):
@@ -538,7 +540,8 @@ def main():
     if args.profile_spmv or args.profile_op:
         # a short, fixed sequence for profilers: 8 launches of one level
         # operator's SpMV (PLAIN mode) on the benchmark hierarchy
-        solver = amg.AMG(rp, cl, val, B)
+        df = args.precision == "df64"
+        solver = amg.AMG(rp, cl, val, B, precision=amg.PREC_DF64 if df else amg.PREC_FP64)
         lvl, op = (0, "A") if not args.profile_op else args.profile_op.split(":")
         lvl, which = int(lvl), "APR".index(op)
         info = [solver.level_info(l) for l in range(solver.nlevels)]
@@ -548,7 +551,7 @@ def main():
         x = torch.randn(nx, dtype=torch.float64, device=dev)
         y = torch.empty(ny, dtype=torch.float64, device=dev)
         for _ in range(8):
-            solver.level_spmv(lvl, which, x, y)
+            solver.level_spmv(lvl, which + (3 if df else 0), x, y)
         torch.cuda.synchronize()
         print(json.dumps({"profile_op": f"{lvl}:{op}", "workload": args.workload,
                           "nnzb": info[lvl]["nnzb_P" if which else "nnzb_A"], "x": nx, "y": ny}))
@@ -727,7 +730,8 @@ def main():
         "metric": METRIC, "value": solve_t, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_t, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f64 CG / f32 V-cycle",
-                                         "bf16": "f64 CG / bf16-stored V-cycle"}[args.precision],
+                                         "bf16": "f64 CG / bf16-stored V-cycle",
+                                         "df64": "f64 CG / f32-pair (emulated f64) V-cycle"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "dofs": p.ndof,
                    "nnzb": p.nnzb, "levels": stats["nlevels"],
