@@ -37,6 +37,7 @@ struct BSell {
     int64_t *slice_ptr = nullptr;
     int *col = nullptr;
     double *val = nullptr;
+    df32 *eval = nullptr;        // the same values as FP32 pairs (AMG_PREC_DF64 V-cycle)
     int *s_inst = nullptr, *s_local = nullptr, *s_G = nullptr;
     int *perm = nullptr;         // concatenated slot -> row maps of the sorted parts
     int64_t *s_pbase = nullptr;  // per slice: its first slot in perm, or -1 (natural order)
@@ -48,6 +49,7 @@ struct BArgs {
     const int64_t *slice_ptr;
     const int *col;
     const double *val;
+    const df32 *eval;
     const int *s_inst, *s_local, *s_G;
     const int *perm;
     const int64_t *s_pbase;
@@ -62,7 +64,7 @@ struct BArgs {
     double *y, *y2;
 };
 
-template <int BR, int BC, int KT, int MODE>
+template <int BR, int BC, int KT, int MODE, bool DF>
 __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
 {
     constexpr int BB = BR * BC;
@@ -86,10 +88,14 @@ __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
         const int64_t yo = a.yoff[inst];
         for (int k0 = 0; k0 < K; k0 += KT) {
             double acc[BR][KT];
+            float sh[BR][KT], sl[BR][KT];  // FP32-pair accumulators (DF)
 #pragma unroll
             for (int r = 0; r < BR; ++r)
 #pragma unroll
-                for (int t = 0; t < KT; ++t) acc[r][t] = 0.0;
+                for (int t = 0; t < KT; ++t) {
+                    acc[r][t] = 0.0;
+                    sh[r][t] = sl[r][t] = 0.0f;
+                }
             for (int d = 0; d < w; ++d) {
                 const int j = __ldg(cp + d * 32);
                 double xv[BC][KT];
@@ -98,6 +104,52 @@ __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
 #pragma unroll
                     for (int t = 0; t < KT; ++t)
                         xv[c][t] = (k0 + t < K) ? __ldg(xb + ((int64_t)j * BC + c) * K + k0 + t) : 0.0;
+                if constexpr (DF) {
+                    // FP64 emulated on FP32 pairs, as in the single-instance
+                    // SELL kernel: hi/lo value pairs in the FP64 lane-pair
+                    // layout, x split on the bits, error-free FP32 products
+                    // and a renormalised double-float sum per (row, rhs)
+                    const df32 *eg = a.eval + (base + (int64_t)d * 32) * BB;
+                    float vh[BB], vl[BB];
+#pragma unroll
+                    for (int pr = 0; pr < BB / 2; ++pr) {
+                        const float4 t4 = __ldg(reinterpret_cast<const float4 *>(eg + pr * 64) + lane);
+                        vh[2 * pr] = t4.x;
+                        vl[2 * pr] = t4.y;
+                        vh[2 * pr + 1] = t4.z;
+                        vl[2 * pr + 1] = t4.w;
+                    }
+                    if constexpr (BB % 2 == 1) {
+                        const float2 t2 = __ldg(reinterpret_cast<const float2 *>(eg + (BB / 2) * 64) + lane);
+                        vh[BB - 1] = t2.x;
+                        vl[BB - 1] = t2.y;
+                    }
+                    float xh[BC][KT], xl[BC][KT];
+#pragma unroll
+                    for (int c = 0; c < BC; ++c)
+#pragma unroll
+                        for (int t = 0; t < KT; ++t) split_f64(xv[c][t], xh[c][t], xl[c][t]);
+#pragma unroll
+                    for (int r = 0; r < BR; ++r)
+#pragma unroll
+                        for (int c = 0; c < BC; ++c)
+#pragma unroll
+                            for (int t = 0; t < KT; ++t) {
+                                const float ah = vh[r * BC + c], al = vl[r * BC + c];
+                                const float pv = __fmul_rn(ah, xh[c][t]);
+                                float er = __fmaf_rn(ah, xh[c][t], -pv);
+                                er = __fmaf_rn(ah, xl[c][t], er);
+                                er = __fmaf_rn(al, xh[c][t], er);
+                                const float sn = __fadd_rn(sh[r][t], pv);
+                                const float bv = __fsub_rn(sn, sh[r][t]);
+                                float te = __fadd_rn(__fsub_rn(sh[r][t], __fsub_rn(sn, bv)),
+                                                     __fsub_rn(pv, bv));
+                                te = __fadd_rn(te, __fadd_rn(sl[r][t], er));
+                                sh[r][t] = __fadd_rn(sn, te);
+                                sl[r][t] = __fsub_rn(te, __fsub_rn(sh[r][t], sn));
+                            }
+                    continue;
+                }
                 // FP64 sliced values: entries 2p, 2p+1 of a lane side by
                 // side (one 16-byte load), an odd last entry after the pairs
                 // (the layout of sell.cu)
@@ -118,6 +170,11 @@ __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
                         for (int t = 0; t < KT; ++t)
                             acc[r][t] = fma(v[r * BC + c], xv[c][t], acc[r][t]);
             }
+            if constexpr (DF)
+#pragma unroll
+                for (int r = 0; r < BR; ++r)
+#pragma unroll
+                    for (int t = 0; t < KT; ++t) acc[r][t] = f32_to_f64(sh[r][t]) + f32_to_f64(sl[r][t]);
             for (int m = G >> 1; m >= 1; m >>= 1)
 #pragma unroll
                 for (int r = 0; r < BR; ++r)
@@ -152,10 +209,20 @@ __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
 template <int BR, int BC, int MODE>
 static int bspmm_kt(const BSell &S, int kt, const BArgs &a, int grid, cudaStream_t s)
 {
+    const bool df = a.eval != nullptr;
     switch (kt) {
-    case 1: bspmm_kernel<BR, BC, 1, MODE><<<grid, BT, 0, s>>>(a); break;
-    case 2: bspmm_kernel<BR, BC, 2, MODE><<<grid, BT, 0, s>>>(a); break;
-    default: bspmm_kernel<BR, BC, 4, MODE><<<grid, BT, 0, s>>>(a); break;
+    case 1:
+        if (df) bspmm_kernel<BR, BC, 1, MODE, true><<<grid, BT, 0, s>>>(a);
+        else bspmm_kernel<BR, BC, 1, MODE, false><<<grid, BT, 0, s>>>(a);
+        break;
+    case 2:
+        if (df) bspmm_kernel<BR, BC, 2, MODE, true><<<grid, BT, 0, s>>>(a);
+        else bspmm_kernel<BR, BC, 2, MODE, false><<<grid, BT, 0, s>>>(a);
+        break;
+    default:
+        if (df) bspmm_kernel<BR, BC, 4, MODE, true><<<grid, BT, 0, s>>>(a);
+        else bspmm_kernel<BR, BC, 4, MODE, false><<<grid, BT, 0, s>>>(a);
+        break;
     }
     count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
@@ -179,13 +246,20 @@ static int bspmm_mode(const BSell &S, int kt, int mode, const BArgs &a, int grid
     return AMG_ERR_ARG;
 }
 
-static int launch_bspmm(const BSell &S, int kt, int mode, BArgs a, const Geom &g, cudaStream_t s)
+// df: the FP32-pair copy of the values (the V-cycle of an AMG_PREC_DF64 batch)
+static int launch_bspmm(const BSell &S, int kt, int mode, BArgs a, const Geom &g, cudaStream_t s,
+                        bool df = false)
 {
     if (S.nslices == 0) return AMG_OK;
+    if (df && !S.eval) {
+        set_error("no FP32-pair copy of this batched operator");
+        return AMG_ERR_STATE;
+    }
     a.nslices = S.nslices;
     a.slice_ptr = S.slice_ptr;
     a.col = S.col;
     a.val = S.val;
+    a.eval = df ? S.eval : nullptr;
     a.s_inst = S.s_inst;
     a.s_local = S.s_local;
     a.s_G = S.s_G;
@@ -566,6 +640,7 @@ struct amg_batch_s {
     int maxiter = 0;
     double setup_seconds = 0;
     std::vector<int> kt_choice;          // autotuned RHS tile per (level, operator)
+    bool df = false;                     // V-cycle on FP32-pair values (AMG_PREC_DF64)
 };
 
 static BVec bvec(amg_batch h)
@@ -631,7 +706,7 @@ static int record_bvcycle(amg_batch h, const double *f0, double *z0, const int *
             a.x = C.u;
             a.f = f;
             a.y = C.e;
-            AMG_TRY(launch_bspmm(C.A, C.A.kt, SPMV_RESID, a, g, s));
+            AMG_TRY(launch_bspmm(C.A, C.A.kt, SPMV_RESID, a, g, s, h->df));
         }
         {  // f_{l+1} = R e ; u_{l+1} = M_{l+1} f_{l+1}
             BArgs a = bargs(h, C, C.voff, N.voff, N.nrows, enable);
@@ -640,7 +715,7 @@ static int record_bvcycle(amg_batch h, const double *f0, double *z0, const int *
             a.y2 = N.u;
             a.M = N.M;
             a.moff = C.moff_next;
-            AMG_TRY(launch_bspmm(C.R, C.R.kt, SPMV_RESTRICT, a, g, s));
+            AMG_TRY(launch_bspmm(C.R, C.R.kt, SPMV_RESTRICT, a, g, s, h->df));
         }
         kti += 3;
     }
@@ -662,7 +737,7 @@ static int record_bvcycle(amg_batch h, const double *f0, double *z0, const int *
             a.x = N.z;
             a.u = C.u;
             a.y = C.u;
-            AMG_TRY(launch_bspmm(C.P, C.P.kt, SPMV_AXPY, a, g, s));
+            AMG_TRY(launch_bspmm(C.P, C.P.kt, SPMV_AXPY, a, g, s, h->df));
         }
         {  // z = u + M (f - A u)
             BArgs a = bargs(h, C, C.voff, C.voff, C.nrows, enable);
@@ -671,7 +746,7 @@ static int record_bvcycle(amg_batch h, const double *f0, double *z0, const int *
             a.M = C.M;
             a.moff = C.moff;
             a.y = zl;
-            AMG_TRY(launch_bspmm(C.A, C.A.kt, SPMV_SMOOTH, a, g, s));
+            AMG_TRY(launch_bspmm(C.A, C.A.kt, SPMV_SMOOTH, a, g, s, h->df));
         }
     }
     return AMG_OK;
@@ -816,6 +891,12 @@ template <class T> static int upload(DevArena &m, const std::vector<T> &v, T **o
 
 // Concatenate the sliced operators `which` (0 A, 1 P, 2 R) of level l over the
 // instances that smooth on level l.
+__global__ void to_df32_kernel(const double *__restrict__ v, df32 *__restrict__ e, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) e[i] = df32(v[i]);
+}
+
 static int concat_sell(amg_batch h, int l, int which, BSell *out)
 {
     cudaStream_t s = h->stream;
@@ -885,6 +966,15 @@ static int concat_sell(amg_batch h, int l, int which, BSell *out)
                                      cudaMemcpyDeviceToDevice, s));
         at += X.nslots;
     }
+    if (h->df) {  // the values as FP32 pairs, element by element (same layout)
+        const int64_t ne = nslots * bb;
+        AMG_TRY(h->mem.alloc_n(&S.eval, (size_t)std::max<int64_t>(ne, 1)));
+        if (ne > 0) {
+            to_df32_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(S.val, S.eval, ne);
+            count_launch(1);
+            AMG_TRY_CUDA(cudaGetLastError());
+        }
+    }
     AMG_TRY_CUDA(cudaStreamSynchronize(s));
     *out = S;
     return AMG_OK;
@@ -912,9 +1002,11 @@ static int autotune_kt(amg_batch h, const BSell &S, const int64_t *xoff, const i
         a.enable = h->all_on;
         a.x = x;
         a.y = y;
-        AMG_TRY(launch_bspmm(S, kt, SPMV_PLAIN, a, h->geom, s));  // warm-up
+        // an emulated-FP64 batch tunes the tile of the V-cycle's (pair) kernels
+        AMG_TRY(launch_bspmm(S, kt, SPMV_PLAIN, a, h->geom, s, h->df));  // warm-up
         AMG_TRY_CUDA(cudaEventRecord(e0, s));
-        for (int rep = 0; rep < 3; ++rep) AMG_TRY(launch_bspmm(S, kt, SPMV_PLAIN, a, h->geom, s));
+        for (int rep = 0; rep < 3; ++rep)
+            AMG_TRY(launch_bspmm(S, kt, SPMV_PLAIN, a, h->geom, s, h->df));
         AMG_TRY_CUDA(cudaEventRecord(e1, s));
         AMG_TRY_CUDA(cudaEventSynchronize(e1));
         float ms = 0;
@@ -958,6 +1050,7 @@ static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, co
     for (int i = 0; i < ni; ++i) {
         amg_handle x = new amg_handle_s();
         x->prm = h->prm;
+        x->prm.precision = AMG_PREC_FP64;  // FP64 sliced copies; the batch makes its pair copies
         x->stream = s;
         x->mem.stream = s;
         x->max_lanes = 32;  // the batched SpMM keeps each row within one warp
@@ -1130,14 +1223,16 @@ int amg_batch_setup(int32_t ninst, const amg_bsr *A, const double *const *B, con
     amg_params p;
     amg_params_default(&p);
     if (prm) p = *prm;
-    if (p.precision != AMG_PREC_FP64 || p.npre != 1 || p.npost != 1 ||
-        p.smoother != AMG_SMOOTH_SPAI0) {
-        set_error("the batched solve runs FP64 V(1,1) cycles with the SPAI0 smoother");
+    if ((p.precision != AMG_PREC_FP64 && p.precision != AMG_PREC_DF64) || p.npre != 1 ||
+        p.npost != 1 || p.smoother != AMG_SMOOTH_SPAI0) {
+        set_error("the batched solve runs FP64 (or emulated-FP64) V(1,1) cycles with the SPAI0 "
+                  "smoother");
         return AMG_ERR_ARG;
     }
     auto t0 = std::chrono::steady_clock::now();
     amg_batch h = new amg_batch_s();
     h->prm = p;
+    h->df = p.precision == AMG_PREC_DF64;
     h->stream = (cudaStream_t)stream;
     h->mem.stream = h->stream;
     h->ninst = ninst;

@@ -109,3 +109,35 @@ def test_host_loop_mode_gives_identical_batch_results():
     U1, it1, r1, s1 = amg.AMGBatch(mats, Bs, nrhs, coarse_enough=150, loop_mode=1).solve(F)
     assert s0 == s1 == amg.AMG_OK and it0 == it1 and r0 == r1
     assert all(torch.equal(a, b) for a, b in zip(U0, U1))
+
+
+def test_emulated_fp64_batch_matches_oracle_and_fp64_batch():
+    """PREC_DF64 batch: the V-cycle's SpMMs on FP32-pair values (the CG's A p
+    and true residual stay FP64).  Every (instance, rhs) meets the oracle's
+    bars; iterations within +-1 of the FP64 batch and solutions within 1e-9
+    of it (the emulated V-cycle matches FP64 to about 1e-13)."""
+    inst = _instances()
+    mats, Bs, nrhs, F = [], [], [], []
+    for p, k in inst:
+        m, B = _dev(p)
+        mats.append(m)
+        Bs.append(B)
+        nrhs.append(k)
+        F.append(torch.from_numpy(np.atleast_2d(p.f).copy()).cuda())
+    U, its, res, st = amg.AMGBatch(mats, Bs, nrhs, coarse_enough=150,
+                                   precision=amg.PREC_DF64).solve(F, tol=1e-8)
+    U64, its64, _, st64 = amg.AMGBatch(mats, Bs, nrhs, coarse_enough=150).solve(F, tol=1e-8)
+    assert st == st64 == amg.AMG_OK
+    for i, (p, k) in enumerate(inst):
+        H = o.Hierarchy(o.from_problem(p), 3, p.B, coarse_enough=150)
+        fs = np.atleast_2d(p.f)
+        for j in range(k):
+            uo, ito, _ = H.solve(fs[j], tol=1e-8)
+            u = U[i][j].cpu().numpy()
+            assert res[i][j] <= 1e-8
+            assert abs(its[i][j] - ito) <= 1 and abs(its[i][j] - its64[i][j]) <= 1, (i, j)
+            assert np.linalg.norm(u - uo) <= 1e-7 * np.linalg.norm(uo), (i, j)
+            u64 = U64[i][j].cpu().numpy()
+            assert np.linalg.norm(u - u64) <= 1e-9 * np.linalg.norm(u64), (i, j)
+    with pytest.raises(amg.AmgError):
+        amg.AMGBatch(mats, Bs, nrhs, coarse_enough=150, precision=amg.PREC_FP32)
