@@ -156,3 +156,28 @@ def test_df64_full_size_inclusions_80():
     A = sp.bsr_matrix((p.val, p.col, p.row_ptr), shape=(p.ndof, p.ndof))
     un = u.cpu().numpy()
     assert np.linalg.norm(p.f - A @ un) / np.linalg.norm(p.f) <= 1.0001e-8
+
+
+def test_df64_with_scalar_storage_and_learned_blocks():
+    """The pair kernels in the other layouts the V-cycle uses: scalar (1x1)
+    storage of every operator, and the learned 3x3 smoother blocks applied in
+    the SpMV epilogue.  Each matches the FP64 V-cycle with the same setting:
+    iterations within +-1, solutions within 1e-9."""
+    p = q.make_problem((10, 9, 8), traction=(0, 0, -1), inclusion_frac=0.2)
+    fb = torch.from_numpy(p.f).cuda()
+    for kw in ({"storage": amg.STORAGE_SCALAR}, {}):
+        G = amg.AMG(*_dev(p), coarse_enough=200, precision=amg.PREC_DF64, **kw)
+        G64 = amg.AMG(*_dev(p), coarse_enough=200, **kw)
+        if not kw:
+            w = amg.learned_init(5)
+            rng = np.random.default_rng(5)
+            w[64 * 13:64 * 13 + 6 * 64] = 0.05 * rng.standard_normal(6 * 64)
+            w = w.astype(np.float32)
+            assert not G.set_learned_smoother(w)
+            assert not G64.set_learned_smoother(w)
+            np.testing.assert_array_equal(G.learned_blocks(), G64.learned_blocks())
+        u, it, res, st = G.solve(fb)
+        u64, it64, _, st64 = G64.solve(fb)
+        assert st == st64 == amg.AMG_OK and res <= 1e-8
+        assert abs(it - it64) <= 1, (kw, it, it64)
+        assert torch.linalg.norm(u - u64) <= 1e-9 * torch.linalg.norm(u64), kw
