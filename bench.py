@@ -746,6 +746,17 @@ def main():
             sc, bl = forms["scalar_" + name], forms[name]
             sc["block_speedup"] = sc["value"] / bl["value"]
             sc["block_memory_ratio"] = bl["operator_bytes"] / sc["operator_bytes"]
+        # the setup side of the same comparison: each level's Galerkin product
+        # R (A P) recomputed with block SpGEMMs and with scalar (1x1) SpGEMMs
+        # on the unblocked operators (best of two, wall time incl. symbolic)
+        gal = []
+        for l in range(solver.nlevels - 1):
+            tb = min(solver.galerkin_timing(l, amg.STORAGE_BLOCK)[0] for _ in range(2))
+            ts, ds = min(solver.galerkin_timing(l, amg.STORAGE_SCALAR) for _ in range(2))
+            gal.append({"level": l, "block_s": tb, "scalar_s": ts, "scalar_rel_diff": ds})
+        tb_all, ts_all = sum(g["block_s"] for g in gal), sum(g["scalar_s"] for g in gal)
+        forms["galerkin_block_vs_scalar"] = {"block_s": tb_all, "scalar_s": ts_all,
+                                             "block_speedup": ts_all / tb_all, "levels": gal}
         if args.precision == "fp64":
             forms["learned"] = learned_form(amg, torch, solver, f, tol, u_ref,
                                             forms["fp64"]["value"], forms["fp64"]["iterations"],

@@ -229,6 +229,20 @@ int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_pt
 int amg_level_spmv(amg_handle h, int32_t level, int32_t which, const double *x, double *y,
                    void *stream);
 
+/* The Galerkin product A_{l+1} = R_l (A_l P_l) of level `level` (Alg. 1,
+ * "A_{i+1} = R_i A_i P_i"; the setup's dominant cost, Sec. 3) recomputed in
+ * block storage (AMG_STORAGE_BLOCK: the setup's own block SpGEMMs) or in
+ * scalar CSR (AMG_STORAGE_SCALAR: A, P, R unblocked, the same SpGEMM kernels
+ * with 1x1 blocks), the setup-phase side of the block vs scalar comparison
+ * of Sec. 4.  *seconds (host) receives the wall time of the product (symbolic
+ * and numeric passes, their allocations, synchronised), *rel_diff (host) the
+ * largest difference from the hierarchy's A_{l+1} (unblocked for scalar)
+ * over its largest entry, or -1 if the patterns differ.  The result is
+ * freed before returning.  Synchronises the stream the handle was set up on;
+ * AMG_ERR_ARG if `level` has no coarser level. */
+int amg_level_galerkin(amg_handle h, int32_t level, int32_t storage, double *seconds,
+                       double *rel_diff);
+
 /* Padding of the sliced layout of A, P, R on `level` (host double[3]): extra
  * stored blocks / structural blocks (0 for an absent operator). */
 int amg_level_padding(amg_handle h, int32_t level, double *pad3);

@@ -79,6 +79,7 @@ class BatchDesc(ctypes.Structure):
 EXPORTED = ["amg_params_default", "amg_setup", "amg_apply_vcycle", "amg_solve", "amg_get_stats",
             "amg_level_info", "amg_level_export", "amg_free", "amg_last_error", "amg_bsr_spmv",
             "amg_bsr_spmv_dot", "amg_kernel_launches", "amg_level_spmv", "amg_level_padding",
+            "amg_level_galerkin",
             "amg_batch_setup", "amg_batch_solve", "amg_batch_info", "amg_batch_free",
             "amg_set_learned_smoother", "amg_clear_learned_smoother", "amg_trainer_create",
             "amg_trainer_add_samples", "amg_trainer_add_generated", "amg_trainer_eval",
@@ -117,6 +118,7 @@ def load(build_if_missing: bool = True):
         "amg_kernel_launches": ([], ctypes.c_int64),
         "amg_level_spmv": ([P, i32, i32, P, P, P], ctypes.c_int),
         "amg_level_padding": ([P, i32, P], ctypes.c_int),
+        "amg_level_galerkin": ([P, i32, i32, P, P], ctypes.c_int),
         "amg_batch_setup": ([i32, P, P, P, P, P, P], ctypes.c_int),
         "amg_batch_solve": ([P, P, P, d, i32, P, P, P], ctypes.c_int),
         "amg_batch_info": ([P, P], ctypes.c_int),
@@ -298,6 +300,14 @@ class AMG:
         _check(self._lib.amg_level_spmv(self._h, l, which, _dptr(x, torch.float64, "x"),
                                         _dptr(y, torch.float64, "y"), _stream(stream)))
         return y
+
+    def galerkin_timing(self, l: int, storage: int = STORAGE_BLOCK) -> tuple:
+        """(seconds, relative difference) of A_{l+1} = R_l (A_l P_l) recomputed in
+        block or scalar storage, against the hierarchy's A_{l+1}."""
+        sec, diff = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(self._lib.amg_level_galerkin(self._h, l, storage, ctypes.byref(sec),
+                                            ctypes.byref(diff)))
+        return sec.value, diff.value
 
     def padding(self, l: int) -> tuple:
         out = (ctypes.c_double * 3)()

@@ -260,6 +260,8 @@ int build_transfer(const BsrD &A, const double *B, int ns, const uint8_t *strong
 int unblock_bsr(const BsrD &B, DevArena &mem, cudaStream_t s, BsrD *out);
 int galerkin(const BsrD &A, const BsrD &P, const BsrD &R, DevArena &keep, DevArena &tmp,
              cudaStream_t s, BsrD *Ac);
+int galerkin_scalar(const BsrD &A, const BsrD &P, const BsrD &R, DevArena &keep, DevArena &tmp,
+                    cudaStream_t s, BsrD *Ac);
 int spai0_diag(const BsrD &A, double scale, double *M, cudaStream_t s);
 int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
                    double **Ainv_out);

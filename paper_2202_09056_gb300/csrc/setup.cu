@@ -969,7 +969,8 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
     if (total == 0) return AMG_OK;
     const int xr = X.br, xc = X.bc, yc = Y.bc;
     if (!((xr == 3 && xc == 3 && yc == 6) || (xr == 6 && xc == 6 && yc == 6) ||
-          (xr == 6 && xc == 3 && yc == 6) || (xr == 3 && xc == 3 && yc == 3))) {
+          (xr == 6 && xc == 3 && yc == 6) || (xr == 3 && xc == 3 && yc == 3) ||
+          (xr == 1 && xc == 1 && yc == 1))) {
         set_error("unsupported block product %dx%d * %dx%d", xr, xc, X.bc, yc);
         return AMG_ERR_ARG;
     }
@@ -980,7 +981,7 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
     const int upper = (symmetric && xr == yc && X.nbr == Y.nbc) ? 1 : 0;
     bool done = false;
     const double xlen = X.nbr ? (double)X.nnzb / X.nbr : 0.0;
-    if (X.nbr < 16384 || xlen >= 32.0) {
+    if (X.nbr < 16384 || (xlen >= 32.0 && xr > 1)) {
         // few rows, or long X rows (the restrictions and the coarse A P):
         // one CTA per output row (the shared-memory row must fit)
         int *mx = nullptr, hm[2] = {0, 0};
@@ -995,7 +996,8 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
         AMG_TRY_CUDA(cudaMemcpyAsync(hm, mx, sizeof(hm), cudaMemcpyDeviceToHost, s));
         AMG_TRY_CUDA(cudaStreamSynchronize(s));
         tmp.release(mx);
-        if (xr == 3 && yc == 3) AMG_TRY((spgemm_cta<3, 3, 3>(X, Y, C, hm[0], hm[1], upper, s, &done)));
+        if (xr == 1) AMG_TRY((spgemm_cta<1, 1, 1>(X, Y, C, hm[0], hm[1], upper, s, &done)));
+        else if (xr == 3 && yc == 3) AMG_TRY((spgemm_cta<3, 3, 3>(X, Y, C, hm[0], hm[1], upper, s, &done)));
         else if (xr == 3) AMG_TRY((spgemm_cta<3, 3, 6>(X, Y, C, hm[0], hm[1], upper, s, &done)));
         else if (xc == 6) AMG_TRY((spgemm_cta<6, 6, 6>(X, Y, C, hm[0], hm[1], upper, s, &done)));
         else AMG_TRY((spgemm_cta<6, 3, 6>(X, Y, C, hm[0], hm[1], upper, s, &done)));
@@ -1017,7 +1019,8 @@ static int spgemm(const BsrD &X, const BsrD &Y, DevArena &keep, DevArena &tmp, c
     // an upper product uses about half of each Y row
     const double ylen = (Y.nbr ? (double)Y.nnzb / Y.nbr : 0.0) * (upper ? 0.5 : 1.0);
     const int lanes = ylen <= 8.0 ? 8 : (ylen <= 16.0 ? 16 : 32);
-    if (xr == 3 && yc == 3) AMG_TRY((spgemm_rows<3, 3, 3>(X, Y, C, cmax, lanes, upper, s, &done)));
+    if (xr == 1) AMG_TRY((spgemm_rows<1, 1, 1>(X, Y, C, cmax, lanes, upper, s, &done)));
+    else if (xr == 3 && yc == 3) AMG_TRY((spgemm_rows<3, 3, 3>(X, Y, C, cmax, lanes, upper, s, &done)));
     else if (xr == 3) AMG_TRY((spgemm_rows<3, 3, 6>(X, Y, C, cmax, lanes, upper, s, &done)));
     else if (xc == 6) AMG_TRY((spgemm_rows<6, 6, 6>(X, Y, C, cmax, lanes, upper, s, &done)));
     else AMG_TRY((spgemm_rows<6, 3, 6>(X, Y, C, cmax, lanes, upper, s, &done)));
@@ -1037,7 +1040,8 @@ per_block:
     spgemm_values_kernel<XR_, XC_, YC_><<<g, 128, 0, s>>>(X.row_ptr, X.col, X.val, Y.row_ptr, \
                                                           Y.col, Y.val, cbrow, C->col, total, \
                                                           upper, C->val)
-    if (xr == 3 && yc == 3) AMG_SPGEMM_VALS(3, 3, 3);
+    if (xr == 1) AMG_SPGEMM_VALS(1, 1, 1);
+    else if (xr == 3 && yc == 3) AMG_SPGEMM_VALS(3, 3, 3);
     else if (xr == 3) AMG_SPGEMM_VALS(3, 3, 6);
     else if (xc == 6) AMG_SPGEMM_VALS(6, 6, 6);
     else AMG_SPGEMM_VALS(6, 3, 6);
@@ -1049,7 +1053,9 @@ per_block:
 mirror:
     if (upper) {
         const int mg = nblk((int64_t)X.nbr * 32);
-        if (yc == 3)
+        if (yc == 1)
+            mirror_lower_kernel<1><<<mg, T1D, 0, s>>>(C->row_ptr, C->col, X.nbr, C->val);
+        else if (yc == 3)
             mirror_lower_kernel<3><<<mg, T1D, 0, s>>>(C->row_ptr, C->col, X.nbr, C->val);
         else
             mirror_lower_kernel<6><<<mg, T1D, 0, s>>>(C->row_ptr, C->col, X.nbr, C->val);
@@ -1069,6 +1075,25 @@ int galerkin(const BsrD &A, const BsrD &P, const BsrD &R, DevArena &keep, DevAre
     int st = spgemm(A, P, apmem, tmp, s, &AP);
     if (st >= 0) st = spgemm(R, AP, keep, tmp, s, Ac, true);
     apmem.release_all();
+    return st;
+}
+
+// The same Galerkin product in scalar arithmetic (the scalar setup of the
+// Sec. 4 comparison): A, P and R unblocked to scalar CSR (every entry of
+// their blocks, explicit zeros kept, so the scalar product has the unblocked
+// block product's pattern), then the two SpGEMMs with 1x1 blocks.
+int galerkin_scalar(const BsrD &A, const BsrD &P, const BsrD &R, DevArena &keep, DevArena &tmp,
+                    cudaStream_t s, BsrD *Ac)
+{
+    BsrD uA, uP, uR;
+    DevArena um;
+    um.stream = s;
+    int st = unblock_bsr(A, um, s, &uA);
+    if (st >= 0) st = unblock_bsr(P, um, s, &uP);
+    if (st >= 0) st = unblock_bsr(R, um, s, &uR);
+    if (st >= 0) st = galerkin(uA, uP, uR, keep, tmp, s, Ac);
+    cudaStreamSynchronize(s);
+    um.release_all();
     return st;
 }
 

@@ -1311,6 +1311,62 @@ int amg_level_spmv(amg_handle h, int32_t level, int32_t which, const double *x, 
     return launch_sell<double, double>(S, SPMV_PLAIN, DOT_NONE, a, h->geom, (cudaStream_t)stream);
 }
 
+int amg_level_galerkin(amg_handle h, int32_t level, int32_t storage, double *seconds,
+                       double *rel_diff)
+{
+    clear_error();
+    if (!h || !seconds || !rel_diff || level < 0 || level + 1 >= (int)h->lv.size() ||
+        (storage != AMG_STORAGE_BLOCK && storage != AMG_STORAGE_SCALAR)) {
+        set_error("bad argument (level must have a coarser level)");
+        return AMG_ERR_ARG;
+    }
+    const Level &L = h->lv[level];
+    const BsrD &Ac0 = h->lv[level + 1].A;
+    cudaStream_t s = h->stream;
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    DevArena keep, tmp;
+    keep.stream = tmp.stream = s;
+    BsrD C;
+    const auto t0 = std::chrono::steady_clock::now();
+    int st = storage == AMG_STORAGE_SCALAR ? galerkin_scalar(L.A, L.P, L.R, keep, tmp, s, &C)
+                                           : galerkin(L.A, L.P, L.R, keep, tmp, s, &C);
+    if (st >= 0 && cudaStreamSynchronize(s) != cudaSuccess) st = AMG_ERR_CUDA;
+    *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    // compare with the hierarchy's A_{l+1} (unblocked for the scalar product)
+    BsrD ref = Ac0;
+    if (st >= 0 && storage == AMG_STORAGE_SCALAR) st = unblock_bsr(Ac0, tmp, s, &ref);
+    if (st >= 0) {
+        const int64_t nv = ref.nnzb * ref.br * ref.bc;
+        std::vector<int> rp1(ref.nbr + 1), rp2(C.nbr + 1), c1(std::max<int64_t>(ref.nnzb, 1)),
+            c2(std::max<int64_t>(C.nnzb, 1));
+        std::vector<double> v1(std::max<int64_t>(nv, 1)), v2(std::max<int64_t>(nv, 1));
+        *rel_diff = -1.0;  // patterns differ
+        if (C.nbr == ref.nbr && C.nnzb == ref.nnzb && C.br == ref.br && C.bc == ref.bc) {
+            cudaMemcpyAsync(rp1.data(), ref.row_ptr, sizeof(int) * (ref.nbr + 1), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(rp2.data(), C.row_ptr, sizeof(int) * (C.nbr + 1), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(c1.data(), ref.col, sizeof(int) * ref.nnzb, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(c2.data(), C.col, sizeof(int) * C.nnzb, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(v1.data(), ref.val, sizeof(double) * nv, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(v2.data(), C.val, sizeof(double) * nv, cudaMemcpyDeviceToHost, s);
+            if (cudaStreamSynchronize(s) != cudaSuccess) st = AMG_ERR_CUDA;
+            if (st >= 0 && rp1 == rp2 && c1 == c2) {
+                double dmax = 0.0, vmax = 0.0;
+                for (int64_t k = 0; k < nv; ++k) {
+                    dmax = std::max(dmax, std::fabs(v1[k] - v2[k]));
+                    vmax = std::max(vmax, std::fabs(v1[k]));
+                }
+                *rel_diff = vmax > 0.0 ? dmax / vmax : dmax;
+            }
+        }
+    }
+    cudaStreamSynchronize(s);
+    keep.release_all();
+    tmp.release_all();
+    if (st < 0) return st;
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
 int amg_level_padding(amg_handle h, int32_t level, double *pad3)
 {
     if (!h || !pad3 || level < 0 || level >= (int)h->lv.size()) return AMG_ERR_ARG;
