@@ -183,6 +183,24 @@ __device__ __forceinline__ double f32_to_f64(float f)
     return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 896) << 52) | m));
 }
 
+// double -> float rounded to nearest (ties to even) on the bits; values
+// outside FP32's normal range are flushed to zero or infinity
+__device__ __forceinline__ float f64_to_f32_rn(double x)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sgn = (unsigned int)(u >> 63) << 31;
+    const int e = (int)((u >> 52) & 0x7ff);
+    const unsigned long long m = u & 0xfffffffffffffull;
+    const int fe = e - 896;  // FP32 biased exponent
+    if (e == 0 || fe <= 0) return __uint_as_float(sgn);
+    if (fe >= 255)
+        return __uint_as_float(sgn | 0x7f800000u | ((e == 0x7ff && m) ? 0x400000u : 0u));
+    unsigned int bits = ((unsigned int)fe << 23) | (unsigned int)(m >> 29);
+    const unsigned long long rem = m & 0x1fffffffull, half = 0x10000000ull;
+    if (rem > half || (rem == half && (bits & 1u))) ++bits;  // a carry may round up to infinity
+    return __uint_as_float(sgn | bits);
+}
+
 struct __align__(8) df32 {
     float h, l;
     __host__ __device__ df32() : h(0.0f), l(0.0f) {}

@@ -38,6 +38,7 @@ struct BSell {
     int *col = nullptr;
     double *val = nullptr;
     df32 *eval = nullptr;        // the same values as FP32 pairs (AMG_PREC_DF64 V-cycle)
+    float *fval = nullptr;       // the same values rounded to FP32 (AMG_PREC_FP32 V-cycle)
     int *s_inst = nullptr, *s_local = nullptr, *s_G = nullptr;
     int *perm = nullptr;         // concatenated slot -> row maps of the sorted parts
     int64_t *s_pbase = nullptr;  // per slice: its first slot in perm, or -1 (natural order)
@@ -50,6 +51,7 @@ struct BArgs {
     const int *col;
     const double *val;
     const df32 *eval;
+    const float *fval;
     const int *s_inst, *s_local, *s_G;
     const int *perm;
     const int64_t *s_pbase;
@@ -64,9 +66,12 @@ struct BArgs {
     double *y, *y2;
 };
 
-template <int BR, int BC, int KT, int MODE, bool DF>
+// VK: values and arithmetic of the block products -- 0 FP64, 1 FP32 pairs
+// (emulated FP64), 2 FP32 (x rounded to FP32, FP32 FMAs); vectors FP64.
+template <int BR, int BC, int KT, int MODE, int VK>
 __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
 {
+    constexpr bool DF = VK == 1, F32 = VK == 2;
     constexpr int BB = BR * BC;
     const int lane = threadIdx.x & 31;
     const int nw = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
@@ -88,7 +93,7 @@ __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
         const int64_t yo = a.yoff[inst];
         for (int k0 = 0; k0 < K; k0 += KT) {
             double acc[BR][KT];
-            float sh[BR][KT], sl[BR][KT];  // FP32-pair accumulators (DF)
+            float sh[BR][KT], sl[BR][KT];  // FP32-pair accumulators (DF); sh alone for F32
 #pragma unroll
             for (int r = 0; r < BR; ++r)
 #pragma unroll
@@ -104,6 +109,32 @@ __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
 #pragma unroll
                     for (int t = 0; t < KT; ++t)
                         xv[c][t] = (k0 + t < K) ? __ldg(xb + ((int64_t)j * BC + c) * K + k0 + t) : 0.0;
+                if constexpr (F32) {
+                    // FP32 values in the FP64 lane-pair layout (one 8-byte
+                    // load per two entries), x rounded to FP32, FP32 FMAs
+                    const float *fg = a.fval + (base + (int64_t)d * 32) * BB;
+                    float vf[BB];
+#pragma unroll
+                    for (int pr = 0; pr < BB / 2; ++pr) {
+                        const float2 t2 = __ldg(reinterpret_cast<const float2 *>(fg + pr * 64) + lane);
+                        vf[2 * pr] = t2.x;
+                        vf[2 * pr + 1] = t2.y;
+                    }
+                    if constexpr (BB % 2 == 1) vf[BB - 1] = __ldg(fg + (BB / 2) * 64 + lane);
+                    float xf[BC][KT];
+#pragma unroll
+                    for (int c = 0; c < BC; ++c)
+#pragma unroll
+                        for (int t = 0; t < KT; ++t) xf[c][t] = f64_to_f32_rn(xv[c][t]);
+#pragma unroll
+                    for (int r = 0; r < BR; ++r)
+#pragma unroll
+                        for (int c = 0; c < BC; ++c)
+#pragma unroll
+                            for (int t = 0; t < KT; ++t)
+                                sh[r][t] = fmaf(vf[r * BC + c], xf[c][t], sh[r][t]);
+                    continue;
+                }
                 if constexpr (DF) {
                     // FP64 emulated on FP32 pairs, as in the single-instance
                     // SELL kernel: hi/lo value pairs in the FP64 lane-pair
@@ -175,6 +206,11 @@ __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
                 for (int r = 0; r < BR; ++r)
 #pragma unroll
                     for (int t = 0; t < KT; ++t) acc[r][t] = f32_to_f64(sh[r][t]) + f32_to_f64(sl[r][t]);
+            if constexpr (F32)
+#pragma unroll
+                for (int r = 0; r < BR; ++r)
+#pragma unroll
+                    for (int t = 0; t < KT; ++t) acc[r][t] = f32_to_f64(sh[r][t]);
             for (int m = G >> 1; m >= 1; m >>= 1)
 #pragma unroll
                 for (int r = 0; r < BR; ++r)
@@ -209,21 +245,19 @@ __global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
 template <int BR, int BC, int MODE>
 static int bspmm_kt(const BSell &S, int kt, const BArgs &a, int grid, cudaStream_t s)
 {
-    const bool df = a.eval != nullptr;
+    const int vk = a.eval ? 1 : (a.fval ? 2 : 0);
+#define AMG_BSPMM(KT_)                                                                        \
+    do {                                                                                      \
+        if (vk == 1) bspmm_kernel<BR, BC, KT_, MODE, 1><<<grid, BT, 0, s>>>(a);               \
+        else if (vk == 2) bspmm_kernel<BR, BC, KT_, MODE, 2><<<grid, BT, 0, s>>>(a);          \
+        else bspmm_kernel<BR, BC, KT_, MODE, 0><<<grid, BT, 0, s>>>(a);                       \
+    } while (0)
     switch (kt) {
-    case 1:
-        if (df) bspmm_kernel<BR, BC, 1, MODE, true><<<grid, BT, 0, s>>>(a);
-        else bspmm_kernel<BR, BC, 1, MODE, false><<<grid, BT, 0, s>>>(a);
-        break;
-    case 2:
-        if (df) bspmm_kernel<BR, BC, 2, MODE, true><<<grid, BT, 0, s>>>(a);
-        else bspmm_kernel<BR, BC, 2, MODE, false><<<grid, BT, 0, s>>>(a);
-        break;
-    default:
-        if (df) bspmm_kernel<BR, BC, 4, MODE, true><<<grid, BT, 0, s>>>(a);
-        else bspmm_kernel<BR, BC, 4, MODE, false><<<grid, BT, 0, s>>>(a);
-        break;
+    case 1: AMG_BSPMM(1); break;
+    case 2: AMG_BSPMM(2); break;
+    default: AMG_BSPMM(4); break;
     }
+#undef AMG_BSPMM
     count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     return AMG_OK;
@@ -246,20 +280,22 @@ static int bspmm_mode(const BSell &S, int kt, int mode, const BArgs &a, int grid
     return AMG_ERR_ARG;
 }
 
-// df: the FP32-pair copy of the values (the V-cycle of an AMG_PREC_DF64 batch)
+// vk: the copy of the values to use -- 0 FP64, 1 FP32 pairs (the V-cycle of
+// an AMG_PREC_DF64 batch), 2 FP32 (the V-cycle of an AMG_PREC_FP32 batch)
 static int launch_bspmm(const BSell &S, int kt, int mode, BArgs a, const Geom &g, cudaStream_t s,
-                        bool df = false)
+                        int vk = 0)
 {
     if (S.nslices == 0) return AMG_OK;
-    if (df && !S.eval) {
-        set_error("no FP32-pair copy of this batched operator");
+    if ((vk == 1 && !S.eval) || (vk == 2 && !S.fval)) {
+        set_error("no reduced copy of this batched operator");
         return AMG_ERR_STATE;
     }
     a.nslices = S.nslices;
     a.slice_ptr = S.slice_ptr;
     a.col = S.col;
     a.val = S.val;
-    a.eval = df ? S.eval : nullptr;
+    a.eval = vk == 1 ? S.eval : nullptr;
+    a.fval = vk == 2 ? S.fval : nullptr;
     a.s_inst = S.s_inst;
     a.s_local = S.s_local;
     a.s_G = S.s_G;
@@ -640,7 +676,7 @@ struct amg_batch_s {
     int maxiter = 0;
     double setup_seconds = 0;
     std::vector<int> kt_choice;          // autotuned RHS tile per (level, operator)
-    bool df = false;                     // V-cycle on FP32-pair values (AMG_PREC_DF64)
+    int vk = 0;                          // V-cycle values: 0 FP64, 1 FP32 pairs, 2 FP32
 };
 
 static BVec bvec(amg_batch h)
@@ -706,7 +742,7 @@ static int record_bvcycle(amg_batch h, const double *f0, double *z0, const int *
             a.x = C.u;
             a.f = f;
             a.y = C.e;
-            AMG_TRY(launch_bspmm(C.A, C.A.kt, SPMV_RESID, a, g, s, h->df));
+            AMG_TRY(launch_bspmm(C.A, C.A.kt, SPMV_RESID, a, g, s, h->vk));
         }
         {  // f_{l+1} = R e ; u_{l+1} = M_{l+1} f_{l+1}
             BArgs a = bargs(h, C, C.voff, N.voff, N.nrows, enable);
@@ -715,7 +751,7 @@ static int record_bvcycle(amg_batch h, const double *f0, double *z0, const int *
             a.y2 = N.u;
             a.M = N.M;
             a.moff = C.moff_next;
-            AMG_TRY(launch_bspmm(C.R, C.R.kt, SPMV_RESTRICT, a, g, s, h->df));
+            AMG_TRY(launch_bspmm(C.R, C.R.kt, SPMV_RESTRICT, a, g, s, h->vk));
         }
         kti += 3;
     }
@@ -737,7 +773,7 @@ static int record_bvcycle(amg_batch h, const double *f0, double *z0, const int *
             a.x = N.z;
             a.u = C.u;
             a.y = C.u;
-            AMG_TRY(launch_bspmm(C.P, C.P.kt, SPMV_AXPY, a, g, s, h->df));
+            AMG_TRY(launch_bspmm(C.P, C.P.kt, SPMV_AXPY, a, g, s, h->vk));
         }
         {  // z = u + M (f - A u)
             BArgs a = bargs(h, C, C.voff, C.voff, C.nrows, enable);
@@ -746,7 +782,7 @@ static int record_bvcycle(amg_batch h, const double *f0, double *z0, const int *
             a.M = C.M;
             a.moff = C.moff;
             a.y = zl;
-            AMG_TRY(launch_bspmm(C.A, C.A.kt, SPMV_SMOOTH, a, g, s, h->df));
+            AMG_TRY(launch_bspmm(C.A, C.A.kt, SPMV_SMOOTH, a, g, s, h->vk));
         }
     }
     return AMG_OK;
@@ -897,6 +933,12 @@ __global__ void to_df32_kernel(const double *__restrict__ v, df32 *__restrict__ 
     if (i < n) e[i] = df32(v[i]);
 }
 
+__global__ void to_f32_kernel(const double *__restrict__ v, float *__restrict__ f, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) f[i] = (float)v[i];
+}
+
 static int concat_sell(amg_batch h, int l, int which, BSell *out)
 {
     cudaStream_t s = h->stream;
@@ -966,11 +1008,14 @@ static int concat_sell(amg_batch h, int l, int which, BSell *out)
                                      cudaMemcpyDeviceToDevice, s));
         at += X.nslots;
     }
-    if (h->df) {  // the values as FP32 pairs, element by element (same layout)
+    if (h->vk) {  // the values as FP32 pairs or FP32, element by element (same layout)
         const int64_t ne = nslots * bb;
-        AMG_TRY(h->mem.alloc_n(&S.eval, (size_t)std::max<int64_t>(ne, 1)));
+        const unsigned grid = (unsigned)((ne + 255) / 256);
+        if (h->vk == 1) AMG_TRY(h->mem.alloc_n(&S.eval, (size_t)std::max<int64_t>(ne, 1)));
+        else AMG_TRY(h->mem.alloc_n(&S.fval, (size_t)std::max<int64_t>(ne, 1)));
         if (ne > 0) {
-            to_df32_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(S.val, S.eval, ne);
+            if (h->vk == 1) to_df32_kernel<<<grid, 256, 0, s>>>(S.val, S.eval, ne);
+            else to_f32_kernel<<<grid, 256, 0, s>>>(S.val, S.fval, ne);
             count_launch(1);
             AMG_TRY_CUDA(cudaGetLastError());
         }
@@ -1002,11 +1047,11 @@ static int autotune_kt(amg_batch h, const BSell &S, const int64_t *xoff, const i
         a.enable = h->all_on;
         a.x = x;
         a.y = y;
-        // an emulated-FP64 batch tunes the tile of the V-cycle's (pair) kernels
-        AMG_TRY(launch_bspmm(S, kt, SPMV_PLAIN, a, h->geom, s, h->df));  // warm-up
+        // a reduced-precision batch tunes the tile of the V-cycle's kernels
+        AMG_TRY(launch_bspmm(S, kt, SPMV_PLAIN, a, h->geom, s, h->vk));  // warm-up
         AMG_TRY_CUDA(cudaEventRecord(e0, s));
         for (int rep = 0; rep < 3; ++rep)
-            AMG_TRY(launch_bspmm(S, kt, SPMV_PLAIN, a, h->geom, s, h->df));
+            AMG_TRY(launch_bspmm(S, kt, SPMV_PLAIN, a, h->geom, s, h->vk));
         AMG_TRY_CUDA(cudaEventRecord(e1, s));
         AMG_TRY_CUDA(cudaEventSynchronize(e1));
         float ms = 0;
@@ -1223,16 +1268,16 @@ int amg_batch_setup(int32_t ninst, const amg_bsr *A, const double *const *B, con
     amg_params p;
     amg_params_default(&p);
     if (prm) p = *prm;
-    if ((p.precision != AMG_PREC_FP64 && p.precision != AMG_PREC_DF64) || p.npre != 1 ||
-        p.npost != 1 || p.smoother != AMG_SMOOTH_SPAI0) {
-        set_error("the batched solve runs FP64 (or emulated-FP64) V(1,1) cycles with the SPAI0 "
-                  "smoother");
+    if (p.precision == AMG_PREC_BF16 || p.npre != 1 || p.npost != 1 ||
+        p.smoother != AMG_SMOOTH_SPAI0) {
+        set_error("the batched solve runs FP64, emulated-FP64 or FP32 V(1,1) cycles with the "
+                  "SPAI0 smoother");
         return AMG_ERR_ARG;
     }
     auto t0 = std::chrono::steady_clock::now();
     amg_batch h = new amg_batch_s();
     h->prm = p;
-    h->df = p.precision == AMG_PREC_DF64;
+    h->vk = p.precision == AMG_PREC_DF64 ? 1 : (p.precision == AMG_PREC_FP32 ? 2 : 0);
     h->stream = (cudaStream_t)stream;
     h->mem.stream = h->stream;
     h->ninst = ninst;
