@@ -787,6 +787,7 @@ def main():
                    "l2": "inputs larger than L2 (fine A values 1.0 GB)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "iterations": its, "rel_resid": res, "setup_s": setup_t, "total_s": step_t,
+        "setup_phases_s": stats["setup_phase_seconds"],
         "operator_complexity": stats["operator_complexity"],
         "sell_padding": [list(solver.padding(l)) for l in range(stats["nlevels"])],
         "memory_mb": stats["bytes_matrices"] / 1e6,

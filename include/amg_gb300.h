@@ -163,6 +163,11 @@ typedef struct {
     int64_t bytes_solve;       /* the solve's operator copies (sliced A_l, P_l, R_l in the
                                   V-cycle's precision and storage, plus the fine FP64 A):
                                   values, column indices, slice pointers, row maps */
+    double setup_phase_seconds[7]; /* wall time of amg_setup by phase, summed over levels:
+                                  0 input copy and pattern check, 1 strength and
+                                  aggregation, 2 transfer operators (tentative QR, omega,
+                                  smoothed P, R), 3 Galerkin products, 4 smoothers (SPAI0,
+                                  ILU(0)), 5 coarsest factor, 6 solve copies and vectors */
 } amg_stats;
 
 /* Fill *prm with the defaults listed above.  Returns AMG_OK. */

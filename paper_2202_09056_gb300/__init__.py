@@ -66,7 +66,10 @@ class Stats(ctypes.Structure):
                 ("bytes_total", ctypes.c_int64), ("operator_complexity", ctypes.c_double),
                 ("learned", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("learned_lambda", ctypes.c_double), ("spai0_lambda", ctypes.c_double),
-                ("bytes_solve", ctypes.c_int64)]
+                ("bytes_solve", ctypes.c_int64), ("setup_phase_seconds", ctypes.c_double * 7)]
+
+SETUP_PHASES = ("input", "strength_aggregation", "transfer", "galerkin", "smoothers", "coarse",
+                "solve_copies")
 
 
 class BatchDesc(ctypes.Structure):
@@ -266,7 +269,9 @@ class AMG:
     def stats(self) -> dict:
         s = Stats()
         _check(self._lib.amg_get_stats(self._h, ctypes.byref(s)))
-        return {k: getattr(s, k) for k, _ in Stats._fields_}
+        out = {k: getattr(s, k) for k, _ in Stats._fields_}
+        out["setup_phase_seconds"] = dict(zip(SETUP_PHASES, list(s.setup_phase_seconds)))
+        return out
 
     def level_info(self, l: int) -> dict:
         d = LevelDesc()

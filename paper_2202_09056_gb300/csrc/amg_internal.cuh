@@ -345,6 +345,7 @@ struct amg_handle_s {
     cudaGraphExec_t exec = nullptr;
     long long body_kernels = 0;   // kernels in one iteration of the graph body
     double setup_seconds = 0.0;
+    double setup_phase[7] = {0, 0, 0, 0, 0, 0, 0};  // see amg_stats.setup_phase_seconds
     int learned = 0;              // level 0 smooths with the learned blocks
     int ilu = 0;                  // every smoothing level uses its block ILU(0)
     double learned_lambda = 0.0;  // estimated lambda_max(M A) of the learned smoother

@@ -746,6 +746,14 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         ~TmpGuard() { t.release_all(); }
     } guard{tmp};
     AMG_TRY(query_geom(&h->geom));
+    // wall time per setup phase (each lap ends with the stream synchronised)
+    auto tp = std::chrono::steady_clock::now();
+    auto lap = [&](int k) {
+        cudaStreamSynchronize(s);
+        const auto t = std::chrono::steady_clock::now();
+        h->setup_phase[k] += std::chrono::duration<double>(t - tp).count();
+        tp = t;
+    };
     {  // level 0: own copy of A and B
         Level L0;
         BsrD &A = L0.A;
@@ -806,6 +814,7 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         }
         h->lv.push_back(L0);
     }
+    lap(0);
     for (;;) {
         Level &C = h->lv.back();
         const int nn = C.A.nbr, n = C.n();
@@ -834,10 +843,12 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
             AMG_TRY_CUDA(cudaStreamSynchronize(s));
             AMG_TRY(aggregate_host(nn, rp.data(), cl.data(), sf.data(), agg.data(), &nagg));
         }
+        lap(1);
         if (nagg == 0 || (double)nagg >= 0.9 * (double)nn) break;
         LevelBuild lb;
         AMG_TRY(build_transfer(C.A, C.B, h->ns, C.strong, agg.data(), nagg, prm.relax, h->mem, tmp, s,
                                &lb));
+        lap(2);
         C.P = lb.P;
         C.R = lb.R;
         C.agg = lb.agg;
@@ -846,20 +857,24 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         C.rho = lb.rho;
         Level N;
         AMG_TRY(galerkin(C.A, C.P, C.R, h->mem, tmp, s, &N.A));
+        lap(3);
         N.B = lb.Bc;
         N.eps = C.eps * 0.5;
         AMG_TRY(h->mem.alloc_n(&C.M, (size_t)std::max(n, 1)));
         AMG_TRY(spai0_diag(C.A, prm.smooth_relax, C.M, s));
+        lap(4);
         h->lv.push_back(N);
     }
     Level &Cc = h->lv.back();
     Cc.coarsest = true;
     AMG_TRY(coarse_inverse(Cc.A, h->mem, tmp, s, &h->Ainv));
     h->nc = Cc.n();
+    lap(5);
     if (prm.smoother == AMG_SMOOTH_ILU0) {  // block ILU(0) of every smoothing level
         for (size_t l = 0; l + 1 < h->lv.size(); ++l)
             AMG_TRY(ilu0_factor(h->lv[l].A, h->max_lanes, h->mem, tmp, s, &h->lv[l].ilu));
         h->ilu = 1;
+        lap(4);
     }
     // V-cycle operators in the sliced layout, in the V-cycle's precision; the
     // fine A is also kept in FP64 for the CG products.
@@ -957,6 +972,7 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
     AMG_TRY(h->mem.alloc_n(&h->st, 1));
     AMG_TRY_CUDA(cudaMallocHost((void **)&h->st_h, sizeof(CgState)));
     AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    lap(6);
     return AMG_OK;
 }
 
@@ -1193,6 +1209,7 @@ int amg_get_stats(amg_handle h, amg_stats *out)
               sell_bytes(L.fP) + sell_bytes(L.fR) + sell_bytes(L.bA) + sell_bytes(L.bP) +
               sell_bytes(L.bR) + sell_bytes(L.eA) + sell_bytes(L.eP) + sell_bytes(L.eR);
     out->bytes_solve = sb;
+    for (int k = 0; k < 7; ++k) out->setup_phase_seconds[k] = h->setup_phase[k];
     out->spai0_lambda = h->spai0_lambda;
     return AMG_OK;
 }
