@@ -1321,6 +1321,89 @@ __global__ void chol_update_kernel(double *__restrict__ D, int n, int j)
     D[(int64_t)i * n + k] -= D[(int64_t)i * n + j] * D[(int64_t)k * n + j];
 }
 
+// Blocked right-looking Cholesky in panels of CHOL_NB columns: the panel's
+// diagonal block factored by one CTA, the rows below it by a triangular solve
+// (one thread per row), then the trailing lower triangle updated by a tiled
+// rank-CHOL_NB product.  A zero row (a dropped near-nullspace column) gets a
+// unit pivot; a pivot <= 0 elsewhere records its column in *err.
+constexpr int CHOL_NB = 32;
+constexpr int CHOL_TILE = 16;
+
+__global__ void __launch_bounds__(256) chol_diag_kernel(double *__restrict__ D, int n, int c0,
+                                                        int nb, const uint8_t *__restrict__ zrow,
+                                                        int *__restrict__ err)
+{
+    __shared__ double blk[CHOL_NB][CHOL_NB + 1];
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        const int r = t / nb, c = t % nb;
+        blk[r][c] = c <= r ? D[(int64_t)(c0 + r) * n + c0 + c] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (threadIdx.x == 0) {
+            double s = blk[j][j];
+            if (zrow[c0 + j]) s = 1.0;
+            if (!(s > 0.0)) {
+                atomicExch(err, c0 + j + 1);
+                s = 1.0;
+            }
+            blk[j][j] = sqrt(s);
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) blk[i][j] /= blk[j][j];
+        __syncthreads();
+        const int m = nb - j - 1;
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+            const int i = j + 1 + t / m, k = j + 1 + t % m;
+            if (k <= i) blk[i][k] -= blk[i][j] * blk[k][j];
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        const int r = t / nb, c = t % nb;
+        if (c <= r) D[(int64_t)(c0 + r) * n + c0 + c] = blk[r][c];
+    }
+}
+
+// rows i >= c0 + nb of the panel: L21[i, :] L11^T = A21[i, :]
+__global__ void chol_trsm_kernel(double *__restrict__ D, int n, int c0, int nb)
+{
+    const int i = c0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double *row = D + (int64_t)i * n + c0;
+    double l[CHOL_NB];
+    for (int t = 0; t < nb; ++t) {
+        const double *lt = D + (int64_t)(c0 + t) * n + c0;
+        double v = row[t];
+        for (int q = 0; q < t; ++q) v -= l[q] * lt[q];
+        l[t] = v / lt[t];
+    }
+    for (int t = 0; t < nb; ++t) row[t] = l[t];
+}
+
+// trailing update D[i][k] -= sum_t L21[i][t] L21[k][t], c1 <= k <= i < n,
+// one CHOL_TILE x CHOL_TILE tile per CTA (tiles above the diagonal skipped)
+__global__ void __launch_bounds__(CHOL_TILE * CHOL_TILE) chol_syrk_kernel(double *__restrict__ D,
+                                                                         int n, int c0, int nb)
+{
+    const int c1 = c0 + nb;
+    const int ti = blockIdx.y, tk = blockIdx.x;
+    if (tk > ti) return;
+    __shared__ double li[CHOL_TILE][CHOL_NB + 1], lk[CHOL_TILE][CHOL_NB + 1];
+    const int i0 = c1 + ti * CHOL_TILE, k0 = c1 + tk * CHOL_TILE;
+    for (int t = threadIdx.y * CHOL_TILE + threadIdx.x; t < CHOL_TILE * nb; t += CHOL_TILE * CHOL_TILE) {
+        const int r = t / nb, c = t % nb;
+        li[r][c] = i0 + r < n ? D[(int64_t)(i0 + r) * n + c0 + c] : 0.0;
+        lk[r][c] = k0 + r < n ? D[(int64_t)(k0 + r) * n + c0 + c] : 0.0;
+    }
+    __syncthreads();
+    const int i = i0 + threadIdx.y, k = k0 + threadIdx.x;
+    if (i >= n || k > i) return;
+    double v = 0.0;
+    for (int t = 0; t < nb; ++t) v += li[threadIdx.y][t] * lk[threadIdx.x][t];
+    D[(int64_t)i * n + k] -= v;
+}
+
 // X[:, k] = A^{-1} e_k by forward/backward substitution with L (lower
 // triangle of D), one CTA per column; zero rows give zero rows/columns.
 __global__ void chol_inverse_kernel(const double *__restrict__ D, int n,
@@ -1376,10 +1459,16 @@ int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
         densify_kernel<<<nblk(A.nnzb), T1D, 0, s>>>(brow, A.col, A.val, A.nnzb, A.br, n, D); ::amg::count_launch(1); }
     zero_rows_kernel<<<nblk(n), T1D, 0, s>>>(D, n, z); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
-    for (int j = 0; j < n; ++j) {
-        chol_column_kernel<<<1, 256, 0, s>>>(D, n, j, z, err); ::amg::count_launch(1);
-        const int64_t m = (int64_t)(n - j - 1) * (n - j - 1);
-        if (m > 0) { chol_update_kernel<<<nblk(m), T1D, 0, s>>>(D, n, j); ::amg::count_launch(1); }
+    for (int c0 = 0; c0 < n; c0 += CHOL_NB) {
+        const int nb = std::min(CHOL_NB, n - c0), rest = n - c0 - nb;
+        chol_diag_kernel<<<1, 256, 0, s>>>(D, n, c0, nb, z, err);
+        ::amg::count_launch(1);
+        if (rest > 0) {
+            chol_trsm_kernel<<<nblk(rest, 128), 128, 0, s>>>(D, n, c0, nb);
+            const int nt = (rest + CHOL_TILE - 1) / CHOL_TILE;
+            chol_syrk_kernel<<<dim3(nt, nt), dim3(CHOL_TILE, CHOL_TILE), 0, s>>>(D, n, c0, nb);
+            ::amg::count_launch(2);
+        }
     }
     AMG_TRY_CUDA(cudaGetLastError());
     int herr = 0;
