@@ -1291,36 +1291,6 @@ __global__ void zero_rows_kernel(const double *__restrict__ D, int n, uint8_t *_
     z[i] = zr;
 }
 
-// Right-looking Cholesky, column j: pivot and scaled column below it.
-__global__ void chol_column_kernel(double *__restrict__ D, int n, int j,
-                                   const uint8_t *__restrict__ zrow, int *__restrict__ err)
-{
-    __shared__ double ljj;
-    if (threadIdx.x == 0) {
-        double s = D[(int64_t)j * n + j];
-        if (zrow[j]) s = 1.0;
-        if (!(s > 0.0)) {
-            atomicExch(err, j + 1);
-            s = 1.0;
-        }
-        ljj = sqrt(s);
-        D[(int64_t)j * n + j] = ljj;
-    }
-    __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) D[(int64_t)i * n + j] /= ljj;
-}
-
-// trailing update D[i][k] -= L[i][j] L[k][j] for j < k <= i < n
-__global__ void chol_update_kernel(double *__restrict__ D, int n, int j)
-{
-    const int m = n - j - 1;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)m * m) return;
-    const int i = j + 1 + (int)(t / m), k = j + 1 + (int)(t % m);
-    if (k > i) return;
-    D[(int64_t)i * n + k] -= D[(int64_t)i * n + j] * D[(int64_t)k * n + j];
-}
-
 // Blocked right-looking Cholesky in panels of CHOL_NB columns: the panel's
 // diagonal block factored by one CTA, the rows below it by a triangular solve
 // (one thread per row), then the trailing lower triangle updated by a tiled
