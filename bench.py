@@ -346,11 +346,15 @@ def ilu0_form(amg, torch, dev_args, f, tol, u_ref, fp64, p, stream, steps, sweep
         sol = amg.AMG(*hargs, **kw)
         torch.cuda.synchronize()
         setup = time.perf_counter() - t0
-        t, it, res, st, _ = _timed_solves(torch, sol, fh, tol, steps, 5000, stream)
-        homog[name] = {"value": t, "iterations": it, "rel_resid": res, "status": st,
-                       "setup_s": setup}
+        try:
+            t, it, res, st, _ = _timed_solves(torch, sol, fh, tol, steps, 5000, stream)
+            homog[name] = {"value": t, "iterations": it, "rel_resid": res, "status": st,
+                           "setup_s": setup}
+        except amg.AmgError as e:  # the Jacobi-swept ILU(0) can break CG down
+            homog[name] = {"value": None, "status": e.status, "error": str(e), "setup_s": setup}
         del sol
-    homog["ilu0_speedup"] = homog["spai0"]["value"] / homog["ilu0"]["value"]
+    if homog["ilu0"]["value"] and homog["spai0"]["value"]:
+        homog["ilu0_speedup"] = homog["spai0"]["value"] / homog["ilu0"]["value"]
     out["homogeneous"] = homog
     return out
 

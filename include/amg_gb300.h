@@ -183,7 +183,8 @@ int amg_params_default(amg_params *prm);
  * checked on the device before any other kernel reads it: row pointers
  * within [0, nnzb] and non-decreasing, columns ascending and in range, a
  * diagonal block in every row, and a symmetric pattern; a violation returns
- * AMG_ERR_ARG naming the lowest offending block row. */
+ * AMG_ERR_ARG naming the lowest offending block row.  A NaN or infinite
+ * value in A or B also returns AMG_ERR_ARG. */
 int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params *prm,
               void *stream, amg_handle *out);
 
@@ -198,8 +199,9 @@ int amg_apply_vcycle(amg_handle h, const double *r, double *z, void *stream);
  * node) until the recurrence residual ||r||/||f|| <= tol is confirmed by the
  * true residual, or maxiter iterations.  *iters (host) receives the number
  * of A*p products and *rel_resid (host) the final true relative residual
- * ||f - A u|| / ||f||.  Returns AMG_OK, AMG_NOT_CONVERGED or an error; the
- * call synchronises `stream`. */
+ * ||f - A u|| / ||f||.  Returns AMG_OK, AMG_NOT_CONVERGED or an error
+ * (AMG_ERR_ARG before any iteration when f or u holds a NaN or infinite
+ * value); the call synchronises `stream`. */
 int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxiter,
               int32_t *iters, double *rel_resid, void *stream);
 
@@ -314,7 +316,8 @@ int amg_batch_setup(int32_t ninst, const amg_bsr *A, const double *const *B, con
  * contiguous vectors of 3 n_i doubles (U[i]: initial guesses in, solutions
  * out).  iters and rel_resid (host, optional) receive one value per rhs in
  * instance order.  Returns AMG_OK when every rhs converged, AMG_NOT_CONVERGED
- * or an error otherwise.  Synchronises `stream`.  A pair's iterates do not
+ * or an error otherwise (AMG_ERR_ARG, naming the pair, when an f or u holds a
+ * NaN or infinite value).  Synchronises `stream`.  A pair's iterates do not
  * depend on the other pairs of the batch. */
 int amg_batch_solve(amg_batch h, const double *const *F, double *const *U, double tol,
                     int32_t maxiter, int32_t *iters, double *rel_resid, void *stream);

@@ -1359,7 +1359,22 @@ int amg_batch_solve(amg_batch h, const double *const *F, double *const *U, doubl
     AMG_TRY_CUDA(cudaGetLastError());
     int any = 0;
     AMG_TRY_CUDA(cudaMemcpyAsync(&any, st.any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    {  // a non-finite f or u would otherwise read as a zero right-hand side
+        std::vector<double> nf0(h->ngl), res0(h->ngl);
+        AMG_TRY_CUDA(cudaMemcpyAsync(nf0.data(), st.nf, sizeof(double) * h->ngl,
+                                     cudaMemcpyDeviceToHost, s));
+        AMG_TRY_CUDA(cudaMemcpyAsync(res0.data(), st.res, sizeof(double) * h->ngl,
+                                     cudaMemcpyDeviceToHost, s));
+        AMG_TRY_CUDA(cudaStreamSynchronize(s));
+        for (int g = 0; g < h->ngl; ++g)
+            if (!std::isfinite(nf0[g]) || !std::isfinite(res0[g])) {
+                const int i = (int)(std::upper_bound(h->goffh.begin(), h->goffh.end(), g) -
+                                    h->goffh.begin()) - 1;
+                set_error("instance %d, right-hand side %d: f or u holds a non-finite value", i,
+                          g - h->goffh[i]);
+                return AMG_ERR_ARG;
+            }
+    }
     if (any) {
         if (!h->exec || h->tol != tol || h->maxiter != maxiter) {
             h->tol = tol;

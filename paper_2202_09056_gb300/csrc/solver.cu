@@ -687,6 +687,16 @@ void amg::destroy_handle(amg_handle h)
 // Galerkin products rely on it); bad[1] = the lowest offending row.  Rows are
 // first checked on their own (codes 1, 2, 4); only a fully valid pattern is
 // searched for the transposed blocks, so no search reads a bad row.
+// bad[0] |= 16 if any of the n values is NaN or infinite
+__global__ void finite_check_kernel(const double *__restrict__ v, int64_t n, int *__restrict__ bad)
+{
+    int nonfinite = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        nonfinite |= !isfinite(v[i]);
+    if (__any_sync(0xffffffffu, nonfinite) && (threadIdx.x & 31) == 0) atomicOr(bad, 16);
+}
+
 __global__ void validate_symmetry_kernel(const int *__restrict__ rp, const int *__restrict__ col,
                                          int nbr, int *__restrict__ bad)
 {
@@ -792,6 +802,15 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
             ::amg::count_launch(2);
             AMG_TRY_CUDA(cudaGetLastError());
         }
+        {  // non-finite values in A or B
+            const int64_t nv = A.nnzb * 9, nb = (int64_t)A.nbr * 3 * h->ns;
+            const int g1 = (int)std::min<int64_t>((nv + 255) / 256, h->geom.max_ctas);
+            const int g2 = (int)std::min<int64_t>((nb + 255) / 256, h->geom.max_ctas);
+            if (nv > 0) finite_check_kernel<<<g1, 256, 0, s>>>(A.val, nv, bad + 2);
+            if (nb > 0) finite_check_kernel<<<g2, 256, 0, s>>>(L0.B, nb, bad + 2);
+            ::amg::count_launch((nv > 0) + (nb > 0));
+            AMG_TRY_CUDA(cudaGetLastError());
+        }
         int hb[3] = {0, 0, 0};
         AMG_TRY_CUDA(cudaMemcpyAsync(hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, s));
         AMG_TRY_CUDA(cudaStreamSynchronize(s));
@@ -810,6 +829,10 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         }
         if (hb[2] & 8) {
             set_error("the block pattern is not symmetric (block row %d)", hb[1]);
+            return AMG_ERR_ARG;
+        }
+        if (hb[2] & 16) {
+            set_error("A or B holds a non-finite value");
             return AMG_ERR_ARG;
         }
         h->lv.push_back(L0);
@@ -1124,6 +1147,10 @@ int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxi
     AMG_TRY_CUDA(cudaMemcpyAsync(h->st_h, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
     AMG_TRY_CUDA(cudaStreamSynchronize(s));
     int status;
+    if (!std::isfinite(h->st_h->nf) || !std::isfinite(h->st_h->res)) {
+        set_error("f or the initial guess u holds a non-finite value");
+        return AMG_ERR_ARG;
+    }
     if (h->st_h->nf == 0.0) {
         AMG_TRY_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, s));
         AMG_TRY_CUDA(cudaStreamSynchronize(s));

@@ -418,3 +418,38 @@ def test_setup_rejects_malformed_patterns():
         amg.AMG(torch.from_numpy(rp).to(d), torch.from_numpy(cl).to(d),
                 torch.from_numpy(np.delete(val0, a, axis=0)).to(d), torch.from_numpy(B0).to(d))
     assert "not symmetric" in str(e.value) and "block row 2" in str(e.value)
+
+
+def test_non_finite_inputs_are_rejected():
+    """A NaN or infinity in f or in the initial guess is an argument error
+    before any iteration (a NaN norm must not read as a zero right-hand side),
+    and the handle stays usable; a NaN in A or B fails the setup's input
+    check; a NaN right-hand side in a batch names its pair."""
+    p = q.make_problem((6, 5, 7), traction=(0, 0, -1), inclusion_frac=0.2)
+    rp, cl, val, B = _dev(p)
+    G = amg.AMG(rp, cl, val, B, coarse_enough=60)
+    fb = torch.from_numpy(p.f).cuda()
+    for bad_f, bad_u in ((float("nan"), None), (float("inf"), None), (None, float("nan"))):
+        f, u = fb.clone(), torch.zeros_like(fb)
+        if bad_f is not None:
+            f[17] = bad_f
+        if bad_u is not None:
+            u[5] = bad_u
+        with pytest.raises(amg.AmgError) as e:
+            G.solve(f, u=u)
+        assert e.value.status == amg.AMG_ERR_ARG
+    u, it, res, st = G.solve(fb)
+    assert st == amg.AMG_OK and res <= 1e-8
+    for arr, idx in ((val, (int(rp[p.nnodes // 2]) + 1, 0, 0)), (B, (4, 2))):
+        bad = arr.clone()
+        bad[idx] = float("nan")
+        args = (rp, cl, bad, B) if arr is val else (rp, cl, val, bad)
+        with pytest.raises(amg.AmgError) as e:
+            amg.AMG(*args, coarse_enough=60)
+        assert e.value.status == amg.AMG_ERR_ARG
+    bat = amg.AMGBatch([(rp, cl, val)], [B], [2], coarse_enough=60)
+    F = torch.stack([fb, fb])
+    F[1, 3] = float("nan")
+    with pytest.raises(amg.AmgError) as e:
+        bat.solve([F])
+    assert e.value.status == amg.AMG_ERR_ARG and "right-hand side 1" in str(e.value)
