@@ -220,7 +220,7 @@ def learned_form(amg, torch, solver, f, tol, u_ref, t_spai0, it_spai0, steps):
     """Learned smoother: train the block-smoother network on the GPU on four
     smaller meshes of the same material model (error samples the SPAI0
     V-cycle leaves, and white noise), then solve the benchmark system with it
-    in place of SPAI0 on level 0; SPAI0 stays the fallback and the judge."""
+    in place of SPAI0 on level 0; SPAI0 stays the fallback and the yardstick."""
     import q1elasticity as q
     dev = f.device
     s = torch.cuda.current_stream()
@@ -801,7 +801,7 @@ def main():
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "kernel": kernel_tag, "achieved": tflops,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
-                     "traffic": traffic, "peak_source": "derived (FP64 pipe, see DESIGN.md)",
+                     "traffic": traffic, "peak_source": "derived: 152 SMs x 2 DFMA/clock x 2 flop x 2.07 GHz (FP64 pipe)",
                      "algorithmic_flops": flops, "launch_ms": 1e3 * t_spmv,
                      "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_kind,
