@@ -1355,6 +1355,32 @@ int amg_level_spmv(amg_handle h, int32_t level, int32_t which, const double *x, 
     return launch_sell<double, double>(S, SPMV_PLAIN, DOT_NONE, a, h->geom, (cudaStream_t)stream);
 }
 
+// Element-wise comparison of two matrices with the same shape: red[0] = 1 if
+// the row pointers or columns differ; red[1], red[2] = the bits of the
+// largest |a - b| and |a| (non-negative doubles order like their bits).
+__global__ void compare_bsr_kernel(const int *__restrict__ rp1, const int *__restrict__ rp2,
+                                   int64_t nrp, const int *__restrict__ c1,
+                                   const int *__restrict__ c2, int64_t nc,
+                                   const double *__restrict__ v1, const double *__restrict__ v2,
+                                   int64_t nv, unsigned long long *__restrict__ red)
+{
+    double dm = 0.0, am = 0.0;
+    int diff = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv || i < nc || i < nrp;
+         i += stride) {
+        if (i < nrp) diff |= rp1[i] != rp2[i];
+        if (i < nc) diff |= c1[i] != c2[i];
+        if (i < nv) {
+            dm = fmax(dm, fabs(v1[i] - v2[i]));
+            am = fmax(am, fabs(v1[i]));
+        }
+    }
+    if (diff) atomicOr(&red[0], 1ull);
+    atomicMax(&red[1], (unsigned long long)__double_as_longlong(dm));
+    atomicMax(&red[2], (unsigned long long)__double_as_longlong(am));
+}
+
 int amg_level_galerkin(amg_handle h, int32_t level, int32_t storage, double *seconds,
                        double *rel_diff)
 {
@@ -1376,30 +1402,35 @@ int amg_level_galerkin(amg_handle h, int32_t level, int32_t storage, double *sec
                                            : galerkin(L.A, L.P, L.R, keep, tmp, s, &C);
     if (st >= 0 && cudaStreamSynchronize(s) != cudaSuccess) st = AMG_ERR_CUDA;
     *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    // compare with the hierarchy's A_{l+1} (unblocked for the scalar product)
+    // compare with the hierarchy's A_{l+1} (unblocked for the scalar product),
+    // on the device: pattern flag, largest |difference| and largest |entry|
     BsrD ref = Ac0;
     if (st >= 0 && storage == AMG_STORAGE_SCALAR) st = unblock_bsr(Ac0, tmp, s, &ref);
     if (st >= 0) {
-        const int64_t nv = ref.nnzb * ref.br * ref.bc;
-        std::vector<int> rp1(ref.nbr + 1), rp2(C.nbr + 1), c1(std::max<int64_t>(ref.nnzb, 1)),
-            c2(std::max<int64_t>(C.nnzb, 1));
-        std::vector<double> v1(std::max<int64_t>(nv, 1)), v2(std::max<int64_t>(nv, 1));
         *rel_diff = -1.0;  // patterns differ
         if (C.nbr == ref.nbr && C.nnzb == ref.nnzb && C.br == ref.br && C.bc == ref.bc) {
-            cudaMemcpyAsync(rp1.data(), ref.row_ptr, sizeof(int) * (ref.nbr + 1), cudaMemcpyDeviceToHost, s);
-            cudaMemcpyAsync(rp2.data(), C.row_ptr, sizeof(int) * (C.nbr + 1), cudaMemcpyDeviceToHost, s);
-            cudaMemcpyAsync(c1.data(), ref.col, sizeof(int) * ref.nnzb, cudaMemcpyDeviceToHost, s);
-            cudaMemcpyAsync(c2.data(), C.col, sizeof(int) * C.nnzb, cudaMemcpyDeviceToHost, s);
-            cudaMemcpyAsync(v1.data(), ref.val, sizeof(double) * nv, cudaMemcpyDeviceToHost, s);
-            cudaMemcpyAsync(v2.data(), C.val, sizeof(double) * nv, cudaMemcpyDeviceToHost, s);
-            if (cudaStreamSynchronize(s) != cudaSuccess) st = AMG_ERR_CUDA;
-            if (st >= 0 && rp1 == rp2 && c1 == c2) {
-                double dmax = 0.0, vmax = 0.0;
-                for (int64_t k = 0; k < nv; ++k) {
-                    dmax = std::max(dmax, std::fabs(v1[k] - v2[k]));
-                    vmax = std::max(vmax, std::fabs(v1[k]));
+            unsigned long long *red = nullptr;  // [0] pattern differs, [1] max |d|, [2] max |a|
+            if (tmp.alloc_n(&red, 3) < 0) st = AMG_ERR_CUDA;
+            if (st >= 0) {
+                const int64_t nv = ref.nnzb * ref.br * ref.bc;
+                const int64_t nidx = std::max<int64_t>(ref.nnzb, (int64_t)ref.nbr + 1);
+                const int grid = (int)std::min<int64_t>((std::max(nv, nidx) + 255) / 256,
+                                                        h->geom.max_ctas);
+                cudaMemsetAsync(red, 0, sizeof(unsigned long long) * 3, s);
+                compare_bsr_kernel<<<std::max(grid, 1), 256, 0, s>>>(
+                    ref.row_ptr, C.row_ptr, ref.nbr + 1, ref.col, C.col, ref.nnzb, ref.val, C.val,
+                    nv, red);
+                count_launch(1);
+                unsigned long long hr[3] = {0, 0, 0};
+                if (cudaMemcpyAsync(hr, red, sizeof(hr), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess)
+                    st = AMG_ERR_CUDA;
+                if (st >= 0 && !hr[0]) {
+                    double dmax, vmax;
+                    std::memcpy(&dmax, &hr[1], sizeof dmax);
+                    std::memcpy(&vmax, &hr[2], sizeof vmax);
+                    *rel_diff = vmax > 0.0 ? dmax / vmax : dmax;
                 }
-                *rel_diff = vmax > 0.0 ? dmax / vmax : dmax;
             }
         }
     }
