@@ -17,7 +17,12 @@
  *     here it is built per aggregate inside block-structured kernels (the
  *     paper's "NS Block" route, Sec. 3, Listing 2 semantics).
  *   - Sec. 4: conjugate gradients preconditioned by one V-cycle, stopping at
- *     relative residual 1e-8.
+ *     relative residual 1e-8; the block vs scalar comparison (storage of the
+ *     solve's operators, and the Galerkin product in either arithmetic) and
+ *     the ILU(0) smoother of the paper's experiments.
+ *   - Options the paper does not have: reduced or emulated precision in the
+ *     V-cycle, aggregation on the device (MIS-2), a learned 3x3 smoother and
+ *     a batched solver for many instances and right-hand sides.
  *
  * Conventions for every call:
  *   - Matrix and vector pointers are DEVICE pointers unless a parameter says
@@ -56,7 +61,9 @@ extern "C" {
                                      as hi + lo floats (the FP64 value truncated to ~48 bits),
                                      products and sums in FP32-pair arithmetic (about 2^-45
                                      relative per product), FP64 vectors; the CG's A p, dots
-                                     and true residual stay FP64 */
+                                     and true residual stay FP64.  Not in the paper: an
+                                     implementation choice for GB300, whose FP64 rate is
+                                     1/64 of its FP32 rate */
 
 /* Storage of the solve's operators (amg_params.storage).  Sec. 4 compares
  * the block-valued solver with a scalar one ("NS Scalar"): the same
