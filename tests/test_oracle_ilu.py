@@ -117,3 +117,31 @@ def test_findings_homogeneous_cube_and_inclusions():
     Minv = np.stack([F.apply(e, 60) for e in np.eye(pi.ndof)], 1)
     lam = np.linalg.eigvals(Minv @ Ad).real
     assert lam.min() < -0.1
+
+
+def test_zero_dof_row_gets_unit_pivot_and_zero_output():
+    """A DOF whose whole row and column are zero (a coarse DOF whose
+    near-nullspace column was dropped in the QR) gets a unit pivot in its
+    diagonal block's inverse, a zero row and column there, and a zero
+    component in every application; the other DOFs are solved as if it were
+    absent."""
+    A, _ = _chain(5, b=3, seed=4)
+    z = 7                                   # DOF 1 of node 2
+    A[z, :] = 0.0
+    A[:, z] = 0.0
+    n = A.shape[0]
+    ptr, col, val = [0], [], []
+    for i in range(n):
+        for j in range(n):
+            if abs(i // 3 - j // 3) <= 1:
+                col.append(j)
+                val.append(A[i, j])
+        ptr.append(len(col))
+    F = o.ILU0(o.CSR(ptr, col, val, (n, n)), 3)
+    _, _, _, dinv = F.factors()
+    assert np.all(dinv[z // 3][z % 3, :] == 0.0) and np.all(dinv[z // 3][:, z % 3] == 0.0)
+    r = np.random.default_rng(6).standard_normal(n)
+    x = F.apply(r, 5)                       # tridiagonal blocks: exact after 5 sweeps
+    assert x[z] == 0.0
+    keep = np.arange(n) != z
+    np.testing.assert_allclose(A[np.ix_(keep, keep)] @ x[keep], r[keep], atol=1e-11 * np.abs(r).max())
