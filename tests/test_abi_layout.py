@@ -1,0 +1,42 @@
+"""The ctypes mirrors of the C-ABI structs have the header's layout: a C
+program compiled against include/amg_gb300.h prints sizeof and offsetof of
+every field, which must equal the ctypes structures' (no GPU needed; gcc)."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import pytest
+
+import paper_2202_09056_gb300 as amg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+STRUCTS = {"amg_bsr": amg.Bsr, "amg_params": amg.Params, "amg_level_desc": amg.LevelDesc,
+           "amg_stats": amg.Stats, "amg_batch_desc": amg.BatchDesc}
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "amg_gb300.h"',
+             "int main(void) {"]
+    for cname, cls in STRUCTS.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        s, f, v = line.split()
+        got[(s, f)] = int(v)
+    for cname, cls in STRUCTS.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
