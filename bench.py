@@ -155,7 +155,7 @@ def _spmv_roofline(solver, torch, n, nbr, nnzb, reps=40, which=0):
 # command that produced it are in profiles/sell_spmv_3x3_fp64_inclusions48.md
 # (48^3 capture, 245.7 MB, scaled by blocks to the 80^3 launch).  A kernel
 # change gets a new tag and reports null until it is captured again.
-NCU_TRAFFIC = {"sell_spmv_kernel<3,3,double,double,PLAIN,NONE>:G1:v4": 1137203321}
+NCU_TRAFFIC = {"sell_spmv_kernel<3,3,double,double,PLAIN,NONE>:G1:v5": 1136945011}
 
 # FP64 FMA peak of GB300: 152 SMs x 2 DFMA per clock x 2 flop x 2.07 GHz
 # (the nominal 1.25 TFLOP/s FP64 rate at the maximum SM clock).
@@ -640,7 +640,7 @@ def main():
     t_spmv, algo = _spmv_roofline(solver, torch, p.ndof, p.nnodes, p.nnzb)
     peak, peak_kind = _peaks()
     achieved = algo / t_spmv / 1e9
-    kernel_tag = "sell_spmv_kernel<3,3,double,double,PLAIN,NONE>:G1:v4"
+    kernel_tag = "sell_spmv_kernel<3,3,double,double,PLAIN,NONE>:G1:v5"
     traffic = NCU_TRAFFIC.get(kernel_tag)
     flops = 2.0 * 9 * p.nnzb
     tflops = flops / t_spmv / 1e12
