@@ -155,7 +155,9 @@ def _spmv_roofline(solver, torch, n, nbr, nnzb, reps=40, which=0):
 # command that produced it are in profiles/sell_spmv_3x3_fp64_inclusions48.md
 # (48^3 capture, 245.7 MB, scaled by blocks to the 80^3 launch).  A kernel
 # change gets a new tag and reports null until it is captured again.
-NCU_TRAFFIC = {"sell_spmv_kernel<3,3,double,double,PLAIN,NONE>:G1:v5": 1136945011}
+NCU_TRAFFIC = {"sell_spmv_kernel<3,3,double,double,PLAIN,NONE>:G1:v5": 1136945011,
+               # profiles/sell_spmv_3x3_df64_inclusions48.md (246.3 MB at 48^3, scaled)
+               "sell_spmv_kernel<3,3,df32,double,PLAIN,NONE>:G1:v1": 1139997327}
 
 # FP64 FMA peak of GB300: 152 SMs x 2 DFMA per clock x 2 flop x 2.07 GHz
 # (the nominal 1.25 TFLOP/s FP64 rate at the maximum SM clock).
@@ -742,7 +744,10 @@ def main():
             "speedup_vs_fp64": forms["fp64"]["value"] / t_df,
             "err_vs_fp64_solution": float(torch.linalg.norm(u_df - u_ref) / torch.linalg.norm(u_ref)),
             "operator_bytes": int(sol.stats()["bytes_solve"]),
-            "fine_spmv": {"launch_ms": t_sp * 1e3, "achieved_gbs": algo_sp / t_sp / 1e9,
+            "fine_spmv": {"kernel": "sell_spmv_kernel<3,3,df32,double,PLAIN,NONE>:G1:v1",
+                          "traffic": NCU_TRAFFIC.get("sell_spmv_kernel<3,3,df32,double,PLAIN,NONE>:G1:v1"),
+                          "algorithmic_bytes": algo_sp,
+                          "launch_ms": t_sp * 1e3, "achieved_gbs": algo_sp / t_sp / 1e9,
                           "frac_of_measured_hbm": algo_sp / t_sp / 1e9 / peak,
                           "frac_of_nominal_8tbs": algo_sp / t_sp / 8e12},
             "vcycle": "V-cycle in FP64 emulated on FP32 pairs (hi + lo floats, ~2^-45 per "
