@@ -34,16 +34,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "PCG time-to-1e-8 (s); BSR SpMV GB/s vs HBM peak; mixed/learned vs FP64"
-# iterations: the method's PCG iteration count on the workload (the GPU path
-# and the oracle agree on it, +-1, in the parity tests); it scales the
-# oracle's sampled time per iteration to the whole workload
 WORKLOADS = {
-    "inclusions80": dict(n=80, desc="q1-hex-80^3-inclusions-20pct-E1000", tol=1e-8,
-                         iterations=92),
-    "inclusions150": dict(n=150, desc="q1-hex-150^3-inclusions-20pct-E1000", tol=1e-8,
-                          iterations=211),
-    "inclusions120": dict(n=120, desc="q1-hex-120^3-inclusions-20pct-E1000", tol=1e-8,
-                          iterations=91),
+    "inclusions80": dict(n=80, desc="q1-hex-80^3-inclusions-20pct-E1000", tol=1e-8),
+    "inclusions150": dict(n=150, desc="q1-hex-150^3-inclusions-20pct-E1000", tol=1e-8),
+    "inclusions120": dict(n=120, desc="q1-hex-120^3-inclusions-20pct-E1000", tol=1e-8),
     "inclusions64": dict(n=64, desc="q1-hex-64^3-inclusions-20pct-E1000", tol=1e-8),
     "inclusions48": dict(n=48, desc="q1-hex-48^3-inclusions-20pct-E1000", tol=1e-8),
     "inclusions40": dict(n=40, desc="q1-hex-40^3-inclusions-20pct-E1000", tol=1e-8),
@@ -151,64 +145,120 @@ def _spmv_roofline(solver, torch, n, nbr, nnzb, reps=40, which=0):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel from ncu, keyed by kernel version; the summary and the
-# command that produced it are in profiles/sell_spmv_3x3_fp64_inclusions48.md
-# (48^3 capture, 245.7 MB, scaled by blocks to the 80^3 launch).  A kernel
-# change gets a new tag and reports null until it is captured again.
+# dominant kernel from one ncu capture at 48^3, scaled by blocks to the 80^3
+# launch, keyed by kernel version.  A kernel change gets a new tag and
+# reports null until it is captured again.
 NCU_TRAFFIC = {"sell_spmv_kernel<3,3,double,double,PLAIN,NONE>:G1:v5": 1136945011,
-               # profiles/sell_spmv_3x3_df64_inclusions48.md (246.3 MB at 48^3, scaled)
                "sell_spmv_kernel<3,3,df32,double,PLAIN,NONE>:G1:v1": 1139997327}
 
-# FP64 FMA peak of GB300: 152 SMs x 2 DFMA per clock x 2 flop x 2.07 GHz
-# (the nominal 1.25 TFLOP/s FP64 rate at the maximum SM clock).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+def fp64_peak(amg):
+    """Measured FP64 FMA rate (the library's FMA-chain kernel, best of 3) as a
+    TFLOP/s peak with its derivation."""
+    runs = [amg.fp64_fma_rate() for _ in range(3)]
+    best = max(runs, key=lambda r: r["tflops"])
+    return best["tflops"], (f"measured: {best['num_sms']} SMs x 4 CTAs x 256 threads x 8 "
+                            f"independent FP64 FMA chains, best of 3 launches of "
+                            f"{best['seconds'] * 1e3:.1f} ms, 2 flops per FMA")
 
 
-def cpu_baseline(sample_n=40, workload="inclusions80", nnz_full=None):
-    """The oracle, as it stands, on a bounded sample of the workload: the same
-    material model on a sample_n^3 mesh, setup + PCG to 1e-8, single thread.
-    value = the sample's PCG time per iteration per fine-matrix nonzero, times
-    the workload's nonzeros and iterations (the oracle's estimated time on the
-    whole workload, in the metric's unit); the raw sample time beside it."""
+# ------------------------------------------------------------------ CPU baseline (oracle)
+def cpu_leg(workload):
+    """The oracle, as it stands, on the whole workload: its setup (Alg. 1 in
+    scalar CSR) and one PCG solve to 1e-8 from u = 0, single thread.  Both
+    are timed with the host clock."""
     import oracle
-    import q1elasticity as q
-    p = q.inclusions(sample_n)
+    p = _problem(workload)
     A = oracle.from_problem(p)
     t0 = time.perf_counter()
     H = oracle.Hierarchy(A, 3, p.B)
     t1 = time.perf_counter()
-    _, it, rel = H.solve(p.f, tol=1e-8, maxiter=3000)
+    u, it, rel = H.solve(p.f, tol=WORKLOADS[workload]["tol"], maxiter=5000)
     t2 = time.perf_counter()
-    w = WORKLOADS.get(workload, {})
-    if nnz_full is None:  # fine-level blocks of the whole workload
-        nnz_full = _problem(workload).nnzb if workload in WORKLOADS and w.get("n") else p.nnzb
-    it_full = w.get("iterations", it)
-    scale = (nnz_full / p.nnzb) * (it_full / it)
-    return {"value": (t2 - t1) * scale, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle setup+PCG on the same material model at {sample_n}^3 elements "
-                      f"({p.ndof} DOFs, {p.nnzb} blocks, {it} iterations, PCG {t2 - t1:.2f} s, "
-                      f"setup {t1 - t0:.2f} s); value = that PCG time x {nnz_full / p.nnzb:.2f} "
-                      f"(blocks) x {it_full}/{it} (iterations) for the whole workload",
-            "sample_value": t2 - t1, "setup_s": t1 - t0, "iterations": it}
+    return {"setup_s": t1 - t0, "solve_s": t2 - t1, "iterations": int(it), "rel_resid": rel,
+            "u_norm": float(np.linalg.norm(u)), "levels": H.nlevels, "dofs": p.ndof,
+            "nnzb": p.nnzb}
+
+
+def start_cpu_leg(workload):
+    """Run cpu_leg in a child process (this script with --cpu-leg) while the
+    GPU measurements proceed; it uses one host core."""
+    return subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-leg",
+                             "--workload", workload], stdout=subprocess.PIPE,
+                            stderr=subprocess.PIPE, text=True)
+
+
+def finish_cpu_leg(proc, timeout=1200):
+    try:
+        out, err = proc.communicate(timeout=timeout)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        return {"error": f"oracle leg exceeded {timeout} s"}
+    for line in reversed(out.splitlines()):
+        if line.startswith("{"):
+            return json.loads(line)
+    return {"error": "oracle leg failed: " + err.strip()[-300:]}
+
+
+def cpu_baseline_record(leg, gpu_iterations):
+    if "error" in leg:
+        return {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": leg["error"]}
+    return {"value": leg["solve_s"], "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"the whole workload ({leg['dofs']} DOFs, {leg['nnzb']} blocks): one "
+                       f"oracle PCG solve to 1e-8 from u = 0 on its own {leg['levels']}-level "
+                       f"hierarchy, timed with the host clock ({leg['iterations']} iterations; "
+                       f"the oracle's setup took {leg['setup_s']:.1f} s), single thread, run in "
+                       f"a child process beside the GPU measurements"),
+            "setup_s": leg["setup_s"], "total_s": leg["setup_s"] + leg["solve_s"],
+            "iterations": leg["iterations"], "gpu_iterations": gpu_iterations,
+            "rel_resid": leg["rel_resid"]}
+
+
+REF_SAMPLE_ITERS = 3
 
 
 def run_reference(args):
+    """The oracle as the reference arm, on the same workload.  Untimed: its
+    setup and one whole PCG solve to 1e-8 (the oracle's own iteration count
+    and time-to-tolerance).  Each step: a bounded sample, a PCG run of
+    REF_SAMPLE_ITERS iterations from u = 0 on the same hierarchy; the step's
+    value is that time x (the oracle's iterations / REF_SAMPLE_ITERS), in the
+    metric's unit.  ms_per_step is the sample's own duration."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    steps = []
-    base = None
-    for _ in range(args.warmup + args.steps):
-        base = cpu_baseline(args.ref_sample, args.workload)
-        steps.append(base["value"])
-    vals = steps[args.warmup:]
+    import oracle
+    p = _problem(args.workload)
+    A = oracle.from_problem(p)
+    t0 = time.perf_counter()
+    H = oracle.Hierarchy(A, 3, p.B)
+    t1 = time.perf_counter()
+    tol = WORKLOADS[args.workload]["tol"]
+    _, it_full, rel = H.solve(p.f, tol=tol, maxiter=5000)
+    t2 = time.perf_counter()
+    m = min(REF_SAMPLE_ITERS, it_full)
+    vals, secs = [], []
+    for k in range(args.warmup + args.steps):
+        s0 = time.perf_counter()
+        H.solve(p.f, tol=tol, maxiter=m)
+        dt = time.perf_counter() - s0
+        if k >= args.warmup:
+            secs.append(dt)
+            vals.append(dt * it_full / m)
     v = float(np.mean(vals))
+    sample = (f"oracle on the workload itself ({p.ndof} DOFs, {p.nnzb} blocks), single thread: "
+              f"setup {t1 - t0:.1f} s and one whole PCG solve to 1e-8 ({it_full} iterations, "
+              f"{t2 - t1:.1f} s) untimed; each step a {m}-iteration PCG sample on that "
+              f"hierarchy, value = its time x {it_full}/{m}")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * v,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload]["desc"], "parallelism": "replicas"},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": base["sample"], "value": v,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "dofs": p.ndof,
+                       "nnzb": p.nnzb, "parallelism": "single"},
+            "iterations": it_full, "rel_resid": rel, "full_solve_s": t2 - t1,
+            "setup_s": t1 - t0,
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": v,
                              "unit": "s"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -218,21 +268,17 @@ def run_reference(args):
 LEARN_TRAIN = ((20, 11), (26, 12), (32, 13), (40, 14))  # (elements per side, inclusion seed)
 
 
-def learned_form(amg, torch, solver, f, tol, u_ref, t_spai0, it_spai0, steps):
-    """Learned smoother: train the block-smoother network on the GPU on four
-    smaller meshes of the same material model (error samples the SPAI0
-    V-cycle leaves, and white noise), then solve the benchmark system with it
-    in place of SPAI0 on level 0; SPAI0 stays the fallback and the yardstick."""
+def train_learned(amg, torch, dev):
+    """Train the block-smoother network on the GPU on four smaller meshes of
+    the same material model (error samples the SPAI0 V-cycle leaves, and
+    white noise): (weights, training record)."""
     import q1elasticity as q
-    dev = f.device
-    s = torch.cuda.current_stream()
     t0 = time.perf_counter()
     train_solvers = []
     T = amg.Trainer(amg.learned_init(0), lr=3e-3)
     for k, (n, seed) in enumerate(LEARN_TRAIN):
         p = q.inclusions(n, seed=seed)
-        S = amg.AMG(torch.from_numpy(p.row_ptr).to(dev), torch.from_numpy(p.col).to(dev),
-                    torch.from_numpy(p.val).to(dev), torch.from_numpy(p.B).to(dev))
+        S = amg.AMG(*_dev_problem(torch, p, dev))
         T.add_generated(S, 8, seed=100 + k)
         train_solvers.append(S)
     loss0, _ = T.eval()
@@ -245,34 +291,30 @@ def learned_form(amg, torch, solver, f, tol, u_ref, t_spai0, it_spai0, steps):
     w = T.params()
     T.close()
     del train_solvers
+    return w, {"meshes": [f"{n}^3 seed {sd}" for n, sd in LEARN_TRAIN], "samples_per_mesh": 8,
+               "adam_steps": 200, "lr": 3e-3, "loss_before": loss0, "loss_after": loss1,
+               "train_s": t_train, "problem_setup_s": t1 - t0}
+
+
+def learned_form(amg, torch, solver, w, f, tol, u_ref, t_spai0, it_spai0, steps):
+    """The trained network's blocks in place of SPAI0 on level 0 of `solver`
+    (FP64 V-cycle); SPAI0 stays the fallback and the yardstick."""
+    s = torch.cuda.current_stream()
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     fb = solver.set_learned_smoother(w)
     torch.cuda.synchronize()
     t_infer = time.perf_counter() - t2
     st = solver.stats()
-    out = {"training": {"meshes": [f"{n}^3 seed {sd}" for n, sd in LEARN_TRAIN],
-                        "samples_per_mesh": 8, "adam_steps": 200, "lr": 3e-3,
-                        "loss_before": loss0, "loss_after": loss1, "train_s": t_train,
-                        "problem_setup_s": t1 - t0},
-           "inference_s": t_infer, "fallback": fb, "lambda_max_MA": st["learned_lambda"],
+    out = {"inference_s": t_infer, "fallback": fb, "lambda_max_MA": st["learned_lambda"],
            "lambda_max_MA_spai0": st["spai0_lambda"], "spai0_value": t_spai0,
            "spai0_iterations": it_spai0,
            "vcycle": "FP64; level 0 smoothed with learned symmetric 3x3 blocks"}
-    solver.solve(f, tol=tol, maxiter=5000)  # warm-up (graph capture)
-    times = []
-    for _ in range(steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        u_l, it_l, res_l, st_l = solver.solve(f, tol=tol, maxiter=5000)
-        e1.record(s)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1) / 1e3)
+    t, it_l, res_l, st_l, u_l = _timed_solves(torch, solver, f, tol, steps, 5000, s)
     solver.clear_learned_smoother()
-    out.update(value=float(np.mean(times)), iterations=it_l, rel_resid=res_l, status=st_l,
+    out.update(value=t, iterations=it_l, rel_resid=res_l, status=st_l,
                err_vs_fp64_solution=float(torch.linalg.norm(u_l - u_ref) / torch.linalg.norm(u_ref)),
-               speedup_vs_fp64=t_spai0 / float(np.mean(times)))
-    out["weights"] = w
+               speedup_vs_fp64=t_spai0 / t, iterations_gain_vs_spai0=it_spai0 - it_l)
     return out
 
 
@@ -282,21 +324,34 @@ def learned_fp32_form(amg, torch, args_dev, w, f, tol, u_ref, t_fp64, fp32_form,
     s = torch.cuda.current_stream()
     sol = amg.AMG(*args_dev, precision=amg.PREC_FP32)
     fb = sol.set_learned_smoother(w)
-    sol.solve(f, tol=tol, maxiter=5000)  # warm-up (graph capture)
-    times = []
-    for _ in range(steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        u_l, it_l, res_l, st_l = sol.solve(f, tol=tol, maxiter=5000)
-        e1.record(s)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1) / 1e3)
-    v = float(np.mean(times))
+    v, it_l, res_l, st_l, u_l = _timed_solves(torch, sol, f, tol, steps, 5000, s)
+    del sol
     return {"value": v, "iterations": it_l, "rel_resid": res_l, "status": st_l, "fallback": fb,
             "err_vs_fp64_solution": float(torch.linalg.norm(u_l - u_ref) / torch.linalg.norm(u_ref)),
             "speedup_vs_fp64": t_fp64 / v, "speedup_vs_spai0_fp32": fp32_form["value"] / v,
             "spai0_fp32_iterations": fp32_form["iterations"],
             "vcycle": "FP32 matrices and vectors; level 0 smoothed with the learned blocks in FP32"}
+
+
+def _dev_problem(torch, p, dev):
+    return (torch.from_numpy(p.row_ptr).to(dev), torch.from_numpy(p.col).to(dev),
+            torch.from_numpy(p.val).to(dev), torch.from_numpy(p.B).to(dev))
+
+
+def _solve_form(amg, torch, dargs, f, tol, steps, stream, u_ref=None, maxiter=5000, **kw):
+    """Set up a hierarchy with the given parameters (host-clock setup time)
+    and time `steps` solves of it: (record, solver, solution)."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sol = amg.AMG(*dargs, **kw)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t0
+    t, it, res, st, u = _timed_solves(torch, sol, f, tol, steps, maxiter, stream)
+    out = {"value": t, "setup_s": setup, "iterations": it, "rel_resid": res, "status": st,
+           "levels": sol.nlevels, "operator_bytes": int(sol.stats()["bytes_solve"])}
+    if u_ref is not None:
+        out["err_vs_fp64_solution"] = float(torch.linalg.norm(u - u_ref) / torch.linalg.norm(u_ref))
+    return out, sol, u
 
 
 def _timed_solves(torch, sol, f, tol, steps, maxiter, stream):
@@ -500,6 +555,247 @@ def run_batch(args, amg, torch, rank=0, world=1, dist=None, local=0):
     }
 
 
+def paper_memory_bytes(sol, scalar):
+    """The hierarchy's memory in the paper's accounting (Sec. 4 tables):
+    A, P and R of every level in the solve's storage (values FP64, int32
+    column indices and row pointers; scalar CSR stores every entry of the
+    blocks), the smoother diagonal and the coarsest level's dense factor."""
+    st = sol.stats()
+    total = 0
+    for l in range(st["nlevels"]):
+        info = sol.level_info(l)
+        b, nb, ns = info["bs"], info["nbrows"], 6
+        mats = [(info["nnzb_A"], nb, b, b)]
+        if not info["is_coarsest"]:
+            mats += [(info["nnzb_P"], nb, b, ns), (info["nnzb_P"], info["nagg"], ns, b)]
+            total += nb * b * 8  # SPAI0 diagonal
+        for nnzb, rows, br, bc in mats:
+            if scalar:
+                total += nnzb * br * bc * (8 + 4) + (rows * br + 1) * 4
+            else:
+                total += nnzb * (br * bc * 8 + 4) + (rows + 1) * 4
+    return total + st["coarse_n"] ** 2 * 8
+
+
+def paper_variants(amg, torch, dargs, f, tol, stream, steps, u_ref):
+    """Sec. 4's comparison on GB300: NS Scalar (scalar setup, scalar solve),
+    NS Hybrid1 (scalar setup, block solve, Listing 1) and NS Block (block
+    setup and solve, Listing 2's route): setup (median of 3, host clock around
+    amg_setup), solve, total and memory in the paper's accounting."""
+    out = {}
+    for name, kw, scalar in (("ns_scalar", dict(setup=amg.SETUP_SCALAR,
+                                                 storage=amg.STORAGE_SCALAR), True),
+                             ("ns_hybrid1", dict(setup=amg.SETUP_SCALAR), False),
+                             ("ns_block", {}, False)):
+        setups = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sol = amg.AMG(*dargs, **kw)
+            torch.cuda.synchronize()
+            setups.append(time.perf_counter() - t0)
+            phases = sol.stats()["setup_phase_seconds"]
+            del sol
+        rec, sol, _ = _solve_form(amg, torch, dargs, f, tol, steps, stream, u_ref, **kw)
+        rec.update(setup_s=float(np.median(setups)), setup_phases_s=phases,
+                   total_s=float(np.median(setups)) + rec["value"],
+                   memory_mb=paper_memory_bytes(sol, scalar) / 1e6,
+                   storage="scalar CSR" if scalar else "blocks",
+                   setup=("scalar arithmetic" if kw.get("setup") else "block arithmetic"))
+        del sol
+        out[name] = rec
+    blk = out["ns_block"]
+    for name in ("ns_scalar", "ns_hybrid1"):
+        v = out[name]
+        v.update(block_total_speedup=v["total_s"] / blk["total_s"],
+                 block_setup_speedup=v["setup_s"] / blk["setup_s"],
+                 block_solve_speedup=v["value"] / blk["value"],
+                 block_memory_ratio=blk["memory_mb"] / v["memory_mb"])
+    out["paper_rod_ns_block_over_ns_scalar"] = {"total": 0.803 / 1.444, "memory": 114.19 / 205.16,
+                                                "hardware": "i5-3570K CPU, ILU(0) smoother"}
+    return out
+
+
+def forms_80(amg, torch, dargs, p, f, tol, solver, stream, steps):
+    """Variants on the benchmark workload (same f): V-cycle precision (FP64,
+    FP32, BF16, emulated FP64), block vs scalar storage, the block solver
+    without rotations, MIS-2 aggregation, block ILU(0), the Galerkin product
+    in block vs scalar arithmetic, and the learned smoother."""
+    rp, cl, val, B = dargs
+    dev = val.device
+    PRECS = {"fp64": amg.PREC_FP64, "fp32": amg.PREC_FP32, "bf16": amg.PREC_BF16}
+    u_ref, _, _, _ = solver.solve(f, tol=tol, maxiter=5000)
+    forms = {}
+    for name in ("fp64", "fp32", "bf16", "scalar_fp64", "scalar_fp32", "scalar_bf16"):
+        # scalar_*: the same hierarchy with every solve operator in scalar
+        # CSR rows (the scalar solver of Sec. 4) instead of blocks
+        scalar = name.startswith("scalar_")
+        pname = name.split("_")[-1]
+        rec, sol, _ = _solve_form(amg, torch, dargs, f, tol, steps, stream, u_ref,
+                                  precision=PRECS[pname],
+                                  storage=amg.STORAGE_SCALAR if scalar else amg.STORAGE_BLOCK)
+        del sol
+        rec["storage"] = "scalar CSR rows" if scalar else "blocks"
+        rec["vcycle"] = {"fp64": "FP64 matrices and vectors",
+                         "fp32": "FP32 matrices and vectors, FP32 accumulation",
+                         "bf16": "BF16-stored matrices, FP32 vectors and accumulation"}[pname]
+        forms[name] = rec
+    for name in ("fp32", "bf16"):
+        forms[name]["speedup_vs_fp64"] = forms["fp64"]["value"] / forms[name]["value"]
+    forms["paper_variants"] = paper_variants(amg, torch, dargs, f, tol, stream, steps, u_ref)
+    # the block solver without a near-nullspace (Sec. 4): B = the three
+    # translations, 3-DOF coarse nodes, FP64
+    T = torch.zeros((p.ndof, 3), dtype=torch.float64, device=dev)
+    for c in range(3):
+        T[c::3, c] = 1.0
+    rec, sol, _ = _solve_form(amg, torch, (rp, cl, val, T), f, tol, steps, stream, u_ref,
+                              maxiter=20000)
+    del sol
+    rec["vcycle"] = "FP64; near-nullspace = 3 translations (no rotations), 3x3 blocks on every level"
+    forms["no_nullspace_fp64"] = rec
+    # aggregation on the device (MIS-2) against the host's greedy passes:
+    # setup times side by side (median of 3), then the MIS-2 hierarchy's solve
+    setups = {"greedy": [], "mis2": []}
+    for _ in range(3):
+        for agg_name, code in (("greedy", amg.AGG_GREEDY), ("mis2", amg.AGG_MIS2)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sol = amg.AMG(*dargs, aggregation=code)
+            torch.cuda.synchronize()
+            setups[agg_name].append(time.perf_counter() - t0)
+            del sol
+    rec, sol, _ = _solve_form(amg, torch, dargs, f, tol, steps, stream, u_ref,
+                              aggregation=amg.AGG_MIS2)
+    del sol
+    rec.update(setup_s=float(np.median(setups["mis2"])),
+               greedy_setup_s=float(np.median(setups["greedy"])),
+               vcycle="FP64; aggregates from a distance-2 maximal independent set on the device")
+    forms["mis2_fp64"] = rec
+    # FP64 emulated on FP32 pairs: the V-cycle's matrices as hi + lo floats,
+    # FP64 vectors and CG; its fine SpMV against HBM
+    peak, _ = _peaks()
+    rec, sol, _ = _solve_form(amg, torch, dargs, f, tol, steps, stream, u_ref,
+                              precision=amg.PREC_DF64)
+    t_sp, algo_sp = _spmv_roofline(sol, torch, p.ndof, p.nnodes, p.nnzb, which=3)
+    del sol
+    tag = "sell_spmv_kernel<3,3,df32,double,PLAIN,NONE>:G1:v1"
+    rec.update(speedup_vs_fp64=forms["fp64"]["value"] / rec["value"],
+               fine_spmv={"kernel": tag, "traffic": NCU_TRAFFIC.get(tag),
+                          "algorithmic_bytes": algo_sp, "launch_ms": t_sp * 1e3,
+                          "achieved_gbs": algo_sp / t_sp / 1e9,
+                          "frac_of_measured_hbm": algo_sp / t_sp / 1e9 / peak,
+                          "frac_of_nominal_8tbs": algo_sp / t_sp / 8e12},
+               vcycle="V-cycle in FP64 emulated on FP32 pairs (hi + lo floats, ~2^-45 per "
+                      "product), FP64 vectors; CG's A p, dots and true residual in FP64")
+    forms["df64"] = rec
+    forms["ilu0_fp64"] = ilu0_form(amg, torch, dargs, f, tol, u_ref, forms["fp64"], p, stream,
+                                   steps)
+    for name in ("fp64", "fp32", "bf16"):
+        sc, bl = forms["scalar_" + name], forms[name]
+        sc["block_speedup"] = sc["value"] / bl["value"]
+        sc["block_memory_ratio"] = bl["operator_bytes"] / sc["operator_bytes"]
+    # the setup side of the same comparison: each level's Galerkin product
+    # R (A P) recomputed with block SpGEMMs and with scalar (1x1) SpGEMMs on
+    # the unblocked operators (best of two, wall time incl. symbolic)
+    gal = []
+    for l in range(solver.nlevels - 1):
+        tb = min(solver.galerkin_timing(l, amg.STORAGE_BLOCK)[0] for _ in range(2))
+        ts, ds = min(solver.galerkin_timing(l, amg.STORAGE_SCALAR) for _ in range(2))
+        gal.append({"level": l, "block_s": tb, "scalar_s": ts, "scalar_rel_diff": ds})
+    tb_all, ts_all = sum(g["block_s"] for g in gal), sum(g["scalar_s"] for g in gal)
+    forms["galerkin_block_vs_scalar"] = {"block_s": tb_all, "scalar_s": ts_all,
+                                         "block_speedup": ts_all / tb_all, "levels": gal}
+    # learned smoother: trained on the GPU on four smaller meshes, applied here
+    w, training = train_learned(amg, torch, dev)
+    lf = learned_form(amg, torch, solver, w, f, tol, u_ref, forms["fp64"]["value"],
+                      forms["fp64"]["iterations"], steps)
+    lf["training"] = training
+    forms["learned"] = lf
+    forms["learned_fp32"] = learned_fp32_form(amg, torch, dargs, w, f, tol, u_ref,
+                                              forms["fp64"]["value"], forms["fp32"], steps)
+    return forms, w
+
+
+def config_precision_150(amg, torch, dev, stream, steps):
+    """150^3 inclusions (10.3 M DOFs): the V-cycle precision forms against
+    the FP64 path (time-to-1e-8, iterations, error against the FP64
+    solution), and MIS-2 aggregation on the same mesh."""
+    p = _problem("inclusions150")
+    dargs = _dev_problem(torch, p, dev)
+    f = torch.from_numpy(p.f).to(dev)
+    tol = WORKLOADS["inclusions150"]["tol"]
+    out = {"workload": WORKLOADS["inclusions150"]["desc"], "dofs": p.ndof, "nnzb": p.nnzb,
+           "timed_solves_per_form": steps}
+    with ClockSampler(_gpu_id(torch)) as clk:
+        rec, sol, u_ref = _solve_form(amg, torch, dargs, f, tol, steps, stream)
+        del sol
+        out["fp64"] = rec
+        for name, prec in (("fp32", amg.PREC_FP32), ("bf16", amg.PREC_BF16),
+                           ("df64", amg.PREC_DF64)):
+            rec, sol, _ = _solve_form(amg, torch, dargs, f, tol, steps, stream, u_ref,
+                                      precision=prec)
+            del sol
+            rec["speedup_vs_fp64"] = out["fp64"]["value"] / rec["value"]
+            out[name] = rec
+        rec, sol, _ = _solve_form(amg, torch, dargs, f, tol, steps, stream, u_ref,
+                                  aggregation=amg.AGG_MIS2)
+        del sol
+        rec["speedup_vs_fp64"] = out["fp64"]["value"] / rec["value"]
+        out["mis2_fp64"] = rec
+    out["clocks"] = clk.summary()
+    out["oracle"] = ("not run at this size: the oracle's setup and solve take tens of minutes "
+                     "on one host core; errors are against the FP64 GPU solution, whose "
+                     "iterations and solution match the oracle's at 80^3")
+    del dargs, f, u_ref
+    torch.cuda.empty_cache()
+    return out
+
+
+def config_learned_120(amg, torch, dev, stream, steps, w):
+    """120^3 inclusions (5.3 M DOFs), the learned smoother's test mesh: the
+    network trained on 20^3-40^3 meshes against SPAI0, in the FP64 and FP32
+    V-cycles."""
+    p = _problem("inclusions120")
+    dargs = _dev_problem(torch, p, dev)
+    f = torch.from_numpy(p.f).to(dev)
+    tol = WORKLOADS["inclusions120"]["tol"]
+    out = {"workload": WORKLOADS["inclusions120"]["desc"], "dofs": p.ndof, "nnzb": p.nnzb,
+           "timed_solves_per_form": steps}
+    with ClockSampler(_gpu_id(torch)) as clk:
+        spai0, sol, u_ref = _solve_form(amg, torch, dargs, f, tol, steps, stream)
+        out["spai0_fp64"] = spai0
+        out["learned_fp64"] = learned_form(amg, torch, sol, w, f, tol, u_ref, spai0["value"],
+                                           spai0["iterations"], steps)
+        del sol
+        fp32, sol, _ = _solve_form(amg, torch, dargs, f, tol, steps, stream, u_ref,
+                                   precision=amg.PREC_FP32)
+        del sol
+        out["spai0_fp32"] = fp32
+        out["learned_fp32"] = learned_fp32_form(amg, torch, dargs, w, f, tol, u_ref,
+                                                spai0["value"], fp32, steps)
+    out["clocks"] = clk.summary()
+    lf = out["learned_fp64"]
+    out["verdict"] = ("learned beats SPAI0 in the FP64 V-cycle"
+                      if lf["value"] < spai0["value"] and lf["iterations"] < spai0["iterations"]
+                      else "no gain over SPAI0 in the FP64 V-cycle on this mesh")
+    del dargs, f, u_ref
+    torch.cuda.empty_cache()
+    return out
+
+
+def config_batch64(args, amg, torch, steps):
+    """The batched form (64 seeded boxes, one graph-launched solve of every
+    right-hand side) against a loop of single FP64 solves."""
+    import types
+    sub = types.SimpleNamespace(steps=steps, warmup=1, loop_mode=args.loop_mode)
+    line = run_batch(sub, amg, torch)
+    keep = ("value", "unit", "config", "batch", "batch_df64", "batch_fp32", "clocks",
+            "gpu_launches", "steps")
+    out = {k: line[k] for k in keep if k in line}
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -508,7 +804,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="inclusions80", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-sample", type=int, default=40)
+    ap.add_argument("--cpu-leg", action="store_true",
+                    help="(internal) run only the oracle's setup and solve on the workload and "
+                         "print them as JSON")
     ap.add_argument("--profile-spmv", action="store_true",
                     help="only build the hierarchy and launch the fine SpMV kernel 8 times "
                          "(a short, fixed command for profilers)")
@@ -518,20 +816,32 @@ def main():
                     help="V-cycle precision of the main line (CG stays FP64); with "
                          "--profile-spmv / --profile-op, df64 profiles the FP32-pair copies")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the FP32/BF16 V-cycle and learned-smoother comparisons "
-                         "on the same workload")
+                    help="skip the variants on the benchmark workload")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 150^3 precision, 64-box batch and 120^3 learned sub-records")
+    ap.add_argument("--form-steps", type=int, default=5,
+                    help="timed solves per variant and sub-record (at most --steps)")
     ap.add_argument("--loop-mode", type=int, default=0,
                     help="1: host-launched CG steps (for profilers); 0: device while loop")
     args = ap.parse_args()
+    if args.cpu_leg:
+        print(json.dumps(cpu_leg(args.workload)), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
-
-    import torch
-    import paper_2202_09056_gb300 as amg
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    profiling = args.profile_spmv or bool(args.profile_op)
+    leg = None
+    if (world == 1 and not args.no_cpu_baseline and not profiling
+            and args.workload != "batch64"):
+        leg = start_cpu_leg(args.workload)  # before CUDA is initialised in this process
+
+    import torch
+    import paper_2202_09056_gb300 as amg
+
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -553,10 +863,8 @@ def main():
         return 0
     p = _problem(args.workload)
     dev = torch.device("cuda", local)
-    rp = torch.from_numpy(p.row_ptr).to(dev)
-    cl = torch.from_numpy(p.col).to(dev)
-    val = torch.from_numpy(p.val).to(dev)
-    B = torch.from_numpy(p.B).to(dev)
+    dargs = _dev_problem(torch, p, dev)
+    rp, cl, val, B = dargs
     f = torch.from_numpy(p.f).to(dev)
     tol = WORKLOADS[args.workload]["tol"]
     s = torch.cuda.current_stream()
@@ -579,7 +887,7 @@ def main():
                             it, res))
         return solver
 
-    if args.profile_spmv or args.profile_op:
+    if profiling:
         # a short, fixed sequence for profilers: 8 launches of one level
         # operator's SpMV (PLAIN mode) on the benchmark hierarchy
         df = args.precision == "df64"
@@ -637,147 +945,28 @@ def main():
     e2e_t = float(np.mean(e2e))
 
     stats = solver.stats()
-    info0 = solver.level_info(0)
     levels = [solver.level_info(l) for l in range(stats["nlevels"])]
+    padding = [list(solver.padding(l)) for l in range(stats["nlevels"])]
     t_spmv, algo = _spmv_roofline(solver, torch, p.ndof, p.nnodes, p.nnzb)
     peak, peak_kind = _peaks()
+    fp64_tflops, fp64_src = fp64_peak(amg)
     achieved = algo / t_spmv / 1e9
     kernel_tag = "sell_spmv_kernel<3,3,double,double,PLAIN,NONE>:G1:v5"
     traffic = NCU_TRAFFIC.get(kernel_tag)
     flops = 2.0 * 9 * p.nnzb
     tflops = flops / t_spmv / 1e12
-    forms = None
-    if not args.no_forms and not args.profile_spmv:
-        # precision form: the same solve with the V-cycle in FP32 / BF16
-        # storage (FP32 accumulation), CG recurrences and dots in FP64
-        u_ref, it_ref, _, _ = solver.solve(f, tol=tol, maxiter=5000)
-        forms = {}
-        for name in ("fp64", "fp32", "bf16", "scalar_fp64", "scalar_fp32", "scalar_bf16"):
-            # scalar_*: the same hierarchy with every solve operator in scalar
-            # CSR rows (the scalar solver of Sec. 4) instead of blocks
-            scalar = name.startswith("scalar_")
-            pname = name.split("_")[-1]
-            sol = amg.AMG(rp, cl, val, B, precision=PRECS[pname],
-                          storage=amg.STORAGE_SCALAR if scalar else amg.STORAGE_BLOCK)
-            sol.solve(f, tol=tol, maxiter=5000)  # warm-up (graph capture)
-            times = []
-            for _ in range(args.steps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(s)
-                u_p, it_p, res_p, st_p = sol.solve(f, tol=tol, maxiter=5000)
-                e1.record(s)
-                torch.cuda.synchronize()
-                times.append(e0.elapsed_time(e1) / 1e3)
-            err = float(torch.linalg.norm(u_p - u_ref) / torch.linalg.norm(u_ref))
-            forms[name] = {"value": float(np.mean(times)), "iterations": it_p, "rel_resid": res_p,
-                           "status": st_p, "err_vs_fp64_solution": err,
-                           "operator_bytes": int(sol.stats()["bytes_solve"]),
-                           "storage": "scalar CSR rows" if scalar else "blocks",
-                           "vcycle": {"fp64": "FP64 matrices and vectors",
-                                      "fp32": "FP32 matrices and vectors, FP32 accumulation",
-                                      "bf16": "BF16-stored matrices, FP32 vectors and accumulation"}[pname]}
-            del sol
-        for name in ("fp32", "bf16"):
-            forms[name]["speedup_vs_fp64"] = forms["fp64"]["value"] / forms[name]["value"]
-        # the block solver without a near-nullspace (Sec. 4): B = the three
-        # translations, 3-DOF coarse nodes, FP64
-        T = torch.zeros((p.ndof, 3), dtype=torch.float64, device=dev)
-        for c in range(3):
-            T[c::3, c] = 1.0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sol = amg.AMG(rp, cl, val, T)
-        torch.cuda.synchronize()
-        t_setup = time.perf_counter() - t0
-        sol.solve(f, tol=tol, maxiter=20000)
-        times = []
-        for _ in range(args.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            u_p, it_p, res_p, st_p = sol.solve(f, tol=tol, maxiter=20000)
-            e1.record(s)
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1) / 1e3)
-        forms["no_nullspace_fp64"] = {
-            "value": float(np.mean(times)), "iterations": it_p, "rel_resid": res_p, "status": st_p,
-            "setup_s": t_setup, "levels": sol.nlevels,
-            "err_vs_fp64_solution": float(torch.linalg.norm(u_p - u_ref) / torch.linalg.norm(u_ref)),
-            "operator_bytes": int(sol.stats()["bytes_solve"]),
-            "vcycle": "FP64; near-nullspace = 3 translations (no rotations), 3x3 blocks on every level"}
-        del sol
-        # aggregation on the device (MIS-2) against the host's greedy passes:
-        # setup times side by side, then the MIS-2 hierarchy's FP64 solve
-        setups = {"greedy": [], "mis2": []}
-        for _ in range(3):
-            for agg_name, code in (("greedy", amg.AGG_GREEDY), ("mis2", amg.AGG_MIS2)):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                sol = amg.AMG(rp, cl, val, B, aggregation=code)
-                torch.cuda.synchronize()
-                setups[agg_name].append(time.perf_counter() - t0)
-                if agg_name == "greedy":
-                    del sol
-        sol.solve(f, tol=tol, maxiter=5000)
-        times = []
-        for _ in range(args.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            u_p, it_p, res_p, st_p = sol.solve(f, tol=tol, maxiter=5000)
-            e1.record(s)
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1) / 1e3)
-        forms["mis2_fp64"] = {
-            "value": float(np.mean(times)), "iterations": it_p, "rel_resid": res_p, "status": st_p,
-            "setup_s": float(np.median(setups["mis2"])),
-            "greedy_setup_s": float(np.median(setups["greedy"])), "levels": sol.nlevels,
-            "err_vs_fp64_solution": float(torch.linalg.norm(u_p - u_ref) / torch.linalg.norm(u_ref)),
-            "operator_bytes": int(sol.stats()["bytes_solve"]),
-            "vcycle": "FP64; aggregates from a distance-2 maximal independent set on the device"}
-        del sol
-        # FP64 emulated on FP32 pairs: the whole solve phase's matrices as
-        # hi + lo floats, FP64 vectors and CG; its fine SpMV against HBM
-        sol = amg.AMG(rp, cl, val, B, precision=amg.PREC_DF64)
-        t_df, it_df, res_df, st_df, u_df = _timed_solves(torch, sol, f, tol, args.steps, 5000, s)
-        t_sp, algo_sp = _spmv_roofline(sol, torch, p.ndof, p.nnodes, p.nnzb, which=3)
-        forms["df64"] = {
-            "value": t_df, "iterations": it_df, "rel_resid": res_df, "status": st_df,
-            "speedup_vs_fp64": forms["fp64"]["value"] / t_df,
-            "err_vs_fp64_solution": float(torch.linalg.norm(u_df - u_ref) / torch.linalg.norm(u_ref)),
-            "operator_bytes": int(sol.stats()["bytes_solve"]),
-            "fine_spmv": {"kernel": "sell_spmv_kernel<3,3,df32,double,PLAIN,NONE>:G1:v1",
-                          "traffic": NCU_TRAFFIC.get("sell_spmv_kernel<3,3,df32,double,PLAIN,NONE>:G1:v1"),
-                          "algorithmic_bytes": algo_sp,
-                          "launch_ms": t_sp * 1e3, "achieved_gbs": algo_sp / t_sp / 1e9,
-                          "frac_of_measured_hbm": algo_sp / t_sp / 1e9 / peak,
-                          "frac_of_nominal_8tbs": algo_sp / t_sp / 8e12},
-            "vcycle": "V-cycle in FP64 emulated on FP32 pairs (hi + lo floats, ~2^-45 per "
-                      "product), FP64 vectors; CG's A p, dots and true residual in FP64"}
-        del sol
-        forms["ilu0_fp64"] = ilu0_form(amg, torch, (rp, cl, val, B), f, tol, u_ref,
-                                       forms["fp64"], p, s, args.steps)
-        for name in ("fp64", "fp32", "bf16"):
-            sc, bl = forms["scalar_" + name], forms[name]
-            sc["block_speedup"] = sc["value"] / bl["value"]
-            sc["block_memory_ratio"] = bl["operator_bytes"] / sc["operator_bytes"]
-        # the setup side of the same comparison: each level's Galerkin product
-        # R (A P) recomputed with block SpGEMMs and with scalar (1x1) SpGEMMs
-        # on the unblocked operators (best of two, wall time incl. symbolic)
-        gal = []
-        for l in range(solver.nlevels - 1):
-            tb = min(solver.galerkin_timing(l, amg.STORAGE_BLOCK)[0] for _ in range(2))
-            ts, ds = min(solver.galerkin_timing(l, amg.STORAGE_SCALAR) for _ in range(2))
-            gal.append({"level": l, "block_s": tb, "scalar_s": ts, "scalar_rel_diff": ds})
-        tb_all, ts_all = sum(g["block_s"] for g in gal), sum(g["scalar_s"] for g in gal)
-        forms["galerkin_block_vs_scalar"] = {"block_s": tb_all, "scalar_s": ts_all,
-                                             "block_speedup": ts_all / tb_all, "levels": gal}
-        if args.precision == "fp64":
-            forms["learned"] = learned_form(amg, torch, solver, f, tol, u_ref,
-                                            forms["fp64"]["value"], forms["fp64"]["iterations"],
-                                            args.steps)
-            w_learned = forms["learned"].pop("weights")
-            forms["learned_fp32"] = learned_fp32_form(amg, torch, (rp, cl, val, B), w_learned, f,
-                                                      tol, u_ref, forms["fp64"]["value"],
-                                                      forms["fp32"], args.steps)
+    fsteps = max(1, min(args.steps, args.form_steps))
+    forms, configs, w = None, None, None
+    if not args.no_forms:
+        forms, w = forms_80(amg, torch, dargs, p, f, tol, solver, s, fsteps)
+    if not args.no_configs and args.workload == "inclusions80" and world == 1:
+        del solver
+        torch.cuda.empty_cache()
+        solver = None
+        configs = {"precision_150": config_precision_150(amg, torch, dev, s, min(fsteps, 2)),
+                   "batch64": config_batch64(args, amg, torch, min(fsteps, 2))}
+        if w is not None:
+            configs["learned_120"] = config_learned_120(amg, torch, dev, s, min(fsteps, 3), w)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -798,15 +987,14 @@ def main():
         "iterations": its, "rel_resid": res, "setup_s": setup_t, "total_s": step_t,
         "setup_phases_s": stats["setup_phase_seconds"],
         "operator_complexity": stats["operator_complexity"],
-        "sell_padding": [list(solver.padding(l)) for l in range(stats["nlevels"])],
         "memory_mb": stats["bytes_matrices"] / 1e6,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_t, "unit": "s", "h2d_bytes_per_step": 8 * p.ndof,
                 "d2h_bytes_per_step": 8 * p.ndof},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "kernel": kernel_tag, "achieved": tflops,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
-                     "traffic": traffic, "peak_source": "derived: 152 SMs x 2 DFMA/clock x 2 flop x 2.07 GHz (FP64 pipe)",
+                     "peak": fp64_tflops, "unit": "TFLOP/s", "frac": tflops / fp64_tflops,
+                     "traffic": traffic, "peak_source": fp64_src,
                      "algorithmic_flops": flops, "launch_ms": 1e3 * t_spmv,
                      "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_kind,
@@ -815,9 +1003,11 @@ def main():
         "wall_s": wall,
         "precision": args.precision,
         "forms": forms,
+        "configs": configs,
     }
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.ref_sample, args.workload, p.nnzb)
+    line["sell_padding"] = padding
+    if leg is not None:
+        line["cpu_baseline"] = cpu_baseline_record(finish_cpu_leg(leg), its)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -39,6 +39,7 @@
 #ifndef AMG_GB300_H
 #define AMG_GB300_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -73,6 +74,23 @@ extern "C" {
  * the two storages run the same arithmetic and differ only in layout. */
 #define AMG_STORAGE_BLOCK 0       /* b x b blocks (3x3 fine, 6x6 coarse) */
 #define AMG_STORAGE_SCALAR 1      /* scalar CSR rows */
+
+/* Arithmetic of the setup (amg_params.setup), the other axis of Sec. 3/4's
+ * comparison.  AMG_SETUP_BLOCK is the paper's "NS Block" route: the
+ * transfer operators built per aggregate straight into b x 6 blocks, the
+ * Galerkin product and the smoother in block arithmetic.  AMG_SETUP_SCALAR
+ * is the scalar setup of "NS Scalar" and "NS Hybrid1": the input is
+ * unblocked, and strength (on the node graph condensed from the scalar
+ * pattern, point-wise with block size 3, then 6), aggregation, tentative
+ * prolongation, its smoothing, R = P^T, the Galerkin product and SPAI0 all
+ * run on scalar CSR rows; the levels are then converted into blocks
+ * (Listing 1's conversion).  With AMG_STORAGE_BLOCK the solve runs on those
+ * blocks ("NS Hybrid1"); with AMG_STORAGE_SCALAR on the scalar matrices
+ * themselves ("NS Scalar").  Both setups give the same hierarchy (patterns
+ * and aggregates bit for bit, values to rounding).  The scalar setup takes
+ * the SPAI0 smoother and single-instance handles only. */
+#define AMG_SETUP_BLOCK 0
+#define AMG_SETUP_SCALAR 1
 
 /* Aggregation (the coarsening step of Alg. 1, point-wise on block rows as in
  * Sec. 4; the paper does not specify the algorithm).  Both run on the strong
@@ -119,6 +137,32 @@ typedef struct {
     const double *val;
 } amg_bsr;
 
+/* Device memory supplier of a hierarchy (amg_params.allocator).  With
+ * allocator == NULL the library allocates stream-ordered with
+ * cudaMallocAsync / cudaFreeAsync.  Otherwise every device buffer that a
+ * handle holds, and every temporary device buffer of a call on that handle,
+ * comes from alloc() and goes back through free(), so that the caller's
+ * memory manager (for example PyTorch's caching allocator) sees and bounds
+ * the hierarchy.
+ *   alloc(ctx, bytes, stream): return a device pointer to at least `bytes`
+ *     bytes, 256-byte aligned, usable by work ordered on `stream` (the
+ *     stream of the call that allocates; NULL = legacy default stream), or
+ *     NULL on failure (the call then returns AMG_ERR_CUDA).
+ *   free(ctx, ptr, bytes, stream): take back a pointer alloc() returned,
+ *     with its size.  Temporaries are given back while work that uses them
+ *     may still be queued on `stream`, as with cudaFreeAsync: the supplier
+ *     must not hand the memory to work on another stream before that work
+ *     completes.  amg_free and amg_batch_free synchronise the device before
+ *     giving back a handle's buffers.
+ * The library copies the struct at setup; ctx and the two functions must
+ * stay valid until the handle is freed.  Both are called on the thread that
+ * makes the library call. */
+typedef struct {
+    void *(*alloc)(void *ctx, size_t bytes, void *stream);
+    void (*free)(void *ctx, void *ptr, size_t bytes, void *stream);
+    void *ctx;
+} amg_allocator;
+
 /* Setup and cycle parameters (the paper names none of them; defaults are the
  * readings of its silent points, see the design notes shipped with the
  * library). */
@@ -138,7 +182,10 @@ typedef struct {
     int32_t aggregation;   /* AMG_AGG_* (AMG_AGG_GREEDY) */
     int32_t smoother;      /* AMG_SMOOTH_* (AMG_SMOOTH_SPAI0) */
     int32_t ilu_sweeps;    /* Jacobi sweeps per triangle of AMG_SMOOTH_ILU0, 0..64 (2) */
-    int32_t reserved[2];   /* must be zero */
+    int32_t setup;         /* AMG_SETUP_* (AMG_SETUP_BLOCK) */
+    int32_t reserved;      /* must be zero */
+    const amg_allocator *allocator; /* device memory supplier, or NULL for the library's
+                              own stream-ordered allocations (NULL) */
 } amg_params;
 
 typedef struct amg_handle_s *amg_handle;
@@ -387,6 +434,19 @@ int amg_trainer_step(amg_trainer t, int32_t nsteps, double *loss, void *stream);
 int amg_trainer_params(amg_trainer t, float *out);
 void amg_trainer_free(amg_trainer t);
 
+/* Measured FP64 FMA rate of the current device (host outputs), the
+ * denominator of the arithmetic roofline of the FP64 SpMV: every SpMV entry
+ * is one FMA (2 b_r b_c flops per block, Sec. 2's block arithmetic), and on
+ * GB300 the FP64 pipe, not HBM, bounds that kernel.  One grid of 4 CTAs x
+ * 256 threads per SM, each thread running 8 independent FMA chains for
+ * `iters` steps, timed with CUDA events on `stream` after one short warm-up
+ * launch.  sink (device, sink_len doubles, caller-owned) receives the
+ * chains' sums so that the work is observable.  *fma_per_second = FMAs / s;
+ * *seconds (may be NULL) = the timed launch; *num_sms (may be NULL) = the
+ * device's SM count.  Synchronises `stream`. */
+int amg_fp64_fma_rate(double *sink, int64_t sink_len, int32_t iters, double *fma_per_second,
+                      double *seconds, int32_t *num_sms, void *stream);
+
 /* Same result as amg_bsr_spmv_dot, without allocating.  (The paper has no
  * counterpart: this serves callers of the library, not the method.)
  * amg_bsr_spmv_dot allocates device scratch for its per-CTA partial sums; a
@@ -399,11 +459,14 @@ void amg_trainer_free(amg_trainer t);
  * cudaMalloc, cudaFree or allocating library call; x, y and the result are
  * the caller's.  The launch needs one partial sum per CTA plus one for the
  * total; a launch that would need more than the array holds is rejected with
- * AMG_ERR_LIMIT (on GB300 the launch needs at most 8 x 152 + 1).  The first
- * call on a device looks up the array's device address, so make that first
- * call before any stream capture.  All calls share the array: calls whose
- * work overlaps on the GPU (two streams, two host threads) race on it; calls
- * ordered on one stream are safe.  Synchronises `stream`. */
+ * AMG_ERR_LIMIT (on GB300 the launch needs at most 8 x 152 + 1).  The
+ * arguments are checked as for amg_bsr_spmv_dot.  The first call on a
+ * device (and the first after that device's context was re-created) looks
+ * up the array's device address, so make that first call before any stream
+ * capture.  All calls share the array, which keeps the last call's partial
+ * sums: calls whose work overlaps on the GPU (two streams, two host threads)
+ * race on it; calls ordered on one stream are safe.  The call reads the
+ * total back to the host and synchronises `stream` before it returns. */
 #define AMG_NOALLOC_SCRATCH_DOUBLES 4096
 int amg_bsr_spmv_dot_noalloc(const amg_bsr *A, const double *x, double *y, double *dot_out,
                              void *stream);

@@ -2,8 +2,10 @@
 
 Thin ctypes binding of the C ABI declared in ``include/amg_gb300.h``.  It only
 marshals arguments: every step of setup and solve runs in the library's CUDA
-kernels.  PyTorch supplies device memory and the current CUDA stream.  There
-is no CPU fallback: without the compiled library every call raises.
+kernels.  PyTorch supplies device memory (its caching allocator, passed to the
+library as an ``amg_allocator``, holds every hierarchy buffer) and the current
+CUDA stream.  There is no CPU fallback: without the compiled library every
+call raises.
 
 Method: Demidov (2022), Alg. 1 (setup), Alg. 2 (V-cycle), Sec. 3 (block
 arithmetic with rigid-body modes), Sec. 4 (CG, relative residual 1e-8).
@@ -29,6 +31,7 @@ PREC_FP64, PREC_FP32, PREC_BF16, PREC_DF64 = 0, 1, 2, 3
 STORAGE_BLOCK, STORAGE_SCALAR = 0, 1
 AGG_GREEDY, AGG_MIS2 = 0, 1
 SMOOTH_SPAI0, SMOOTH_ILU0 = 0, 1
+SETUP_BLOCK, SETUP_SCALAR = 0, 1
 
 
 class AmgError(RuntimeError):
@@ -43,6 +46,16 @@ class Bsr(ctypes.Structure):
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                            ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    """amg_allocator: the device memory supplier of a hierarchy."""
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
 class Params(ctypes.Structure):
     _fields_ = [("eps_strong", ctypes.c_double), ("relax", ctypes.c_double),
                 ("smooth_relax", ctypes.c_double), ("coarse_enough", ctypes.c_int32),
@@ -50,7 +63,43 @@ class Params(ctypes.Structure):
                 ("npost", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("loop_mode", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("aggregation", ctypes.c_int32), ("smoother", ctypes.c_int32),
-                ("ilu_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("ilu_sweeps", ctypes.c_int32), ("setup", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("allocator", ctypes.c_void_p)]
+
+
+def _torch_alloc(ctx, nbytes, stream):
+    import torch
+    try:
+        return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0)))
+    except Exception:  # the library reports the failure (NULL) as an error status
+        return None
+
+
+def _torch_free(ctx, ptr, nbytes, stream):
+    import torch
+    torch.cuda.caching_allocator_delete(int(ptr))
+
+
+_TORCH_ALLOCATOR = None
+
+
+def torch_allocator() -> Allocator:
+    """PyTorch's CUDA caching allocator as an amg_allocator: the hierarchy's
+    buffers then count in torch.cuda.memory_allocated() and obey its limits.
+    The struct and its callbacks live for the whole process."""
+    global _TORCH_ALLOCATOR
+    if _TORCH_ALLOCATOR is None:
+        _TORCH_ALLOCATOR = Allocator(_ALLOC_FN(_torch_alloc), _FREE_FN(_torch_free), None)
+    return _TORCH_ALLOCATOR
+
+
+def _with_allocator(params: Params, allocator) -> Params:
+    """allocator: "torch" (PyTorch's caching allocator), None (the library's
+    own cudaMallocAsync) or an Allocator the caller keeps alive."""
+    if allocator == "torch":
+        allocator = torch_allocator()
+    params.allocator = None if allocator is None else ctypes.addressof(allocator)
+    return params
 
 
 class LevelDesc(ctypes.Structure):
@@ -86,7 +135,7 @@ EXPORTED = ["amg_params_default", "amg_setup", "amg_apply_vcycle", "amg_solve", 
             "amg_batch_setup", "amg_batch_solve", "amg_batch_info", "amg_batch_free",
             "amg_set_learned_smoother", "amg_clear_learned_smoother", "amg_trainer_create",
             "amg_trainer_add_samples", "amg_trainer_add_generated", "amg_trainer_eval",
-            "amg_trainer_step", "amg_trainer_params", "amg_trainer_free"]
+            "amg_trainer_step", "amg_trainer_params", "amg_trainer_free", "amg_fp64_fma_rate"]
 
 LEARNED_NPARAM = 1222   # W1 [64][12], b1 [64], W2 [6][64], b2 [6]
 
@@ -135,6 +184,7 @@ def load(build_if_missing: bool = True):
         "amg_trainer_step": ([P, i32, P, P], ctypes.c_int),
         "amg_trainer_params": ([P, P], ctypes.c_int),
         "amg_trainer_free": ([P], None),
+        "amg_fp64_fma_rate": ([P, ctypes.c_int64, i32, P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -193,6 +243,18 @@ def kernel_launches() -> int:
     return int(load().amg_kernel_launches())
 
 
+def fp64_fma_rate(iters: int = 40000, stream=None) -> dict:
+    """Measured FP64 FMA rate of the current device: {"fma_per_s", "tflops"
+    (2 flops per FMA), "seconds" (the timed launch), "num_sms"}."""
+    import torch
+    sink = torch.empty(1 << 16, dtype=torch.float64, device="cuda")
+    rate, sec, nsm = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_int32(0)
+    _check(load().amg_fp64_fma_rate(sink.data_ptr(), sink.numel(), int(iters), ctypes.byref(rate),
+                                    ctypes.byref(sec), ctypes.byref(nsm), _stream(stream)))
+    return {"fma_per_s": rate.value, "tflops": 2.0 * rate.value / 1e12, "seconds": sec.value,
+            "num_sms": nsm.value}
+
+
 def bsr_spmv(row_ptr, col, val, x, y=None, nbcols=None, stream=None):
     """y = A x (block SpMV kernel) on CUDA tensors."""
     import torch
@@ -220,10 +282,12 @@ def bsr_spmv_dot(row_ptr, col, val, x, y=None, stream=None):
 class AMG:
     """Hierarchy handle: setup (Alg. 1) on construction, V-cycle and PCG solve."""
 
-    def __init__(self, row_ptr, col, val, B, params: Params | None = None, stream=None, **kw):
+    def __init__(self, row_ptr, col, val, B, params: Params | None = None, stream=None,
+                 allocator="torch", **kw):
         import torch
         self._lib = load()
         self.params = params if params is not None else default_params(**kw)
+        _with_allocator(self.params, allocator)
         A = make_bsr(row_ptr, col, val)
         self.n = A.nbrows * A.bs_r
         self.ns = int(B.shape[1])
@@ -372,10 +436,12 @@ class AMGBatch:
     """Batched form: independent instances, each with several right-hand sides,
     one hierarchy per instance and one graph-launched solve for all of them."""
 
-    def __init__(self, mats, Bs, nrhs, params: Params | None = None, stream=None, **kw):
+    def __init__(self, mats, Bs, nrhs, params: Params | None = None, stream=None,
+                 allocator="torch", **kw):
         import torch
         self._lib = load()
         self.params = params if params is not None else default_params(**kw)
+        _with_allocator(self.params, allocator)
         n = len(mats)
         if not (len(Bs) == len(nrhs) == n):
             raise ValueError("mats, Bs and nrhs must have the same length")

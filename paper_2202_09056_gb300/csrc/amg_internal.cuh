@@ -40,15 +40,33 @@ void end_launch_capture();
     } while (0)
 
 // ---------------------------------------------------------------- device memory
-// Stream-ordered device allocations owned by a handle (or a call).
+// The caller's device memory supplier for the duration of a library call on
+// a handle (amg_params.allocator); null = the library's own stream-ordered
+// cudaMallocAsync.  Scoped per thread: entry points install their handle's.
+struct AllocScope {
+    const amg_allocator *prev;
+    explicit AllocScope(const amg_allocator *a);
+    ~AllocScope();
+};
+const amg_allocator *current_allocator();
+
+// Device allocations owned by a handle (or a call).  Each pointer remembers
+// the supplier it came from (the scope's at allocation time) and goes back
+// to it.
 struct DevArena {
+    struct Rec {
+        void *p;
+        size_t n;
+        amg_allocator al;   // al.alloc == nullptr: cudaMallocAsync
+    };
     cudaStream_t stream = nullptr;
-    std::vector<void *> ptrs;
+    std::vector<Rec> recs;
     size_t bytes = 0;
     int alloc(void **p, size_t n);
     template <class T> int alloc_n(T **p, size_t n) { return alloc((void **)p, n * sizeof(T)); }
     void release(void *p);   // free one pointer early
     void release_all();
+    bool has_custom() const;
 };
 
 // A device BSR matrix owned by the library.  Values are stored in T.
@@ -60,6 +78,10 @@ template <class T> struct Bsr {
     T *val = nullptr;
 };
 using BsrD = Bsr<double>;
+
+// Argument check of a borrowed BSR matrix (dimensions, nnzb within int32,
+// pointers; square with square blocks when want_square).
+int check_bsr(const amg_bsr *A, int want_square);
 
 // ---------------------------------------------------------------- launch geometry
 struct Geom {
@@ -281,6 +303,17 @@ int galerkin(const BsrD &A, const BsrD &P, const BsrD &R, DevArena &keep, DevAre
 int galerkin_scalar(const BsrD &A, const BsrD &P, const BsrD &R, DevArena &keep, DevArena &tmp,
                     cudaStream_t s, BsrD *Ac);
 int spai0_diag(const BsrD &A, double scale, double *M, cudaStream_t s);
+// scalar setup (the Sec. 3/4 scalar and hybrid solvers): S is scalar CSR
+// (1x1 blocks), nodes are b consecutive rows.  The node graph (pattern in
+// `graph`, flags in *strong, allocated in keep) with the block setup's
+// strength test; the transfer operators P, R as scalar CSR; a scalar CSR
+// matrix converted into br x bc blocks (explicit zeros where absent).
+int scalar_strength(const BsrD &S, int b, double eps, DevArena &keep, DevArena &tmp,
+                    cudaStream_t s, BsrD *graph, uint8_t **strong);
+int scalar_transfer(const BsrD &S, int b, const double *B, int ns, const int *agg_h, int nagg,
+                    double relax, DevArena &keep, DevArena &tmp, cudaStream_t s, LevelBuild *out);
+int scalar_to_block(const BsrD &S, int br, int bc, DevArena &keep, DevArena &tmp, cudaStream_t s,
+                    BsrD *out);
 int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
                    double **Ainv_out);
 
@@ -320,6 +353,8 @@ struct Level {
     double *Mb = nullptr;     // learned 3x3 smoother blocks (level 0), replaces M when set
     float *Mbf = nullptr;     // FP32 copy of Mb for the FP32 / BF16 V-cycles
     Ilu ilu;                  // block ILU(0) smoother (when selected), replaces M
+    BsrD xA, xP, xR;          // scalar CSR of A, P, R built by the scalar setup (kept until
+                              // the solve's copies are made)
     int n() const { return A.nbr * A.br; }
 };
 
@@ -328,6 +363,8 @@ struct Level {
 // The hierarchy handle behind the C ABI's opaque amg_handle.
 struct amg_handle_s {
     amg_params prm;
+    amg_allocator alloc{};        // copy of *prm.allocator (alloc == nullptr: none)
+    const amg_allocator *allocator() const { return alloc.alloc ? &alloc : nullptr; }
     cudaStream_t stream = nullptr;
     amg::Geom geom;
     int max_lanes = 128;          // cap on lanes per row of the sliced copies

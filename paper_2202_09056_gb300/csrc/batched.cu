@@ -395,7 +395,9 @@ struct BState {
     int *inst_active, *inst_check, *any_active;
 };
 
-// elementwise: p = z + beta p (active rhs)
+// elementwise: p = z + beta p (active rhs); beta = 0 only on a pair's first
+// iteration (a zero r.z later stops the pair as a breakdown), where p = z
+// without reading p, which holds no earlier direction
 __global__ void bdirection_kernel(BVec v, const int *__restrict__ active, const double *__restrict__ beta,
                                   const double *__restrict__ z, double *__restrict__ p)
 {
@@ -403,7 +405,7 @@ __global__ void bdirection_kernel(BVec v, const int *__restrict__ active, const 
          e += (int64_t)gridDim.x * blockDim.x) {
         const int inst = inst_of(v.off, v.ninst, e);
         const int g = v.goff[inst] + (int)((e - v.off[inst]) % v.K[inst]);
-        if (active[g]) p[e] = z[e] + beta[g] * p[e];
+        if (active[g]) p[e] = beta[g] == 0.0 ? z[e] : z[e] + beta[g] * p[e];
     }
 }
 
@@ -644,6 +646,8 @@ struct BLevelData {
 
 struct amg_batch_s {
     amg_params prm;
+    amg_allocator alloc{};               // copy of *prm.allocator (alloc == nullptr: none)
+    const amg_allocator *allocator() const { return alloc.alloc ? &alloc : nullptr; }
     cudaStream_t stream = nullptr;
     Geom geom;
     DevArena mem;
@@ -1072,16 +1076,21 @@ static void bdestroy(amg_batch h)
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     for (amg_handle x : h->inst) destroy_handle(x);
-    h->mem.release_all();
-    if (h->stream) cudaStreamSynchronize(h->stream);
-    else cudaDeviceSynchronize();
+    if (h->mem.has_custom()) {
+        cudaDeviceSynchronize();  // see destroy_handle
+        h->mem.release_all();
+    } else {
+        h->mem.release_all();
+        if (h->stream) cudaStreamSynchronize(h->stream);
+        else cudaDeviceSynchronize();
+    }
     delete h;
 }
 
 static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, const int32_t *nrhs)
 {
-    if (h->prm.storage != AMG_STORAGE_BLOCK) {
-        set_error("the batched solve uses block storage");
+    if (h->prm.storage != AMG_STORAGE_BLOCK || h->prm.setup != AMG_SETUP_BLOCK) {
+        set_error("the batched solve uses block storage and the block setup");
         return AMG_ERR_ARG;
     }
     cudaStream_t s = h->stream;
@@ -1095,6 +1104,7 @@ static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, co
     for (int i = 0; i < ni; ++i) {
         amg_handle x = new amg_handle_s();
         x->prm = h->prm;
+        x->alloc = h->alloc;
         x->prm.precision = AMG_PREC_FP64;  // FP64 sliced copies; the batch makes its pair copies
         x->stream = s;
         x->mem.stream = s;
@@ -1275,8 +1285,15 @@ int amg_batch_setup(int32_t ninst, const amg_bsr *A, const double *const *B, con
         return AMG_ERR_ARG;
     }
     auto t0 = std::chrono::steady_clock::now();
+    if (p.allocator && (!p.allocator->alloc || !p.allocator->free)) {
+        set_error("amg_params.allocator needs both alloc and free");
+        return AMG_ERR_ARG;
+    }
     amg_batch h = new amg_batch_s();
     h->prm = p;
+    if (p.allocator) h->alloc = *p.allocator;
+    h->prm.allocator = nullptr;
+    AllocScope scope(h->allocator());
     h->vk = p.precision == AMG_PREC_DF64 ? 1 : (p.precision == AMG_PREC_FP32 ? 2 : 0);
     h->stream = (cudaStream_t)stream;
     h->mem.stream = h->stream;
@@ -1303,6 +1320,7 @@ int amg_batch_solve(amg_batch h, const double *const *F, double *const *U, doubl
         set_error("amg_batch_solve: bad argument");
         return AMG_ERR_ARG;
     }
+    AllocScope scope(h->allocator());
     cudaStream_t s = (cudaStream_t)stream;
     const int ni = h->ninst;
     BLevelData &L0 = h->lv[0];

@@ -1,4 +1,5 @@
-// Error reporting, stream-ordered device memory and launch geometry.
+// Error reporting, device memory (the library's stream-ordered allocations or
+// the caller's supplier) and launch geometry.
 #include <atomic>
 #include <cstdarg>
 #include <cstring>
@@ -33,38 +34,98 @@ void begin_launch_capture(long long *counter) { t_capture = counter; }
 void end_launch_capture() { t_capture = nullptr; }
 long long launches() { return g_launches.load(); }
 
+static thread_local const amg_allocator *t_allocator = nullptr;
+
+AllocScope::AllocScope(const amg_allocator *a) : prev(t_allocator) { t_allocator = a; }
+AllocScope::~AllocScope() { t_allocator = prev; }
+const amg_allocator *current_allocator() { return t_allocator; }
+
 int DevArena::alloc(void **p, size_t n)
 {
     *p = nullptr;
     if (n == 0) n = 16;
-    cudaError_t e = cudaMallocAsync(p, n, stream);
-    if (e != cudaSuccess) {
-        set_error("cudaMallocAsync(%zu bytes): %s", n, cudaGetErrorString(e));
-        *p = nullptr;
-        return AMG_ERR_CUDA;
+    const amg_allocator *a = t_allocator;
+    Rec r{nullptr, n, amg_allocator{}};
+    if (a && a->alloc) {
+        r.p = a->alloc(a->ctx, n, (void *)stream);
+        if (!r.p) {
+            set_error("the caller's allocator returned NULL for %zu bytes", n);
+            return AMG_ERR_CUDA;
+        }
+        if (((uintptr_t)r.p & 255u) != 0) {
+            if (a->free) a->free(a->ctx, r.p, n, (void *)stream);
+            set_error("the caller's allocator returned a pointer that is not 256-byte aligned");
+            return AMG_ERR_ARG;
+        }
+        r.al = *a;
+    } else {
+        cudaError_t e = cudaMallocAsync(&r.p, n, stream);
+        if (e != cudaSuccess) {
+            set_error("cudaMallocAsync(%zu bytes): %s", n, cudaGetErrorString(e));
+            return AMG_ERR_CUDA;
+        }
     }
-    ptrs.push_back(*p);
+    *p = r.p;
+    recs.push_back(r);
     bytes += n;
     return AMG_OK;
+}
+
+static void give_back(const DevArena::Rec &r, cudaStream_t s)
+{
+    if (r.al.alloc) {
+        if (r.al.free) r.al.free(r.al.ctx, r.p, r.n, (void *)s);
+    } else {
+        cudaFreeAsync(r.p, s);
+    }
 }
 
 void DevArena::release(void *p)
 {
     if (!p) return;
-    for (size_t i = 0; i < ptrs.size(); ++i)
-        if (ptrs[i] == p) {
-            cudaFreeAsync(p, stream);
-            ptrs[i] = ptrs.back();
-            ptrs.pop_back();
+    for (size_t i = 0; i < recs.size(); ++i)
+        if (recs[i].p == p) {
+            give_back(recs[i], stream);
+            bytes -= recs[i].n;
+            recs[i] = recs.back();
+            recs.pop_back();
             return;
         }
 }
 
 void DevArena::release_all()
 {
-    for (void *p : ptrs) cudaFreeAsync(p, stream);
-    ptrs.clear();
+    for (const Rec &r : recs) give_back(r, stream);
+    recs.clear();
     bytes = 0;
+}
+
+bool DevArena::has_custom() const
+{
+    for (const Rec &r : recs)
+        if (r.al.alloc) return true;
+    return false;
+}
+
+int check_bsr(const amg_bsr *A, int want_square)
+{
+    if (!A) {
+        set_error("null matrix");
+        return AMG_ERR_ARG;
+    }
+    if (A->nbrows < 0 || A->nbcols < 0 || A->nnzb < 0 || A->nnzb > 2147483647LL) {
+        set_error("bad matrix dimensions");
+        return AMG_ERR_ARG;
+    }
+    if (want_square && (A->nbrows != A->nbcols || A->bs_r != A->bs_c)) {
+        set_error("matrix must be square with square blocks");
+        return AMG_ERR_ARG;
+    }
+    if (!A->row_ptr || (A->nnzb > 0 && (!A->col || !A->val))) {
+        set_error("null matrix array");
+        return AMG_ERR_ARG;
+    }
+    return AMG_OK;
 }
 
 int query_geom(Geom *g)

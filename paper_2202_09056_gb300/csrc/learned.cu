@@ -785,6 +785,7 @@ int amg_set_learned_smoother(amg_handle h, const float *params, int32_t *fell_ba
         set_error("null argument");
         return AMG_ERR_ARG;
     }
+    AllocScope scope(h->allocator());
     cudaStream_t s = (cudaStream_t)stream;
     if (h->lv.size() < 2 || h->lv[0].A.br != 3 || h->prm.storage != AMG_STORAGE_BLOCK) {
         set_error("the learned smoother needs a multi-level hierarchy in block storage");

@@ -15,6 +15,8 @@
 // exits.  All calls share it and it keeps the contents of the last call, so
 // two calls whose work overlaps on the GPU (different streams, or different
 // host threads) race on it; calls on one stream are ordered and safe.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "amg_internal.cuh"
@@ -24,26 +26,72 @@ namespace amg {
 // Partial sums of one launch (one per CTA) followed by the final sum.
 static __device__ __align__(256) double g_spmv_dot_scratch[AMG_NOALLOC_SCRATCH_DOUBLES];
 
-// Device address of the array, looked up once per device with that device
-// current.  In host code the array's name is only a host-side stand-in, so
-// the kernels must be given this address, never the name.
+// The calling thread's current CUDA context (driver entry point fetched once
+// through the runtime, so the library needs no link to the driver library).
+static int current_context(void **out)
+{
+    using CtxGetCurrent = CUresult (*)(CUcontext *);
+    static CtxGetCurrent fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrent>(p);
+    });
+    if (!fn) {
+        set_error("cuCtxGetCurrent is not available");
+        return AMG_ERR_CUDA;
+    }
+    CUcontext c = nullptr;
+    if (fn(&c) != CUDA_SUCCESS) {
+        set_error("cuCtxGetCurrent failed");
+        return AMG_ERR_CUDA;
+    }
+    *out = (void *)c;
+    return AMG_OK;
+}
+
+// Device address of the array, looked up once per device and context with
+// that device current.  In host code the array's name is only a host-side
+// stand-in, so the kernels must be given this address, never the name.  The
+// address belongs to the context that loaded the module: a context made
+// after the device was reset loads it again, possibly elsewhere, so the
+// lookup is keyed by the context as well as the device.
 static int scratch_address(double **out)
 {
+    struct Entry {
+        int dev;
+        void *ctx;
+        double *addr;
+    };
+    constexpr int kEntries = 16;
+    static Entry table[kEntries];
+    static int used = 0, next = 0;
     static std::mutex mu;
-    static double *addr[64] = {nullptr};
     int dev = 0;
     AMG_TRY_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) {
-        set_error("device ordinal %d out of range", dev);
-        return AMG_ERR_LIMIT;
-    }
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void *p = nullptr;
-        AMG_TRY_CUDA(cudaGetSymbolAddress(&p, g_spmv_dot_scratch));
-        addr[dev] = static_cast<double *>(p);
+    void *ctx = nullptr;
+    AMG_TRY(current_context(&ctx));
+    if (ctx)
+        for (int i = 0; i < used; ++i)
+            if (table[i].dev == dev && table[i].ctx == ctx) {
+                *out = table[i].addr;
+                return AMG_OK;
+            }
+    void *p = nullptr;
+    AMG_TRY_CUDA(cudaGetSymbolAddress(&p, g_spmv_dot_scratch));  // makes the context current
+    AMG_TRY(current_context(&ctx));
+    Entry e{dev, ctx, static_cast<double *>(p)};
+    if (used < kEntries) table[used++] = e;
+    else {
+        table[next] = e;  // more devices or contexts than entries: replace the oldest
+        next = (next + 1) % kEntries;
     }
-    *out = addr[dev];
+    *out = e.addr;
     return AMG_OK;
 }
 
@@ -55,9 +103,9 @@ extern "C" int amg_bsr_spmv_dot_noalloc(const amg_bsr *A, const double *x, doubl
                                         double *dot_out, void *stream)
 {
     clear_error();
-    if (!A || !x || !y || !dot_out || A->nbrows < 0 || A->nbrows != A->nbcols ||
-        A->bs_r != A->bs_c || A->nnzb < 0 || !A->row_ptr || (A->nnzb > 0 && (!A->col || !A->val))) {
-        set_error("amg_bsr_spmv_dot_noalloc: bad argument");
+    AMG_TRY(check_bsr(A, 1));  // the same checks as amg_bsr_spmv_dot
+    if (!x || !y || !dot_out) {
+        set_error("amg_bsr_spmv_dot_noalloc: null argument");
         return AMG_ERR_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;

@@ -512,8 +512,14 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
     if (S.nslices > 0) {
         int *w = nullptr, *pw = nullptr;
         unsigned long long *tot = nullptr;
-        AMG_TRY_CUDA(cudaMallocAsync((void **)&w, sizeof(int) * S.nslices, s));
-        AMG_TRY_CUDA(cudaMallocAsync((void **)&tot, sizeof(unsigned long long) * 2, s));
+        DevArena tmp;  // temporaries of this conversion (same supplier as the handle's)
+        tmp.stream = s;
+        struct Release {
+            DevArena &a;
+            ~Release() { a.release_all(); }
+        } release_tmp{tmp};
+        AMG_TRY(tmp.alloc_n(&w, (size_t)S.nslices));
+        AMG_TRY(tmp.alloc_n(&tot, 2));
         AMG_TRY_CUDA(cudaMemsetAsync(tot, 0, sizeof(unsigned long long) * 2, s));
         sell_group_width_kernel<<<(ngroups + 255) / 256, 256, 0, s>>>(B.row_ptr, nrows, G, rpg, spg,
                                                                       ngroups, nullptr, w, tot);
@@ -526,7 +532,7 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
         bool sorted = false;
         if (B.nnzb > 0 && (double)(nat - B.nnzb) > 0.05 * (double)B.nnzb) {
             const int win = 32 * rpg;
-            AMG_TRY_CUDA(cudaMallocAsync((void **)&pw, sizeof(int) * nslots, s));
+            AMG_TRY(tmp.alloc_n(&pw, (size_t)nslots));
             AMG_TRY_CUDA(cudaMemsetAsync(pw, 0xff, sizeof(int) * nslots, s));  // -1: padding slots
             sell_window_rank_kernel<<<(nrows + win - 1) / win, 256, 0, s>>>(B.row_ptr, nrows, win, pw);
             sell_group_width_kernel<<<(ngroups + 255) / 256, 256, 0, s>>>(
@@ -563,7 +569,7 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
             for (int k = 0; k < ngroups; ++k)
                 for (int q = 0; q < spg; ++q) wh[(size_t)k * spg + q] = w2[(size_t)order[k] * spg + q];
             int *dorder = nullptr;
-            AMG_TRY_CUDA(cudaMallocAsync((void **)&dorder, sizeof(int) * ngroups, s));
+            AMG_TRY(tmp.alloc_n(&dorder, (size_t)ngroups));
             AMG_TRY_CUDA(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * ngroups,
                                          cudaMemcpyHostToDevice, s));
             AMG_TRY(keep.alloc_n(&S.perm, (size_t)nslots));
@@ -572,11 +578,7 @@ int bsr_to_sell(const BsrD &B, DevArena &keep, cudaStream_t s, Sell<T> *out, dou
             count_launch(1);
             AMG_TRY_CUDA(cudaGetLastError());
             AMG_TRY_CUDA(cudaStreamSynchronize(s));  // order is host memory
-            AMG_TRY_CUDA(cudaFreeAsync(dorder, s));
         }
-        if (pw) AMG_TRY_CUDA(cudaFreeAsync(pw, s));
-        AMG_TRY_CUDA(cudaFreeAsync(w, s));
-        AMG_TRY_CUDA(cudaFreeAsync(tot, s));
     }
     std::vector<int64_t> sp(S.nslices + 1, 0);
     for (int i = 0; i < S.nslices; ++i) sp[i + 1] = sp[i] + 32LL * wh[i];

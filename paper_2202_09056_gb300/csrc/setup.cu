@@ -157,14 +157,20 @@ int compute_strength(const BsrD &A, double eps, uint8_t *strong, cudaStream_t s)
 {
     if (A.nbr == 0) return AMG_OK;
     double *dn = nullptr;
-    AMG_TRY_CUDA(cudaMallocAsync((void **)&dn, sizeof(double) * A.nbr, s));
+    DevArena tmp;
+    tmp.stream = s;
+    AMG_TRY(tmp.alloc_n(&dn, (size_t)A.nbr));
     diag_norm_kernel<<<nblk(A.nbr), T1D, 0, s>>>(A.row_ptr, A.col, A.val, A.nbr, A.br, dn); ::amg::count_launch(1);
     const double e2 = eps * eps;
     strength_kernel<<<nblk((int64_t)A.nbr * 32), T1D, 0, s>>>(A.row_ptr, A.col, A.val, A.nbr, A.br,
                                                               e2, dn, strong);
     ::amg::count_launch(1);
-    AMG_TRY_CUDA(cudaGetLastError());
-    AMG_TRY_CUDA(cudaFreeAsync(dn, s));
+    const cudaError_t e = cudaGetLastError();
+    tmp.release_all();
+    if (e != cudaSuccess) {
+        set_error("strength kernels: %s", cudaGetErrorString(e));
+        return AMG_ERR_CUDA;
+    }
     return AMG_OK;
 }
 
@@ -1532,6 +1538,320 @@ int unblock_bsr(const BsrD &B, DevArena &mem, cudaStream_t s, BsrD *out)
     }
     AMG_TRY_CUDA(cudaGetLastError());
     *out = U;
+    return AMG_OK;
+}
+
+
+// ---------------------------------------------------------------- scalar setup
+// The hierarchy built in scalar arithmetic, as the paper's scalar solvers do
+// (Sec. 3: "NS Scalar", and "NS Hybrid1", which converts the scalar
+// hierarchy into blocks afterwards, Listing 1): every matrix is scalar CSR
+// (1x1 blocks) and a level's nodes are groups of b consecutive scalar rows
+// (b = 3 on the finest level, the near-nullspace size below).  Strength and
+// aggregation see the node graph condensed from the scalar pattern
+// (point-wise aggregation with block size b, Sec. 4); the tentative
+// prolongation, its smoothing, the Galerkin product and SPAI0 run on scalar
+// rows.  The arithmetic of every value is the block setup's, entry by entry.
+
+__global__ void node_membership_kernel(int nn, int b, int *__restrict__ xrp, int *__restrict__ xcol)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= nn) xrp[i] = i * b;
+    if (i < nn * b) xcol[i] = i;
+}
+
+__global__ void col_div_kernel(const int *__restrict__ col, int64_t nnz, int bc, int *__restrict__ out)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < nnz) out[k] = col[k] / bc;
+}
+
+// Block pattern of a scalar CSR matrix S in br x bc blocks (Sec. 2's block
+// CSR): block (I, J) is present iff a scalar of rows I br .. I br + br - 1
+// lies in columns J bc .. J bc + bc - 1.  The symbolic product of the row
+// membership (block row I -> its br scalar rows) with S's pattern read in
+// block columns: sorted, each block once.
+static int condense_pattern(const BsrD &S, int br, int bc, DevArena &keep, DevArena &tmp,
+                            cudaStream_t s, BsrD *out)
+{
+    const int nbr = S.nbr / br, nbc = S.nbc / bc;
+    int *xrp = nullptr, *xcol = nullptr, *ycol = nullptr;
+    AMG_TRY(tmp.alloc_n(&xrp, (size_t)nbr + 1));
+    AMG_TRY(tmp.alloc_n(&xcol, (size_t)std::max(S.nbr, 1)));
+    AMG_TRY(tmp.alloc_n(&ycol, (size_t)std::max<int64_t>(S.nnzb, 1)));
+    node_membership_kernel<<<nblk((int64_t)nbr * br + 1), T1D, 0, s>>>(nbr, br, xrp, xcol);
+    ::amg::count_launch(1);
+    if (S.nnzb > 0) {
+        col_div_kernel<<<nblk(S.nnzb), T1D, 0, s>>>(S.col, S.nnzb, bc, ycol);
+        ::amg::count_launch(1);
+    }
+    AMG_TRY_CUDA(cudaGetLastError());
+    int total = 0;
+    AMG_TRY(spgemm_symbolic(xrp, xcol, nbr, S.row_ptr, ycol, nbc, keep, tmp, s, &out->row_ptr,
+                            &out->col, &total));
+    out->nbr = nbr;
+    out->nbc = nbc;
+    out->br = br;
+    out->bc = bc;
+    out->nnzb = total;
+    out->val = nullptr;
+    tmp.release(xrp);
+    tmp.release(xcol);
+    tmp.release(ycol);
+    return AMG_OK;
+}
+
+// Block (I, J) of S: for each of its br scalar rows, the entries in columns
+// J bc .. J bc + bc - 1 (located by binary search in the sorted row); absent
+// scalars are explicit zeros.  One thread per block.
+__global__ void block_values_kernel(const int *__restrict__ brow, const int *__restrict__ bcol,
+                                    int64_t nnzb, int br, int bc, const int *__restrict__ srp,
+                                    const int *__restrict__ scol, const double *__restrict__ sval,
+                                    double *__restrict__ bval)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nnzb) return;
+    const int I = brow[k], c0 = bcol[k] * bc;
+    double *dst = bval + k * br * bc;
+    for (int r = 0; r < br; ++r) {
+        const int row = I * br + r, hi = srp[row + 1];
+        int p = find_sorted(scol, srp[row], hi, c0);
+        for (int c = 0; c < bc; ++c) {
+            double v = 0.0;
+            if (p < hi && scol[p] == c0 + c) v = sval[p++];
+            dst[r * bc + c] = v;
+        }
+    }
+}
+
+// Squared Frobenius norm of node block (I, J), its scalars summed in
+// row-major order without FMA contraction (the order of the block strength
+// kernel; absent scalars add nothing).  One thread per node-graph entry.
+__global__ void node_norm2_kernel(const int *__restrict__ brow, const int *__restrict__ bcol,
+                                  int64_t nnzb, int b, const int *__restrict__ srp,
+                                  const int *__restrict__ scol, const double *__restrict__ sval,
+                                  double *__restrict__ norm2)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nnzb) return;
+    const int I = brow[k], c0 = bcol[k] * b;
+    double acc = 0.0;
+    for (int r = 0; r < b; ++r) {
+        const int row = I * b + r, hi = srp[row + 1];
+        for (int p = find_sorted(scol, srp[row], hi, c0); p < hi && scol[p] < c0 + b; ++p)
+            acc = __dadd_rn(acc, __dmul_rn(sval[p], sval[p]));
+    }
+    norm2[k] = acc;
+}
+
+__global__ void node_diag_norm_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                                      const double *__restrict__ norm2, int nn,
+                                      double *__restrict__ dn)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nn) return;
+    double v = 0.0;
+    for (int p = rp[I]; p < rp[I + 1]; ++p)
+        if (col[p] == I) v = __dsqrt_rn(norm2[p]);
+    dn[I] = v;
+}
+
+// the block strength test on the node graph's norms (same operations)
+__global__ void node_strength_kernel(const int *__restrict__ brow, const int *__restrict__ bcol,
+                                     int64_t nnzb, const double *__restrict__ norm2,
+                                     const double *__restrict__ dn, double e2,
+                                     uint8_t *__restrict__ strong)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nnzb) return;
+    const int I = brow[k], J = bcol[k];
+    uint8_t st = 0;
+    if (J != I) {
+        double thr = __dmul_rn(e2, dn[I]);
+        thr = __dmul_rn(thr, dn[J]);
+        st = norm2[k] > thr ? 1 : 0;
+    }
+    strong[k] = st;
+}
+
+int scalar_to_block(const BsrD &S, int br, int bc, DevArena &keep, DevArena &tmp, cudaStream_t s,
+                    BsrD *out)
+{
+    AMG_TRY(condense_pattern(S, br, bc, keep, tmp, s, out));
+    AMG_TRY(keep.alloc_n(&out->val, (size_t)std::max<int64_t>(out->nnzb, 1) * br * bc));
+    if (out->nnzb > 0) {
+        int *brow = nullptr;
+        AMG_TRY(tmp.alloc_n(&brow, (size_t)out->nnzb));
+        block_rows_kernel<<<nblk(out->nbr), T1D, 0, s>>>(out->row_ptr, out->nbr, brow);
+        block_values_kernel<<<nblk(out->nnzb), T1D, 0, s>>>(brow, out->col, out->nnzb, br, bc,
+                                                            S.row_ptr, S.col, S.val, out->val);
+        ::amg::count_launch(2);
+        AMG_TRY_CUDA(cudaGetLastError());
+        tmp.release(brow);
+    }
+    return AMG_OK;
+}
+
+int scalar_strength(const BsrD &S, int b, double eps, DevArena &keep, DevArena &tmp,
+                    cudaStream_t s, BsrD *graph, uint8_t **strong)
+{
+    AMG_TRY(condense_pattern(S, b, b, keep, tmp, s, graph));
+    const int nn = graph->nbr;
+    AMG_TRY(keep.alloc_n(strong, (size_t)std::max<int64_t>(graph->nnzb, 1)));
+    if (graph->nnzb == 0) return AMG_OK;
+    int *brow = nullptr;
+    double *norm2 = nullptr, *dn = nullptr;
+    AMG_TRY(tmp.alloc_n(&brow, (size_t)graph->nnzb));
+    AMG_TRY(tmp.alloc_n(&norm2, (size_t)graph->nnzb));
+    AMG_TRY(tmp.alloc_n(&dn, (size_t)std::max(nn, 1)));
+    block_rows_kernel<<<nblk(nn), T1D, 0, s>>>(graph->row_ptr, nn, brow);
+    node_norm2_kernel<<<nblk(graph->nnzb), T1D, 0, s>>>(brow, graph->col, graph->nnzb, b,
+                                                         S.row_ptr, S.col, S.val, norm2);
+    node_diag_norm_kernel<<<nblk(nn), T1D, 0, s>>>(graph->row_ptr, graph->col, norm2, nn, dn);
+    node_strength_kernel<<<nblk(graph->nnzb), T1D, 0, s>>>(brow, graph->col, graph->nnzb, norm2,
+                                                            dn, eps * eps, *strong);
+    ::amg::count_launch(4);
+    AMG_TRY_CUDA(cudaGetLastError());
+    tmp.release(brow);
+    tmp.release(norm2);
+    tmp.release(dn);
+    return AMG_OK;
+}
+
+// tentative prolongation rows: scalar row i of an aggregated node holds the
+// ns columns of its aggregate (all stored, zeros included)
+__global__ void ptent_count_kernel(const int *__restrict__ agg, int n, int b, int ns,
+                                   int *__restrict__ cnt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cnt[i] = agg[i / b] >= 0 ? ns : 0;
+}
+
+__global__ void ptent_fill_kernel(const int *__restrict__ agg, int n, int b, int ns,
+                                  const int *__restrict__ rp, const double *__restrict__ ptent,
+                                  int *__restrict__ col, double *__restrict__ val)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int a = agg[i / b];
+    if (a < 0) return;
+    for (int k = 0; k < ns; ++k) {
+        col[rp[i] + k] = ns * a + k;
+        val[rp[i] + k] = ptent[(int64_t)i * ns + k];
+    }
+}
+
+// P = P_tent - omega D^-1 (A P_tent) in place on A P_tent's entries (its
+// pattern holds P_tent's: A keeps its diagonal): s_i = omega / d_i (0 when
+// d_i = 0), then p_ij - s_i (A P_tent)_ij, p_ij = 0 outside P_tent.
+__global__ void scalar_smooth_p_kernel(const int *__restrict__ prow, const int *__restrict__ pcol,
+                                       int64_t nnz, const int *__restrict__ agg, int b, int ns,
+                                       const double *__restrict__ ptent,
+                                       const double *__restrict__ d, double omega,
+                                       double *__restrict__ val)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nnz) return;
+    const int i = prow[k], j = pcol[k], a = agg[i / b];
+    const double pt = (a >= 0 && j / ns == a) ? ptent[(int64_t)i * ns + (j - ns * a)] : 0.0;
+    const double di = d[i];
+    const double sc = di != 0.0 ? __ddiv_rn(omega, di) : 0.0;
+    val[k] = __dsub_rn(pt, __dmul_rn(sc, val[k]));
+}
+
+int scalar_transfer(const BsrD &S, int b, const double *B, int ns, const int *agg_h, int nagg,
+                    double relax, DevArena &keep, DevArena &tmp, cudaStream_t s, LevelBuild *out)
+{
+    const int n = S.nbr, nn = n / b;
+    std::vector<int> aptr(nagg + 1, 0), mem;
+    for (int I = 0; I < nn; ++I)
+        if (agg_h[I] >= 0) aptr[agg_h[I] + 1]++;
+    for (int a = 0; a < nagg; ++a) aptr[a + 1] += aptr[a];
+    mem.resize(std::max(aptr[nagg], 1));
+    {
+        std::vector<int> fill(aptr.begin(), aptr.end() - 1);
+        for (int I = 0; I < nn; ++I)
+            if (agg_h[I] >= 0) mem[fill[agg_h[I]]++] = I;
+    }
+    int *d_aptr = nullptr, *d_mem = nullptr, *cnt = nullptr;
+    double *Qs = nullptr, *ptent = nullptr, *d = nullptr;
+    unsigned long long *rho_bits = nullptr;
+    AMG_TRY(tmp.alloc_n(&d_aptr, nagg + 1));
+    AMG_TRY(tmp.alloc_n(&d_mem, mem.size()));
+    AMG_TRY(keep.alloc_n(&out->agg, std::max(nn, 1)));
+    AMG_TRY(tmp.alloc_n(&Qs, (size_t)std::max(aptr[nagg], 1) * b * ns));
+    AMG_TRY(tmp.alloc_n(&ptent, (size_t)std::max(n, 1) * ns));
+    AMG_TRY(tmp.alloc_n(&d, (size_t)std::max(n, 1)));
+    AMG_TRY(tmp.alloc_n(&rho_bits, 1));
+    AMG_TRY(tmp.alloc_n(&cnt, (size_t)n + 1));
+    AMG_TRY(keep.alloc_n(&out->Bc, (size_t)std::max(nagg, 1) * ns * ns));
+    AMG_TRY_CUDA(cudaMemcpyAsync(d_aptr, aptr.data(), sizeof(int) * (nagg + 1),
+                                 cudaMemcpyHostToDevice, s));
+    AMG_TRY_CUDA(cudaMemcpyAsync(d_mem, mem.data(), sizeof(int) * mem.size(),
+                                 cudaMemcpyHostToDevice, s));
+    AMG_TRY_CUDA(cudaMemcpyAsync(out->agg, agg_h, sizeof(int) * nn, cudaMemcpyHostToDevice, s));
+    AMG_TRY_CUDA(cudaMemsetAsync(ptent, 0, sizeof(double) * (size_t)n * ns, s));
+    AMG_TRY_CUDA(cudaMemsetAsync(rho_bits, 0, sizeof(unsigned long long), s));
+    out->nagg = nagg;
+    // per-aggregate QR of the stacked near-nullspace rows (the same kernel
+    // as the block setup: it is scalar arithmetic in either setup)
+    if (nagg > 0) {
+        if (ns == 6)
+            tentative_kernel<6><<<nblk((int64_t)nagg * 32), T1D, 0, s>>>(nagg, b, d_aptr, d_mem, B,
+                                                                          Qs, ptent, out->Bc);
+        else
+            tentative_kernel<3><<<nblk((int64_t)nagg * 32), T1D, 0, s>>>(nagg, b, d_aptr, d_mem, B,
+                                                                          Qs, ptent, out->Bc);
+        ::amg::count_launch(1);
+    }
+    // scalar rows: d_i and the Gershgorin bound, columns ascending
+    jacobi_rho_kernel<<<nblk(n), T1D, 0, s>>>(S.row_ptr, S.col, S.val, n, 1, d, rho_bits);
+    ptent_count_kernel<<<nblk(n), T1D, 0, s>>>(out->agg, n, b, ns, cnt);
+    ::amg::count_launch(2);
+    AMG_TRY_CUDA(cudaGetLastError());
+    unsigned long long rb = 0;
+    AMG_TRY_CUDA(cudaMemcpyAsync(&rb, rho_bits, sizeof(rb), cudaMemcpyDeviceToHost, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope after this
+    double rho;
+    std::memcpy(&rho, &rb, sizeof rho);
+    out->rho = rho;
+    out->omega = (rho > 0.0) ? relax * (4.0 / 3.0) / rho : 0.0;
+    // P_tent as scalar CSR
+    BsrD Pt;
+    Pt.nbr = n;
+    Pt.nbc = nagg * ns;
+    Pt.br = Pt.bc = 1;
+    int total = 0;
+    AMG_TRY(tmp.alloc_n(&Pt.row_ptr, (size_t)n + 1));
+    AMG_TRY(exclusive_scan_i32(cnt, Pt.row_ptr, n, &total, tmp, s));
+    Pt.nnzb = total;
+    AMG_TRY(tmp.alloc_n(&Pt.col, (size_t)std::max(total, 1)));
+    AMG_TRY(tmp.alloc_n(&Pt.val, (size_t)std::max(total, 1)));
+    ptent_fill_kernel<<<nblk(n), T1D, 0, s>>>(out->agg, n, b, ns, Pt.row_ptr, ptent, Pt.col,
+                                              Pt.val);
+    ::amg::count_launch(1);
+    AMG_TRY_CUDA(cudaGetLastError());
+    // A P_tent (scalar SpGEMM), then P in place on its entries
+    BsrD &P = out->P;
+    AMG_TRY(spgemm(S, Pt, keep, tmp, s, &P));
+    if (P.nnzb > 0) {
+        int *prow = nullptr;
+        AMG_TRY(tmp.alloc_n(&prow, (size_t)P.nnzb));
+        block_rows_kernel<<<nblk(n), T1D, 0, s>>>(P.row_ptr, n, prow);
+        scalar_smooth_p_kernel<<<nblk(P.nnzb), T1D, 0, s>>>(prow, P.col, P.nnzb, out->agg, b, ns,
+                                                            ptent, d, out->omega, P.val);
+        ::amg::count_launch(2);
+        AMG_TRY_CUDA(cudaGetLastError());
+        AMG_TRY(transpose_bsr(P, prow, keep, tmp, s, &out->R));
+        tmp.release(prow);
+    } else {
+        AMG_TRY(transpose_bsr(P, nullptr, keep, tmp, s, &out->R));
+    }
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    for (void *q : {(void *)d_aptr, (void *)d_mem, (void *)Qs, (void *)ptent, (void *)d,
+                    (void *)rho_bits, (void *)cnt, (void *)Pt.row_ptr, (void *)Pt.col,
+                    (void *)Pt.val})
+        tmp.release(q);
     return AMG_OK;
 }
 

@@ -125,10 +125,13 @@ __global__ void cg_direction_kernel(const TV *__restrict__ z, double *__restrict
                                     const CgState *__restrict__ st, int64_t n)
 {
     if (st->stop) return;
+    // the first direction is z itself: p holds no earlier direction to scale
+    // (0 * p would carry whatever its memory held, NaN included)
     const double beta = st->beta;
+    const bool first = st->it == 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = (double)z[i] + beta * p[i];
+        p[i] = first ? (double)z[i] : (double)z[i] + beta * p[i];
 }
 
 __global__ void __launch_bounds__(FIN_THREADS) cg_alpha_kernel(CgState *st,
@@ -646,27 +649,6 @@ int amg_params_default(amg_params *prm)
 
 const char *amg_last_error(void) { return amg::last_error(); }
 
-static int check_bsr(const amg_bsr *A, int want_square)
-{
-    if (!A) {
-        set_error("null matrix");
-        return AMG_ERR_ARG;
-    }
-    if (A->nbrows < 0 || A->nbcols < 0 || A->nnzb < 0 || A->nnzb > 2147483647LL) {
-        set_error("bad matrix dimensions");
-        return AMG_ERR_ARG;
-    }
-    if (want_square && (A->nbrows != A->nbcols || A->bs_r != A->bs_c)) {
-        set_error("matrix must be square with square blocks");
-        return AMG_ERR_ARG;
-    }
-    if (!A->row_ptr || (A->nnzb > 0 && (!A->col || !A->val))) {
-        set_error("null matrix array");
-        return AMG_ERR_ARG;
-    }
-    return AMG_OK;
-}
-
 }  // extern "C"
 
 void amg::destroy_handle(amg_handle h)
@@ -674,9 +656,16 @@ void amg::destroy_handle(amg_handle h)
     if (!h) return;
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
-    h->mem.release_all();
-    if (h->stream) cudaStreamSynchronize(h->stream);
-    else cudaDeviceSynchronize();
+    if (h->mem.has_custom()) {
+        // the caller's supplier may hand the buffers to work on any stream:
+        // nothing of this handle may still be queued when they go back
+        cudaDeviceSynchronize();
+        h->mem.release_all();
+    } else {
+        h->mem.release_all();
+        if (h->stream) cudaStreamSynchronize(h->stream);
+        else cudaDeviceSynchronize();
+    }
     if (h->st_h) cudaFreeHost(h->st_h);
     delete h;
 }
@@ -743,6 +732,89 @@ __global__ void validate_pattern_kernel(const int *__restrict__ rp, const int *_
         atomicOr(bad, code);
         atomicMin(bad + 1, I);
     }
+}
+
+// Alg. 1 in scalar arithmetic (AMG_SETUP_SCALAR): level 0 unblocked, then
+// per level the node graph's strength, aggregation (host greedy passes or
+// device MIS-2 on the node graph), the scalar transfer operators, the scalar
+// Galerkin product and SPAI0; the coarsest scalar matrix is factored; last,
+// every level is converted into blocks (level 0 keeps the input blocks).
+// The scalar matrices stay in L.xA, L.xP, L.xR for the solve copies.
+template <class Lap>
+static int setup_levels_scalar(amg_handle h, DevArena &tmp, Lap &lap)
+{
+    cudaStream_t s = h->stream;
+    const amg_params &prm = h->prm;
+    AMG_TRY(unblock_bsr(h->lv[0].A, h->mem, s, &h->lv[0].xA));
+    lap(0);
+    for (;;) {
+        Level &C = h->lv.back();
+        const int b = h->lv.size() == 1 ? 3 : h->ns;
+        const BsrD &S = C.xA;
+        const int n = S.nbr, nn = n / b;
+        if (n <= prm.coarse_enough || (int)h->lv.size() >= prm.max_levels) break;
+        BsrD G;
+        AMG_TRY(scalar_strength(S, b, C.eps, h->mem, tmp, s, &G, &C.strong));
+        std::vector<int> agg(std::max(nn, 1));
+        int nagg = 0;
+        if (prm.aggregation == AMG_AGG_MIS2) {
+            int *dagg = nullptr;
+            AMG_TRY(tmp.alloc_n(&dagg, (size_t)nn));
+            AMG_TRY(aggregate_mis2(G, C.strong, dagg, &nagg, nullptr, tmp, s));
+            AMG_TRY_CUDA(cudaMemcpyAsync(agg.data(), dagg, sizeof(int) * nn,
+                                         cudaMemcpyDeviceToHost, s));
+            AMG_TRY_CUDA(cudaStreamSynchronize(s));
+            tmp.release(dagg);
+        } else {
+            std::vector<int> rp(nn + 1), cl(std::max<int64_t>(G.nnzb, 1));
+            std::vector<uint8_t> sf(std::max<int64_t>(G.nnzb, 1));
+            AMG_TRY_CUDA(cudaMemcpyAsync(rp.data(), G.row_ptr, sizeof(int) * (nn + 1),
+                                         cudaMemcpyDeviceToHost, s));
+            AMG_TRY_CUDA(cudaMemcpyAsync(cl.data(), G.col, sizeof(int) * G.nnzb,
+                                         cudaMemcpyDeviceToHost, s));
+            AMG_TRY_CUDA(cudaMemcpyAsync(sf.data(), C.strong, G.nnzb, cudaMemcpyDeviceToHost, s));
+            AMG_TRY_CUDA(cudaStreamSynchronize(s));
+            AMG_TRY(aggregate_host(nn, rp.data(), cl.data(), sf.data(), agg.data(), &nagg));
+        }
+        h->mem.release(G.row_ptr);
+        h->mem.release(G.col);
+        lap(1);
+        if (nagg == 0 || (double)nagg >= 0.9 * (double)nn) break;
+        LevelBuild lb;
+        AMG_TRY(scalar_transfer(S, b, C.B, h->ns, agg.data(), nagg, prm.relax, h->mem, tmp, s,
+                                &lb));
+        lap(2);
+        C.xP = lb.P;
+        C.xR = lb.R;
+        C.agg = lb.agg;
+        C.nagg = nagg;
+        C.omega = lb.omega;
+        C.rho = lb.rho;
+        Level N;
+        AMG_TRY(galerkin(S, C.xP, C.xR, h->mem, tmp, s, &N.xA));
+        lap(3);
+        N.B = lb.Bc;
+        N.eps = C.eps * 0.5;
+        AMG_TRY(h->mem.alloc_n(&C.M, (size_t)std::max(n, 1)));
+        AMG_TRY(spai0_diag(S, prm.smooth_relax, C.M, s));
+        lap(4);
+        h->lv.push_back(N);
+    }
+    Level &Cc = h->lv.back();
+    Cc.coarsest = true;
+    AMG_TRY(coarse_inverse(Cc.xA, h->mem, tmp, s, &h->Ainv));
+    h->nc = Cc.xA.nbr;
+    lap(5);
+    for (size_t l = 0; l < h->lv.size(); ++l) {
+        Level &L = h->lv[l];
+        const int b = l == 0 ? 3 : h->ns;
+        if (l > 0) AMG_TRY(scalar_to_block(L.xA, b, b, h->mem, tmp, s, &L.A));
+        if (!L.coarsest) {
+            AMG_TRY(scalar_to_block(L.xP, b, h->ns, h->mem, tmp, s, &L.P));
+            AMG_TRY(scalar_to_block(L.xR, h->ns, b, h->mem, tmp, s, &L.R));
+        }
+    }
+    return AMG_OK;
 }
 
 int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
@@ -838,7 +910,9 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         h->lv.push_back(L0);
     }
     lap(0);
-    for (;;) {
+    if (prm.setup == AMG_SETUP_SCALAR) {
+        AMG_TRY(setup_levels_scalar(h, tmp, lap));
+    } else for (;;) {
         Level &C = h->lv.back();
         const int nn = C.A.nbr, n = C.n();
         if (n <= prm.coarse_enough || (int)h->lv.size() >= prm.max_levels) break;
@@ -888,11 +962,13 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         lap(4);
         h->lv.push_back(N);
     }
-    Level &Cc = h->lv.back();
-    Cc.coarsest = true;
-    AMG_TRY(coarse_inverse(Cc.A, h->mem, tmp, s, &h->Ainv));
-    h->nc = Cc.n();
-    lap(5);
+    if (prm.setup != AMG_SETUP_SCALAR) {
+        Level &Cc = h->lv.back();
+        Cc.coarsest = true;
+        AMG_TRY(coarse_inverse(Cc.A, h->mem, tmp, s, &h->Ainv));
+        h->nc = Cc.n();
+        lap(5);
+    }
     if (prm.smoother == AMG_SMOOTH_ILU0) {  // block ILU(0) of every smoothing level
         for (size_t l = 0; l + 1 < h->lv.size(); ++l)
             AMG_TRY(ilu0_factor(h->lv[l].A, h->max_lanes, h->mem, tmp, s, &h->lv[l].ilu));
@@ -910,7 +986,13 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
         // scalar unblocking (temporary; only the sliced copies are kept)
         BsrD uA, uP, uR;
         const BsrD *oA = &L.A, *oP = &L.P, *oR = &L.R;
-        if (scalar) {
+        if (scalar && L.xA.row_ptr) {  // the scalar setup's own matrices
+            oA = &L.xA;
+            if (vc) {
+                oP = &L.xP;
+                oR = &L.xR;
+            }
+        } else if (scalar) {
             if (l == 0 || vc) {
                 AMG_TRY(unblock_bsr(L.A, tmp, s, &uA));
                 oA = &uA;
@@ -953,6 +1035,15 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
             }
         }
     }
+    // the scalar setup's matrices are not kept past the solve copies
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    for (Level &L : h->lv)
+        for (BsrD *x : {&L.xA, &L.xP, &L.xR}) {
+            h->mem.release(x->row_ptr);
+            h->mem.release(x->col);
+            h->mem.release(x->val);
+            *x = BsrD();
+        }
     for (size_t l = 0; l < h->lv.size(); ++l) {
         Level &L = h->lv[l];
         const size_t n = (size_t)std::max(L.n(), 1);
@@ -1027,8 +1118,13 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
         p.loop_mode < 0 || p.loop_mode > 1 || p.storage < AMG_STORAGE_BLOCK ||
         p.storage > AMG_STORAGE_SCALAR || p.aggregation < AMG_AGG_GREEDY ||
         p.aggregation > AMG_AGG_MIS2 || p.smoother < AMG_SMOOTH_SPAI0 ||
-        p.smoother > AMG_SMOOTH_ILU0 || p.ilu_sweeps < 0 || p.ilu_sweeps > 64) {
+        p.smoother > AMG_SMOOTH_ILU0 || p.ilu_sweeps < 0 || p.ilu_sweeps > 64 ||
+        p.setup < AMG_SETUP_BLOCK || p.setup > AMG_SETUP_SCALAR || p.reserved != 0) {
         set_error("bad parameters");
+        return AMG_ERR_ARG;
+    }
+    if (p.setup == AMG_SETUP_SCALAR && p.smoother != AMG_SMOOTH_SPAI0) {
+        set_error("the scalar setup builds the SPAI0 smoother");
         return AMG_ERR_ARG;
     }
     if (p.smoother == AMG_SMOOTH_ILU0 &&
@@ -1039,9 +1135,19 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
     auto t0 = std::chrono::steady_clock::now();
     amg_handle h = new amg_handle_s();
     h->prm = p;
+    if (p.allocator) {
+        if (!p.allocator->alloc || !p.allocator->free) {
+            delete h;
+            set_error("amg_params.allocator needs both alloc and free");
+            return AMG_ERR_ARG;
+        }
+        h->alloc = *p.allocator;
+    }
+    h->prm.allocator = nullptr;  // the caller's struct is not kept; h->alloc is the copy
     h->ns = nb_ns;
     h->stream = (cudaStream_t)stream;
     h->mem.stream = h->stream;
+    AllocScope scope(h->allocator());
     int st = setup_impl(h, A, B);
     if (st < 0) {
         std::string msg = amg::last_error();
@@ -1064,6 +1170,7 @@ int amg_apply_vcycle(amg_handle h, const double *r, double *z, void *stream)
         set_error("null argument");
         return AMG_ERR_ARG;
     }
+    AllocScope scope(h->allocator());
     cudaStream_t s = (cudaStream_t)stream;
     Level &L0 = h->lv[0];
     const int64_t n = L0.n();
@@ -1108,6 +1215,7 @@ int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxi
         set_error("bad tolerance or iteration limit");
         return AMG_ERR_ARG;
     }
+    AllocScope scope(h->allocator());
     cudaStream_t s = (cudaStream_t)stream;
     Level &L0 = h->lv[0];
     const int64_t n = L0.n();
@@ -1283,6 +1391,7 @@ int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_pt
         set_error("bad level");
         return AMG_ERR_ARG;
     }
+    AllocScope scope(h->allocator());
     const Level &L = h->lv[level];
     cudaStream_t s = h->stream;
     switch (which) {
@@ -1332,6 +1441,7 @@ int amg_level_spmv(amg_handle h, int32_t level, int32_t which, const double *x, 
         set_error("bad argument");
         return AMG_ERR_ARG;
     }
+    AllocScope scope(h->allocator());
     const Level &L = h->lv[level];
     if (which >= 3) {  // the FP32-pair copies of an AMG_PREC_DF64 hierarchy
         const Sell<df32> &E = which == 3 ? L.eA : which == 4 ? L.eP : L.eR;
@@ -1390,6 +1500,7 @@ int amg_level_galerkin(amg_handle h, int32_t level, int32_t storage, double *sec
         set_error("bad argument (level must have a coarser level)");
         return AMG_ERR_ARG;
     }
+    AllocScope scope(h->allocator());
     const Level &L = h->lv[level];
     const BsrD &Ac0 = h->lv[level + 1].A;
     cudaStream_t s = h->stream;

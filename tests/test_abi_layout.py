@@ -12,7 +12,8 @@ import paper_2202_09056_gb300 as amg
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = {"amg_bsr": amg.Bsr, "amg_params": amg.Params, "amg_level_desc": amg.LevelDesc,
-           "amg_stats": amg.Stats, "amg_batch_desc": amg.BatchDesc}
+           "amg_stats": amg.Stats, "amg_batch_desc": amg.BatchDesc,
+           "amg_allocator": amg.Allocator}
 
 
 def test_ctypes_structs_match_the_header(tmp_path):
