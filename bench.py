@@ -157,9 +157,10 @@ def fp64_peak(amg):
     TFLOP/s peak with its derivation."""
     runs = [amg.fp64_fma_rate() for _ in range(3)]
     best = max(runs, key=lambda r: r["tflops"])
-    return best["tflops"], (f"measured: {best['num_sms']} SMs x 4 CTAs x 256 threads x 8 "
-                            f"independent FP64 FMA chains, best of 3 launches of "
-                            f"{best['seconds'] * 1e3:.1f} ms, 2 flops per FMA")
+    return best["tflops"], (f"measured: FP64 FMA chains (4, 8 or 16 per thread, 2, 4 or 8 "
+                            f"CTAs of 256 threads per SM on {best['num_sms']} SMs), the fastest "
+                            f"configuration of 3 runs ({best['seconds'] * 1e3:.1f} ms), "
+                            f"2 flops per FMA")
 
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
@@ -534,6 +535,8 @@ def run_batch(args, amg, torch, rank=0, world=1, dist=None, local=0):
                    "parallelism": (f"dp{world}: every rank its own seeded batch of 64"
                                    if world > 1 else "single")},
         "batch": {"setup_s": setup_t, "rhs_tile_per_level_A_P_R": info["rhs_tile"],
+                  "cta_threads_per_level_A_P_R": info["cta_threads"],
+                  "ctas_per_sm_per_level_A_P_R": info["ctas_per_sm"],
                   "iterations_max": int(max(max(x) for x in its)),
                   "iterations_mean": float(np.mean([y for x in its for y in x])),
                   "rel_resid_max": float(max(max(x) for x in res)),

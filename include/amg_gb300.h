@@ -168,9 +168,13 @@ typedef struct {
  * library). */
 typedef struct {
     double eps_strong;     /* strength threshold on level 1; halved per level (0.08) */
-    double relax;          /* multiplier of omega = (4/3)/rho in P smoothing (1.0) */
+    double relax;          /* multiplier of omega = (4/3)/rho in P smoothing (2.0: the
+                              Gershgorin rho over-estimates lambda_max(D^-1 A) by
+                              1.4-2.2x on elasticity matrices) */
     double smooth_relax;   /* damping of the SPAI0 smoother (0.8) */
-    int32_t coarse_enough; /* stop coarsening at <= this many scalar rows (3000) */
+    int32_t coarse_enough; /* stop coarsening at <= this many scalar rows (3000); a level
+                              below the finest with <= 2 coarse_enough rows also stops
+                              when its aggregates would give < coarse_enough / 4 rows */
     int32_t max_levels;    /* at most this many levels (15) */
     int32_t npre, npost;   /* smoothing sweeps before / after the correction (1, 1) */
     int32_t precision;     /* AMG_PREC_* of the V-cycle (AMG_PREC_FP64) */
@@ -347,6 +351,11 @@ typedef struct {
     int64_t dofs_total;     /* fine-level unknowns over all instances */
     int64_t bytes_total;    /* device memory held by the batch */
     int32_t rhs_tile[48];   /* autotuned right-hand-side tile of A, P, R per level */
+    int32_t cta_threads[48];/* autotuned block-row tiling of A, P, R per level: threads
+                               per CTA (64, 128, 256; each warp one slice of 32 / G
+                               block rows), 0 for an absent operator */
+    int32_t ctas_per_sm[48];/* ... and the CTAs per SM before the warp-strided loop
+                               wraps (16, 32) */
 } amg_batch_desc;
 
 /* Many independent instances of Eq. 1, each with its own near-nullspace and
@@ -437,13 +446,15 @@ void amg_trainer_free(amg_trainer t);
 /* Measured FP64 FMA rate of the current device (host outputs), the
  * denominator of the arithmetic roofline of the FP64 SpMV: every SpMV entry
  * is one FMA (2 b_r b_c flops per block, Sec. 2's block arithmetic), and on
- * GB300 the FP64 pipe, not HBM, bounds that kernel.  One grid of 4 CTAs x
- * 256 threads per SM, each thread running 8 independent FMA chains for
- * `iters` steps, timed with CUDA events on `stream` after one short warm-up
- * launch.  sink (device, sink_len doubles, caller-owned) receives the
- * chains' sums so that the work is observable.  *fma_per_second = FMAs / s;
- * *seconds (may be NULL) = the timed launch; *num_sms (may be NULL) = the
- * device's SM count.  Synchronises `stream`. */
+ * GB300 the FP64 pipe, not HBM, bounds that kernel.  Threads of 256-thread
+ * CTAs run 4, 8 or 16 independent FMA chains at 2, 4 or 8 CTAs per SM, the
+ * same total work (about 8 x 4 x 256 x `iters` FMAs per SM) in every
+ * configuration, each timed with CUDA events on `stream` after a short
+ * warm-up launch; the fastest configuration's rate is reported.  sink
+ * (device, sink_len doubles, caller-owned, at least 2048 x the SM count)
+ * receives the chains' sums so that the work is observable.  *fma_per_second = FMAs / s; *seconds (may
+ * be NULL) = the duration of the fastest configuration; *num_sms (may be
+ * NULL) = the device's SM count.  Synchronises `stream`. */
 int amg_fp64_fma_rate(double *sink, int64_t sink_len, int32_t iters, double *fma_per_second,
                       double *seconds, int32_t *num_sms, void *stream);
 

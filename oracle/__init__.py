@@ -329,7 +329,7 @@ class Hierarchy:
     """Alg. 1 on a scalar CSR matrix; V-cycle (Alg. 2) and PCG on top."""
 
     def __init__(self, A: CSR, bs: int, B: np.ndarray, *, eps_strong=0.08, coarse_enough=3000,
-                 max_levels=15, npre=1, npost=1, relax=1.0, smooth_relax=0.8, smoother="spai0",
+                 max_levels=15, npre=1, npost=1, relax=2.0, smooth_relax=0.8, smoother="spai0",
                  ilu_sweeps=2, aggregation="greedy"):
         lib = _load()
         B = np.ascontiguousarray(B, dtype=np.float64)

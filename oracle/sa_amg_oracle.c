@@ -35,14 +35,21 @@
  *               (zero Q column, zero R row).  B_{i+1} = R.
  *   P smoother: damped Jacobi on the unfiltered matrix, P = P_tent -
  *               omega D^{-1} A P_tent with D = diag(A), rho = max_i
- *               sum_j |a_ij| / |a_ii| (Gershgorin), omega = (4/3) / rho, and
- *               the symbolic pattern.  The strength graph drives only the
+ *               sum_j |a_ij| / |a_ii| (Gershgorin), omega = relax (4/3) / rho
+ *               with relax = 2 by default (Gershgorin over-estimates
+ *               lambda_max(D^{-1} A) by a factor 1.4-2.2 on these matrices,
+ *               so relax = 1 leaves P under-smoothed), and the symbolic
+ *               pattern.  The strength graph drives only the
  *               aggregation: lumping weak entries into the diagonal (the
  *               classical filtered matrix) leaves near-zero and negative
  *               diagonals on elasticity matrices, which collapses omega.  With
  *               A B = 0, P B_{i+1} = B holds for any threshold.
- *   coarsening stops when n <= coarse_enough, at max_levels levels, or when
- *               the aggregates are not fewer than 0.9 x the nodes.
+ *   coarsening stops when n <= coarse_enough, at max_levels levels, when
+ *               the aggregates are not fewer than 0.9 x the nodes, or when a
+ *               level below the finest has at most 2 coarse_enough rows and
+ *               its aggregates would make a level of fewer than
+ *               coarse_enough / 4 rows (a tiny last level, aggregated from a
+ *               dense operator, doubles the CG iterations or worse).
  *   smoother:   damped SPAI0, M = w_s diag(a_ii / sum_j a_ij^2) (0 for an
  *               empty row), w_s = 0.8 by default: undamped SPAI0 has
  *               lambda_max(M A) of about 2.1-2.25 on Q1 elasticity, which
@@ -782,7 +789,7 @@ typedef struct {
     int coarse_enough;   /* 3000 */
     int max_levels;      /* 15 */
     int npre, npost;     /* 1, 1 */
-    double relax;        /* omega multiplier, 1.0 */
+    double relax;        /* omega multiplier, 2.0 */
     double smooth_relax; /* smoother damping w_s, 0.8 */
     int ns;              /* near-nullspace columns of B: 6 (rigid-body modes) or 3 */
     int smoother;        /* 0: damped SPAI0; 1: block ILU(0) */
@@ -797,7 +804,7 @@ void orc_params_default(orc_params *p)
     p->max_levels = 15;
     p->npre = 1;
     p->npost = 1;
-    p->relax = 1.0;
+    p->relax = 2.0;
     p->smooth_relax = 0.8;
     p->ns = 6;
     p->smoother = 0;
@@ -1070,7 +1077,13 @@ orc_hier *orc_setup(const orc_csr *A0, int bs, const double *B0, const orc_param
             orc_free(H);
             return NULL;
         }
-        if (C->nagg == 0 || (double)C->nagg >= 0.9 * (double)nn) {
+        /* Stop rule (Alg. 1 leaves it open): no aggregates, or too few nodes
+         * merged; and a level below the finest that is already small (at most
+         * 2 coarse_enough rows) becomes the coarsest instead of being
+         * coarsened into a tiny level (fewer than coarse_enough / 4 rows). */
+        if (C->nagg == 0 || (double)C->nagg >= 0.9 * (double)nn ||
+            (H->nlev > 1 && n <= 2 * (int64_t)prm->coarse_enough &&
+             4 * C->nagg * (int64_t)ns < (int64_t)prm->coarse_enough)) {
             orc_graph_free(C->G);
             C->G = NULL;
             free(C->agg);

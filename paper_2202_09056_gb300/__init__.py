@@ -125,7 +125,8 @@ class BatchDesc(ctypes.Structure):
     _fields_ = [("ninst", ctypes.c_int32), ("nrhs_total", ctypes.c_int32),
                 ("nlevels", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("setup_seconds", ctypes.c_double), ("dofs_total", ctypes.c_int64),
-                ("bytes_total", ctypes.c_int64), ("rhs_tile", ctypes.c_int32 * 48)]
+                ("bytes_total", ctypes.c_int64), ("rhs_tile", ctypes.c_int32 * 48),
+                ("cta_threads", ctypes.c_int32 * 48), ("ctas_per_sm", ctypes.c_int32 * 48)]
 
 
 EXPORTED = ["amg_params_default", "amg_setup", "amg_apply_vcycle", "amg_solve", "amg_get_stats",
@@ -243,11 +244,12 @@ def kernel_launches() -> int:
     return int(load().amg_kernel_launches())
 
 
-def fp64_fma_rate(iters: int = 40000, stream=None) -> dict:
+def fp64_fma_rate(iters: int = 20000, stream=None) -> dict:
     """Measured FP64 FMA rate of the current device: {"fma_per_s", "tflops"
     (2 flops per FMA), "seconds" (the timed launch), "num_sms"}."""
     import torch
-    sink = torch.empty(1 << 16, dtype=torch.float64, device="cuda")
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.empty(2048 * sms, dtype=torch.float64, device="cuda")
     rate, sec, nsm = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_int32(0)
     _check(load().amg_fp64_fma_rate(sink.data_ptr(), sink.numel(), int(iters), ctypes.byref(rate),
                                     ctypes.byref(sec), ctypes.byref(nsm), _stream(stream)))
@@ -490,8 +492,13 @@ class AMGBatch:
     def info(self) -> dict:
         d = BatchDesc()
         _check(self._lib.amg_batch_info(self._h, ctypes.byref(d)))
-        out = {k: getattr(d, k) for k, _ in BatchDesc._fields_ if k != "rhs_tile"}
+        out = {k: getattr(d, k) for k, _ in BatchDesc._fields_
+               if k not in ("rhs_tile", "cta_threads", "ctas_per_sm")}
         out["rhs_tile"] = [[d.rhs_tile[3 * l + j] for j in range(3)] for l in range(d.nlevels)]
+        out["cta_threads"] = [[d.cta_threads[3 * l + j] for j in range(3)]
+                              for l in range(d.nlevels)]
+        out["ctas_per_sm"] = [[d.ctas_per_sm[3 * l + j] for j in range(3)]
+                              for l in range(d.nlevels)]
         return out
 
 

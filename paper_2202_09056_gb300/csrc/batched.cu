@@ -29,11 +29,14 @@ namespace amg {
 
 constexpr int BKMAX = 16;       // right-hand sides per instance
 constexpr int BCHUNK = 2048;    // dofs per dot-product chunk
-constexpr int BT = 128;         // threads of the SpMM CTAs
+constexpr int BT = 128;         // default threads of the SpMM CTAs (autotuned: 64, 128, 256)
+constexpr int BT_MAX = 256;
 
 // Concatenated sliced operator of one level.
 struct BSell {
     int nslices = 0, br = 0, bc = 0, kt = 1;
+    int cta = BT, cap = 32;      // launch shape: threads per CTA (32 / G block rows per warp),
+                                 // at most cap CTAs per SM
     int64_t *slice_ptr = nullptr;
     int *col = nullptr;
     double *val = nullptr;
@@ -69,7 +72,7 @@ struct BArgs {
 // VK: values and arithmetic of the block products -- 0 FP64, 1 FP32 pairs
 // (emulated FP64), 2 FP32 (x rounded to FP32, FP32 FMAs); vectors FP64.
 template <int BR, int BC, int KT, int MODE, int VK>
-__global__ void __launch_bounds__(BT) bspmm_kernel(BArgs a)
+__global__ void __launch_bounds__(BT_MAX) bspmm_kernel(BArgs a)
 {
     constexpr bool DF = VK == 1, F32 = VK == 2;
     constexpr int BB = BR * BC;
@@ -248,9 +251,9 @@ static int bspmm_kt(const BSell &S, int kt, const BArgs &a, int grid, cudaStream
     const int vk = a.eval ? 1 : (a.fval ? 2 : 0);
 #define AMG_BSPMM(KT_)                                                                        \
     do {                                                                                      \
-        if (vk == 1) bspmm_kernel<BR, BC, KT_, MODE, 1><<<grid, BT, 0, s>>>(a);               \
-        else if (vk == 2) bspmm_kernel<BR, BC, KT_, MODE, 2><<<grid, BT, 0, s>>>(a);          \
-        else bspmm_kernel<BR, BC, KT_, MODE, 0><<<grid, BT, 0, s>>>(a);                       \
+        if (vk == 1) bspmm_kernel<BR, BC, KT_, MODE, 1><<<grid, S.cta, 0, s>>>(a);            \
+        else if (vk == 2) bspmm_kernel<BR, BC, KT_, MODE, 2><<<grid, S.cta, 0, s>>>(a);       \
+        else bspmm_kernel<BR, BC, KT_, MODE, 0><<<grid, S.cta, 0, s>>>(a);                    \
     } while (0)
     switch (kt) {
     case 1: AMG_BSPMM(1); break;
@@ -302,10 +305,12 @@ static int launch_bspmm(const BSell &S, int kt, int mode, BArgs a, const Geom &g
     a.perm = S.perm;
     a.s_pbase = S.s_pbase;
     a.order = S.order;
-    // one slice group per CTA up to 32 CTAs per SM, widest slices first: the
-    // hardware scheduler balances the instances' uneven rows
-    int grid = (S.nslices + BT / 32 - 1) / (BT / 32);
-    grid = std::min(grid, g.num_sms * 32);
+    // one warp per slice, widest slices first, up to S.cap CTAs per SM (the
+    // warp-strided loop covers the rest): the hardware scheduler balances the
+    // instances' uneven rows
+    const int wpc = S.cta / 32;
+    int grid = (S.nslices + wpc - 1) / wpc;
+    grid = std::min(grid, g.num_sms * S.cap);
     if (S.br == 3 && S.bc == 3) return bspmm_mode<3, 3>(S, kt, mode, a, grid, s);
     if (S.br == 6 && S.bc == 6) return bspmm_mode<6, 6>(S, kt, mode, a, grid, s);
     if (S.br == 3 && S.bc == 6) return bspmm_mode<3, 6>(S, kt, mode, a, grid, s);
@@ -680,6 +685,7 @@ struct amg_batch_s {
     int maxiter = 0;
     double setup_seconds = 0;
     std::vector<int> kt_choice;          // autotuned RHS tile per (level, operator)
+    std::vector<int> cta_choice, cap_choice;  // autotuned launch shape per (level, operator)
     int vk = 0;                          // V-cycle values: 0 FP64, 1 FP32 pairs, 2 FP32
 };
 
@@ -943,7 +949,15 @@ __global__ void to_f32_kernel(const double *__restrict__ v, float *__restrict__ 
     if (i < n) f[i] = (float)v[i];
 }
 
-static int concat_sell(amg_batch h, int l, int which, BSell *out)
+// The sliced operator `which` (0 A, 1 P, 2 R) of level l of instance i.
+static const Sell<double> &inst_sell(amg_batch h, int i, int l, int which)
+{
+    const Level &L = h->inst[i]->lv[l];
+    return which == 0 ? L.sA : which == 1 ? L.sP : L.sR;
+}
+// Concatenate sliced parts (null: the instance does not smooth on this
+// level) into one operator held by the batch.
+static int concat_parts(amg_batch h, const std::vector<const Sell<double> *> &parts, BSell *out)
 {
     cudaStream_t s = h->stream;
     BSell S;
@@ -951,12 +965,9 @@ static int concat_sell(amg_batch h, int l, int which, BSell *out)
     std::vector<int64_t> sp(1, 0), s_pbase;
     int64_t nslots = 0, nperm = 0;
     int bb = 0;
-    std::vector<const Sell<double> *> parts(h->ninst, nullptr);
     for (int i = 0; i < h->ninst; ++i) {
-        if (l >= h->depth[i] - 1) continue;  // not a smoothing level of instance i
-        const Level &L = h->inst[i]->lv[l];
-        const Sell<double> &X = which == 0 ? L.sA : which == 1 ? L.sP : L.sR;
-        parts[i] = &X;
+        if (!parts[i]) continue;
+        const Sell<double> &X = *parts[i];
         S.br = X.br;
         S.bc = X.bc;
         bb = X.br * X.bc;
@@ -1029,11 +1040,22 @@ static int concat_sell(amg_batch h, int l, int which, BSell *out)
     return AMG_OK;
 }
 
-// Time the RHS tiles 1, 2, 4 of an operator in PLAIN mode; return the best.
+static int concat_sell(amg_batch h, int l, int which, BSell *out)
+{
+    std::vector<const Sell<double> *> parts(h->ninst, nullptr);
+    for (int i = 0; i < h->ninst; ++i)
+        if (l < h->depth[i] - 1) parts[i] = &inst_sell(h, i, l, which);  // smoothing levels only
+    return concat_parts(h, parts, out);
+}
+
+// Time the RHS tiles 1, 2, 4 of an operator in PLAIN mode; return the best
+// (and its time for three launches in *best_ms, if asked).
 static int autotune_kt(amg_batch h, const BSell &S, const int64_t *xoff, const int64_t *yoff,
-                       const int *nrows, const double *x, double *y, int *best)
+                       const int *nrows, const double *x, double *y, int *best,
+                       float *best_ms = nullptr)
 {
     *best = 1;
+    if (best_ms) *best_ms = 0.f;
     if (S.nslices == 0) return AMG_OK;
     int kmax = *std::max_element(h->Kh.begin(), h->Kh.end());
     cudaStream_t s = h->stream;
@@ -1067,7 +1089,73 @@ static int autotune_kt(amg_batch h, const BSell &S, const int64_t *xoff, const i
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (best_ms) *best_ms = bestt;
     return AMG_OK;
+}
+
+// Time two launches of an operator in PLAIN mode with its own launch shape
+// and RHS tile, after one warm-up launch.
+static int time_shape(amg_batch h, const BSell &S, const int64_t *xoff, const int64_t *yoff,
+                      const int *nrows, const double *x, double *y, cudaEvent_t e0,
+                      cudaEvent_t e1, float *ms)
+{
+    BArgs a{};
+    a.K = h->K;
+    a.nrows = nrows;
+    a.xoff = xoff;
+    a.yoff = yoff;
+    a.enable = h->all_on;
+    a.x = x;
+    a.y = y;
+    cudaStream_t s = h->stream;
+    AMG_TRY(launch_bspmm(S, S.kt, SPMV_PLAIN, a, h->geom, s, h->vk));
+    AMG_TRY_CUDA(cudaEventRecord(e0, s));
+    for (int rep = 0; rep < 2; ++rep) AMG_TRY(launch_bspmm(S, S.kt, SPMV_PLAIN, a, h->geom, s, h->vk));
+    AMG_TRY_CUDA(cudaEventRecord(e1, s));
+    AMG_TRY_CUDA(cudaEventSynchronize(e1));
+    AMG_TRY_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    return AMG_OK;
+}
+
+// Block-row tiling of one concatenated operator (the autotuner's second
+// axis): the launch shape, i.e. how many warps (each one slice of 32 / G
+// block rows) a CTA holds -- 64, 128 or 256 threads -- and how many CTAs an
+// SM may take before the warp-strided loop wraps -- 16 or 32.  The RHS tile
+// is tuned at the default shape (128 threads, 32 CTAs per SM); every other
+// shape is then timed with that tile, and the fastest replaces the default
+// when it is more than 3 % faster.  The shape only schedules the same
+// per-row work, so results do not depend on the choice (lanes per row, which
+// would change each row's summation split, stay the size heuristic's).
+static int autotune_tiling(amg_batch h, BSell *cur, const int64_t *xoff, const int64_t *yoff,
+                           const int *nrows, const double *x, double *y)
+{
+    if (cur->nslices == 0) return AMG_OK;
+    cur->cta = BT;
+    cur->cap = 32;
+    AMG_TRY(autotune_kt(h, *cur, xoff, yoff, nrows, x, y, &cur->kt));
+    cudaEvent_t e0, e1;
+    AMG_TRY_CUDA(cudaEventCreate(&e0));
+    AMG_TRY_CUDA(cudaEventCreate(&e1));
+    float best = 0.f;
+    int st = time_shape(h, *cur, xoff, yoff, nrows, x, y, e0, e1, &best);
+    const BSell base = *cur;
+    for (int cta : {64, 128, 256})
+        for (int cap : {16, 32}) {
+            if (st < 0 || (cta == BT && cap == 32)) continue;
+            BSell cand = base;
+            cand.cta = cta;
+            cand.cap = cap;
+            float ms = 0.f;
+            st = time_shape(h, cand, xoff, yoff, nrows, x, y, e0, e1, &ms);
+            if (st >= 0 && ms < 0.97f * best) {
+                best = ms;
+                cur->cta = cta;
+                cur->cap = cap;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
 }
 
 static void bdestroy(amg_batch h)
@@ -1234,20 +1322,27 @@ static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, co
     // from the CG residual directly (f pointer filled per solve below)
     AMG_TRY(upload(h->mem, fp, &h->fptr, s));
     AMG_TRY(upload(h->mem, zp, &h->zptr, s));
-    // autotune the RHS tile of every concatenated operator (PLAIN mode)
+    // autotune the block-row tiling and the RHS tile of every concatenated
+    // operator (PLAIN mode, on zeroed vectors)
     AMG_TRY_CUDA(cudaMemsetAsync(h->p, 0, sizeof(double) * n0, s));
     for (int l = 0; l < h->nlev; ++l) {
         BLevelData &D = h->lv[l];
         const bool has_next = l + 1 < h->nlev;
-        AMG_TRY(autotune_kt(h, D.A, D.voff, D.voff, D.nrows, D.z, D.e, &D.A.kt));
+        for (double *v : {D.z, D.e})
+            if (v) AMG_TRY_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * (size_t)std::max<int64_t>(D.len, 1), s));
+        AMG_TRY(autotune_tiling(h, &D.A, D.voff, D.voff, D.nrows, D.z, D.e));
         if (has_next) {
             BLevelData &N = h->lv[l + 1];
-            AMG_TRY(autotune_kt(h, D.P, N.voff, D.voff, D.nrows, N.z, D.e, &D.P.kt));
-            AMG_TRY(autotune_kt(h, D.R, D.voff, N.voff, N.nrows, D.z, N.e, &D.R.kt));
+            for (double *v : {N.z, N.e})
+                if (v) AMG_TRY_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * (size_t)std::max<int64_t>(N.len, 1), s));
+            AMG_TRY(autotune_tiling(h, &D.P, N.voff, D.voff, D.nrows, N.z, D.e));
+            AMG_TRY(autotune_tiling(h, &D.R, D.voff, N.voff, N.nrows, D.z, N.e));
         }
-        h->kt_choice.push_back(D.A.kt);
-        h->kt_choice.push_back(D.P.kt);
-        h->kt_choice.push_back(D.R.kt);
+        for (const BSell *op : {&D.A, &D.P, &D.R}) {
+            h->kt_choice.push_back(op->kt);
+            h->cta_choice.push_back(op->nslices ? op->cta : 0);
+            h->cap_choice.push_back(op->nslices ? op->cap : 0);
+        }
     }
     AMG_TRY_CUDA(cudaStreamSynchronize(s));
     return AMG_OK;
@@ -1478,6 +1573,10 @@ int amg_batch_info(amg_batch h, amg_batch_desc *out)
     out->dofs_total = dofs;
     const int nk = std::min<int>((int)h->kt_choice.size(), 48);
     for (int k = 0; k < nk; ++k) out->rhs_tile[k] = h->kt_choice[k];
+    for (int k = 0; k < nk; ++k) {
+        out->cta_threads[k] = h->cta_choice[k];
+        out->ctas_per_sm[k] = h->cap_choice[k];
+    }
     out->bytes_total = (int64_t)h->mem.bytes;
     for (amg_handle x : h->inst) out->bytes_total += (int64_t)x->mem.bytes;
     return AMG_OK;

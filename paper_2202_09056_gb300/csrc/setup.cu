@@ -1380,33 +1380,134 @@ __global__ void __launch_bounds__(CHOL_TILE * CHOL_TILE) chol_syrk_kernel(double
     D[(int64_t)i * n + k] -= v;
 }
 
-// X[:, k] = A^{-1} e_k by forward/backward substitution with L (lower
-// triangle of D), one CTA per column; zero rows give zero rows/columns.
-__global__ void chol_inverse_kernel(const double *__restrict__ D, int n,
-                                    const uint8_t *__restrict__ zrow, double *__restrict__ X)
+// Explicit inverse from the Cholesky factor: X = A^-1 solves L L^T X = I,
+// blockwise over CHOL_NB-row blocks of L: forward, Y = L^-1 I (lower
+// triangular), then backward, X = L^-T Y.  X is symmetric, so only its lower
+// triangle (row >= column) is formed and then mirrored; every lower entry
+// depends only on lower entries.  Zero rows (unit pivot, zero row of L off
+// the diagonal) start from a zero right-hand side and end as zero rows and
+// columns of X.
+
+// one thread per column c < ncols: the block's rows of L Y = B (forward) or
+// L^T X = Y (backward) by substitution against the block's diagonal part
+template <bool BWD>
+__global__ void __launch_bounds__(256) inv_panel_kernel(const double *__restrict__ D,
+                                                        double *__restrict__ X, int n, int r0,
+                                                        int nb, int ncols)
 {
-    extern __shared__ double y[];
-    for (int k = blockIdx.x; k < n; k += gridDim.x) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (i == k) ? 1.0 : 0.0;
-        __syncthreads();
-        for (int i = 0; i < n; ++i) {  // L y = e_k
-            if (threadIdx.x == 0) y[i] = zrow[i] ? 0.0 : y[i] / D[(int64_t)i * n + i];
-            __syncthreads();
-            const double yi = y[i];
-            for (int m = i + 1 + threadIdx.x; m < n; m += blockDim.x)
-                y[m] -= D[(int64_t)m * n + i] * yi;
-            __syncthreads();
+    __shared__ double Lb[CHOL_NB][CHOL_NB + 1];
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        const int r = t / nb, q = t % nb;
+        Lb[r][q] = q <= r ? D[(int64_t)(r0 + r) * n + r0 + q] : 0.0;
+    }
+    __syncthreads();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    double y[CHOL_NB];
+    if (!BWD) {
+#pragma unroll
+        for (int t = 0; t < CHOL_NB; ++t) {
+            if (t >= nb) break;
+            double v = X[(int64_t)(r0 + t) * n + c];
+#pragma unroll
+            for (int q = 0; q < t; ++q) v -= Lb[t][q] * y[q];
+            y[t] = v / Lb[t][t];
+            X[(int64_t)(r0 + t) * n + c] = y[t];
         }
-        for (int i = n - 1; i >= 0; --i) {  // L^T x = y
-            if (threadIdx.x == 0) y[i] = y[i] / D[(int64_t)i * n + i];
-            __syncthreads();
-            const double xi = y[i];
-            for (int m = threadIdx.x; m < i; m += blockDim.x) y[m] -= D[(int64_t)i * n + m] * xi;
-            __syncthreads();
+    } else {
+#pragma unroll
+        for (int t = CHOL_NB - 1; t >= 0; --t) {
+            if (t >= nb) continue;
+            double v = X[(int64_t)(r0 + t) * n + c];
+#pragma unroll
+            for (int q = t + 1; q < CHOL_NB; ++q)
+                if (q < nb) v -= Lb[q][t] * y[q];
+            y[t] = v / Lb[t][t];
+            X[(int64_t)(r0 + t) * n + c] = y[t];
         }
-        for (int i = threadIdx.x; i < n; i += blockDim.x)
-            X[(int64_t)i * n + k] = (zrow[i] || zrow[k]) ? 0.0 : y[i];
-        __syncthreads();
+    }
+}
+
+// C -= A B on X's rows [i0, i1) and columns [0, j1), the inner index over the
+// block's nb rows r0 .. r0 + nb - 1: forward A(i, t) = L[i][r0 + t], backward
+// A(i, t) = L[r0 + t][i] with only j <= i written; B(t, j) = X[r0 + t][j].
+// 64 x 64 output tiles, 4 x 4 per thread.
+constexpr int INV_TILE = 64;
+template <bool BWD>
+__global__ void __launch_bounds__(256) inv_update_kernel(const double *__restrict__ D,
+                                                         double *__restrict__ X, int n, int r0,
+                                                         int nb, int i0, int i1, int j1)
+{
+    const int ti0 = i0 + blockIdx.y * INV_TILE, tj0 = blockIdx.x * INV_TILE;
+    if (ti0 >= i1 || tj0 >= j1) return;
+    if (BWD && tj0 > ti0 + INV_TILE - 1) return;  // tile wholly above the diagonal
+    __shared__ double As[CHOL_NB][INV_TILE + 1], Bs[CHOL_NB][INV_TILE + 1];
+    for (int e = threadIdx.x; e < nb * INV_TILE; e += blockDim.x) {
+        int t, ii;
+        if (BWD) {
+            t = e / INV_TILE;
+            ii = e % INV_TILE;  // row r0 + t of L, consecutive columns
+        } else {
+            ii = e / nb;
+            t = e % nb;         // row i of L, consecutive columns r0 + t
+        }
+        const int i = ti0 + ii;
+        As[t][ii] = i < i1 ? (BWD ? D[(int64_t)(r0 + t) * n + i] : D[(int64_t)i * n + r0 + t])
+                           : 0.0;
+        const int tb = e / INV_TILE, jj = e % INV_TILE, j = tj0 + jj;
+        Bs[tb][jj] = j < j1 ? X[(int64_t)(r0 + tb) * n + j] : 0.0;
+    }
+    __syncthreads();
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int t = 0; t < nb; ++t) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = As[t][ty * 4 + a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Bs[t][tx * 4 + b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = ti0 + ty * 4 + a;
+        if (i >= i1) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int j = tj0 + tx * 4 + b;
+            if (j < j1 && (!BWD || j <= i)) X[(int64_t)i * n + j] -= acc[a][b];
+        }
+    }
+}
+
+__global__ void unit_diag_kernel(double *__restrict__ X, int n, const uint8_t *__restrict__ zrow)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) X[(int64_t)i * n + i] = zrow[i] ? 0.0 : 1.0;
+}
+
+// upper triangle = transpose of the lower one, 32 x 32 tiles through shared memory
+__global__ void mirror_upper_kernel(double *__restrict__ X, int n)
+{
+    const int bi = blockIdx.y, bj = blockIdx.x;  // destination tile (bi, bj), bj >= bi
+    if (bj < bi) return;
+    __shared__ double t[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8 threads
+    for (int r = ty; r < 32; r += 8) {  // source tile (bj, bi): rows of the lower triangle
+        const int i = bj * 32 + r, j = bi * 32 + tx;
+        t[r][tx] = (i < n && j < n) ? X[(int64_t)i * n + j] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bi * 32 + r, j = bj * 32 + tx;
+        if (i < n && j < n && j > i) X[(int64_t)i * n + j] = t[tx][r];
     }
 }
 
@@ -1454,13 +1555,37 @@ int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
         set_error("coarsest matrix is not positive definite (pivot %d)", herr - 1);
         return AMG_ERR_COARSE;
     }
-    const size_t smem = sizeof(double) * (size_t)n;
-    if (smem > 48 * 1024)
-        AMG_TRY_CUDA(cudaFuncSetAttribute(chol_inverse_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int grid = n < 1 ? 1 : n;
-    if (grid > 4096) grid = 4096;
-    if (n > 0) { chol_inverse_kernel<<<grid, 256, smem, s>>>(D, n, z, X); ::amg::count_launch(1); }
+    AMG_TRY_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * n, s));
+    if (n > 0) {
+        unit_diag_kernel<<<nblk(n), T1D, 0, s>>>(X, n, z);
+        ::amg::count_launch(1);
+    }
+    for (int r0 = 0; r0 < n; r0 += CHOL_NB) {  // forward: L Y = I, columns < r1
+        const int nb = std::min(CHOL_NB, n - r0), r1 = r0 + nb;
+        inv_panel_kernel<false><<<(r1 + 255) / 256, 256, 0, s>>>(D, X, n, r0, nb, r1);
+        ::amg::count_launch(1);
+        if (r1 < n) {
+            const dim3 g((r1 + INV_TILE - 1) / INV_TILE, (n - r1 + INV_TILE - 1) / INV_TILE);
+            inv_update_kernel<false><<<g, 256, 0, s>>>(D, X, n, r0, nb, r1, n, r1);
+            ::amg::count_launch(1);
+        }
+    }
+    const int nblk_rows = (n + CHOL_NB - 1) / CHOL_NB;
+    for (int b = nblk_rows - 1; b >= 0; --b) {  // backward: L^T X = Y, lower triangle
+        const int r0 = b * CHOL_NB, nb = std::min(CHOL_NB, n - r0), r1 = r0 + nb;
+        inv_panel_kernel<true><<<(r1 + 255) / 256, 256, 0, s>>>(D, X, n, r0, nb, r1);
+        ::amg::count_launch(1);
+        if (r0 > 0) {
+            const dim3 g((r0 + INV_TILE - 1) / INV_TILE, (r0 + INV_TILE - 1) / INV_TILE);
+            inv_update_kernel<true><<<g, 256, 0, s>>>(D, X, n, r0, nb, 0, r0, r0);
+            ::amg::count_launch(1);
+        }
+    }
+    if (n > 0) {
+        const int nt = (n + 31) / 32;
+        mirror_upper_kernel<<<dim3(nt, nt), dim3(32, 8), 0, s>>>(X, n);
+        ::amg::count_launch(1);
+    }
     AMG_TRY_CUDA(cudaGetLastError());
     AMG_TRY_CUDA(cudaStreamSynchronize(s));
     tmp.release(D);

@@ -636,7 +636,7 @@ int amg_params_default(amg_params *prm)
     if (!prm) return AMG_ERR_ARG;
     std::memset(prm, 0, sizeof *prm);
     prm->eps_strong = 0.08;
-    prm->relax = 1.0;
+    prm->relax = 2.0;
     prm->smooth_relax = 0.8;
     prm->coarse_enough = 3000;
     prm->max_levels = 15;
@@ -734,6 +734,20 @@ __global__ void validate_pattern_kernel(const int *__restrict__ rp, const int *_
     }
 }
 
+// Stop rule of the coarsening loop after level `nlev - 1` (n rows, nn nodes)
+// was aggregated into nagg aggregates: no aggregates, or too few nodes
+// merged (aggregates >= 0.9 x nodes); and a level below the finest that is
+// already small (at most 2 coarse_enough rows) stays the coarsest rather
+// than being coarsened into a tiny level (fewer than coarse_enough / 4 rows,
+// aggregated from a dense operator: such a last step doubles the CG
+// iterations or worse on these meshes).
+static bool stop_coarsening(const amg_params &prm, int nlev, int64_t n, int nn, int nagg, int ns)
+{
+    if (nagg == 0 || (double)nagg >= 0.9 * (double)nn) return true;
+    return nlev > 1 && n <= 2 * (int64_t)prm.coarse_enough &&
+           4 * (int64_t)nagg * ns < (int64_t)prm.coarse_enough;
+}
+
 // Alg. 1 in scalar arithmetic (AMG_SETUP_SCALAR): level 0 unblocked, then
 // per level the node graph's strength, aggregation (host greedy passes or
 // device MIS-2 on the node graph), the scalar transfer operators, the scalar
@@ -779,7 +793,7 @@ static int setup_levels_scalar(amg_handle h, DevArena &tmp, Lap &lap)
         h->mem.release(G.row_ptr);
         h->mem.release(G.col);
         lap(1);
-        if (nagg == 0 || (double)nagg >= 0.9 * (double)nn) break;
+        if (stop_coarsening(prm, (int)h->lv.size(), n, nn, nagg, h->ns)) break;
         LevelBuild lb;
         AMG_TRY(scalar_transfer(S, b, C.B, h->ns, agg.data(), nagg, prm.relax, h->mem, tmp, s,
                                 &lb));
@@ -941,7 +955,7 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
             AMG_TRY(aggregate_host(nn, rp.data(), cl.data(), sf.data(), agg.data(), &nagg));
         }
         lap(1);
-        if (nagg == 0 || (double)nagg >= 0.9 * (double)nn) break;
+        if (stop_coarsening(prm, (int)h->lv.size(), n, nn, nagg, h->ns)) break;
         LevelBuild lb;
         AMG_TRY(build_transfer(C.A, C.B, h->ns, C.strong, agg.data(), nagg, prm.relax, h->mem, tmp, s,
                                &lb));

@@ -41,7 +41,7 @@ def test_build_targets_sm103a_only():
 
 def test_default_params():
     p = amg.default_params()
-    assert (p.eps_strong, p.relax, p.smooth_relax) == (0.08, 1.0, 0.8)
+    assert (p.eps_strong, p.relax, p.smooth_relax) == (0.08, 2.0, 0.8)
     assert (p.coarse_enough, p.max_levels, p.npre, p.npost, p.precision) == (3000, 15, 1, 1, 0)
 
 

@@ -49,6 +49,10 @@ def test_batch_matches_oracle_per_rhs():
     info = bat.info()
     assert info["ninst"] == 4 and info["nrhs_total"] == sum(nrhs)
     assert all(t in (1, 2, 4) for lev in info["rhs_tile"] for t in lev)
+    # the autotuned launch shape of every present operator (0: absent)
+    assert all(c in (0, 64, 128, 256) for lev in info["cta_threads"] for c in lev)
+    assert all(c in (0, 16, 32) for lev in info["ctas_per_sm"] for c in lev)
+    assert info["cta_threads"][0][0] in (64, 128, 256)
     for i, (p, k) in enumerate(inst):
         H = o.Hierarchy(o.from_problem(p), 3, p.B, coarse_enough=150)
         fs = np.atleast_2d(p.f)

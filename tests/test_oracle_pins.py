@@ -254,6 +254,45 @@ def test_default_stop_rule_on_ten_cube():
     assert L1["b"] == 6 and L1["n"] == 6 * H.level(0)["nagg"] <= 3000
 
 
+@pytest.mark.parametrize("shape,ce", [((16, 16, 16), 300), ((14, 12, 13), 200),
+                                      ((18, 18, 18), 400), ((20, 20, 20), 600)])
+def test_stop_rule_against_separate_aggregation(shape, ce):
+    """The coarsening stop rule, level by level, against the aggregation
+    function called on its own for every level: a level below the finest is
+    coarsened only if it holds more than coarse_enough rows and is not small
+    (<= 2 ce rows) with a tiny aggregation (< ce / 4 coarse rows); the
+    coarsest level is there because one of the stop conditions holds; the
+    finest level above ce is always coarsened."""
+    p = q.make_problem(shape, traction=(0, 0, -1), inclusion_frac=0.2)
+    H = _hierarchy(p, coarse_enough=ce)
+    assert H.nlevels >= 2
+    triggered = False
+    for l in range(1, H.nlevels):
+        L = H.level(l)
+        agg, nagg = o.aggregate(L["A"], L["b"], L["eps"])
+        nn = L["n"] // L["b"]
+        small, tiny = L["n"] <= 2 * ce, 4 * nagg * 6 < ce
+        if l < H.nlevels - 1:
+            assert L["n"] > ce and not (small and tiny) and nagg == L["nagg"]
+            assert np.array_equal(agg, L["agg"])
+        else:
+            assert L["n"] <= ce or (small and tiny) or nagg == 0 or nagg >= 0.9 * nn
+            triggered = L["n"] > ce
+    if shape == (16, 16, 16):
+        assert triggered  # 1842 -> 342 rows; 342 <= 600 and 6 x 11 < 75 stops there
+
+
+def test_default_omega_is_twice_the_gershgorin_textbook_value():
+    """omega = relax (4/3) / rho with relax = 2 by default: exactly twice the
+    relax = 1 value, with rho the Gershgorin bound of the level's matrix."""
+    p = q.make_problem((9, 8, 10), traction=(0, 0, -1), inclusion_frac=0.2)
+    H2, H1 = _hierarchy(p, coarse_enough=100), _hierarchy(p, coarse_enough=100, relax=1.0)
+    L2, L1 = H2.level(0), H1.level(0)
+    _, rho = o.jacobi_rho(L2["A"])
+    assert L2["rho"] == rho and L2["omega"] == 2.0 * (4.0 / 3.0) / rho
+    assert L2["omega"] == 2.0 * L1["omega"]
+
+
 def _hierarchy(p, **kw):
     return o.Hierarchy(o.from_problem(p), 3, p.B, **kw)
 
