@@ -289,8 +289,8 @@ int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_pt
  * level `level` (0: A, 1: P, 2: R), in the sliced block-ELL layout the solve
  * uses.  which = 3, 4, 5: the same operators in the FP32-pair copies of an
  * AMG_PREC_DF64 hierarchy (AMG_ERR_STATE otherwise).  x has (columns x block
- * columns) and y (rows x block rows) doubles, device, not overlapping.
- * Asynchronous on `stream`. */
+ * columns) and y (rows x block rows) doubles, device, not overlapping, x
+ * 8-byte aligned (AMG_ERR_ARG otherwise).  Asynchronous on `stream`. */
 int amg_level_spmv(amg_handle h, int32_t level, int32_t which, const double *x, double *y,
                    void *stream);
 

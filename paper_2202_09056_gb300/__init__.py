@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 
 import numpy as np
 
@@ -76,8 +77,17 @@ def _torch_alloc(ctx, nbytes, stream):
 
 
 def _torch_free(ctx, ptr, nbytes, stream):
+    if sys.is_finalizing():  # the process is ending: its memory goes with it
+        return
     import torch
     torch.cuda.caching_allocator_delete(int(ptr))
+
+
+def _finalizing() -> bool:
+    """Handles still alive while the interpreter shuts down are not freed
+    through the library: the allocator callbacks can no longer run Python,
+    and the process exit returns the device memory anyway."""
+    return sys.is_finalizing()
 
 
 _TORCH_ALLOCATOR = None
@@ -302,7 +312,8 @@ class AMG:
 
     def close(self):
         if getattr(self, "_h", None):
-            self._lib.amg_free(self._h)
+            if not _finalizing():
+                self._lib.amg_free(self._h)
             self._h = None
 
     def __del__(self):
@@ -460,7 +471,8 @@ class AMGBatch:
 
     def close(self):
         if getattr(self, "_h", None):
-            self._lib.amg_batch_free(self._h)
+            if not _finalizing():
+                self._lib.amg_batch_free(self._h)
             self._h = None
 
     def __del__(self):
@@ -525,7 +537,8 @@ class Trainer:
 
     def close(self):
         if getattr(self, "_t", None):
-            self._lib.amg_trainer_free(self._t)
+            if not _finalizing():
+                self._lib.amg_trainer_free(self._t)
             self._t = None
 
     def __del__(self):

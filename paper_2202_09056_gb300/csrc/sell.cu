@@ -345,6 +345,10 @@ int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom
     a.perm = A.perm;
     int grid = sell_grid_cap(A.nslices, sell_cap_t<VT>(A.br, A.bc), g);
     if (max_grid > 0 && grid > max_grid) grid = max_grid;
+    if (((uintptr_t)a.x & (sizeof(TV) - 1)) != 0) {
+        set_error("the sliced SpMV needs x aligned to its element size");
+        return AMG_ERR_ARG;
+    }
     if (grid_out) *grid_out = grid;
     if (dot != DOT_NONE && grid > g.max_partials) {
         set_error("fused dot needs %d partial sums, the buffer holds %d", grid, g.max_partials);

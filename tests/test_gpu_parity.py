@@ -279,6 +279,21 @@ def test_level_spmv_sell_matches_oracle():
                                    nbcols=ncols), x)
             assert np.abs(y.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max(), (l, which)
         assert all(x >= 0 for x in G.padding(l))
+    # the gather loads pairs of entries where the address allows: an x view
+    # 8 bytes into an allocation (not 16-byte aligned) gives the same bits as
+    # an aligned copy, on every operator of levels 0 and 1
+    for l in range(min(2, G.nlevels - 1)):
+        ex = G.export(l)
+        b, nagg, nb = ex["info"]["bs"], ex["info"]["nagg"], ex["info"]["nbrows"]
+        for which, (ny, nx) in enumerate(((nb * b, nb * b), (nb * b, nagg * 6), (nagg * 6, nb * b))):
+            xs = torch.zeros(nx + 1, dtype=torch.float64, device="cuda")
+            xs[1:] = torch.from_numpy(rng.standard_normal(nx)).cuda()
+            x_al = xs[1:].clone()
+            y_off = torch.empty(ny, dtype=torch.float64, device="cuda")
+            y_al = torch.empty(ny, dtype=torch.float64, device="cuda")
+            G.level_spmv(l, which, xs[1:], y_off)
+            G.level_spmv(l, which, x_al, y_al)
+            assert xs[1:].data_ptr() % 16 == 8 and torch.equal(y_off, y_al), (l, which)
 
 
 def test_host_loop_mode_gives_identical_results():
