@@ -208,8 +208,20 @@ __global__ void __launch_bounds__(256) coarse_gemv_kernel(const double *__restri
     const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
     for (int row = warp; row < n; row += nwarps) {
         const double *ar = Ainv + (int64_t)row * n;
-        double acc = 0.0;
-        for (int j = lane; j < n; j += 32) acc = fma(__ldg(ar + j), (double)x[j], acc);
+        // eight independent partial sums per lane keep eight loads in flight
+        // (one chain would wait on every load); summed in a fixed order
+        double p[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p[q] = 0.0;
+        int j = lane;
+        for (; j + 7 * 32 < n; j += 8 * 32) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) p[q] = fma(__ldg(ar + j + q * 32), (double)x[j + q * 32], p[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 7; ++q)  // at most seven strides remain
+            if (j + q * 32 < n) p[q] = fma(__ldg(ar + j + q * 32), (double)x[j + q * 32], p[q]);
+        double acc = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
         acc = warp_sum(acc);
         if (lane == 0) y[row] = (TV)acc;
     }
