@@ -621,12 +621,27 @@ __global__ void bcoarse_kernel(int nitems, const int *__restrict__ item_inst,
         const int row = item_row[t], n = nc[inst], Ki = K[inst];
         const double *ar = Ainv + aoff[inst] + (int64_t)row * n;
         const double *f = fptr[inst];
-        for (int k = 0; k < Ki; ++k) {
-            double acc = 0.0;
-            for (int j = lane; j < n; j += 32) acc = fma(ar[j], f[(int64_t)j * Ki + k], acc);
+        // one pass over the row: each entry feeds the Ki right-hand sides'
+        // sums (the row is read once, Ki independent chains); every sum runs
+        // over the row in the same order whatever Ki is, so a pair's result
+        // does not depend on how many right-hand sides share its instance
+        double acc[BKMAX];
 #pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
-            if (lane == 0) zptr[inst][(int64_t)row * Ki + k] = acc;
+        for (int k = 0; k < BKMAX; ++k) acc[k] = 0.0;
+        for (int j = lane; j < n; j += 32) {
+            const double a = ar[j];
+            const double *fj = f + (int64_t)j * Ki;
+#pragma unroll
+            for (int k = 0; k < BKMAX; ++k)
+                if (k < Ki) acc[k] = fma(a, fj[k], acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < BKMAX; ++k) {
+            if (k >= Ki) break;
+            double v = acc[k];
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+            if (lane == 0) zptr[inst][(int64_t)row * Ki + k] = v;
         }
     }
 }
@@ -1093,8 +1108,8 @@ static int autotune_kt(amg_batch h, const BSell &S, const int64_t *xoff, const i
     return AMG_OK;
 }
 
-// Time two launches of an operator in PLAIN mode with its own launch shape
-// and RHS tile, after one warm-up launch.
+// Time one launch of an operator in PLAIN mode with its own launch shape and
+// RHS tile (the kernels are warm from the RHS-tile tuning).
 static int time_shape(amg_batch h, const BSell &S, const int64_t *xoff, const int64_t *yoff,
                       const int *nrows, const double *x, double *y, cudaEvent_t e0,
                       cudaEvent_t e1, float *ms)
@@ -1108,9 +1123,8 @@ static int time_shape(amg_batch h, const BSell &S, const int64_t *xoff, const in
     a.x = x;
     a.y = y;
     cudaStream_t s = h->stream;
-    AMG_TRY(launch_bspmm(S, S.kt, SPMV_PLAIN, a, h->geom, s, h->vk));
     AMG_TRY_CUDA(cudaEventRecord(e0, s));
-    for (int rep = 0; rep < 2; ++rep) AMG_TRY(launch_bspmm(S, S.kt, SPMV_PLAIN, a, h->geom, s, h->vk));
+    AMG_TRY(launch_bspmm(S, S.kt, SPMV_PLAIN, a, h->geom, s, h->vk));
     AMG_TRY_CUDA(cudaEventRecord(e1, s));
     AMG_TRY_CUDA(cudaEventSynchronize(e1));
     AMG_TRY_CUDA(cudaEventElapsedTime(ms, e0, e1));

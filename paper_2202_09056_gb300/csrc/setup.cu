@@ -1389,7 +1389,10 @@ __global__ void __launch_bounds__(CHOL_TILE * CHOL_TILE) chol_syrk_kernel(double
 // columns of X.
 
 // one thread per column c < ncols: the block's rows of L Y = B (forward) or
-// L^T X = Y (backward) by substitution against the block's diagonal part
+// L^T X = Y (backward) by substitution against the block's diagonal part.
+// Each thread runs about CHOL_NB^2 / 2 FP64 FMAs, so small CTAs spread the
+// columns over many SMs (the FP64 pipe of an SM is the limit).
+constexpr int INV_PANEL_T = 64;
 template <bool BWD>
 __global__ void __launch_bounds__(256) inv_panel_kernel(const double *__restrict__ D,
                                                         double *__restrict__ X, int n, int r0,
@@ -1562,7 +1565,8 @@ int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
     }
     for (int r0 = 0; r0 < n; r0 += CHOL_NB) {  // forward: L Y = I, columns < r1
         const int nb = std::min(CHOL_NB, n - r0), r1 = r0 + nb;
-        inv_panel_kernel<false><<<(r1 + 255) / 256, 256, 0, s>>>(D, X, n, r0, nb, r1);
+        inv_panel_kernel<false><<<(r1 + INV_PANEL_T - 1) / INV_PANEL_T, INV_PANEL_T, 0, s>>>(
+            D, X, n, r0, nb, r1);
         ::amg::count_launch(1);
         if (r1 < n) {
             const dim3 g((r1 + INV_TILE - 1) / INV_TILE, (n - r1 + INV_TILE - 1) / INV_TILE);
@@ -1573,7 +1577,8 @@ int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
     const int nblk_rows = (n + CHOL_NB - 1) / CHOL_NB;
     for (int b = nblk_rows - 1; b >= 0; --b) {  // backward: L^T X = Y, lower triangle
         const int r0 = b * CHOL_NB, nb = std::min(CHOL_NB, n - r0), r1 = r0 + nb;
-        inv_panel_kernel<true><<<(r1 + 255) / 256, 256, 0, s>>>(D, X, n, r0, nb, r1);
+        inv_panel_kernel<true><<<(r1 + INV_PANEL_T - 1) / INV_PANEL_T, INV_PANEL_T, 0, s>>>(
+            D, X, n, r0, nb, r1);
         ::amg::count_launch(1);
         if (r0 > 0) {
             const dim3 g((r0 + INV_TILE - 1) / INV_TILE, (r0 + INV_TILE - 1) / INV_TILE);
