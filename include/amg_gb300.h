@@ -156,7 +156,14 @@ typedef struct {
  *     giving back a handle's buffers.
  * The library copies the struct at setup; ctx and the two functions must
  * stay valid until the handle is freed.  Both are called on the thread that
- * makes the library call. */
+ * makes the library call, except in amg_batch_setup: it sets its instances
+ * up on up to 8 host threads at once, each allocating for a stream of its
+ * own (non-blocking streams that the library creates per device on first
+ * use and keeps for the life of the process, so a caching supplier can reuse
+ * what it cached for them at the next batch setup), so there the two
+ * functions must be safe to call concurrently.  Memory allocated for such a
+ * stream may later be given back with the caller's stream once the setup
+ * has synchronised that stream. */
 typedef struct {
     void *(*alloc)(void *ctx, size_t bytes, void *stream);
     void (*free)(void *ctx, void *ptr, size_t bytes, void *stream);
@@ -356,19 +363,27 @@ typedef struct {
                                block rows), 0 for an absent operator */
     int32_t ctas_per_sm[48];/* ... and the CTAs per SM before the warp-strided loop
                                wraps (16, 32) */
+    double setup_phase_seconds[4]; /* wall time of the setup's phases: the instances'
+                               hierarchies (set up by several host threads at once),
+                               the concatenated level operators and vectors, the
+                               coarse inverses and CG state, the autotuner */
 } amg_batch_desc;
 
 /* Many independent instances of Eq. 1, each with its own near-nullspace and
  * nrhs[i] (1..16) load cases, solved together.  Builds one hierarchy per
- * instance exactly as amg_setup would (Alg. 1, same parameters, FP64, V(1,1))
- * and the grouped structures of the batched V-cycle: level l of every
- * instance in one concatenated sliced operator, right-hand sides interleaved
- * so the SpMM reads each block once per tile of right-hand sides, and the
- * tile chosen per operator by timing the candidates (1, 2, 4).
- * A[i] (3x3 BSR) and B[i] (n_i x 6) are device arrays, read only.  FP64 and
- * block storage only (prm->precision and prm->storage at their defaults;
- * prm->loop_mode 1 launches one captured iteration per host step, for
- * profilers, with the same results). */
+ * instance exactly as amg_setup would (Alg. 1, same parameters, V(1,1) with
+ * SPAI0), on up to 8 host threads at once, and the grouped structures of the
+ * batched V-cycle: level l of every instance in one concatenated sliced
+ * operator, right-hand sides interleaved so the SpMM reads each block once
+ * per tile of right-hand sides, and per operator the tile (1, 2, 4) and the
+ * launch shape (threads per CTA, CTAs per SM) chosen by timing the
+ * candidates.  A[i] (3x3 BSR) and B[i] (n_i x 6) are device arrays, read
+ * only, written on `stream` before the call.  Block storage and the block
+ * setup only; prm->precision FP64, FP32 or emulated FP64 (the V-cycle's
+ * operators; CG stays FP64); prm->loop_mode 1 launches one captured
+ * iteration per host step, for profilers, with the same results.  An error
+ * in an instance's setup is reported as "instance <i>: <message>" for the
+ * lowest-numbered failing instance.  Synchronises `stream`. */
 int amg_batch_setup(int32_t ninst, const amg_bsr *A, const double *const *B, const int32_t *nrhs,
                     const amg_params *prm, void *stream, amg_batch *out);
 

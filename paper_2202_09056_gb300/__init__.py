@@ -136,7 +136,8 @@ class BatchDesc(ctypes.Structure):
                 ("nlevels", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("setup_seconds", ctypes.c_double), ("dofs_total", ctypes.c_int64),
                 ("bytes_total", ctypes.c_int64), ("rhs_tile", ctypes.c_int32 * 48),
-                ("cta_threads", ctypes.c_int32 * 48), ("ctas_per_sm", ctypes.c_int32 * 48)]
+                ("cta_threads", ctypes.c_int32 * 48), ("ctas_per_sm", ctypes.c_int32 * 48),
+                ("setup_phase_seconds", ctypes.c_double * 4)]
 
 
 EXPORTED = ["amg_params_default", "amg_setup", "amg_apply_vcycle", "amg_solve", "amg_get_stats",
@@ -505,7 +506,9 @@ class AMGBatch:
         d = BatchDesc()
         _check(self._lib.amg_batch_info(self._h, ctypes.byref(d)))
         out = {k: getattr(d, k) for k, _ in BatchDesc._fields_
-               if k not in ("rhs_tile", "cta_threads", "ctas_per_sm")}
+               if k not in ("rhs_tile", "cta_threads", "ctas_per_sm", "setup_phase_seconds")}
+        out["setup_phase_seconds"] = dict(zip(("instances", "operators", "coarse_and_state",
+                                               "autotune"), list(d.setup_phase_seconds)))
         out["rhs_tile"] = [[d.rhs_tile[3 * l + j] for j in range(3)] for l in range(d.nlevels)]
         out["cta_threads"] = [[d.cta_threads[3 * l + j] for j in range(3)]
                               for l in range(d.nlevels)]

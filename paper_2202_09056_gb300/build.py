@@ -47,7 +47,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         return LIB
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-I", INCLUDE,
+              "-I", CSRC]
     cuda_flags = ARCH + ["-lineinfo", "--expt-relaxed-constexpr"]
     if ptxas_v:
         cuda_flags += ["-Xptxas", "-v"]
@@ -71,7 +72,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
                 print(err)
     objs = [o for o, _ in results]
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared",
+    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared", "-Xcompiler", "-pthread",
                                                        "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

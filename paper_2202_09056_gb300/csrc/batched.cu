@@ -19,9 +19,12 @@
 // so an instance solved inside a batch gives bitwise the same iterates as the
 // same instance solved alone through this path.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <thread>
 
 #include "amg_internal.cuh"
 
@@ -31,6 +34,7 @@ constexpr int BKMAX = 16;       // right-hand sides per instance
 constexpr int BCHUNK = 2048;    // dofs per dot-product chunk
 constexpr int BT = 128;         // default threads of the SpMM CTAs (autotuned: 64, 128, 256)
 constexpr int BT_MAX = 256;
+constexpr int BSETUP_THREADS = 8;  // host threads setting up instances at once
 
 // Concatenated sliced operator of one level.
 struct BSell {
@@ -672,7 +676,7 @@ struct amg_batch_s {
     Geom geom;
     DevArena mem;
     int ninst = 0, ngl = 0, nlev = 0;
-    std::vector<amg_handle> inst;        // per-instance hierarchies
+    std::vector<amg_handle> inst;        // per-instance hierarchies (during setup only)
     std::vector<int> Kh, goffh, depth;   // host copies
     std::vector<int64_t> ndof0;
     std::vector<BLevelData> lv;
@@ -691,6 +695,7 @@ struct amg_batch_s {
            *part = nullptr;
     BState st{};
     int *all_on = nullptr;               // enable array with every instance on
+    int *all_off = nullptr;              // ... and with every instance off (warm-up launches)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long body_kernels = 0;
@@ -699,6 +704,7 @@ struct amg_batch_s {
     double tol = 0;
     int maxiter = 0;
     double setup_seconds = 0;
+    double phase_s[4] = {0, 0, 0, 0};  // instances, operators, coarse + state, autotune
     std::vector<int> kt_choice;          // autotuned RHS tile per (level, operator)
     std::vector<int> cta_choice, cap_choice;  // autotuned launch shape per (level, operator)
     int vk = 0;                          // V-cycle values: 0 FP64, 1 FP32 pairs, 2 FP32
@@ -1063,8 +1069,9 @@ static int concat_sell(amg_batch h, int l, int which, BSell *out)
     return concat_parts(h, parts, out);
 }
 
-// Time the RHS tiles 1, 2, 4 of an operator in PLAIN mode; return the best
-// (and its time for three launches in *best_ms, if asked).
+// Time the RHS tiles 1, 2, 4 of an operator in PLAIN mode, one launch each
+// after a launch with every instance disabled (which loads the kernel and
+// does no work); return the best (and its time in *best_ms, if asked).
 static int autotune_kt(amg_batch h, const BSell &S, const int64_t *xoff, const int64_t *yoff,
                        const int *nrows, const double *x, double *y, int *best,
                        float *best_ms = nullptr)
@@ -1089,10 +1096,11 @@ static int autotune_kt(amg_batch h, const BSell &S, const int64_t *xoff, const i
         a.x = x;
         a.y = y;
         // a reduced-precision batch tunes the tile of the V-cycle's kernels
+        a.enable = h->all_off;
         AMG_TRY(launch_bspmm(S, kt, SPMV_PLAIN, a, h->geom, s, h->vk));  // warm-up
+        a.enable = h->all_on;
         AMG_TRY_CUDA(cudaEventRecord(e0, s));
-        for (int rep = 0; rep < 3; ++rep)
-            AMG_TRY(launch_bspmm(S, kt, SPMV_PLAIN, a, h->geom, s, h->vk));
+        AMG_TRY(launch_bspmm(S, kt, SPMV_PLAIN, a, h->geom, s, h->vk));
         AMG_TRY_CUDA(cudaEventRecord(e1, s));
         AMG_TRY_CUDA(cudaEventSynchronize(e1));
         float ms = 0;
@@ -1146,12 +1154,12 @@ static int autotune_tiling(amg_batch h, BSell *cur, const int64_t *xoff, const i
     if (cur->nslices == 0) return AMG_OK;
     cur->cta = BT;
     cur->cap = 32;
-    AMG_TRY(autotune_kt(h, *cur, xoff, yoff, nrows, x, y, &cur->kt));
+    float best = 0.f;  // the default shape's time at the chosen tile
+    AMG_TRY(autotune_kt(h, *cur, xoff, yoff, nrows, x, y, &cur->kt, &best));
     cudaEvent_t e0, e1;
     AMG_TRY_CUDA(cudaEventCreate(&e0));
     AMG_TRY_CUDA(cudaEventCreate(&e1));
-    float best = 0.f;
-    int st = time_shape(h, *cur, xoff, yoff, nrows, x, y, e0, e1, &best);
+    int st = AMG_OK;
     const BSell base = *cur;
     for (int cta : {64, 128, 256})
         for (int cap : {16, 32}) {
@@ -1189,6 +1197,112 @@ static void bdestroy(amg_batch h)
     delete h;
 }
 
+// Streams of the setup threads: BSETUP_THREADS non-blocking streams per
+// device, created on first use and kept for the life of the process.  A
+// caller-supplied allocator receives the stream an allocation is made for,
+// and a caching allocator (PyTorch's) keeps freed blocks for reuse on that
+// stream only: streams that outlive one setup let the next setup reuse them,
+// where a fresh stream per setup would leave them stranded.
+static int setup_stream(int dev, int w, cudaStream_t *out)
+{
+    constexpr int kDev = 64;
+    static cudaStream_t table[kDev][BSETUP_THREADS] = {};
+    static std::mutex mu;
+    if (dev < 0 || dev >= kDev || w < 0 || w >= BSETUP_THREADS) {
+        set_error("setup stream: device %d, thread %d out of range", dev, w);
+        return AMG_ERR_LIMIT;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!table[dev][w]) AMG_TRY_CUDA(cudaStreamCreateWithFlags(&table[dev][w], cudaStreamNonBlocking));
+    *out = table[dev][w];
+    return AMG_OK;
+}
+
+// The instances' hierarchies are independent problems: up to BSETUP_THREADS
+// host threads take instances in index order, each setting them up on a
+// setup stream of its own that first waits for the caller's stream (where
+// the inputs were written).  One instance's host aggregation and
+// synchronisations then overlap the kernels of the others.  Every instance
+// runs the same kernels on the same inputs as when it is set up alone, so
+// its hierarchy does not depend on the thread or on the other instances.
+// Once a thread has finished, the instance's memory and later work belong to
+// the caller's stream.  On failure the lowest-numbered failing instance is
+// reported, its number before its message (instances are started in index
+// order, so every lower one has been set up); no thread starts an instance
+// after a failure.
+static int setup_instances(amg_batch h, const amg_bsr *A, const double *const *B)
+{
+    const int ni = h->ninst;
+    cudaStream_t s = h->stream;
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int nw = std::min(ni, std::min(BSETUP_THREADS, hw));
+    if (nw <= 1) {
+        for (int i = 0; i < ni; ++i) {
+            const int st = setup_impl(h->inst[i], &A[i], B[i]);
+            if (st < 0) {
+                const std::string m = last_error();
+                set_error("instance %d: %s", i, m.c_str());
+                return st;
+            }
+        }
+        return AMG_OK;
+    }
+    int dev = 0;
+    AMG_TRY_CUDA(cudaGetDevice(&dev));
+    cudaEvent_t ready;
+    AMG_TRY_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    if (cudaEventRecord(ready, s) != cudaSuccess) {
+        cudaEventDestroy(ready);
+        AMG_TRY_CUDA(cudaGetLastError());
+    }
+    std::vector<int> status(ni, 1);  // 1 = not started
+    std::vector<std::string> msg(ni);
+    std::atomic<int> next{0};
+    std::atomic<bool> failed{false};
+    const amg_allocator *alloc = h->allocator();
+    auto worker = [&](int w) {
+        cudaStream_t ws = nullptr;
+        int ok = cudaSetDevice(dev) == cudaSuccess ? setup_stream(dev, w, &ws) : AMG_ERR_CUDA;
+        if (ok >= 0 && cudaStreamWaitEvent(ws, ready, 0) != cudaSuccess) ok = AMG_ERR_CUDA;
+        const std::string why = ok >= 0 ? std::string() : std::string(last_error());
+        AllocScope scope(alloc);
+        for (;;) {
+            if (failed.load()) break;
+            const int i = next.fetch_add(1);
+            if (i >= ni) break;
+            amg_handle x = h->inst[i];
+            int st;
+            if (ok < 0) {
+                set_error("instance setup stream: %s", why.c_str());
+                st = ok;
+            } else {
+                x->stream = ws;
+                x->mem.stream = ws;
+                st = setup_impl(x, &A[i], B[i]);
+                cudaStreamSynchronize(ws);  // nothing of the instance stays queued on ws
+                x->stream = s;
+                x->mem.stream = s;
+            }
+            status[i] = st < 0 ? st : 0;
+            if (st < 0) {
+                msg[i] = last_error();
+                failed.store(true);
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    pool.reserve(nw);
+    for (int w = 0; w < nw; ++w) pool.emplace_back(worker, w);
+    for (std::thread &t : pool) t.join();
+    cudaEventDestroy(ready);
+    for (int i = 0; i < ni; ++i)
+        if (status[i] < 0) {
+            set_error("instance %d: %s", i, msg[i].c_str());
+            return status[i];
+        }
+    return AMG_OK;
+}
+
 static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, const int32_t *nrhs)
 {
     if (h->prm.storage != AMG_STORAGE_BLOCK || h->prm.setup != AMG_SETUP_BLOCK) {
@@ -1212,9 +1326,19 @@ static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, co
         x->mem.stream = s;
         x->max_lanes = 32;  // the batched SpMM keeps each row within one warp
         h->inst.push_back(x);
-        AMG_TRY(setup_impl(x, &A[i], B[i]));
-        h->depth.push_back((int)x->lv.size());
-        h->ndof0.push_back((int64_t)x->lv[0].n());
+    }
+    auto tp = std::chrono::steady_clock::now();
+    auto lap = [&](int k) {  // wall time of phase k (the stream drained first)
+        cudaStreamSynchronize(s);
+        const auto now = std::chrono::steady_clock::now();
+        h->phase_s[k] = std::chrono::duration<double>(now - tp).count();
+        tp = now;
+    };
+    AMG_TRY(setup_instances(h, A, B));
+    lap(0);
+    for (int i = 0; i < ni; ++i) {
+        h->depth.push_back((int)h->inst[i]->lv.size());
+        h->ndof0.push_back((int64_t)h->inst[i]->lv[0].n());
     }
     h->nlev = *std::max_element(h->depth.begin(), h->depth.end());
     std::vector<int> gi(h->ngl);
@@ -1223,8 +1347,9 @@ static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, co
     AMG_TRY(upload(h->mem, h->Kh, &h->K, s));
     AMG_TRY(upload(h->mem, h->goffh, &h->goff, s));
     AMG_TRY(upload(h->mem, gi, &h->g_inst, s));
-    std::vector<int> on(ni, 1);
+    std::vector<int> on(ni, 1), off(ni, 0);
     AMG_TRY(upload(h->mem, on, &h->all_on, s));
+    AMG_TRY(upload(h->mem, off, &h->all_off, s));
     // levels: vector offsets, smoother diagonals, concatenated operators
     h->lv.resize(h->nlev);
     for (int l = 0; l < h->nlev; ++l) {
@@ -1283,6 +1408,7 @@ static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, co
     AMG_TRY(upload(h->mem, cinst, &h->chunk_inst, s));
     AMG_TRY(upload(h->mem, cfirst, &h->chunk_first, s));
     AMG_TRY(h->mem.alloc_n(&h->part, (size_t)std::max(h->nchunks, 1) * BKMAX));
+    lap(1);
     // coarse solves: each instance's dense inverse at its own coarsest level
     std::vector<int64_t> aoff(ni, 0);
     std::vector<int> nc(ni), iinst, irow;
@@ -1336,6 +1462,7 @@ static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, co
     // from the CG residual directly (f pointer filled per solve below)
     AMG_TRY(upload(h->mem, fp, &h->fptr, s));
     AMG_TRY(upload(h->mem, zp, &h->zptr, s));
+    lap(2);
     // autotune the block-row tiling and the RHS tile of every concatenated
     // operator (PLAIN mode, on zeroed vectors)
     AMG_TRY_CUDA(cudaMemsetAsync(h->p, 0, sizeof(double) * n0, s));
@@ -1359,6 +1486,11 @@ static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, co
         }
     }
     AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    lap(3);
+    // the batch holds copies of everything its solve reads (operators,
+    // smoother diagonals, coarse inverses): the instances' own hierarchies go
+    for (amg_handle x : h->inst) destroy_handle(x);
+    h->inst.clear();
     return AMG_OK;
 }
 
@@ -1582,6 +1714,7 @@ int amg_batch_info(amg_batch h, amg_batch_desc *out)
     out->nrhs_total = h->ngl;
     out->nlevels = h->nlev;
     out->setup_seconds = h->setup_seconds;
+    for (int k = 0; k < 4; ++k) out->setup_phase_seconds[k] = h->phase_s[k];
     int64_t dofs = 0;
     for (int i = 0; i < h->ninst; ++i) dofs += h->ndof0[i];
     out->dofs_total = dofs;

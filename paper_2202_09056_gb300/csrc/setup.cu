@@ -1298,63 +1298,91 @@ __global__ void zero_rows_kernel(const double *__restrict__ D, int n, uint8_t *_
 }
 
 // Blocked right-looking Cholesky in panels of CHOL_NB columns: the panel's
-// diagonal block factored by one CTA, the rows below it by a triangular solve
-// (one thread per row), then the trailing lower triangle updated by a tiled
-// rank-CHOL_NB product.  A zero row (a dropped near-nullspace column) gets a
-// unit pivot; a pivot <= 0 elsewhere records its column in *err.
+// diagonal block factored by one CTA, which also forms the inverse of that
+// factor, the rows below it by a product with that inverse, then the trailing
+// lower triangle updated by a tiled rank-CHOL_NB product.  A zero row (a
+// dropped near-nullspace column) gets a unit pivot; a pivot <= 0 elsewhere
+// records its column in *err.  Every step but the diagonal factor is a
+// product spread over many CTAs: the FP64 rate of one SM is small, so a
+// substitution chain per thread on a few SMs would dominate.
 constexpr int CHOL_NB = 32;
 constexpr int CHOL_TILE = 16;
+constexpr int CHOL_W = CHOL_NB * CHOL_NB;  // doubles per diagonal-block inverse
 
+// One CTA of 256 threads: the nb x nb diagonal block of panel c0 factored in
+// shared memory (per column: pivot, scale of the column below it, update of
+// the trailing lower triangle), and W = L11^-1 formed alongside by the same
+// row operations applied to the identity (row j scaled by the reciprocal
+// pivot, then subtracted L[i][j] times from every row i > j).  L11 goes back
+// to D; W goes to Wd as CHOL_NB x CHOL_NB, zero above the diagonal and past nb.
 __global__ void __launch_bounds__(256) chol_diag_kernel(double *__restrict__ D, int n, int c0,
                                                         int nb, const uint8_t *__restrict__ zrow,
-                                                        int *__restrict__ err)
+                                                        int *__restrict__ err,
+                                                        double *__restrict__ Wd)
 {
-    __shared__ double blk[CHOL_NB][CHOL_NB + 1];
-    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-        const int r = t / nb, c = t % nb;
-        blk[r][c] = c <= r ? D[(int64_t)(c0 + r) * n + c0 + c] : 0.0;
+    __shared__ double blk[CHOL_NB][CHOL_NB + 1], w[CHOL_NB][CHOL_NB + 1];
+    __shared__ double rpiv;
+    for (int t = threadIdx.x; t < CHOL_W; t += blockDim.x) {
+        const int r = t / CHOL_NB, c = t % CHOL_NB;
+        blk[r][c] = (r < nb && c <= r) ? D[(int64_t)(c0 + r) * n + c0 + c] : 0.0;
+        w[r][c] = (r == c && r < nb) ? 1.0 : 0.0;
     }
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
         if (threadIdx.x == 0) {
-            double s = blk[j][j];
-            if (zrow[c0 + j]) s = 1.0;
-            if (!(s > 0.0)) {
+            double sj = blk[j][j];
+            if (zrow[c0 + j]) sj = 1.0;
+            if (!(sj > 0.0)) {
                 atomicExch(err, c0 + j + 1);
-                s = 1.0;
+                sj = 1.0;
             }
-            blk[j][j] = sqrt(s);
+            const double d = sqrt(sj);
+            blk[j][j] = d;
+            rpiv = 1.0 / d;
         }
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) blk[i][j] /= blk[j][j];
-        __syncthreads();
+        const double r = rpiv;
         const int m = nb - j - 1;
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-            const int i = j + 1 + t / m, k = j + 1 + t % m;
-            if (k <= i) blk[i][k] -= blk[i][j] * blk[k][j];
+        for (int t = threadIdx.x; t < m + j + 1; t += blockDim.x) {
+            if (t < m) blk[j + 1 + t][j] *= r;  // column j of L
+            else w[j][t - m] *= r;              // row j of W, columns <= j
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < m * m + m * (j + 1); t += blockDim.x) {
+            if (t < m * m) {
+                const int i = j + 1 + t / m, k = j + 1 + t % m;
+                if (k <= i) blk[i][k] -= blk[i][j] * blk[k][j];
+            } else {
+                const int u = t - m * m, i = j + 1 + u / (j + 1), k = u % (j + 1);
+                w[i][k] -= blk[i][j] * w[j][k];
+            }
         }
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-        const int r = t / nb, c = t % nb;
-        if (c <= r) D[(int64_t)(c0 + r) * n + c0 + c] = blk[r][c];
+    for (int t = threadIdx.x; t < CHOL_W; t += blockDim.x) {
+        const int r = t / CHOL_NB, c = t % CHOL_NB;
+        if (r < nb && c <= r) D[(int64_t)(c0 + r) * n + c0 + c] = blk[r][c];
+        Wd[t] = w[r][c];
     }
 }
 
-// rows i >= c0 + nb of the panel: L21[i, :] L11^T = A21[i, :]
-__global__ void chol_trsm_kernel(double *__restrict__ D, int n, int c0, int nb)
+// rows i >= c0 + nb of panel c0: L21 = A21 L11^-T = A21 W^T, 8 rows x CHOL_NB
+// columns per CTA (the rows staged in shared memory, then overwritten; W's
+// zero entries make every output a full CHOL_NB-term sum)
+__global__ void __launch_bounds__(256) chol_trsm_kernel(double *__restrict__ D, int n, int c0,
+                                                        int nb, const double *__restrict__ Wd)
 {
-    const int i = c0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double *row = D + (int64_t)i * n + c0;
-    double l[CHOL_NB];
-    for (int t = 0; t < nb; ++t) {
-        const double *lt = D + (int64_t)(c0 + t) * n + c0;
-        double v = row[t];
-        for (int q = 0; q < t; ++q) v -= l[q] * lt[q];
-        l[t] = v / lt[t];
-    }
-    for (int t = 0; t < nb; ++t) row[t] = l[t];
+    __shared__ double a[8][CHOL_NB + 1], w[CHOL_NB][CHOL_NB + 1];
+    for (int e = threadIdx.x; e < CHOL_W; e += blockDim.x) w[e / CHOL_NB][e % CHOL_NB] = Wd[e];
+    const int r = threadIdx.x / CHOL_NB, t = threadIdx.x % CHOL_NB;
+    const int i = c0 + nb + blockIdx.x * 8 + r;
+    a[r][t] = (i < n && t < nb) ? D[(int64_t)i * n + c0 + t] : 0.0;
+    __syncthreads();
+    if (i >= n || t >= nb) return;
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < CHOL_NB; ++q) v = fma(a[r][q], w[t][q], v);
+    D[(int64_t)i * n + c0 + t] = v;
 }
 
 // trailing update D[i][k] -= sum_t L21[i][t] L21[k][t], c1 <= k <= i < n,
@@ -1388,106 +1416,103 @@ __global__ void __launch_bounds__(CHOL_TILE * CHOL_TILE) chol_syrk_kernel(double
 // the diagonal) start from a zero right-hand side and end as zero rows and
 // columns of X.
 
-// one thread per column c < ncols: the block's rows of L Y = B (forward) or
-// L^T X = Y (backward) by substitution against the block's diagonal part.
-// Each thread runs about CHOL_NB^2 / 2 FP64 FMAs, so small CTAs spread the
-// columns over many SMs (the FP64 pipe of an SM is the limit).
-constexpr int INV_PANEL_T = 64;
+// The block's rows r0 .. r0 + nb - 1 of X, columns c < ncols: forward
+// Y_b = W X_b, backward X_b = W^T Y_b, with W the inverse of the block's
+// diagonal factor.  CHOL_NB rows x 8 columns per CTA (the strip staged in
+// shared memory, then overwritten).
 template <bool BWD>
-__global__ void __launch_bounds__(256) inv_panel_kernel(const double *__restrict__ D,
+__global__ void __launch_bounds__(256) inv_panel_kernel(const double *__restrict__ Wd,
                                                         double *__restrict__ X, int n, int r0,
                                                         int nb, int ncols)
 {
-    __shared__ double Lb[CHOL_NB][CHOL_NB + 1];
-    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-        const int r = t / nb, q = t % nb;
-        Lb[r][q] = q <= r ? D[(int64_t)(r0 + r) * n + r0 + q] : 0.0;
-    }
+    __shared__ double w[CHOL_NB][CHOL_NB + 1], xs[CHOL_NB][9];
+    for (int e = threadIdx.x; e < CHOL_W; e += blockDim.x) w[e / CHOL_NB][e % CHOL_NB] = Wd[e];
+    const int t = threadIdx.x / 8, cc = threadIdx.x % 8, c = blockIdx.x * 8 + cc;
+    xs[t][cc] = (t < nb && c < ncols) ? X[(int64_t)(r0 + t) * n + c] : 0.0;
     __syncthreads();
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncols) return;
-    double y[CHOL_NB];
-    if (!BWD) {
+    if (t >= nb || c >= ncols) return;
+    double v = 0.0;
 #pragma unroll
-        for (int t = 0; t < CHOL_NB; ++t) {
-            if (t >= nb) break;
-            double v = X[(int64_t)(r0 + t) * n + c];
-#pragma unroll
-            for (int q = 0; q < t; ++q) v -= Lb[t][q] * y[q];
-            y[t] = v / Lb[t][t];
-            X[(int64_t)(r0 + t) * n + c] = y[t];
-        }
-    } else {
-#pragma unroll
-        for (int t = CHOL_NB - 1; t >= 0; --t) {
-            if (t >= nb) continue;
-            double v = X[(int64_t)(r0 + t) * n + c];
-#pragma unroll
-            for (int q = t + 1; q < CHOL_NB; ++q)
-                if (q < nb) v -= Lb[q][t] * y[q];
-            y[t] = v / Lb[t][t];
-            X[(int64_t)(r0 + t) * n + c] = y[t];
-        }
-    }
+    for (int q = 0; q < CHOL_NB; ++q) v = fma(BWD ? w[q][t] : w[t][q], xs[q][cc], v);
+    X[(int64_t)(r0 + t) * n + c] = v;
 }
 
 // C -= A B on X's rows [i0, i1) and columns [0, j1), the inner index over the
 // block's nb rows r0 .. r0 + nb - 1: forward A(i, t) = L[i][r0 + t], backward
 // A(i, t) = L[r0 + t][i] with only j <= i written; B(t, j) = X[r0 + t][j].
-// 64 x 64 output tiles, 4 x 4 per thread.
-constexpr int INV_TILE = 64;
-template <bool BWD>
+// TILE x TILE output tiles (64 or 32), (TILE / 16)^2 per thread; every
+// output sums its nb terms in the same order whatever the tile.
+template <bool BWD, int TILE>
 __global__ void __launch_bounds__(256) inv_update_kernel(const double *__restrict__ D,
                                                          double *__restrict__ X, int n, int r0,
                                                          int nb, int i0, int i1, int j1)
 {
-    const int ti0 = i0 + blockIdx.y * INV_TILE, tj0 = blockIdx.x * INV_TILE;
+    constexpr int TM = TILE / 16;
+    const int ti0 = i0 + blockIdx.y * TILE, tj0 = blockIdx.x * TILE;
     if (ti0 >= i1 || tj0 >= j1) return;
-    if (BWD && tj0 > ti0 + INV_TILE - 1) return;  // tile wholly above the diagonal
-    __shared__ double As[CHOL_NB][INV_TILE + 1], Bs[CHOL_NB][INV_TILE + 1];
-    for (int e = threadIdx.x; e < nb * INV_TILE; e += blockDim.x) {
+    if (BWD && tj0 > ti0 + TILE - 1) return;  // tile wholly above the diagonal
+    __shared__ double As[CHOL_NB][TILE + 1], Bs[CHOL_NB][TILE + 1];
+    for (int e = threadIdx.x; e < nb * TILE; e += blockDim.x) {
         int t, ii;
         if (BWD) {
-            t = e / INV_TILE;
-            ii = e % INV_TILE;  // row r0 + t of L, consecutive columns
+            t = e / TILE;
+            ii = e % TILE;  // row r0 + t of L, consecutive columns
         } else {
             ii = e / nb;
-            t = e % nb;         // row i of L, consecutive columns r0 + t
+            t = e % nb;     // row i of L, consecutive columns r0 + t
         }
         const int i = ti0 + ii;
         As[t][ii] = i < i1 ? (BWD ? D[(int64_t)(r0 + t) * n + i] : D[(int64_t)i * n + r0 + t])
                            : 0.0;
-        const int tb = e / INV_TILE, jj = e % INV_TILE, j = tj0 + jj;
+        const int tb = e / TILE, jj = e % TILE, j = tj0 + jj;
         Bs[tb][jj] = j < j1 ? X[(int64_t)(r0 + tb) * n + j] : 0.0;
     }
     __syncthreads();
     const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-    double acc[4][4];
+    double acc[TM][TM];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < TM; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int b = 0; b < TM; ++b) acc[a][b] = 0.0;
     for (int t = 0; t < nb; ++t) {
-        double av[4], bv[4];
+        double av[TM], bv[TM];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = As[t][ty * 4 + a];
+        for (int a = 0; a < TM; ++a) av[a] = As[t][ty * TM + a];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = Bs[t][tx * 4 + b];
+        for (int b = 0; b < TM; ++b) bv[b] = Bs[t][tx * TM + b];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < TM; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+            for (int b = 0; b < TM; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int i = ti0 + ty * 4 + a;
+    for (int a = 0; a < TM; ++a) {
+        const int i = ti0 + ty * TM + a;
         if (i >= i1) continue;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int j = tj0 + tx * 4 + b;
+        for (int b = 0; b < TM; ++b) {
+            const int j = tj0 + tx * TM + b;
             if (j < j1 && (!BWD || j <= i)) X[(int64_t)i * n + j] -= acc[a][b];
         }
     }
+}
+
+// one inverse update over rows [i0, i1) x columns [0, j1): 64 x 64 tiles when
+// they give at least two CTAs per SM, else 32 x 32 (four times the CTAs)
+template <bool BWD>
+static void launch_inv_update(const double *D, double *X, int n, int r0, int nb, int i0, int i1,
+                              int j1, int num_sms, cudaStream_t s)
+{
+    const int64_t t64 = (int64_t)((i1 - i0 + 63) / 64) * ((j1 + 63) / 64);
+    const int64_t live64 = BWD ? (t64 + (i1 - i0 + 63) / 64) / 2 : t64;  // lower tiles only
+    if (live64 >= 2 * (int64_t)num_sms) {
+        const dim3 g((j1 + 63) / 64, (i1 - i0 + 63) / 64);
+        inv_update_kernel<BWD, 64><<<g, 256, 0, s>>>(D, X, n, r0, nb, i0, i1, j1);
+    } else {
+        const dim3 g((j1 + 31) / 32, (i1 - i0 + 31) / 32);
+        inv_update_kernel<BWD, 32><<<g, 256, 0, s>>>(D, X, n, r0, nb, i0, i1, j1);
+    }
+    ::amg::count_launch(1);
 }
 
 __global__ void unit_diag_kernel(double *__restrict__ X, int n, const uint8_t *__restrict__ zrow)
@@ -1524,11 +1549,15 @@ int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
         set_error("coarsest system has %d unknowns (limit %d)", n, COARSE_MAX);
         return AMG_ERR_LIMIT;
     }
-    double *D = nullptr, *X = nullptr;
+    Geom g;
+    AMG_TRY(query_geom(&g));
+    const int nblk_rows = (n + CHOL_NB - 1) / CHOL_NB;
+    double *D = nullptr, *X = nullptr, *Wd = nullptr;
     uint8_t *z = nullptr;
     int *brow = nullptr, *err = nullptr;
     AMG_TRY(tmp.alloc_n(&D, (size_t)n * n));
     AMG_TRY(keep.alloc_n(&X, (size_t)n * n));
+    AMG_TRY(tmp.alloc_n(&Wd, (size_t)std::max(nblk_rows, 1) * CHOL_W));
     AMG_TRY(tmp.alloc_n(&z, n));
     AMG_TRY(tmp.alloc_n(&brow, (size_t)std::max<int64_t>(A.nnzb, 1)));
     AMG_TRY(tmp.alloc_n(&err, 1));
@@ -1539,12 +1568,13 @@ int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
         densify_kernel<<<nblk(A.nnzb), T1D, 0, s>>>(brow, A.col, A.val, A.nnzb, A.br, n, D); ::amg::count_launch(1); }
     zero_rows_kernel<<<nblk(n), T1D, 0, s>>>(D, n, z); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
-    for (int c0 = 0; c0 < n; c0 += CHOL_NB) {
-        const int nb = std::min(CHOL_NB, n - c0), rest = n - c0 - nb;
-        chol_diag_kernel<<<1, 256, 0, s>>>(D, n, c0, nb, z, err);
+    for (int b = 0; b < nblk_rows; ++b) {
+        const int c0 = b * CHOL_NB, nb = std::min(CHOL_NB, n - c0), rest = n - c0 - nb;
+        double *W = Wd + (size_t)b * CHOL_W;
+        chol_diag_kernel<<<1, 256, 0, s>>>(D, n, c0, nb, z, err, W);
         ::amg::count_launch(1);
         if (rest > 0) {
-            chol_trsm_kernel<<<nblk(rest, 128), 128, 0, s>>>(D, n, c0, nb);
+            chol_trsm_kernel<<<(rest + 7) / 8, 256, 0, s>>>(D, n, c0, nb, W);
             const int nt = (rest + CHOL_TILE - 1) / CHOL_TILE;
             chol_syrk_kernel<<<dim3(nt, nt), dim3(CHOL_TILE, CHOL_TILE), 0, s>>>(D, n, c0, nb);
             ::amg::count_launch(2);
@@ -1563,28 +1593,19 @@ int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
         unit_diag_kernel<<<nblk(n), T1D, 0, s>>>(X, n, z);
         ::amg::count_launch(1);
     }
-    for (int r0 = 0; r0 < n; r0 += CHOL_NB) {  // forward: L Y = I, columns < r1
-        const int nb = std::min(CHOL_NB, n - r0), r1 = r0 + nb;
-        inv_panel_kernel<false><<<(r1 + INV_PANEL_T - 1) / INV_PANEL_T, INV_PANEL_T, 0, s>>>(
-            D, X, n, r0, nb, r1);
+    for (int b = 0; b < nblk_rows; ++b) {  // forward: L Y = I, columns < r1
+        const int r0 = b * CHOL_NB, nb = std::min(CHOL_NB, n - r0), r1 = r0 + nb;
+        inv_panel_kernel<false><<<(r1 + 7) / 8, 256, 0, s>>>(Wd + (size_t)b * CHOL_W, X, n, r0,
+                                                              nb, r1);
         ::amg::count_launch(1);
-        if (r1 < n) {
-            const dim3 g((r1 + INV_TILE - 1) / INV_TILE, (n - r1 + INV_TILE - 1) / INV_TILE);
-            inv_update_kernel<false><<<g, 256, 0, s>>>(D, X, n, r0, nb, r1, n, r1);
-            ::amg::count_launch(1);
-        }
+        if (r1 < n) launch_inv_update<false>(D, X, n, r0, nb, r1, n, r1, g.num_sms, s);
     }
-    const int nblk_rows = (n + CHOL_NB - 1) / CHOL_NB;
     for (int b = nblk_rows - 1; b >= 0; --b) {  // backward: L^T X = Y, lower triangle
         const int r0 = b * CHOL_NB, nb = std::min(CHOL_NB, n - r0), r1 = r0 + nb;
-        inv_panel_kernel<true><<<(r1 + INV_PANEL_T - 1) / INV_PANEL_T, INV_PANEL_T, 0, s>>>(
-            D, X, n, r0, nb, r1);
+        inv_panel_kernel<true><<<(r1 + 7) / 8, 256, 0, s>>>(Wd + (size_t)b * CHOL_W, X, n, r0,
+                                                             nb, r1);
         ::amg::count_launch(1);
-        if (r0 > 0) {
-            const dim3 g((r0 + INV_TILE - 1) / INV_TILE, (r0 + INV_TILE - 1) / INV_TILE);
-            inv_update_kernel<true><<<g, 256, 0, s>>>(D, X, n, r0, nb, 0, r0, r0);
-            ::amg::count_launch(1);
-        }
+        if (r0 > 0) launch_inv_update<true>(D, X, n, r0, nb, 0, r0, r0, g.num_sms, s);
     }
     if (n > 0) {
         const int nt = (n + 31) / 32;
@@ -1593,6 +1614,7 @@ int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
     }
     AMG_TRY_CUDA(cudaGetLastError());
     AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    tmp.release(Wd);
     tmp.release(D);
     tmp.release(z);
     tmp.release(brow);

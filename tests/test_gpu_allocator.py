@@ -103,6 +103,26 @@ def test_failing_allocator_is_an_error_and_leaks_nothing(k):
     assert st == amg.AMG_OK and res <= 1e-8
 
 
+@pytest.mark.parametrize("k", [1, 30, 90])
+def test_failing_allocator_in_batch_setup_leaks_nothing(k):
+    """The batch sets its instances up on several host threads, each calling
+    the allocator; once one call fails, every instance's memory and the
+    batch's own go back through the allocator."""
+    mats, Bs = [], []
+    for shape in ((6, 5, 7), (5, 5, 5), (7, 6, 5), (4, 6, 5), (6, 6, 6)):
+        p = q.make_problem(shape, body=(0, 0, -1))
+        rp, cl, val, B = dev_args(p, torch)
+        mats.append((rp, cl, val))
+        Bs.append(B)
+    base = _allocated()
+    fa = _Failing(k)
+    with pytest.raises(amg.AmgError) as e:
+        amg.AMGBatch(mats, Bs, [1] * 5, coarse_enough=100, allocator=fa.struct)
+    assert e.value.status == amg.AMG_ERR_CUDA and "allocator" in str(e.value)
+    assert fa.calls >= k and not fa.live
+    assert _allocated() == base
+
+
 def test_allocator_without_free_is_rejected():
     p = q.cube(4)
     args = dev_args(p, torch)

@@ -84,6 +84,29 @@ def test_instance_in_batch_equals_instance_alone():
             assert res1[0][0] == res[i][j]
 
 
+def test_failing_instance_is_named():
+    """Instances are set up by several host threads at once; a batch with two
+    bad instances (a NaN in A) reports the lower-numbered one, every time."""
+    mats, Bs = [], []
+    for k, shape in enumerate(((5, 5, 5), (6, 5, 4), (4, 4, 6), (5, 6, 5), (4, 5, 4))):
+        p = q.make_problem(shape, body=(0, 0, -1))
+        (rp, cl, val), B = _dev(p)
+        if k in (1, 3):
+            val = val.clone()
+            val[3, 1, 1] = float("nan")
+        mats.append((rp, cl, val))
+        Bs.append(B)
+    for _ in range(3):
+        with pytest.raises(amg.AmgError) as e:
+            amg.AMGBatch(mats, Bs, [1] * 5, coarse_enough=100)
+        assert e.value.status == amg.AMG_ERR_ARG
+        assert str(e.value).count("instance 1: A or B holds a non-finite value") == 1, str(e.value)
+    # the good instances alone still set up and solve
+    good = [0, 2, 4]
+    bat = amg.AMGBatch([mats[i] for i in good], [Bs[i] for i in good], [1] * 3, coarse_enough=100)
+    assert bat.info()["ninst"] == 3
+
+
 def test_batch_zero_rhs_and_cap():
     p = q.make_problem((5, 4, 6), body=[(0, 0, -1), (0, 0, 0), (1, 0, 0)])
     m, B = _dev(p)

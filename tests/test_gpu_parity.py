@@ -166,6 +166,30 @@ def test_pcg_edge_cases():
     assert it == 1 and res <= 1e-10
 
 
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 1, 1), (2, 2, 2), (5, 4, 3), (6, 6, 6),
+                                   (9, 9, 9)])
+def test_coarse_inverse_is_the_inverse(shape):
+    """A one-level hierarchy's V-cycle is the dense coarse inverse applied to
+    r: against a dense solve of the assembled matrix, within cond(A) times the
+    unit roundoff.  Sizes from 24 to 3000 unknowns: a single partial panel of
+    the 32-column blocked factor, then several panels with a ragged last one
+    (4, 17, 8, 5 and 24 rows), and at 3000 inverse updates on both tile sizes
+    (64 x 64 once they fill two CTAs per SM, 32 x 32 before)."""
+    p = q.make_problem(shape, body=(0, 0, -1))
+    A = o.from_problem(p).to_scipy().toarray()
+    ev = np.linalg.eigvalsh(A)
+    cond = ev[-1] / ev[0]
+    rp, cl, val, B = _dev(p)
+    G = amg.AMG(rp, cl, val, B, coarse_enough=10 ** 6)
+    assert G.nlevels == 1
+    rng = np.random.default_rng(11)
+    for _ in range(2):
+        r = rng.standard_normal(p.ndof)
+        z = G.vcycle(torch.from_numpy(r).cuda()).cpu().numpy()
+        ze = np.linalg.solve(A, r)
+        assert np.linalg.norm(z - ze) <= 50 * cond * 2.2e-16 * np.linalg.norm(ze), shape
+
+
 def test_solve_is_bitwise_reproducible():
     p = q.inclusions(10)
     rp, cl, val, B = _dev(p)
