@@ -1440,8 +1440,7 @@ __global__ void __launch_bounds__(256) inv_panel_kernel(const double *__restrict
 // C -= A B on X's rows [i0, i1) and columns [0, j1), the inner index over the
 // block's nb rows r0 .. r0 + nb - 1: forward A(i, t) = L[i][r0 + t], backward
 // A(i, t) = L[r0 + t][i] with only j <= i written; B(t, j) = X[r0 + t][j].
-// TILE x TILE output tiles (64 or 32), (TILE / 16)^2 per thread; every
-// output sums its nb terms in the same order whatever the tile.
+// TILE x TILE output tiles, (TILE / 16)^2 per thread.
 template <bool BWD, int TILE>
 __global__ void __launch_bounds__(256) inv_update_kernel(const double *__restrict__ D,
                                                          double *__restrict__ X, int n, int r0,
@@ -1497,21 +1496,16 @@ __global__ void __launch_bounds__(256) inv_update_kernel(const double *__restric
     }
 }
 
-// one inverse update over rows [i0, i1) x columns [0, j1): 64 x 64 tiles when
-// they give at least two CTAs per SM, else 32 x 32 (four times the CTAs)
+// one inverse update over rows [i0, i1) x columns [0, j1) in 32 x 32 tiles:
+// with an SM's FP64 rate the limit, small CTAs (32k FMAs each) spread evenly
+// over the SMs, where 64 x 64 tiles left a few SMs with one CTA more than the
+// rest; four FMAs per four shared loads stay ahead of the FP64 pipe
 template <bool BWD>
 static void launch_inv_update(const double *D, double *X, int n, int r0, int nb, int i0, int i1,
-                              int j1, int num_sms, cudaStream_t s)
+                              int j1, cudaStream_t s)
 {
-    const int64_t t64 = (int64_t)((i1 - i0 + 63) / 64) * ((j1 + 63) / 64);
-    const int64_t live64 = BWD ? (t64 + (i1 - i0 + 63) / 64) / 2 : t64;  // lower tiles only
-    if (live64 >= 2 * (int64_t)num_sms) {
-        const dim3 g((j1 + 63) / 64, (i1 - i0 + 63) / 64);
-        inv_update_kernel<BWD, 64><<<g, 256, 0, s>>>(D, X, n, r0, nb, i0, i1, j1);
-    } else {
-        const dim3 g((j1 + 31) / 32, (i1 - i0 + 31) / 32);
-        inv_update_kernel<BWD, 32><<<g, 256, 0, s>>>(D, X, n, r0, nb, i0, i1, j1);
-    }
+    const dim3 g((j1 + 31) / 32, (i1 - i0 + 31) / 32);
+    inv_update_kernel<BWD, 32><<<g, 256, 0, s>>>(D, X, n, r0, nb, i0, i1, j1);
     ::amg::count_launch(1);
 }
 
@@ -1549,8 +1543,6 @@ int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
         set_error("coarsest system has %d unknowns (limit %d)", n, COARSE_MAX);
         return AMG_ERR_LIMIT;
     }
-    Geom g;
-    AMG_TRY(query_geom(&g));
     const int nblk_rows = (n + CHOL_NB - 1) / CHOL_NB;
     double *D = nullptr, *X = nullptr, *Wd = nullptr;
     uint8_t *z = nullptr;
@@ -1598,14 +1590,14 @@ int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
         inv_panel_kernel<false><<<(r1 + 7) / 8, 256, 0, s>>>(Wd + (size_t)b * CHOL_W, X, n, r0,
                                                               nb, r1);
         ::amg::count_launch(1);
-        if (r1 < n) launch_inv_update<false>(D, X, n, r0, nb, r1, n, r1, g.num_sms, s);
+        if (r1 < n) launch_inv_update<false>(D, X, n, r0, nb, r1, n, r1, s);
     }
     for (int b = nblk_rows - 1; b >= 0; --b) {  // backward: L^T X = Y, lower triangle
         const int r0 = b * CHOL_NB, nb = std::min(CHOL_NB, n - r0), r1 = r0 + nb;
         inv_panel_kernel<true><<<(r1 + 7) / 8, 256, 0, s>>>(Wd + (size_t)b * CHOL_W, X, n, r0,
                                                              nb, r1);
         ::amg::count_launch(1);
-        if (r0 > 0) launch_inv_update<true>(D, X, n, r0, nb, 0, r0, r0, g.num_sms, s);
+        if (r0 > 0) launch_inv_update<true>(D, X, n, r0, nb, 0, r0, r0, s);
     }
     if (n > 0) {
         const int nt = (n + 31) / 32;

@@ -173,8 +173,8 @@ def test_coarse_inverse_is_the_inverse(shape):
     r: against a dense solve of the assembled matrix, within cond(A) times the
     unit roundoff.  Sizes from 24 to 3000 unknowns: a single partial panel of
     the 32-column blocked factor, then several panels with a ragged last one
-    (4, 17, 8, 5 and 24 rows), and at 3000 inverse updates on both tile sizes
-    (64 x 64 once they fill two CTAs per SM, 32 x 32 before)."""
+    (4, 17, 8, 5 and 24 rows), up to 94 panels whose updates span from one
+    tile row to thousands of tiles."""
     p = q.make_problem(shape, body=(0, 0, -1))
     A = o.from_problem(p).to_scipy().toarray()
     ev = np.linalg.eigvalsh(A)
