@@ -609,12 +609,43 @@ __global__ void __launch_bounds__(BS_T) bdecide_kernel(int ngl, int ninst, const
     if (threadIdx.x == 0 && use_cond && !*st.any_active) cudaGraphSetConditional(cond, 0);
 }
 
+// Coarse right-hand sides of every enabled instance rounded to FP32 (VK 2)
+// or split into FP32 pairs (VK 1), once per V-cycle, into one array indexed
+// by coff (instance i's n_i K_i values from coff[i]): the coarse GEMV's inner
+// loop then reads them as they are, without a conversion per product.
+template <int VK>
+__global__ void bcoarse_prep_kernel(int ninst, const int64_t *__restrict__ coff,
+                                    const int *__restrict__ enable,
+                                    double *const *__restrict__ fptr, void *__restrict__ out)
+{
+    const int64_t total = coff[ninst];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        int lo = 0, hi = ninst;  // coff[lo] <= e < coff[hi] (offsets strictly increase)
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (coff[mid] <= e) lo = mid;
+            else hi = mid;
+        }
+        if (!enable[lo]) continue;
+        const double v = fptr[lo][e - coff[lo]];
+        if constexpr (VK == 2) static_cast<float *>(out)[e] = f64_to_f32_rn(v);
+        else static_cast<df32 *>(out)[e] = df32(v);
+    }
+}
+
 // Coarse solves of every instance at its own coarsest level: y_i = Ainv_i f_i
-// for the instance's K right-hand sides; one warp per (instance, row).
+// for the instance's K right-hand sides; one warp per (instance, row).  The
+// arithmetic follows the batch's V-cycle: FP64 (VK 0), FP64 emulated on FP32
+// pairs (VK 1: the inverse as hi/lo pairs, the double-float product and sum
+// of the SpMMs) or FP32 (VK 2: an FP32 copy of the inverse, FP32 FMAs); in
+// the reduced forms the right-hand sides come from bcoarse_prep_kernel.
+template <int VK>
 __global__ void bcoarse_kernel(int nitems, const int *__restrict__ item_inst,
                                const int *__restrict__ item_row, const int *__restrict__ enable,
                                const int *__restrict__ nc, const int64_t *__restrict__ aoff,
-                               const double *__restrict__ Ainv, const int *__restrict__ K,
+                               const void *__restrict__ Ainv, const int64_t *__restrict__ coff,
+                               const void *__restrict__ fconv, const int *__restrict__ K,
                                double *const *__restrict__ fptr, double *const *__restrict__ zptr)
 {
     const int lane = threadIdx.x & 31;
@@ -623,28 +654,87 @@ __global__ void bcoarse_kernel(int nitems, const int *__restrict__ item_inst,
         const int inst = item_inst[t];
         if (!enable[inst]) continue;
         const int row = item_row[t], n = nc[inst], Ki = K[inst];
-        const double *ar = Ainv + aoff[inst] + (int64_t)row * n;
-        const double *f = fptr[inst];
+        const int64_t r0 = aoff[inst] + (int64_t)row * n;
         // one pass over the row: each entry feeds the Ki right-hand sides'
         // sums (the row is read once, Ki independent chains); every sum runs
         // over the row in the same order whatever Ki is, so a pair's result
         // does not depend on how many right-hand sides share its instance
-        double acc[BKMAX];
+        double out[BKMAX];
+        if constexpr (VK == 0) {
+            const double *ar = static_cast<const double *>(Ainv) + r0;
+            const double *f = fptr[inst];
+            double acc[BKMAX];
 #pragma unroll
-        for (int k = 0; k < BKMAX; ++k) acc[k] = 0.0;
-        for (int j = lane; j < n; j += 32) {
-            const double a = ar[j];
-            const double *fj = f + (int64_t)j * Ki;
+            for (int k = 0; k < BKMAX; ++k) acc[k] = 0.0;
+            for (int j = lane; j < n; j += 32) {
+                const double a = ar[j];
+                const double *fj = f + (int64_t)j * Ki;
 #pragma unroll
-            for (int k = 0; k < BKMAX; ++k)
-                if (k < Ki) acc[k] = fma(a, fj[k], acc[k]);
+                for (int k = 0; k < BKMAX; ++k)
+                    if (k < Ki) acc[k] = fma(a, fj[k], acc[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < BKMAX; ++k) out[k] = acc[k];
+        } else if constexpr (VK == 2) {
+            const float *ar = static_cast<const float *>(Ainv) + r0;
+            const float *f = static_cast<const float *>(fconv) + coff[inst];
+            float acc[BKMAX];
+#pragma unroll
+            for (int k = 0; k < BKMAX; ++k) acc[k] = 0.0f;
+            for (int j = lane; j < n; j += 32) {
+                const float a = ar[j];
+                const float *fj = f + (int64_t)j * Ki;
+#pragma unroll
+                for (int k = 0; k < BKMAX; ++k)
+                    if (k < Ki) acc[k] = fmaf(a, fj[k], acc[k]);
+            }
+            // FP32 butterfly, then exactly to FP64
+#pragma unroll
+            for (int k = 0; k < BKMAX; ++k) {
+                if (k >= Ki) break;
+                float v = acc[k];
+#pragma unroll
+                for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+                out[k] = f32_to_f64(v);
+            }
+        } else {
+            const df32 *ar = static_cast<const df32 *>(Ainv) + r0;
+            const df32 *f = static_cast<const df32 *>(fconv) + coff[inst];
+            float sh[BKMAX], sl[BKMAX];
+#pragma unroll
+            for (int k = 0; k < BKMAX; ++k) sh[k] = sl[k] = 0.0f;
+            for (int j = lane; j < n; j += 32) {
+                const df32 a = ar[j];
+                const df32 *fj = f + (int64_t)j * Ki;
+#pragma unroll
+                for (int k = 0; k < BKMAX; ++k) {
+                    if (k >= Ki) break;
+                    const df32 x = fj[k];
+                    // error-free product of the his plus the cross terms,
+                    // then the renormalised double-float sum (nothing
+                    // contracted: every rounding written out)
+                    const float pv = __fmul_rn(a.h, x.h);
+                    float er = __fmaf_rn(a.h, x.h, -pv);
+                    er = __fmaf_rn(a.h, x.l, er);
+                    er = __fmaf_rn(a.l, x.h, er);
+                    const float sn = __fadd_rn(sh[k], pv);
+                    const float bv = __fsub_rn(sn, sh[k]);
+                    float te = __fadd_rn(__fsub_rn(sh[k], __fsub_rn(sn, bv)), __fsub_rn(pv, bv));
+                    te = __fadd_rn(te, __fadd_rn(sl[k], er));
+                    sh[k] = __fadd_rn(sn, te);
+                    sl[k] = __fsub_rn(te, __fsub_rn(sh[k], sn));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < BKMAX; ++k) out[k] = f32_to_f64(sh[k]) + f32_to_f64(sl[k]);
         }
 #pragma unroll
         for (int k = 0; k < BKMAX; ++k) {
             if (k >= Ki) break;
-            double v = acc[k];
+            double v = out[k];
+            if constexpr (VK != 2)
 #pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+                for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
             if (lane == 0) zptr[inst][(int64_t)row * Ki + k] = v;
         }
     }
@@ -685,7 +775,11 @@ struct amg_batch_s {
     int *chunk_inst = nullptr, *chunk_first = nullptr;
     int nchunks = 0;
     // coarse
-    double *Ainv = nullptr;
+    double *Ainv = nullptr;              // FP64 inverses (FP64 V-cycle)
+    void *AinvR = nullptr;               // ... rounded to FP32 or split into FP32 pairs
+    int64_t *coff = nullptr;             // reduced forms: offsets of the converted rhs
+    void *fconv = nullptr;               // ... and the converted coarse right-hand sides
+    int64_t ctot = 0;
     int64_t *aoff = nullptr;
     int *nc = nullptr, *item_inst = nullptr, *item_row = nullptr;
     int nitems = 0;
@@ -787,10 +881,22 @@ static int record_bvcycle(amg_batch h, const double *f0, double *z0, const int *
         kti += 3;
     }
     {
-        int grid = std::min((h->nitems + 7) / 8, g.max_ctas);
-        bcoarse_kernel<<<std::max(grid, 1), 256, 0, s>>>(h->nitems, h->item_inst, h->item_row, enable,
-                                                         h->nc, h->aoff, h->Ainv, h->K, h->fptr,
-                                                         h->zptr);
+        const int grid = std::max(std::min((h->nitems + 7) / 8, g.max_ctas), 1);
+        if (h->vk) {
+            const int pg = (int)std::max<int64_t>(1, std::min<int64_t>((h->ctot + 255) / 256,
+                                                                       g.max_ctas));
+            if (h->vk == 1)
+                bcoarse_prep_kernel<1><<<pg, 256, 0, s>>>(h->ninst, h->coff, enable, h->fptr, h->fconv);
+            else
+                bcoarse_prep_kernel<2><<<pg, 256, 0, s>>>(h->ninst, h->coff, enable, h->fptr, h->fconv);
+            count_launch(1);
+        }
+#define BCOARSE_ARGS h->nitems, h->item_inst, h->item_row, enable, h->nc, h->aoff, \
+                     h->vk ? h->AinvR : (const void *)h->Ainv, h->coff, h->fconv, h->K, h->fptr, h->zptr
+        if (h->vk == 1) bcoarse_kernel<1><<<grid, 256, 0, s>>>(BCOARSE_ARGS);
+        else if (h->vk == 2) bcoarse_kernel<2><<<grid, 256, 0, s>>>(BCOARSE_ARGS);
+        else bcoarse_kernel<0><<<grid, 256, 0, s>>>(BCOARSE_ARGS);
+#undef BCOARSE_ARGS
         count_launch(1);
         AMG_TRY_CUDA(cudaGetLastError());
     }
@@ -1436,6 +1542,43 @@ static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, co
         AMG_TRY_CUDA(cudaMemcpyAsync(h->Ainv + aoff[i], h->inst[i]->Ainv,
                                      sizeof(double) * h->inst[i]->nc * h->inst[i]->nc,
                                      cudaMemcpyDeviceToDevice, s));
+    if (h->vk) {
+        // the reduced V-cycles solve their coarse levels in their own
+        // arithmetic: the inverses rounded to FP32 or split into FP32 pairs
+        // (the FP64 copy goes), and room for the converted right-hand sides
+        const int64_t ne = std::max<int64_t>(atot, 1);
+        const unsigned cg = (unsigned)((ne + 255) / 256);
+        if (h->vk == 1) {
+            df32 *e = nullptr;
+            AMG_TRY(h->mem.alloc_n(&e, (size_t)ne));
+            to_df32_kernel<<<cg, 256, 0, s>>>(h->Ainv, e, atot);
+            h->AinvR = e;
+        } else {
+            float *f = nullptr;
+            AMG_TRY(h->mem.alloc_n(&f, (size_t)ne));
+            to_f32_kernel<<<cg, 256, 0, s>>>(h->Ainv, f, atot);
+            h->AinvR = f;
+        }
+        count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+        AMG_TRY_CUDA(cudaStreamSynchronize(s));
+        h->mem.release(h->Ainv);
+        h->Ainv = nullptr;
+        std::vector<int64_t> coff(ni + 1, 0);
+        for (int i = 0; i < ni; ++i) coff[i + 1] = coff[i] + (int64_t)nc[i] * h->Kh[i];
+        h->ctot = coff[ni];
+        AMG_TRY(upload(h->mem, coff, &h->coff, s));
+        const size_t nconv = (size_t)std::max<int64_t>(h->ctot, 1);
+        if (h->vk == 1) {
+            df32 *e = nullptr;
+            AMG_TRY(h->mem.alloc_n(&e, nconv));
+            h->fconv = e;
+        } else {
+            float *f = nullptr;
+            AMG_TRY(h->mem.alloc_n(&f, nconv));
+            h->fconv = f;
+        }
+    }
     h->nitems = (int)iinst.size();
     AMG_TRY(upload(h->mem, aoff, &h->aoff, s));
     AMG_TRY(upload(h->mem, nc, &h->nc, s));

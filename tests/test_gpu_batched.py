@@ -64,7 +64,12 @@ def test_batch_matches_oracle_per_rhs():
             assert np.linalg.norm(u - uo) <= 1e-7 * np.linalg.norm(uo), (i, j)
 
 
-def test_instance_in_batch_equals_instance_alone():
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+def test_instance_in_batch_equals_instance_alone(prec):
+    """In every V-cycle precision (the coarse solve included), an (instance,
+    rhs) pair gives bitwise the same iterates in the batch as alone."""
+    kw = {"fp64": {}, "df64": {"precision": amg.PREC_DF64},
+          "fp32": {"precision": amg.PREC_FP32}}[prec]
     inst = _instances()
     mats, Bs, nrhs, F = [], [], [], []
     for p, k in inst:
@@ -73,11 +78,11 @@ def test_instance_in_batch_equals_instance_alone():
         Bs.append(B)
         nrhs.append(k)
         F.append(torch.from_numpy(np.atleast_2d(p.f).copy()).cuda())
-    bat = amg.AMGBatch(mats, Bs, nrhs, coarse_enough=150)
+    bat = amg.AMGBatch(mats, Bs, nrhs, coarse_enough=150, **kw)
     U, its, res, _ = bat.solve(F, tol=1e-8)
     for i in (0, 2):
         for j in range(nrhs[i]):
-            one = amg.AMGBatch([mats[i]], [Bs[i]], [1], coarse_enough=150)
+            one = amg.AMGBatch([mats[i]], [Bs[i]], [1], coarse_enough=150, **kw)
             U1, it1, res1, _ = one.solve([F[i][j:j + 1].clone()], tol=1e-8)
             assert it1[0][0] == its[i][j]
             assert torch.equal(U1[0][0], U[i][j]), (i, j)
