@@ -1310,51 +1310,67 @@ constexpr int CHOL_TILE = 16;
 constexpr int CHOL_W = CHOL_NB * CHOL_NB;  // doubles per diagonal-block inverse
 
 // One CTA of 256 threads: the nb x nb diagonal block of panel c0 factored in
-// shared memory (per column: pivot, scale of the column below it, update of
+// shared memory (per column: scale of the column below the pivot, update of
 // the trailing lower triangle), and W = L11^-1 formed alongside by the same
 // row operations applied to the identity (row j scaled by the reciprocal
-// pivot, then subtracted L[i][j] times from every row i > j).  L11 goes back
-// to D; W goes to Wd as CHOL_NB x CHOL_NB, zero above the diagonal and past nb.
+// pivot, then subtracted L[i][j] times from every row i > j).  Two barriers a
+// column: thread 0 alone updates the next diagonal entry and at once takes
+// its pivot (one reciprocal square root: d = s rsqrt(s), 1/d = rsqrt(s)),
+// while the other threads update the rest, so the serial pivot overlaps the
+// update.  L11 goes back to D; W goes to Wd as CHOL_NB x CHOL_NB, zero above
+// the diagonal and past nb.
+__device__ __forceinline__ void chol_pivot(double *diag, double *rp, int col, bool zero_row,
+                                           int *err)
+{
+    double sj = *diag;
+    if (zero_row) sj = 1.0;
+    if (!(sj > 0.0)) {
+        atomicExch(err, col + 1);
+        sj = 1.0;
+    }
+    const double r = rsqrt(sj);
+    *diag = sj * r;
+    *rp = r;
+}
+
 __global__ void __launch_bounds__(256) chol_diag_kernel(double *__restrict__ D, int n, int c0,
                                                         int nb, const uint8_t *__restrict__ zrow,
                                                         int *__restrict__ err,
                                                         double *__restrict__ Wd)
 {
     __shared__ double blk[CHOL_NB][CHOL_NB + 1], w[CHOL_NB][CHOL_NB + 1];
-    __shared__ double rpiv;
+    __shared__ double rpiv[CHOL_NB];
     for (int t = threadIdx.x; t < CHOL_W; t += blockDim.x) {
         const int r = t / CHOL_NB, c = t % CHOL_NB;
         blk[r][c] = (r < nb && c <= r) ? D[(int64_t)(c0 + r) * n + c0 + c] : 0.0;
         w[r][c] = (r == c && r < nb) ? 1.0 : 0.0;
     }
     __syncthreads();
+    if (threadIdx.x == 0) chol_pivot(&blk[0][0], &rpiv[0], c0, zrow[c0] != 0, err);
+    __syncthreads();
     for (int j = 0; j < nb; ++j) {
-        if (threadIdx.x == 0) {
-            double sj = blk[j][j];
-            if (zrow[c0 + j]) sj = 1.0;
-            if (!(sj > 0.0)) {
-                atomicExch(err, c0 + j + 1);
-                sj = 1.0;
-            }
-            const double d = sqrt(sj);
-            blk[j][j] = d;
-            rpiv = 1.0 / d;
-        }
-        __syncthreads();
-        const double r = rpiv;
+        const double r = rpiv[j];
         const int m = nb - j - 1;
         for (int t = threadIdx.x; t < m + j + 1; t += blockDim.x) {
             if (t < m) blk[j + 1 + t][j] *= r;  // column j of L
             else w[j][t - m] *= r;              // row j of W, columns <= j
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < m * m + m * (j + 1); t += blockDim.x) {
-            if (t < m * m) {
-                const int i = j + 1 + t / m, k = j + 1 + t % m;
-                if (k <= i) blk[i][k] -= blk[i][j] * blk[k][j];
-            } else {
-                const int u = t - m * m, i = j + 1 + u / (j + 1), k = u % (j + 1);
-                w[i][k] -= blk[i][j] * w[j][k];
+        if (threadIdx.x == 0) {
+            if (m > 0) {  // the next diagonal entry, then its pivot
+                blk[j + 1][j + 1] -= blk[j + 1][j] * blk[j + 1][j];
+                chol_pivot(&blk[j + 1][j + 1], &rpiv[j + 1], c0 + j + 1, zrow[c0 + j + 1] != 0,
+                           err);
+            }
+        } else {
+            for (int t = threadIdx.x - 1; t < m * m + m * (j + 1); t += blockDim.x - 1) {
+                if (t < m * m) {
+                    const int i = j + 1 + t / m, k = j + 1 + t % m;
+                    if (k <= i && !(i == j + 1 && k == j + 1)) blk[i][k] -= blk[i][j] * blk[k][j];
+                } else {
+                    const int u = t - m * m, i = j + 1 + u / (j + 1), k = u % (j + 1);
+                    w[i][k] -= blk[i][j] * w[j][k];
+                }
             }
         }
         __syncthreads();
