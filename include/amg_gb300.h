@@ -380,7 +380,7 @@ typedef struct {
  * candidates.  A[i] (3x3 BSR) and B[i] (n_i x 6) are device arrays, read
  * only, written on `stream` before the call.  Block storage and the block
  * setup only; prm->precision FP64, FP32 or emulated FP64 (the V-cycle's
- * operators; CG stays FP64); prm->loop_mode 1 launches one captured
+ * operators and its coarse solves; CG stays FP64); prm->loop_mode 1 launches one captured
  * iteration per host step, for profilers, with the same results.  An error
  * in an instance's setup is reported as "instance <i>: <message>" for the
  * lowest-numbered failing instance.  Synchronises `stream`. */
