@@ -815,12 +815,16 @@ __global__ void __launch_bounds__(128) spgemm_rows_kernel(
     }
 }
 
-// C = X Y for few, long rows (the coarse levels): one CTA per output row,
-// the row's block accumulators in shared memory.  For each X_ik, k
-// ascending, the threads first locate the columns of Y row k in C's row,
-// then take its (block, entry) pairs, so every accumulator entry sees the
-// same FMA sequence as in the kernels above (k ascending, then the inner
-// index) and gets the same bits, with the whole CTA on one row.
+// C = X Y for few, long rows (the coarse levels): gridDim.y CTAs per output
+// row, each holding a contiguous share of the row's output blocks as
+// accumulators in shared memory and taking from Y row k only the entries
+// whose columns fall in its share (with fewer than four rows per SM one CTA a
+// row left most SMs idle: 161 rows of the 80^3 level-2 R (A P) took 5.2 ms).
+// For each X_ik, k ascending, the threads first locate those columns of Y
+// row k in the share, then take its (block, entry) pairs, so every
+// accumulator entry sees the same FMA sequence as in the kernels above (k
+// ascending, then the inner index) and gets the same bits, whatever the
+// split.
 constexpr int SPG_CT = 256;
 template <int XR, int XC, int YC>
 __global__ void __launch_bounds__(SPG_CT) spgemm_cta_kernel(
@@ -831,22 +835,32 @@ __global__ void __launch_bounds__(SPG_CT) spgemm_cta_kernel(
 {
     constexpr int CB = XR * YC, XB = XR * XC, YB = XC * YC;
     extern __shared__ double sm[];
-    double *acc = sm;                                     // [cmax * CB]
+    double *acc = sm;                                     // [cmax * CB] (cmax: a share's bound)
     double *xb = sm + (size_t)cmax * CB;                  // [XB]
     int *cols = reinterpret_cast<int *>(xb + XB);         // [cmax]
     int *ypos = cols + cmax;                              // [ymax]
-    const int i = blockIdx.x, tid = threadIdx.x;
+    const int i = blockIdx.x, tid = threadIdx.x, nsh = gridDim.y, sh = blockIdx.y;
     const int r0 = crp[i], r1 = crp[i + 1];
-    const int c0 = upper ? find_sorted(ccol, r0, r1, i) : r0, len = r1 - c0;
-    for (int t = tid; t < len; t += SPG_CT) cols[t] = ccol[c0 + t];
+    const int c0 = upper ? find_sorted(ccol, r0, r1, i) : r0, full = r1 - c0;
+    if (upper && sh == 0)  // lower blocks: zero here, mirror_lower_kernel fills them
+        for (int t = tid; t < (c0 - r0) * CB; t += SPG_CT) cval[(int64_t)r0 * CB + t] = 0.0;
+    const int q0 = (int)((int64_t)full * sh / nsh), q1 = (int)((int64_t)full * (sh + 1) / nsh);
+    const int len = q1 - q0;  // <= cmax; the same for the whole CTA
+    if (len <= 0) return;
+    const int cfirst = ccol[c0 + q0], clast = ccol[c0 + q1 - 1];
+    for (int t = tid; t < len; t += SPG_CT) cols[t] = ccol[c0 + q0 + t];
     for (int t = tid; t < len * CB; t += SPG_CT) acc[t] = 0.0;
     __syncthreads();
     for (int p = xrp[i]; p < xrp[i + 1]; ++p) {
         const int k = xcol[p];
+        // Y row k's entries in the share's column range (the whole row, or
+        // its tail from column i, when one CTA holds the row)
+        int lo = yrp[k], hi = yrp[k + 1];
+        if (nsh > 1 || upper) lo = find_sorted(ycol, lo, hi, cfirst);
+        if (nsh > 1) hi = find_sorted(ycol, lo, hi, clast + 1);
+        const int ny = hi - lo;  // <= ymax; the same for the whole CTA
+        if (ny == 0) continue;
         if (tid < XB) xb[tid] = xval[(int64_t)p * XB + tid];
-        const int hi = yrp[k + 1];
-        const int lo = upper ? find_sorted(ycol, yrp[k], hi, i) : yrp[k];
-        const int ny = hi - lo;  // <= ymax
         for (int t = tid; t < ny; t += SPG_CT) {
             const int j = ycol[lo + t];
             const int pos = find_sorted(cols, 0, len, j);
@@ -866,26 +880,44 @@ __global__ void __launch_bounds__(SPG_CT) spgemm_cta_kernel(
         }
         __syncthreads();
     }
-    for (int t = tid; t < len * CB; t += SPG_CT) cval[(int64_t)c0 * CB + t] = acc[t];
-    if (upper)  // lower blocks: zero here, mirror_lower_kernel fills them
-        for (int t = tid; t < (c0 - r0) * CB; t += SPG_CT) cval[(int64_t)r0 * CB + t] = 0.0;
+    for (int t = tid; t < len * CB; t += SPG_CT) cval[(int64_t)(c0 + q0) * CB + t] = acc[t];
 }
 
+// shares per row: one CTA a row with four or more rows per SM, else enough
+// shares for about four CTAs per SM (at most 16); more when a share's
+// accumulators would not fit in 200 KB of shared memory (rows longer than
+// that otherwise go to the per-block kernel)
 template <int XR, int XC, int YC>
 static int spgemm_cta(const BsrD &X, const BsrD &Y, BsrD *C, int cmax, int ymax, int upper,
                       cudaStream_t s, bool *done)
 {
     constexpr int CB = XR * YC, XB = XR * XC;
     *done = false;
-    const size_t smem = (size_t)cmax * CB * sizeof(double) + XB * sizeof(double) +
-                        (size_t)(cmax + ymax) * sizeof(int);
-    if (smem > 200 * 1024) return AMG_OK;  // rows too long: the per-block kernel
+    if (X.nbr == 0) {
+        *done = true;
+        return AMG_OK;
+    }
+    Geom g;
+    AMG_TRY(query_geom(&g));
+    int nsh = 1;
+    if (X.nbr < 4 * g.num_sms) nsh = std::min(16, (4 * g.num_sms + X.nbr - 1) / X.nbr);
+    nsh = std::max(1, std::min(nsh, std::max(cmax, 1)));
+    size_t smem = 0;
+    int cm = 0;
+    for (;;) {
+        cm = (cmax + nsh - 1) / nsh;
+        smem = (size_t)cm * CB * sizeof(double) + XB * sizeof(double) +
+               (size_t)(cm + ymax) * sizeof(int);
+        if (smem <= 200 * 1024) break;
+        if (nsh >= 64 || nsh >= cmax) return AMG_OK;  // the per-block kernel
+        nsh *= 2;
+    }
     auto kern = spgemm_cta_kernel<XR, XC, YC>;
     if (smem > 48 * 1024)
         AMG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
-    kern<<<X.nbr, SPG_CT, smem, s>>>(X.row_ptr, X.col, X.val, Y.row_ptr, Y.col, Y.val, C->row_ptr,
-                                     C->col, cmax, ymax, upper, C->val);
+    kern<<<dim3(X.nbr, nsh), SPG_CT, smem, s>>>(X.row_ptr, X.col, X.val, Y.row_ptr, Y.col, Y.val,
+                                                C->row_ptr, C->col, cm, ymax, upper, C->val);
     ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     *done = true;
