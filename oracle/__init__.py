@@ -91,6 +91,9 @@ def _load():
         "orc_level_vectors": ([P, i, P, P, P, P], None),
         "orc_coarse_factor": ([P, P, P], None),
         "orc_set_block_smoother": ([P, i, P], i),
+        "orc_level_blocks": ([P, i, P], i),
+        "orc_block_jacobi": ([P, i, ctypes.c_double, P], i),
+        "orc_block_jacobi_lambda": ([P, i, P, i], ctypes.c_double),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -271,6 +274,25 @@ def spai0(A: CSR) -> np.ndarray:
     return m
 
 
+def block_jacobi(A: CSR, b: int, w: float = 2.0 / 3.0) -> np.ndarray:
+    """Block damped Jacobi blocks M_I = w A_II^{-1} (zero rows and columns of
+    A_II left out), [n / b, b, b]; raises on a non-positive pivot."""
+    o = _Owned(A)
+    Mb = np.empty((A.shape[0] // b, b, b))
+    rc = _load().orc_block_jacobi(o.h, b, w, _p(Mb))
+    if rc != 0:
+        raise ValueError(f"non-positive pivot in node block {-rc - 1}")
+    return Mb
+
+
+def block_jacobi_lambda(A: CSR, b: int, W: np.ndarray, iters: int = 20) -> float:
+    """Rayleigh-quotient estimate of lambda_max(D_b^{-1} A) after `iters`
+    power iterations from the hashed start vector; W = block_jacobi(A, b, 1)."""
+    o = _Owned(A)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    return float(_load().orc_block_jacobi_lambda(o.h, b, _p(W), iters))
+
+
 def cholesky(Adense: np.ndarray):
     """(L, zero_row, status) of the dense Cholesky with the zero-row rule."""
     L = np.ascontiguousarray(Adense, dtype=np.float64).copy()
@@ -335,7 +357,7 @@ class Hierarchy:
         B = np.ascontiguousarray(B, dtype=np.float64)
         self.ns = B.shape[1]
         prm = _Params(eps_strong, coarse_enough, max_levels, npre, npost, relax, smooth_relax,
-                      self.ns, {"spai0": 0, "ilu0": 1}[smoother], ilu_sweeps,
+                      self.ns, {"spai0": 0, "ilu0": 1, "bjacobi": 2}[smoother], ilu_sweeps,
                       {"greedy": 0, "mis2": 1}[aggregation])
         self._A = _Owned(A)
         st = ctypes.c_int(0)
@@ -355,10 +377,11 @@ class Hierarchy:
     def level(self, l: int) -> dict:
         lib = _load()
         info = np.zeros(5, dtype=np.int64)
-        sc = np.zeros(3)
+        sc = np.zeros(4)
         lib.orc_level_info(self.h, l, _p(info), _p(sc))
         n, b, nagg, hasP = (int(x) for x in info[:4])
-        out = {"n": n, "b": b, "nagg": nagg, "eps": sc[0], "omega": sc[1], "rho": sc[2]}
+        out = {"n": n, "b": b, "nagg": nagg, "eps": sc[0], "omega": sc[1], "rho": sc[2],
+               "bj_lambda": sc[3]}
         out["A"] = CSR._from_handle(lib.orc_level_matrix(self.h, l, 0), free=False)
         agg = np.empty(n // b, dtype=np.int32) if hasP else None
         M = np.empty(n) if hasP else None
@@ -366,6 +389,10 @@ class Hierarchy:
         d = np.empty(n) if hasP else None
         lib.orc_level_vectors(self.h, l, _p(agg), _p(M), _p(B), _p(d))
         out.update(agg=agg, M=M, B=B, d=d)
+        Mb = np.empty((n // b, b, b)) if hasP else None
+        if Mb is not None and lib.orc_level_blocks(self.h, l, _p(Mb)) != 0:
+            Mb = None
+        out["Mb"] = Mb
         if hasP:
             out["P"] = CSR._from_handle(lib.orc_level_matrix(self.h, l, 1), free=False)
             out["R"] = CSR._from_handle(lib.orc_level_matrix(self.h, l, 2), free=False)

@@ -56,6 +56,14 @@
  *               makes the symmetric V-cycle indefinite and stalls CG.
  *               V(1,1): pre-smoothing from zero is u = M f, post-smoothing is
  *               u += M (f - A u).
+ *               Block damped Jacobi (option; the paper names damped Jacobi
+ *               among the smoothers of Sec. 2 without a block form or a
+ *               damping): M_I = (2 w_s / lambda) A_II^{-1} per node block,
+ *               lambda the Rayleigh-quotient estimate of lambda_max(D_b^{-1}
+ *               A) after 20 power iterations (orc_block_jacobi_lambda), so the
+ *               damped M A peaks near 2 w_s = 1.6: the undamped block Jacobi
+ *               of Q1 elasticity has lambda_max 2.6-3.9 (nu 0.2-0.45), and a
+ *               fixed damping of 2/3 makes the V-cycle indefinite.
  *   coarsest:   dense Cholesky; a zero row gets a unit pivot and a zero
  *               solution component.
  *   CG:         stop when the recurrence residual ||r||/||f|| <= tol and the
@@ -705,6 +713,111 @@ void orc_spai0(const orc_csr *A, double *m)
     }
 }
 
+/* Block damped Jacobi: M_I = w A_II^{-1} for every node block I (b x b,
+ * row-major in Mb[I * b * b]).  A_II is taken as a dense block (absent
+ * entries zero).  A row of A_II that is entirely zero -- a near-nullspace
+ * column dropped on the level above gives a zero row and column -- is left
+ * out: the inverse is taken of the block on the other rows and columns, and
+ * M_I is zero in that row and column.  The inverse is formed in place by
+ * Gauss-Jordan elimination without pivoting (A_II is SPD on the kept rows):
+ * for each pivot j in turn, row j is multiplied by 1 / a_jj (with a_jj
+ * replaced by 1 first), then every other row i loses a_ij times row j (with
+ * a_ij replaced by 0 first).  The result is symmetrised exactly, M_ab = M_ba =
+ * w (X_ab + X_ba) / 2.  Returns 0, or -(I + 1) for a non-positive pivot in
+ * node block I. */
+int orc_block_jacobi(const orc_csr *A, int b, double w, double *Mb)
+{
+    int64_t nn = A->nrows / b;
+    for (int64_t I = 0; I < nn; ++I) {
+        double blk[6][6] = {{0.0}}, X[6][6] = {{0.0}};
+        int keep[6], k = 0;
+        for (int r = 0; r < b; ++r) {
+            int64_t i = I * b + r;
+            for (int64_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p) {
+                int64_t j = A->col[p];
+                if (j >= I * b && j < I * b + b) blk[r][j - I * b] += A->val[p];
+            }
+        }
+        for (int r = 0; r < b; ++r) {
+            int z = 1;
+            for (int c = 0; c < b; ++c)
+                if (blk[r][c] != 0.0) z = 0;
+            if (!z) keep[k++] = r;
+        }
+        for (int x = 0; x < k; ++x)
+            for (int y = 0; y < k; ++y) X[x][y] = blk[keep[x]][keep[y]];
+        for (int j = 0; j < k; ++j) {
+            double piv = X[j][j];
+            if (!(piv > 0.0)) return (int)-(I + 1);
+            double inv = 1.0 / piv;
+            X[j][j] = 1.0;
+            for (int c = 0; c < k; ++c) X[j][c] = X[j][c] * inv;
+            for (int i = 0; i < k; ++i) {
+                if (i == j) continue;
+                double f = X[i][j];
+                X[i][j] = 0.0;
+                for (int c = 0; c < k; ++c) X[i][c] = X[i][c] - f * X[j][c];
+            }
+        }
+        double *M = Mb + I * b * b;
+        for (int e = 0; e < b * b; ++e) M[e] = 0.0;
+        for (int x = 0; x < k; ++x)
+            for (int y = 0; y < k; ++y)
+                M[keep[x] * b + keep[y]] = w * ((X[x][y] + X[y][x]) * 0.5);
+    }
+    return 0;
+}
+
+/* Power-iteration estimate of lambda_max(D_b^{-1} A) for the block diagonal
+ * D_b of A (b x b node blocks) whose inverse blocks are W (from
+ * orc_block_jacobi with w = 1): x_0 from the integer hash h(i) = (i + 1) *
+ * 2654435761 mod 2^32 as x_0[i] = h(i) / 2^32 - 1/2, then `iters` times x
+ * = D_b^{-1} A x scaled to unit 2-norm, and last the Rayleigh quotient (x, A
+ * x) / (x, D_b x), which never exceeds lambda_max (the generalised
+ * eigenvalues of (A, D_b) are those of D_b^{-1} A).  Returns the estimate (0
+ * for a zero operator). */
+double orc_block_jacobi_lambda(const orc_csr *A, int b, const double *W, int iters)
+{
+    int64_t n = A->nrows, nn = n / b;
+    double *x = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *t = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t h = (uint32_t)((uint64_t)(i + 1) * 2654435761u);
+        x[i] = (double)h / 4294967296.0 - 0.5;
+    }
+    for (int k = 0; k < iters; ++k) {
+        orc_spmv(A, x, t);
+        double nrm = 0.0;
+        for (int64_t I = 0; I < nn; ++I)
+            for (int a = 0; a < b; ++a) {
+                double v = 0.0;
+                for (int c = 0; c < b; ++c) v += W[I * b * b + a * b + c] * t[I * b + c];
+                x[I * b + a] = v;
+                nrm += v * v;
+            }
+        nrm = sqrt(nrm);
+        if (nrm == 0.0) break;
+        for (int64_t i = 0; i < n; ++i) x[i] = x[i] / nrm;
+    }
+    /* Rayleigh quotient: D_b x from A's diagonal blocks */
+    orc_spmv(A, x, t);
+    double xax = 0.0, xdx = 0.0;
+    for (int64_t i = 0; i < n; ++i) xax += x[i] * t[i];
+    for (int64_t I = 0; I < nn; ++I)
+        for (int r = 0; r < b; ++r) {
+            int64_t i = I * b + r;
+            double v = 0.0;
+            for (int64_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p) {
+                int64_t j = A->col[p];
+                if (j >= I * b && j < I * b + b) v += A->val[p] * x[j];
+            }
+            xdx += x[i] * v;
+        }
+    free(x);
+    free(t);
+    return xdx > 0.0 ? xax / xdx : 0.0;
+}
+
 /* Dense Cholesky A = L L^T in place (lower triangle, row-major n x n).  A row
  * of the original matrix that is entirely zero gets a unit pivot and is
  * flagged in zero_row[] (its solution component is set to 0).  Returns 0, or
@@ -762,7 +875,8 @@ typedef struct {
     int b;
     double eps, omega, rho;
     double *M;  /* SPAI0 diagonal */
-    double *Mb; /* optional block smoother (3x3 per node, row-major), replaces M */
+    double *Mb; /* optional block smoother (b x b per node, row-major), replaces M */
+    double bj_lambda; /* block damped Jacobi: the lambda_max(D_b^{-1} A) estimate */
     double *B;  /* near-nullspace of this level, n x ns */
     double *d;  /* filtered diagonal */
     struct orc_ilu *ilu; /* block ILU(0) smoother, when selected */
@@ -792,7 +906,7 @@ typedef struct {
     double relax;        /* omega multiplier, 2.0 */
     double smooth_relax; /* smoother damping w_s, 0.8 */
     int ns;              /* near-nullspace columns of B: 6 (rigid-body modes) or 3 */
-    int smoother;        /* 0: damped SPAI0; 1: block ILU(0) */
+    int smoother;        /* 0: damped SPAI0; 1: block ILU(0); 2: block damped Jacobi */
     int ilu_sweeps;      /* Jacobi sweeps per triangular solve of ILU(0) (2) */
     int aggregation;     /* 0: three greedy passes; 1: MIS-2 (orc_aggregate_mis2) */
 } orc_params;
@@ -1106,6 +1220,18 @@ orc_hier *orc_setup(const orc_csr *A0, int bs, const double *B0, const orc_param
         C->M = (double *)malloc(sizeof(double) * (size_t)n);
         orc_spai0(C->A, C->M);
         for (int64_t i = 0; i < n; ++i) C->M[i] = prm->smooth_relax * C->M[i];
+        if (prm->smoother == 2) {
+            C->Mb = (double *)malloc(sizeof(double) * (size_t)(n * C->b));
+            if (orc_block_jacobi(C->A, C->b, 1.0, C->Mb) != 0) {
+                *status = -4;
+                orc_free(H);
+                return NULL;
+            }
+            double lam = orc_block_jacobi_lambda(C->A, C->b, C->Mb, 20);
+            double w = lam > 0.0 ? 2.0 * prm->smooth_relax / lam : 0.0;
+            for (int64_t e = 0; e < n * C->b; ++e) C->Mb[e] = w * C->Mb[e];
+            C->bj_lambda = lam;
+        }
         if (prm->smoother == 1) {
             C->ilu = orc_ilu0(C->A, C->b);
             if (!C->ilu) {
@@ -1144,8 +1270,9 @@ orc_hier *orc_setup(const orc_csr *A0, int bs, const double *B0, const orc_param
     return H;
 }
 
-/* out = M x (diagonal SPAI0), the 3x3 block smoother when one is set, or the
- * block ILU(0) smoother; with add != 0, out += M x. */
+/* out = M x (diagonal SPAI0), the b x b block smoother when one is set
+ * (block damped Jacobi, or learned 3x3 blocks), or the block ILU(0)
+ * smoother; with add != 0, out += M x. */
 static void apply_smoother(const orc_hier *H, const orc_level *L, int64_t n, const double *x,
                            double *out, int add)
 {
@@ -1154,11 +1281,13 @@ static void apply_smoother(const orc_hier *H, const orc_level *L, int64_t n, con
         orc_ilu_apply(L->ilu, H->ilu_sweeps, x, z, H->iwork);
         for (int64_t i = 0; i < n; ++i) out[i] = add ? out[i] + z[i] : z[i];
     } else if (L->Mb) {
-        for (int64_t I = 0; I < n / 3; ++I)
-            for (int a = 0; a < 3; ++a) {
+        const int bs = L->b;
+        for (int64_t I = 0; I < n / bs; ++I)
+            for (int a = 0; a < bs; ++a) {
                 double v = 0.0;
-                for (int b = 0; b < 3; ++b) v += L->Mb[I * 9 + a * 3 + b] * x[I * 3 + b];
-                out[I * 3 + a] = add ? out[I * 3 + a] + v : v;
+                for (int c = 0; c < bs; ++c)
+                    v += L->Mb[I * bs * bs + a * bs + c] * x[I * bs + c];
+                out[I * bs + a] = add ? out[I * bs + a] + v : v;
             }
     } else {
         for (int64_t i = 0; i < n; ++i) out[i] = add ? out[i] + L->M[i] * x[i] : L->M[i] * x[i];
@@ -1297,6 +1426,7 @@ void orc_level_info(const orc_hier *H, int l, int64_t *info, double *scal)
     scal[0] = L->eps;
     scal[1] = L->omega;
     scal[2] = L->rho;
+    scal[3] = L->bj_lambda;
 }
 
 const orc_csr *orc_level_matrix(const orc_hier *H, int l, int which) /* 0 A, 1 P, 2 R */
@@ -1315,6 +1445,16 @@ void orc_level_vectors(const orc_hier *H, int l, int32_t *agg, double *M, double
     if (M && L->M) memcpy(M, L->M, sizeof(double) * (size_t)n);
     if (B && L->B) memcpy(B, L->B, sizeof(double) * (size_t)(n * H->ns));
     if (d && L->d) memcpy(d, L->d, sizeof(double) * (size_t)n);
+}
+
+/* The block smoother of level l (n / b blocks of b x b, row-major); returns
+ * 0, or -1 when the level has none. */
+int orc_level_blocks(const orc_hier *H, int l, double *Mb)
+{
+    const orc_level *L = &H->lv[l];
+    if (!L->Mb) return -1;
+    memcpy(Mb, L->Mb, sizeof(double) * (size_t)(L->A->nrows * L->b));
+    return 0;
 }
 
 void orc_coarse_factor(const orc_hier *H, double *L, uint8_t *zrow)
