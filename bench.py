@@ -691,6 +691,19 @@ def forms_80(amg, torch, dargs, p, f, tol, solver, stream, steps):
                vcycle="V-cycle in FP64 emulated on FP32 pairs (hi + lo floats, ~2^-45 per "
                       "product), FP64 vectors; CG's A p, dots and true residual in FP64")
     forms["df64"] = rec
+    # block damped Jacobi (the paper's damped Jacobi relaxation over node
+    # blocks) in place of SPAI0, FP64 and FP32 V-cycles
+    for name, prec in (("bjacobi_fp64", amg.PREC_FP64), ("bjacobi_fp32", amg.PREC_FP32)):
+        rec, sol, _ = _solve_form(amg, torch, dargs, f, tol, steps, stream, u_ref,
+                                  precision=prec, smoother=amg.SMOOTH_BJACOBI)
+        rec["lambda_per_level"] = [sol.level_info(l)["smoother_lambda"]
+                                   for l in range(sol.nlevels - 1)]
+        del sol
+        rec["speedup_vs_fp64_spai0"] = forms["fp64"]["value"] / rec["value"]
+        rec["spai0_iterations"] = forms["fp64"]["iterations"]
+        rec["vcycle"] = ("block damped Jacobi M_I = (2 w_s / lambda) A_II^-1 on every level, "
+                         + ("FP64" if name.endswith("64") else "FP32 matrices and vectors"))
+        forms[name] = rec
     forms["ilu0_fp64"] = ilu0_form(amg, torch, dargs, f, tol, u_ref, forms["fp64"], p, stream,
                                    steps)
     for name in ("fp64", "fp32", "bf16"):
@@ -745,6 +758,12 @@ def config_precision_150(amg, torch, dev, stream, steps):
         del sol
         rec["speedup_vs_fp64"] = out["fp64"]["value"] / rec["value"]
         out["mis2_fp64"] = rec
+        for name, prec in (("bjacobi_fp64", amg.PREC_FP64), ("bjacobi_fp32", amg.PREC_FP32)):
+            rec, sol, _ = _solve_form(amg, torch, dargs, f, tol, steps, stream, u_ref,
+                                      precision=prec, smoother=amg.SMOOTH_BJACOBI)
+            del sol
+            rec["speedup_vs_fp64"] = out["fp64"]["value"] / rec["value"]
+            out[name] = rec
     out["clocks"] = clk.summary()
     out["oracle"] = ("not run at this size: the oracle's setup and solve take tens of minutes "
                      "on one host core; errors are against the FP64 GPU solution, whose "

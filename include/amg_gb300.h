@@ -120,9 +120,20 @@ extern "C" {
  * from x = U_D^-1 y), before and after the coarse correction.  FP64 V-cycle
  * and block storage only.  The sweeps make the preconditioner slightly
  * non-symmetric; on matrices where ILU(0) itself is indefinite (stiff
- * inclusions) CG can break down (AMG_ERR_BREAKDOWN). */
+ * inclusions) CG can break down (AMG_ERR_BREAKDOWN).
+ * AMG_SMOOTH_BJACOBI: block damped Jacobi, the damped Jacobi relaxation of
+ * Sec. 2 over the node blocks of every smoothing level: M_I = (2 smooth_relax
+ * / lambda) A_II^-1, lambda the Rayleigh quotient (x, A x) / (x, D_b x) after
+ * 20 power iterations of D_b^-1 A (D_b = the block diagonal of A) from a
+ * fixed hashed start vector, an estimate from below of lambda_max(D_b^-1 A);
+ * with smooth_relax = 0.8 the damped M A peaks near 1.6 on any material
+ * (undamped block Jacobi peaks at 2.6-3.9 on Q1 elasticity, nu 0.2-0.45, and
+ * a damping above 2 / lambda_max makes the V-cycle indefinite).  A zero row
+ * and column of A_II (a near-nullspace column dropped above) stays zero in
+ * M_I.  Block storage only; every V-cycle precision. */
 #define AMG_SMOOTH_SPAI0 0
 #define AMG_SMOOTH_ILU0 1
+#define AMG_SMOOTH_BJACOBI 2
 
 /* Block CSR matrix, borrowed for the duration of a call.
  * row_ptr[nbrows+1] and col[nnzb] are int32 with columns strictly ascending
@@ -178,7 +189,8 @@ typedef struct {
     double relax;          /* multiplier of omega = (4/3)/rho in P smoothing (2.0: the
                               Gershgorin rho over-estimates lambda_max(D^-1 A) by
                               1.4-2.2x on elasticity matrices) */
-    double smooth_relax;   /* damping of the SPAI0 smoother (0.8) */
+    double smooth_relax;   /* damping of the SPAI0 smoother; with AMG_SMOOTH_BJACOBI,
+                              half the target top eigenvalue of M A (0.8) */
     int32_t coarse_enough; /* stop coarsening at <= this many scalar rows (3000); a level
                               below the finest with <= 2 coarse_enough rows also stops
                               when its aggregates would give < coarse_enough / 4 rows */
@@ -210,6 +222,8 @@ typedef struct {
     int32_t nagg;          /* aggregates = block rows of the next level (0 on the coarsest) */
     int32_t is_coarsest;
     double eps, omega, rho;
+    double smoother_lambda; /* AMG_SMOOTH_BJACOBI: the lambda_max(D_b^-1 A) estimate of
+                               this level (0 otherwise) */
 } amg_level_desc;
 
 /* Whole-hierarchy statistics (host struct). */
@@ -283,8 +297,9 @@ int amg_level_info(amg_handle h, int32_t level, amg_level_desc *out);
  * -1 for an isolated node); which = 4: the smoother diagonal (val receives
  * nbrows*bs doubles); which = 5: the near-nullspace of the level (val
  * receives nbrows*bs*nb_ns doubles); which = 6: the strong-connection flags of A
- * (row_ptr receives nnzb_A bytes); which = 7: the learned smoother blocks of
- * level 0 (val receives nbrows*9 doubles); with AMG_SMOOTH_ILU0, which = 8:
+ * (row_ptr receives nnzb_A bytes); which = 7: the smoother blocks of the
+ * level -- block damped Jacobi, or the learned blocks of level 0 -- (val
+ * receives nbrows*bs*bs doubles); with AMG_SMOOTH_ILU0, which = 8:
  * the block ILU(0) factor on A's block pattern (val receives nnzb_A*bs*bs
  * doubles: L below the diagonal, U on and above it) and which = 9: the
  * inverses of U's diagonal blocks (val receives nbrows*bs*bs doubles).

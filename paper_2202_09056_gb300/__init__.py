@@ -31,7 +31,7 @@ _ERRORS = {-1: "bad argument", -2: "CUDA error", -3: "CG breakdown",
 PREC_FP64, PREC_FP32, PREC_BF16, PREC_DF64 = 0, 1, 2, 3
 STORAGE_BLOCK, STORAGE_SCALAR = 0, 1
 AGG_GREEDY, AGG_MIS2 = 0, 1
-SMOOTH_SPAI0, SMOOTH_ILU0 = 0, 1
+SMOOTH_SPAI0, SMOOTH_ILU0, SMOOTH_BJACOBI = 0, 1, 2
 SETUP_BLOCK, SETUP_SCALAR = 0, 1
 
 
@@ -116,7 +116,8 @@ class LevelDesc(ctypes.Structure):
     _fields_ = [("nbrows", ctypes.c_int32), ("bs", ctypes.c_int32), ("nnzb_A", ctypes.c_int64),
                 ("nnzb_P", ctypes.c_int64), ("nagg", ctypes.c_int32),
                 ("is_coarsest", ctypes.c_int32), ("eps", ctypes.c_double),
-                ("omega", ctypes.c_double), ("rho", ctypes.c_double)]
+                ("omega", ctypes.c_double), ("rho", ctypes.c_double),
+                ("smoother_lambda", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -437,6 +438,10 @@ class AMG:
             M = np.empty(nbr * bs)
             _check(self._lib.amg_level_export(self._h, l, 4, None, None, M.ctypes.data))
             out["M"] = M
+            if self.params.smoother == SMOOTH_BJACOBI:
+                Mb = np.empty((nbr, bs, bs))
+                _check(self._lib.amg_level_export(self._h, l, 7, None, None, Mb.ctypes.data))
+                out["Mb"] = Mb
             strong = np.empty(max(info["nnzb_A"], 1), np.uint8)
             _check(self._lib.amg_level_export(self._h, l, 6, strong.ctypes.data, None, None))
             out["strong"] = strong[:info["nnzb_A"]]

@@ -112,7 +112,7 @@ enum SpmvMode {
     SPMV_SMOOTH = 2,  // y = x + M (f - A x)           (x = u, square A)
     SPMV_AXPY = 3,    // y = u + A x                  (prolongation, y may alias u)
     SPMV_RESTRICT = 4,// y = A x ; y2 = M y           (restriction + next pre-smoothing)
-    SPMV_SMOOTHB = 5, // y = x + Mb (f - A x)          (3x3 block smoother, Mb 9 per row)
+    SPMV_SMOOTHB = 5, // y = x + Mb (f - A x)          (block smoother, b x b per block row)
 };
 
 enum DotMode {
@@ -246,7 +246,8 @@ template <class T> struct Sell {
 };
 
 template <class TV> struct SellArgs {
-    const TV *Mb;        // 3x3 smoother blocks (SPMV_SMOOTHB), in the vectors' precision
+    const TV *Mb;        // b x b smoother blocks (SPMV_SMOOTHB), in the vectors' precision
+    const TV *Mbn;       // SPMV_RESTRICT: the next level's blocks, y2 = Mbn y per block row
     int nrows, nslices, G;
     const int64_t *slice_ptr;
     const int *col;
@@ -314,6 +315,9 @@ int scalar_transfer(const BsrD &S, int b, const double *B, int ns, const int *ag
                     double relax, DevArena &keep, DevArena &tmp, cudaStream_t s, LevelBuild *out);
 int scalar_to_block(const BsrD &S, int br, int bc, DevArena &keep, DevArena &tmp, cudaStream_t s,
                     BsrD *out);
+// Block damped Jacobi blocks of every smoothing level (bjacobi.cu).
+int bjacobi_setup(amg_handle h, DevArena &tmp, cudaStream_t s);
+
 int coarse_inverse(const BsrD &A, DevArena &keep, DevArena &tmp, cudaStream_t s,
                    double **Ainv_out);
 
@@ -350,8 +354,10 @@ struct Level {
     bool coarsest = false;
     double eps = 0, omega = 0, rho = 0;
     double *f = nullptr, *u = nullptr, *e = nullptr, *z = nullptr, *t = nullptr;
-    double *Mb = nullptr;     // learned 3x3 smoother blocks (level 0), replaces M when set
+    double *Mb = nullptr;     // smoother blocks, replacing M when set: learned 3x3 (level
+                              // 0) or block damped Jacobi (b x b, every smoothing level)
     float *Mbf = nullptr;     // FP32 copy of Mb for the FP32 / BF16 V-cycles
+    double bj_lambda = 0;     // block Jacobi: the lambda_max(D_b^-1 A) estimate
     Ilu ilu;                  // block ILU(0) smoother (when selected), replaces M
     BsrD xA, xP, xR;          // scalar CSR of A, P, R built by the scalar setup (kept until
                               // the solve's copies are made)

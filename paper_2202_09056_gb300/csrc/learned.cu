@@ -791,8 +791,9 @@ int amg_set_learned_smoother(amg_handle h, const float *params, int32_t *fell_ba
         set_error("the learned smoother needs a multi-level hierarchy in block storage");
         return AMG_ERR_ARG;
     }
-    if (h->ilu) {
-        set_error("the hierarchy smooths with ILU(0); the learned smoother replaces SPAI0 only");
+    if (h->ilu || h->prm.smoother != AMG_SMOOTH_SPAI0) {
+        set_error("the hierarchy smooths with ILU(0) or block Jacobi; the learned smoother "
+                  "replaces SPAI0 only");
         return AMG_ERR_STATE;
     }
     DevArena tmp;

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(SELL_THREADS, sell_minb_dot<VT>(BR, BC, DOT)) 
             __syncthreads();
         }
         if (MODE == SPMV_SMOOTHB && owner && row >= 0 && row < a.nrows) {
-            // u + Mb (f - A u) with the row's 3x3 block (BR == 3)
+            // u + Mb (f - A u) with the row's BR x BR block
             Acc res[BR];
 #pragma unroll
             for (int r = 0; r < BR; ++r) res[r] = a.f[(int64_t)row * BR + r] - acc[r];
@@ -260,10 +260,22 @@ __global__ void __launch_bounds__(SELL_THREADS, sell_minb_dot<VT>(BR, BC, DOT)) 
                 else if (MODE == SPMV_AXPY) out = a.u[i] + acc[r];
                 else out = acc[r];
                 a.y[i] = out;
-                if (MODE == SPMV_RESTRICT && a.y2) a.y2[i] = a.M ? a.M[i] * out : Acc(0);
+                if (MODE == SPMV_RESTRICT && a.y2 && !a.Mbn) a.y2[i] = a.M ? a.M[i] * out : Acc(0);
                 if (DOT == DOT_XY) dot += (double)x[i] * (double)out;
                 if (DOT == DOT_FY) dot += (double)a.f[i] * (double)out;
                 if (DOT == DOT_YY) dot += (double)out * (double)out;
+            }
+            if (MODE == SPMV_RESTRICT && a.y2 && a.Mbn) {
+                // the next level's pre-smoothing from zero with its blocks:
+                // y2 = Mbn y on this block row (the BR outputs are acc[])
+                const TV *mb = a.Mbn + (int64_t)row * BR * BR;
+#pragma unroll
+                for (int r = 0; r < BR; ++r) {
+                    Acc v = Acc(0);
+#pragma unroll
+                    for (int c = 0; c < BR; ++c) v = fma((Acc)mb[r * BR + c], acc[c], v);
+                    a.y2[(int64_t)row * BR + r] = v;
+                }
             }
         }
     }
@@ -334,9 +346,9 @@ static int sell_mode(int mode, int dot, const SellArgs<TV> &a, int grid, cudaStr
     case SPMV_AXPY: return sell_dot<BR, BC, VT, TV, SPMV_AXPY>(dot, a, grid, s);
     case SPMV_RESTRICT: return sell_dot<BR, BC, VT, TV, SPMV_RESTRICT>(dot, a, grid, s);
     case SPMV_SMOOTHB:
-        if constexpr (BR == 3 && BC == 3)
+        if constexpr (BR == BC && BR > 1)
             return sell_dot<BR, BC, VT, TV, SPMV_SMOOTHB>(dot, a, grid, s);
-        set_error("block smoothing needs 3x3 blocks");
+        set_error("block smoothing needs square node blocks");
         return AMG_ERR_ARG;
     default: set_error("bad spmv mode %d", mode); return AMG_ERR_ARG;
     }

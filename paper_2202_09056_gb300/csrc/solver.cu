@@ -330,9 +330,22 @@ template <> int vec_add<float>(const float *, const float *, float *, int64_t, c
 // rz_partials, the last level-0 kernel also leaves the per-CTA partial sums
 // of f0 . z0 (accumulated in FP64).
 // The learned blocks in the V-cycle's vector precision.
-template <class TV> static const TV *learned_blocks_ptr(const amg_handle h);
-template <> const double *learned_blocks_ptr<double>(const amg_handle h) { return h->lv[0].Mb; }
-template <> const float *learned_blocks_ptr<float>(const amg_handle h) { return h->lv[0].Mbf; }
+// The smoother blocks of level l, in the V-cycle vectors' precision, or null
+// when the level smooths with the SPAI0 diagonal: block damped Jacobi blocks
+// on every smoothing level, or the learned 3x3 blocks on level 0.
+template <class TV> static const TV *blocks_ptr(const amg_handle h, size_t l);
+template <> const double *blocks_ptr<double>(const amg_handle h, size_t l)
+{
+    if (l + 1 >= h->lv.size()) return nullptr;
+    const bool on = h->prm.smoother == AMG_SMOOTH_BJACOBI || (l == 0 && h->learned);
+    return on ? h->lv[l].Mb : nullptr;
+}
+template <> const float *blocks_ptr<float>(const amg_handle h, size_t l)
+{
+    if (l + 1 >= h->lv.size()) return nullptr;
+    const bool on = h->prm.smoother == AMG_SMOOTH_BJACOBI || (l == 0 && h->learned);
+    return on ? h->lv[l].Mbf : nullptr;
+}
 
 template <class VT, class TV>
 static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials, cudaStream_t s)
@@ -363,12 +376,13 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
             }
         }
         for (int sweep = 1; sweep < npre && !ilu; ++sweep) {  // further pre-smoothing sweeps
-            const bool blocks = l == 0 && h->learned;
+            const TV *mb = blocks_ptr<TV>(h, l);
+            const bool blocks = mb != nullptr;
             SellArgs<TV> a{};
             a.x = u;
             a.f = f;
             a.M = C.M;
-            a.Mb = learned_blocks_ptr<TV>(h);
+            a.Mb = mb;
             a.y = t;
             AMG_TRY((launch_sell<VT, TV>(*C.A, blocks ? SPMV_SMOOTHB : SPMV_SMOOTH, DOT_NONE, a, g,
                                          s)));
@@ -391,6 +405,9 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
             // with ILU(0) the next level pre-smooths itself (npre = 0: zero u)
             a.y2 = (next_smooths && !ilu_pre) ? N.u : nullptr;
             a.M = (next_smooths && npre > 0) ? N.M : nullptr;
+            // with smoother blocks on the next level, its pre-smoothing is
+            // the block product (npre = 0: zero u, written by a null M)
+            if (next_smooths && npre > 0) a.Mbn = blocks_ptr<TV>(h, l + 1);
             AMG_TRY((launch_sell<VT, TV>(*C.R, SPMV_RESTRICT, DOT_NONE, a, g, s)));
         }
     }
@@ -428,7 +445,8 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
                 AMG_TRY(launch_vec_dot<TV>(h, f0, z0, C.n, rz_partials, s));
         }
         const TV *w = u;
-        const bool blocks = l == 0 && h->learned;
+        const TV *mb = blocks_ptr<TV>(h, l);
+        const bool blocks = mb != nullptr;
         for (int sweep = 0; sweep < npost && !ilu; ++sweep) {  // u += M (f - A u)
             const bool last = (sweep == npost - 1);
             TV *out = last ? zl : t;
@@ -436,7 +454,7 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
             a.x = w;
             a.f = f;
             a.M = C.M;
-            a.Mb = learned_blocks_ptr<TV>(h);
+            a.Mb = mb;
             a.y = out;
             a.partials = rz_partials;
             const int dot = (l == 0 && last && rz_partials) ? DOT_FY : DOT_NONE;
@@ -496,7 +514,7 @@ static int record_cg_iteration_t(amg_handle h, cudaStream_t s, cudaGraphConditio
         AMG_TRY((launch_sell<double, double>(L0.sA, SPMV_PLAIN, DOT_XY, a, g, s, &grid)));
     }
     cg_alpha_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, grid); ::amg::count_launch(1);
-    const bool blocks = h->learned && multi && npre > 0;
+    const bool blocks = blocks_ptr<TV>(h, 0) != nullptr && multi && npre > 0;
     // the next pre-smoothing M r fused into the update (ILU(0) smooths inside the V-cycle)
     const bool fuse_pre = multi && !blocks && !(h->ilu && npre > 0);
     cg_update_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(h->uu, h->r, h->p, h->q, V0.M,
@@ -521,8 +539,8 @@ static int record_cg_iteration_t(amg_handle h, cudaStream_t s, cudaGraphConditio
                                                       fuse_pre ? V0.u : nullptr, rv, h->st,
                                                       n, npre > 0); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
-    if (blocks)  // next pre-smoothing with the learned blocks: u0 = Mb r
-        AMG_TRY(launch_block_apply<TV>(learned_blocks_ptr<TV>(h), f0, V0.u, L0.A.nbr, g, s));
+    if (blocks)  // next pre-smoothing with the level-0 blocks: u0 = Mb r
+        AMG_TRY(launch_block_apply<TV>(blocks_ptr<TV>(h, 0), f0, V0.u, L0.A.nbr, g, s));
     return AMG_OK;
 }
 
@@ -1049,6 +1067,11 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
             }
         }
     }
+    if (prm.smoother == AMG_SMOOTH_BJACOBI) {  // block damped Jacobi of every smoothing level
+        lap(6);                                // (its power iteration uses the sliced copies)
+        AMG_TRY(bjacobi_setup(h, tmp, s));
+        lap(4);
+    }
     // the scalar setup's matrices are not kept past the solve copies
     AMG_TRY_CUDA(cudaStreamSynchronize(s));
     for (Level &L : h->lv)
@@ -1132,7 +1155,7 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
         p.loop_mode < 0 || p.loop_mode > 1 || p.storage < AMG_STORAGE_BLOCK ||
         p.storage > AMG_STORAGE_SCALAR || p.aggregation < AMG_AGG_GREEDY ||
         p.aggregation > AMG_AGG_MIS2 || p.smoother < AMG_SMOOTH_SPAI0 ||
-        p.smoother > AMG_SMOOTH_ILU0 || p.ilu_sweeps < 0 || p.ilu_sweeps > 64 ||
+        p.smoother > AMG_SMOOTH_BJACOBI || p.ilu_sweeps < 0 || p.ilu_sweeps > 64 ||
         p.setup < AMG_SETUP_BLOCK || p.setup > AMG_SETUP_SCALAR || p.reserved != 0) {
         set_error("bad parameters");
         return AMG_ERR_ARG;
@@ -1144,6 +1167,11 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
     if (p.smoother == AMG_SMOOTH_ILU0 &&
         (p.precision != AMG_PREC_FP64 || p.storage != AMG_STORAGE_BLOCK)) {
         set_error("the ILU(0) smoother runs in the FP64 V-cycle with block storage");
+        return AMG_ERR_ARG;
+    }
+    if (p.smoother == AMG_SMOOTH_BJACOBI &&
+        (p.storage != AMG_STORAGE_BLOCK || !(p.smooth_relax > 0.0))) {
+        set_error("the block Jacobi smoother needs block storage and smooth_relax > 0");
         return AMG_ERR_ARG;
     }
     auto t0 = std::chrono::steady_clock::now();
@@ -1191,7 +1219,7 @@ int amg_apply_vcycle(amg_handle h, const double *r, double *z, void *stream)
     const bool multi = h->lv.size() > 1;
     const int zero = h->prm.npre == 0;
     if (h->prm.precision == AMG_PREC_FP64 || h->prm.precision == AMG_PREC_DF64) {
-        if (multi && h->learned && !zero) {
+        if (multi && blocks_ptr<double>(h, 0) && !zero) {
             AMG_TRY(launch_block_apply(L0.Mb, r, L0.u, L0.A.nbr, h->geom, s));
         } else if (multi && !(h->ilu && !zero)) {  // ILU(0) pre-smooths inside the V-cycle
             scale_kernel<double><<<vgrid(h, n), 256, 0, s>>>(L0.M, r, L0.u, nullptr, n, zero);
@@ -1201,7 +1229,7 @@ int amg_apply_vcycle(amg_handle h, const double *r, double *z, void *stream)
         if (h->prm.precision == AMG_PREC_DF64) return record_vcycle<df32, double>(h, r, z, nullptr, s);
         return record_vcycle<double, double>(h, r, z, nullptr, s);
     }
-    const bool lb = multi && h->learned && !zero;
+    const bool lb = multi && blocks_ptr<float>(h, 0) && !zero;
     scale_kernel<float><<<vgrid(h, n), 256, 0, s>>>(L0.Mf, r, (multi && !lb) ? L0.vu : nullptr,
                                                     h->rv, n, zero);
     count_launch(1);
@@ -1250,7 +1278,7 @@ int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxi
     AMG_TRY(launch_reduce_sum(h->partials, grid, h->scal + 1, s));
     cg_start_kernel<<<1, 1, 0, s>>>(h->st, h->scal, tol, maxiter); ::amg::count_launch(1);
     if (h->prm.precision == AMG_PREC_FP64 || h->prm.precision == AMG_PREC_DF64) {
-        if (multi && h->learned && h->prm.npre > 0) {
+        if (multi && blocks_ptr<double>(h, 0) && h->prm.npre > 0) {
             AMG_TRY(launch_block_apply(L0.Mb, h->r, L0.u, L0.A.nbr, h->geom, s));
         } else if (multi && !(h->ilu && h->prm.npre > 0)) {  // ILU(0) pre-smooths in the V-cycle
             scale_kernel<double><<<vgrid(h, n), 256, 0, s>>>(L0.M, h->r, L0.u, nullptr, n,
@@ -1258,7 +1286,7 @@ int amg_solve(amg_handle h, const double *f, double *u, double tol, int32_t maxi
             count_launch(1);
         }
     } else {
-        const bool lb = multi && h->learned && h->prm.npre > 0;
+        const bool lb = multi && blocks_ptr<float>(h, 0) && h->prm.npre > 0;
         scale_kernel<float><<<vgrid(h, n), 256, 0, s>>>(L0.Mf, h->r,
                                                         (multi && !lb) ? L0.vu : nullptr, h->rv,
                                                         n, h->prm.npre == 0);
@@ -1380,6 +1408,7 @@ int amg_level_info(amg_handle h, int32_t level, amg_level_desc *out)
     out->eps = L.eps;
     out->omega = L.omega;
     out->rho = L.rho;
+    out->smoother_lambda = L.bj_lambda;
     return AMG_OK;
 }
 
@@ -1423,10 +1452,14 @@ int amg_level_export(amg_handle h, int32_t level, int32_t which, int32_t *row_pt
     case 5:
         if (val) AMG_TRY_CUDA(cudaMemcpyAsync(val, L.B, sizeof(double) * L.n() * h->ns, cudaMemcpyDeviceToHost, s));
         break;
-    case 7:
-        if (!L.Mb || !h->learned) { set_error("no learned smoother blocks on this level"); return AMG_ERR_STATE; }
-        if (val) AMG_TRY_CUDA(cudaMemcpyAsync(val, L.Mb, sizeof(double) * L.A.nbr * 9, cudaMemcpyDeviceToHost, s));
+    case 7: {
+        const double *mb = blocks_ptr<double>(h, (size_t)level);
+        if (!mb) { set_error("no smoother blocks on this level"); return AMG_ERR_STATE; }
+        if (val)
+            AMG_TRY_CUDA(cudaMemcpyAsync(val, mb, sizeof(double) * L.A.nbr * L.A.br * L.A.br,
+                                         cudaMemcpyDeviceToHost, s));
         break;
+    }
     case 8:
     case 9:
         if (!L.ilu.F) { set_error("no ILU(0) factor on this level"); return AMG_ERR_STATE; }
