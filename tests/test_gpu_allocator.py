@@ -5,6 +5,7 @@ back to torch when the handle is freed; results do not depend on where the
 memory came from; an allocator that fails makes setup return an error with
 every buffer it had handed out given back."""
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -20,6 +21,11 @@ from parity_util import dev_args  # noqa: E402
 
 
 def _allocated():
+    """Bytes allocated through torch's caching allocator, after collecting
+    garbage: tensors of an earlier test that a reference cycle (a caught
+    exception's traceback) keeps alive would otherwise be freed in the middle
+    of a measurement."""
+    gc.collect()
     torch.cuda.synchronize()
     return torch.cuda.memory_allocated()
 
