@@ -15,6 +15,7 @@ The file sorts last so that a run stopping at the first failure has run
 every other test before it.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -68,23 +69,31 @@ def test_noalloc_spmv_dot_matches_allocating_entry_point():
         refs = [amg.bsr_spmv_dot(rp, cl, val, x) for x in xs]
         ys = [torch.full_like(x, np.nan) for x in xs]
         ds = [ctypes.c_double(np.nan) for _ in xs]
-        torch.cuda.synchronize()
-        torch_before = torch.cuda.memory_allocated()
-        torch.cuda.reset_peak_memory_stats()
-        reset()
-        pool_before, _ = used()
-        for call in range(2):
-            st = fn(ctypes.byref(A), ctypes.c_void_p(xs[call].data_ptr()),
-                    ctypes.c_void_p(ys[call].data_ptr()), ctypes.byref(ds[call]),
-                    ctypes.c_void_p(stream))
-            assert st == 0, lib.amg_last_error()
-        torch.cuda.synchronize()
-        pool_now, pool_high = used()
+        # no garbage collection inside the measured window: an earlier
+        # tensor freed there would lower torch's count for reasons of its own
+        gc.collect()
+        gc.disable()
+        try:
+            torch.cuda.synchronize()
+            torch_before = torch.cuda.memory_allocated()
+            torch.cuda.reset_peak_memory_stats()
+            reset()
+            pool_before, _ = used()
+            for call in range(2):
+                st = fn(ctypes.byref(A), ctypes.c_void_p(xs[call].data_ptr()),
+                        ctypes.c_void_p(ys[call].data_ptr()), ctypes.byref(ds[call]),
+                        ctypes.c_void_p(stream))
+                assert st == 0, lib.amg_last_error()
+            torch.cuda.synchronize()
+            pool_now, pool_high = used()
+            torch_now, torch_high = torch.cuda.memory_allocated(), torch.cuda.max_memory_allocated()
+        finally:
+            gc.enable()
         # an allocation during the calls would lift the watermark above the
         # memory in use before them
         assert pool_now == pool_before and pool_high <= pool_before, (pool_before, pool_high)
-        assert torch.cuda.memory_allocated() == torch_before
-        assert torch.cuda.max_memory_allocated() == torch_before
+        assert torch_now == torch_before
+        assert torch_high == torch_before
         for call in range(2):
             y_ref, d_ref = refs[call]
             assert torch.equal(ys[call], y_ref), call
