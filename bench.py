@@ -482,9 +482,13 @@ def run_batch(args, amg, torch, rank=0, world=1, dist=None, local=0):
     # the same batch with the V-cycle's SpMMs on FP32-pair values (emulated
     # FP64) and on FP32 values; the CG's A p and true residual stay FP64
     variants = {}
-    for vname, vprec in (("df64", amg.PREC_DF64), ("fp32", amg.PREC_FP32)):
+    for vname, vprec, vsm in (("df64", amg.PREC_DF64, amg.SMOOTH_SPAI0),
+                              ("fp32", amg.PREC_FP32, amg.SMOOTH_SPAI0),
+                              ("bjacobi", amg.PREC_FP64, amg.SMOOTH_BJACOBI),
+                              ("bjacobi_fp32", amg.PREC_FP32, amg.SMOOTH_BJACOBI)):
         t0 = time.perf_counter()
-        bv = amg.AMGBatch(mats, Bs, nrhs, loop_mode=args.loop_mode, precision=vprec)
+        bv = amg.AMGBatch(mats, Bs, nrhs, loop_mode=args.loop_mode, precision=vprec,
+                          smoother=vsm)
         torch.cuda.synchronize()
         v_setup = time.perf_counter() - t0
         bv.solve(F)
@@ -551,7 +555,10 @@ def run_batch(args, amg, torch, rank=0, world=1, dist=None, local=0):
                           "rel_resid_max": float(max(max(x) for x in resv)),
                           "max_rel_diff_vs_fp64_batch": vd, "rhs_tile_per_level_A_P_R": tiles,
                           "vcycle": {"df64": "SpMMs on FP32-pair values (emulated FP64)",
-                                     "fp32": "SpMMs on FP32 values, FP32 FMAs, FP64 vectors"}[k]
+                                     "fp32": "SpMMs on FP32 values, FP32 FMAs, FP64 vectors",
+                                     "bjacobi": "FP64 SpMMs, block damped Jacobi smoother",
+                                     "bjacobi_fp32": "SpMMs on FP32 values, FP32 FMAs, FP64 "
+                                                     "vectors, block damped Jacobi smoother"}[k]
                                     + "; CG A p, dots and true residual in FP64"}
            for k, (t, stv, vs, itsv, resv, vd, tiles) in variants.items()},
         "clocks": clk.summary(), "gpu_launches": int(launches),
@@ -811,8 +818,8 @@ def config_batch64(args, amg, torch, steps):
     import types
     sub = types.SimpleNamespace(steps=steps, warmup=1, loop_mode=args.loop_mode)
     line = run_batch(sub, amg, torch)
-    keep = ("value", "unit", "config", "batch", "batch_df64", "batch_fp32", "clocks",
-            "gpu_launches", "steps")
+    keep = ("value", "unit", "config", "batch", "batch_df64", "batch_fp32", "batch_bjacobi",
+            "batch_bjacobi_fp32", "clocks", "gpu_launches", "steps")
     out = {k: line[k] for k in keep if k in line}
     torch.cuda.empty_cache()
     return out

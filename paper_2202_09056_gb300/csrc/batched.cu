@@ -35,6 +35,10 @@ constexpr int BCHUNK = 2048;    // dofs per dot-product chunk
 constexpr int BT = 128;         // default threads of the SpMM CTAs (autotuned: 64, 128, 256)
 constexpr int BT_MAX = 256;
 constexpr int BSETUP_THREADS = 8;  // host threads setting up instances at once
+// the block smoother's two epilogues (block damped Jacobi): SPMV_SMOOTHB for
+// u + M_I (f - A u) and this one for the restriction whose next-level
+// pre-smoothing is a block product (y2 = M_I y)
+constexpr int BMODE_RESTRICTB = 6;
 
 // Concatenated sliced operator of one level.
 struct BSell {
@@ -70,6 +74,8 @@ struct BArgs {
     const int64_t *moff;    // instance offsets of the smoother diagonal (-1: none)
     const int *enable;      // per instance: run this instance
     const double *x, *f, *u, *M;
+    const double *Mb;       // smoother blocks (SPMV_SMOOTHB: this level's; BMODE_RESTRICTB:
+                            // the next level's), instance i's from moff[i] * BR
     double *y, *y2;
 };
 
@@ -225,6 +231,35 @@ __global__ void __launch_bounds__(BT_MAX) bspmm_kernel(BArgs a)
                     for (int t = 0; t < KT; ++t)
                         acc[r][t] += __shfl_xor_sync(0xffffffffu, acc[r][t], m);
             if (sub != 0 || !live) continue;
+            if constexpr (MODE == SPMV_SMOOTHB || MODE == BMODE_RESTRICTB) {
+                // block epilogues: the row's BR x BR block times its BR residuals
+                // (smoothing) or its BR outputs (the next level's pre-smoothing)
+                const int64_t mo = a.moff[inst];
+                const double *mb = mo >= 0 ? a.Mb + (mo + (int64_t)row * BR) * BR : nullptr;
+#pragma unroll
+                for (int t = 0; t < KT; ++t) {
+                    const int k = k0 + t;
+                    if (k >= K) continue;
+                    double v[BR];
+#pragma unroll
+                    for (int c = 0; c < BR; ++c) {
+                        const int64_t i = yo + ((int64_t)row * BR + c) * K + k;
+                        v[c] = MODE == SPMV_SMOOTHB ? a.f[i] - acc[c][t] : acc[c][t];
+                        if (MODE == BMODE_RESTRICTB) a.y[i] = acc[c][t];
+                    }
+#pragma unroll
+                    for (int r = 0; r < BR; ++r) {
+                        const int64_t i = yo + ((int64_t)row * BR + r) * K + k;
+                        double corr = 0.0;
+                        if (mb)
+#pragma unroll
+                            for (int c = 0; c < BR; ++c) corr = fma(mb[r * BR + c], v[c], corr);
+                        if (MODE == SPMV_SMOOTHB) a.y[i] = a.x[i] + corr;
+                        else if (a.y2) a.y2[i] = corr;
+                    }
+                }
+                continue;
+            }
 #pragma unroll
             for (int r = 0; r < BR; ++r)
 #pragma unroll
@@ -281,6 +316,12 @@ static int bspmm_mode(const BSell &S, int kt, int mode, const BArgs &a, int grid
         break;
     case SPMV_AXPY: return bspmm_kt<BR, BC, SPMV_AXPY>(S, kt, a, grid, s);
     case SPMV_RESTRICT: return bspmm_kt<BR, BC, SPMV_RESTRICT>(S, kt, a, grid, s);
+    case SPMV_SMOOTHB:
+        if constexpr (BR == BC) return bspmm_kt<BR, BC, SPMV_SMOOTHB>(S, kt, a, grid, s);
+        break;
+    case BMODE_RESTRICTB:
+        if constexpr (BR == 6) return bspmm_kt<BR, BC, BMODE_RESTRICTB>(S, kt, a, grid, s);
+        break;
     default: break;
     }
     set_error("unsupported batched spmm mode %d", mode);
@@ -456,6 +497,39 @@ __global__ void breplace_kernel(BVec v, const int *__restrict__ replace,
         const double ri = rt[e];
         r[e] = ri;
         if (t0) t0[e] = (moff[inst] >= 0) ? M[moff[inst] + le / K] * ri : 0.0;
+    }
+}
+
+// t0 = M_I r on level 0 with the block smoother (3 x 3 blocks per node), for
+// every entry of the enabled instances: the next V-cycle's pre-smoothing from
+// zero.  Vectors interleave an instance's K right-hand sides ([dof][K]);
+// instance i's blocks start at moff[i] * 3.
+__global__ void bblock_apply_kernel(BVec v, const int *__restrict__ enable,
+                                    const double *__restrict__ Mb,
+                                    const int64_t *__restrict__ moff,
+                                    const double *__restrict__ r, double *__restrict__ t0)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < v.n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int inst = inst_of(v.off, v.ninst, e);
+        if (!enable[inst]) continue;
+        const int K = v.K[inst];
+        const int64_t le = e - v.off[inst];
+        const int64_t dof = le / K;
+        const int k = (int)(le % K);
+        const int64_t node = dof / 3;
+        const int rr = (int)(dof % 3);
+        const int64_t mo = moff[inst];
+        if (mo < 0) {
+            t0[e] = 0.0;
+            continue;
+        }
+        const double *m = Mb + (mo + node * 3) * 3 + rr * 3;
+        const double *rb = r + v.off[inst] + node * 3 * K + k;
+        double val = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) val = fma(m[c], rb[(int64_t)c * K], val);
+        t0[e] = val;
     }
 }
 
@@ -749,6 +823,7 @@ using namespace amg;
 struct BLevelData {
     BSell A, P, R;
     double *M = nullptr;                 // concatenated smoother diagonals
+    double *Mb = nullptr;                // ... and blocks (block damped Jacobi; from moff * br)
     int64_t *moff = nullptr;             // instance offsets into M (-1: none)
     int64_t *voff = nullptr;             // instance offsets of this level's vectors (-1: absent)
     int64_t *moff_next = nullptr;        // offsets of the next level's M (restriction epilogue)
@@ -875,8 +950,10 @@ static int record_bvcycle(amg_batch h, const double *f0, double *z0, const int *
             a.y = N.f;
             a.y2 = N.u;
             a.M = N.M;
+            a.Mb = N.Mb;
             a.moff = C.moff_next;
-            AMG_TRY(launch_bspmm(C.R, C.R.kt, SPMV_RESTRICT, a, g, s, h->vk));
+            AMG_TRY(launch_bspmm(C.R, C.R.kt, N.Mb ? BMODE_RESTRICTB : SPMV_RESTRICT, a, g, s,
+                                 h->vk));
         }
         kti += 3;
     }
@@ -917,9 +994,10 @@ static int record_bvcycle(amg_batch h, const double *f0, double *z0, const int *
             a.x = C.u;
             a.f = f;
             a.M = C.M;
+            a.Mb = C.Mb;
             a.moff = C.moff;
             a.y = zl;
-            AMG_TRY(launch_bspmm(C.A, C.A.kt, SPMV_SMOOTH, a, g, s, h->vk));
+            AMG_TRY(launch_bspmm(C.A, C.A.kt, C.Mb ? SPMV_SMOOTHB : SPMV_SMOOTH, a, g, s, h->vk));
         }
     }
     return AMG_OK;
@@ -949,8 +1027,12 @@ static int record_biteration(amg_batch h, cudaStream_t s, cudaGraphConditionalHa
     AMG_TRY(record_bdot(h, h->p, h->q, st.inst_active, st.dot, s));
     balpha_kernel<<<1, BS_T, 0, s>>>(ngl, st, st.dot);
     count_launch(1);
+    // the next pre-smoothing M r fused into the update (diagonal smoother) or,
+    // with smoother blocks, one block product after the residual replacement
+    const bool blocks = L0.Mb != nullptr;
     bupdate_kernel<<<bgrid(h, n), 256, 0, s>>>(bvec(h), st.active, st.alpha, h->uu, h->r, h->p,
-                                               h->q, L0.M, L0.moff, h->nlev > 1 ? L0.u : nullptr);
+                                               h->q, L0.M, L0.moff,
+                                               (h->nlev > 1 && !blocks) ? L0.u : nullptr);
     count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     AMG_TRY(record_bdot(h, h->r, h->r, st.inst_active, st.dot, s));
@@ -968,8 +1050,13 @@ static int record_biteration(amg_batch h, cudaStream_t s, cudaGraphConditionalHa
                                       use_cond);
     count_launch(1);
     breplace_kernel<<<bgrid(h, n), 256, 0, s>>>(bvec(h), st.replace, h->r, h->rt, L0.M, L0.moff,
-                                                h->nlev > 1 ? L0.u : nullptr);
+                                                (h->nlev > 1 && !blocks) ? L0.u : nullptr);
     count_launch(1);
+    if (h->nlev > 1 && blocks) {
+        bblock_apply_kernel<<<bgrid(h, n), 256, 0, s>>>(bvec(h), st.inst_active, L0.Mb, L0.moff,
+                                                        h->r, L0.u);
+        count_launch(1);
+    }
     AMG_TRY_CUDA(cudaGetLastError());
     return AMG_OK;
 }
@@ -1486,6 +1573,27 @@ static int bsetup_impl(amg_batch h, const amg_bsr *A, const double *const *B, co
                 AMG_TRY_CUDA(cudaMemcpyAsync(D.M + moff[i], h->inst[i]->lv[l].M,
                                              sizeof(double) * h->inst[i]->lv[l].n(),
                                              cudaMemcpyDeviceToDevice, s));
+        if (h->prm.smoother == AMG_SMOOTH_BJACOBI) {
+            // the instances' block damped Jacobi blocks, br x br per block row
+            // (br = 3 on level 0, 6 below), instance i's from moff[i] * br
+            int br = 0;
+            for (int i = 0; i < ni; ++i)
+                if (moff[i] >= 0) br = h->inst[i]->lv[l].A.br;
+            if (br > 0) {
+                AMG_TRY(h->mem.alloc_n(&D.Mb, (size_t)std::max<int64_t>(mlen * br, 1)));
+                for (int i = 0; i < ni; ++i) {
+                    if (moff[i] < 0) continue;
+                    const Level &Li = h->inst[i]->lv[l];
+                    if (!Li.Mb || Li.A.br != br) {
+                        set_error("instance %d: level %d has no %dx%d smoother blocks", i, l, br, br);
+                        return AMG_ERR_STATE;
+                    }
+                    AMG_TRY_CUDA(cudaMemcpyAsync(D.Mb + moff[i] * br, Li.Mb,
+                                                 sizeof(double) * Li.n() * br,
+                                                 cudaMemcpyDeviceToDevice, s));
+                }
+            }
+        }
         const size_t vl = (size_t)std::max<int64_t>(len, 1);
         if (l > 0) AMG_TRY(h->mem.alloc_n(&D.f, vl));
         AMG_TRY(h->mem.alloc_n(&D.u, vl));
@@ -1663,9 +1771,9 @@ int amg_batch_setup(int32_t ninst, const amg_bsr *A, const double *const *B, con
     amg_params_default(&p);
     if (prm) p = *prm;
     if (p.precision == AMG_PREC_BF16 || p.npre != 1 || p.npost != 1 ||
-        p.smoother != AMG_SMOOTH_SPAI0) {
+        (p.smoother != AMG_SMOOTH_SPAI0 && p.smoother != AMG_SMOOTH_BJACOBI)) {
         set_error("the batched solve runs FP64, emulated-FP64 or FP32 V(1,1) cycles with the "
-                  "SPAI0 smoother");
+                  "SPAI0 or block Jacobi smoother");
         return AMG_ERR_ARG;
     }
     auto t0 = std::chrono::steady_clock::now();
@@ -1754,7 +1862,11 @@ int amg_batch_solve(amg_batch h, const double *const *F, double *const *U, doubl
     bstart_kernel<<<1, BS_T, 0, s>>>(h->ngl, st, st.nf, st.res, tol);
     binit_flags_kernel<<<1, BS_T, 0, s>>>(ni, h->goff, st);
     count_launch(2);
-    if (h->nlev > 1) {
+    if (h->nlev > 1 && L0.Mb) {
+        bblock_apply_kernel<<<bgrid(h, L0.len), 256, 0, s>>>(bvec(h), h->all_on, L0.Mb, L0.moff,
+                                                             h->r, L0.u);
+        count_launch(1);
+    } else if (h->nlev > 1) {
         bscale_kernel<<<bgrid(h, L0.len), 256, 0, s>>>(bvec(h), h->r, L0.M, L0.moff, L0.u);
         count_launch(1);
     }

@@ -64,12 +64,15 @@ def test_batch_matches_oracle_per_rhs():
             assert np.linalg.norm(u - uo) <= 1e-7 * np.linalg.norm(uo), (i, j)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32", "fp64_bjacobi", "fp32_bjacobi"])
 def test_instance_in_batch_equals_instance_alone(prec):
-    """In every V-cycle precision (the coarse solve included), an (instance,
-    rhs) pair gives bitwise the same iterates in the batch as alone."""
+    """In every V-cycle precision (the coarse solve included) and with either
+    smoother, an (instance, rhs) pair gives bitwise the same iterates in the
+    batch as alone."""
+    bj = {"smoother": amg.SMOOTH_BJACOBI}
     kw = {"fp64": {}, "df64": {"precision": amg.PREC_DF64},
-          "fp32": {"precision": amg.PREC_FP32}}[prec]
+          "fp32": {"precision": amg.PREC_FP32}, "fp64_bjacobi": bj,
+          "fp32_bjacobi": dict(bj, precision=amg.PREC_FP32)}[prec]
     inst = _instances()
     mats, Bs, nrhs, F = [], [], [], []
     for p, k in inst:
@@ -87,6 +90,35 @@ def test_instance_in_batch_equals_instance_alone(prec):
             assert it1[0][0] == its[i][j]
             assert torch.equal(U1[0][0], U[i][j]), (i, j)
             assert res1[0][0] == res[i][j]
+
+
+def test_batch_with_block_jacobi_matches_oracle_per_rhs():
+    """Block damped Jacobi in the batched V-cycle (block smoothing epilogue,
+    block pre-smoothing in the restriction, level-0 block product): every
+    (instance, rhs) within 1e-7 of the oracle's block Jacobi solve, iterations
+    within +-1, and fewer iterations than the SPAI0 batch in total."""
+    inst = _instances()
+    mats, Bs, nrhs, F = [], [], [], []
+    for p, k in inst:
+        m, B = _dev(p)
+        mats.append(m)
+        Bs.append(B)
+        nrhs.append(k)
+        F.append(torch.from_numpy(np.atleast_2d(p.f).copy()).cuda())
+    bat = amg.AMGBatch(mats, Bs, nrhs, coarse_enough=150, smoother=amg.SMOOTH_BJACOBI)
+    U, its, res, st = bat.solve(F, tol=1e-8)
+    assert st == amg.AMG_OK
+    _, its0, _, _ = amg.AMGBatch(mats, Bs, nrhs, coarse_enough=150).solve(F, tol=1e-8)
+    assert sum(map(sum, its)) < sum(map(sum, its0)), (its, its0)
+    for i, (p, k) in enumerate(inst):
+        H = o.Hierarchy(o.from_problem(p), 3, p.B, coarse_enough=150, smoother="bjacobi")
+        fs = np.atleast_2d(p.f)
+        for j in range(k):
+            uo, ito, _ = H.solve(fs[j], tol=1e-8)
+            u = U[i][j].cpu().numpy()
+            assert res[i][j] <= 1e-8
+            assert abs(its[i][j] - ito) <= 1, (i, j, its[i][j], ito)
+            assert np.linalg.norm(u - uo) <= 1e-7 * np.linalg.norm(uo), (i, j)
 
 
 def test_failing_instance_is_named():
