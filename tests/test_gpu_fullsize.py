@@ -125,3 +125,23 @@ def test_bench80_solve_kernels_sampled(bench80):
             rows = rng.choice(ny, size=min(200, ny), replace=False)
             _sampled_rows(C, x, y.cpu().numpy(), rows, (l, "APR"[which]))
         assert nb == G.level_info(l)["nbrows"]
+
+
+@pytest.mark.slow
+def test_bench80_block_jacobi_pcg_matches_oracle(bench80):
+    """The benchmark mesh with the block damped Jacobi smoother (the bench's
+    bjacobi forms): the smoother blocks of every level within 1e-12 of the
+    oracle's, the lambda estimates within 1e-10, and the PCG iterations
+    within +-1 and the solution within 1e-7 of the oracle's block Jacobi
+    solve (the hierarchy is the default one, compared above)."""
+    p, _, _ = bench80
+    H = o.Hierarchy(o.from_problem(p), 3, p.B, smoother="bjacobi")
+    rp, cl, val, B = dev_args(p, torch)
+    G = amg.AMG(rp, cl, val, B, smoother=amg.SMOOTH_BJACOBI)
+    for l in range(H.nlevels - 1):
+        ol, gi = H.level(l), G.level_info(l)
+        assert abs(gi["smoother_lambda"] - ol["bj_lambda"]) <= 1e-10 * ol["bj_lambda"], l
+        gMb = G.export(l)["Mb"]
+        assert np.abs(gMb - ol["Mb"]).max() <= 1e-12 * np.abs(ol["Mb"]).max(), l
+    it, ito = _pcg_parity(H, G, p.f)
+    assert it > 10
