@@ -1,9 +1,9 @@
 // Host-side greedy aggregation on the strong-connection graph of a block
 // matrix: the coarsening step of Alg. 1 ("construct P_i from A_i"), with the
-// point-wise (node = block row) aggregation of Sec. 4.  The graph is tiny
-// next to the matrix values and the passes are inherently sequential, so
-// this one step of the setup runs on the host; the strength flags come from
-// the device and the aggregate map goes back to it.
+// point-wise (node = block row) aggregation of Sec. 4.  The passes are
+// inherently sequential, so this one step of the setup runs on the host; the
+// device sends each node's strong neighbours (column order) and the
+// aggregate map goes back to it.
 //
 // Three passes over the nodes in ascending order:
 //   1. a free node all of whose strong neighbours are free becomes the root
@@ -21,46 +21,41 @@
 
 namespace amg {
 
-int aggregate_host(int nn, const int *row_ptr, const int *col, const uint8_t *strong, int *agg,
-                   int *nagg)
+// srp[nn + 1], scol: node i's strong neighbours are scol[srp[i] .. srp[i+1])
+int aggregate_host(int nn, const int *srp, const int *scol, int *agg, int *nagg)
 {
     constexpr int kUnassigned = -1;
     constexpr int kLonely = -2;
     std::vector<char> root_pass(nn, 0);  // placed during pass 1
-    for (int node = 0; node < nn; ++node) {
-        int links = 0;
-        for (int e = row_ptr[node]; e < row_ptr[node + 1]; ++e) links += strong[e] ? 1 : 0;
-        agg[node] = links ? kUnassigned : kLonely;
-    }
+    for (int node = 0; node < nn; ++node) agg[node] = srp[node + 1] > srp[node] ? kUnassigned : kLonely;
     int count = 0;
     for (int node = 0; node < nn; ++node) {  // pass 1
         if (agg[node] != kUnassigned) continue;
         bool neighbourhood_free = true;
-        for (int e = row_ptr[node]; e < row_ptr[node + 1] && neighbourhood_free; ++e)
-            if (strong[e] && agg[col[e]] != kUnassigned) neighbourhood_free = false;
+        for (int e = srp[node]; e < srp[node + 1] && neighbourhood_free; ++e)
+            if (agg[scol[e]] != kUnassigned) neighbourhood_free = false;
         if (!neighbourhood_free) continue;
         agg[node] = count;
         root_pass[node] = 1;
-        for (int e = row_ptr[node]; e < row_ptr[node + 1]; ++e)
-            if (strong[e]) {
-                agg[col[e]] = count;
-                root_pass[col[e]] = 1;
-            }
+        for (int e = srp[node]; e < srp[node + 1]; ++e) {
+            agg[scol[e]] = count;
+            root_pass[scol[e]] = 1;
+        }
         ++count;
     }
     for (int node = 0; node < nn; ++node) {  // pass 2
         if (agg[node] != kUnassigned) continue;
-        for (int e = row_ptr[node]; e < row_ptr[node + 1]; ++e)
-            if (strong[e] && root_pass[col[e]]) {
-                agg[node] = agg[col[e]];
+        for (int e = srp[node]; e < srp[node + 1]; ++e)
+            if (root_pass[scol[e]]) {
+                agg[node] = agg[scol[e]];
                 break;
             }
     }
     for (int node = 0; node < nn; ++node) {  // pass 3
         if (agg[node] != kUnassigned) continue;
         agg[node] = count;
-        for (int e = row_ptr[node]; e < row_ptr[node + 1]; ++e)
-            if (strong[e] && agg[col[e]] == kUnassigned) agg[col[e]] = count;
+        for (int e = srp[node]; e < srp[node + 1]; ++e)
+            if (agg[scol[e]] == kUnassigned) agg[scol[e]] = count;
         ++count;
     }
     for (int node = 0; node < nn; ++node)

@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstdio>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -292,8 +293,16 @@ int compute_strength(const BsrD &A, double eps, uint8_t *strong, cudaStream_t s)
 // aggregate count (and, if asked, the number of rounds) to the host.
 int aggregate_mis2(const BsrD &A, const uint8_t *strong, int *agg, int *nagg_host, int *rounds_host,
                    DevArena &tmp, cudaStream_t s);
-int aggregate_host(int nn, const int *row_ptr, const int *col, const uint8_t *strong,
-                   int *agg, int *nagg);   // host arrays
+// The strong links of a level's node graph on the host: per node its strong
+// neighbours in column order (CSR, host memory, not zero-filled).
+struct HostStrongGraph {
+    int nn = 0;
+    std::unique_ptr<int[]> srp, scol;
+};
+int strong_graph_to_host(const BsrD &A, const uint8_t *strong, DevArena &tmp, cudaStream_t s,
+                         HostStrongGraph *out);
+// greedy aggregation (aggregate.cpp) on the strong graph; agg[nn] host
+int aggregate_host(int nn, const int *srp, const int *scol, int *agg, int *nagg);
 int build_transfer(const BsrD &A, const double *B, int ns, const uint8_t *strong,
                    const int *agg_h, int nagg, double relax, DevArena &keep, DevArena &tmp,
                    cudaStream_t s, LevelBuild *out);

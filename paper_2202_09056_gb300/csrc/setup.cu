@@ -174,6 +174,66 @@ int compute_strength(const BsrD &A, double eps, uint8_t *strong, cudaStream_t s)
     return AMG_OK;
 }
 
+// ---------------------------------------------------------------- strong graph to the host
+// The host's greedy aggregation reads, per node, its strong neighbours in
+// column order.  Only those go to the host: per row the strong columns
+// (row order kept), as CSR (srp, scol), instead of the whole pattern and a
+// flag per block.
+__global__ void strong_count_kernel(const int *__restrict__ rp, const uint8_t *__restrict__ strong,
+                                    int nbr, int *__restrict__ cnt)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nbr) return;
+    int c = 0;
+    for (int p = rp[I]; p < rp[I + 1]; ++p) c += strong[p] ? 1 : 0;
+    cnt[I] = c;
+}
+
+__global__ void strong_fill_kernel(const int *__restrict__ rp, const int *__restrict__ col,
+                                   const uint8_t *__restrict__ strong, int nbr,
+                                   const int *__restrict__ srp, int *__restrict__ scol)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nbr) return;
+    int q = srp[I];
+    for (int p = rp[I]; p < rp[I + 1]; ++p)
+        if (strong[p]) scol[q++] = col[p];
+}
+
+int strong_graph_to_host(const BsrD &A, const uint8_t *strong, DevArena &tmp, cudaStream_t s,
+                         HostStrongGraph *out)
+{
+    const int nbr = A.nbr;
+    out->nn = nbr;
+    out->srp.reset(new int[(size_t)nbr + 1]);
+    int *cnt = nullptr, *srp = nullptr, *scol = nullptr;
+    AMG_TRY(tmp.alloc_n(&cnt, (size_t)std::max(nbr, 1)));
+    AMG_TRY(tmp.alloc_n(&srp, (size_t)nbr + 1));
+    if (nbr > 0) {
+        strong_count_kernel<<<nblk(nbr), T1D, 0, s>>>(A.row_ptr, strong, nbr, cnt);
+        ::amg::count_launch(1);
+    }
+    int total = 0;
+    AMG_TRY(exclusive_scan_i32(cnt, srp, nbr, &total, tmp, s));
+    AMG_TRY(tmp.alloc_n(&scol, (size_t)std::max(total, 1)));
+    if (nbr > 0 && total > 0) {
+        strong_fill_kernel<<<nblk(nbr), T1D, 0, s>>>(A.row_ptr, A.col, strong, nbr, srp, scol);
+        ::amg::count_launch(1);
+    }
+    AMG_TRY_CUDA(cudaGetLastError());
+    out->scol.reset(new int[(size_t)std::max(total, 1)]);
+    AMG_TRY_CUDA(cudaMemcpyAsync(out->srp.get(), srp, sizeof(int) * ((size_t)nbr + 1),
+                                 cudaMemcpyDeviceToHost, s));
+    if (total > 0)
+        AMG_TRY_CUDA(cudaMemcpyAsync(out->scol.get(), scol, sizeof(int) * (size_t)total,
+                                     cudaMemcpyDeviceToHost, s));
+    AMG_TRY_CUDA(cudaStreamSynchronize(s));
+    tmp.release(cnt);
+    tmp.release(srp);
+    tmp.release(scol);
+    return AMG_OK;
+}
+
 // ---------------------------------------------------------------- tentative P
 template <class T> __device__ __forceinline__ T wsum(T v)
 {

@@ -798,15 +798,9 @@ static int setup_levels_scalar(amg_handle h, DevArena &tmp, Lap &lap)
             AMG_TRY_CUDA(cudaStreamSynchronize(s));
             tmp.release(dagg);
         } else {
-            std::vector<int> rp(nn + 1), cl(std::max<int64_t>(G.nnzb, 1));
-            std::vector<uint8_t> sf(std::max<int64_t>(G.nnzb, 1));
-            AMG_TRY_CUDA(cudaMemcpyAsync(rp.data(), G.row_ptr, sizeof(int) * (nn + 1),
-                                         cudaMemcpyDeviceToHost, s));
-            AMG_TRY_CUDA(cudaMemcpyAsync(cl.data(), G.col, sizeof(int) * G.nnzb,
-                                         cudaMemcpyDeviceToHost, s));
-            AMG_TRY_CUDA(cudaMemcpyAsync(sf.data(), C.strong, G.nnzb, cudaMemcpyDeviceToHost, s));
-            AMG_TRY_CUDA(cudaStreamSynchronize(s));
-            AMG_TRY(aggregate_host(nn, rp.data(), cl.data(), sf.data(), agg.data(), &nagg));
+            HostStrongGraph hg;
+            AMG_TRY(strong_graph_to_host(G, C.strong, tmp, s, &hg));
+            AMG_TRY(aggregate_host(nn, hg.srp.get(), hg.scol.get(), agg.data(), &nagg));
         }
         h->mem.release(G.row_ptr);
         h->mem.release(G.col);
@@ -962,15 +956,9 @@ int amg::setup_impl(amg_handle h, const amg_bsr *Ain, const double *B)
             AMG_TRY_CUDA(cudaStreamSynchronize(s));
             tmp.release(dagg);
         } else {
-            std::vector<int> rp(nn + 1), cl(std::max<int64_t>(C.A.nnzb, 1));
-            std::vector<uint8_t> sf(std::max<int64_t>(C.A.nnzb, 1));
-            AMG_TRY_CUDA(cudaMemcpyAsync(rp.data(), C.A.row_ptr, sizeof(int) * (nn + 1),
-                                         cudaMemcpyDeviceToHost, s));
-            AMG_TRY_CUDA(cudaMemcpyAsync(cl.data(), C.A.col, sizeof(int) * C.A.nnzb,
-                                         cudaMemcpyDeviceToHost, s));
-            AMG_TRY_CUDA(cudaMemcpyAsync(sf.data(), C.strong, C.A.nnzb, cudaMemcpyDeviceToHost, s));
-            AMG_TRY_CUDA(cudaStreamSynchronize(s));
-            AMG_TRY(aggregate_host(nn, rp.data(), cl.data(), sf.data(), agg.data(), &nagg));
+            HostStrongGraph hg;
+            AMG_TRY(strong_graph_to_host(C.A, C.strong, tmp, s, &hg));
+            AMG_TRY(aggregate_host(nn, hg.srp.get(), hg.scol.get(), agg.data(), &nagg));
         }
         lap(1);
         if (stop_coarsening(prm, (int)h->lv.size(), n, nn, nagg, h->ns)) break;
