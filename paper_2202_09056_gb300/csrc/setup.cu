@@ -646,6 +646,77 @@ __global__ void __launch_bounds__(PV_CT) p_values_cta_kernel(
     }
 }
 
+// The same per-row product for rows of at most 32 blocks (the finest level,
+// 27 on a hex mesh): the row's A blocks and the tentative blocks of its
+// columns are staged in shared memory, and the first warp sorts the row's
+// entries by output block (each lane one entry: its rank among the entries
+// of the same output block by __match_any_sync, the blocks' offsets by a warp
+// scan of their counts), so each output entry runs over the entries of its
+// own block only, in ascending order.  In p_values_cta_kernel every task
+// scanned the whole row, and the FMAs of the tasks of a warp (two or three
+// output blocks) were issued once per entry of any of them: the FP64 pipe
+// spent several times the products' work.  The same terms in the same order
+// as there (the same bits).  One CTA of PV_ST threads per block row.
+constexpr int PV_ST = 64;
+template <int B, int NS>
+__global__ void __launch_bounds__(PV_ST) p_values_staged_kernel(
+    const int *__restrict__ rp, const int *__restrict__ col, const double *__restrict__ val,
+    const int *__restrict__ agg, const double *__restrict__ ptent, const double *__restrict__ d,
+    double omega, const int *__restrict__ prp, const int *__restrict__ pcol,
+    double *__restrict__ pval)
+{
+    __shared__ double sa[32 * B * B], sp[32 * B * NS];
+    __shared__ int list[32], first[33];
+    const int I = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const int a0 = rp[I], na = rp[I + 1] - a0;  // <= 32 (checked on the host)
+    const int p0 = prp[I], np = prp[I + 1] - p0;  // <= na
+    for (int e = tid; e < na * B * B; e += PV_ST) sa[e] = val[(int64_t)a0 * B * B + e];
+    for (int e = tid; e < na * B * NS; e += PV_ST) {
+        const int t = e / (B * NS);
+        sp[e] = ptent[(int64_t)col[a0 + t] * B * NS + e % (B * NS)];
+    }
+    if (tid < 32) {
+        int sl = -1;
+        if (lane < na) {
+            const int g = agg[col[a0 + lane]];
+            const int pos = g >= 0 ? find_sorted(pcol, p0, p0 + np, g) : p0 + np;
+            sl = (pos < p0 + np && pcol[pos] == g) ? pos - p0 : -1;
+        }
+        const unsigned same = __match_any_sync(0xffffffffu, sl);
+        const int rank = __popc(same & ((1u << lane) - 1u));
+        // entries per output block (lane s counts block s), then offsets
+        int cnt = 0;
+        for (int t = 0; t < na; ++t) cnt += (__shfl_sync(0xffffffffu, sl, t) == lane) ? 1 : 0;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        first[lane + 1] = incl;
+        if (lane == 0) first[0] = 0;
+        __syncwarp();
+        if (sl >= 0) list[first[sl] + rank] = lane;
+    }
+    __syncthreads();
+    const int gI = agg[I];
+    for (int task = tid; task < np * B * NS; task += PV_ST) {
+        const int sl = task / (B * NS), e = task % (B * NS), r = e / NS, q = e % NS;
+        double acc = 0.0;
+        for (int j = first[sl]; j < first[sl + 1]; ++j) {
+            const int t = list[j];
+            const double *blk = sa + t * B * B + r * B;
+            const double *pt = sp + t * B * NS + q;
+#pragma unroll
+            for (int c = 0; c < B; ++c) acc += blk[c] * pt[c * NS];
+        }
+        const double dr = d[(int64_t)I * B + r];
+        const double sc = (dr != 0.0) ? omega / dr : 0.0;
+        const double own = (gI == pcol[p0 + sl]) ? ptent[((int64_t)I * B + r) * NS + q] : 0.0;
+        pval[(int64_t)(p0 + sl) * B * NS + e] = own - sc * acc;
+    }
+}
+
 // ---------------------------------------------------------------- transpose
 __global__ void col_count_kernel(const int *__restrict__ col, int64_t nnz, int *__restrict__ cnt)
 {
@@ -1291,7 +1362,16 @@ int build_transfer(const BsrD &A, const double *B, int ns, const uint8_t *strong
         AMG_TRY_CUDA(cudaStreamSynchronize(s));
         tmp.release(mx);
     }
-    if (nnzp > 0 && amax <= 12 * 1024) {
+    if (nnzp > 0 && amax <= 32 && b == 3 && (ns == 6 || ns == 3)) {
+        if (ns == 6)
+            p_values_staged_kernel<3, 6><<<nn, PV_ST, 0, s>>>(
+                A.row_ptr, A.col, A.val, out->agg, ptent, d, out->omega, P.row_ptr, P.col, P.val);
+        else
+            p_values_staged_kernel<3, 3><<<nn, PV_ST, 0, s>>>(
+                A.row_ptr, A.col, A.val, out->agg, ptent, d, out->omega, P.row_ptr, P.col, P.val);
+        ::amg::count_launch(1);
+        AMG_TRY_CUDA(cudaGetLastError());
+    } else if (nnzp > 0 && amax <= 12 * 1024) {
 #define AMG_PVALS(B_, NS_)                                                                   \
     p_values_cta_kernel<B_, NS_><<<nn, PV_CT, sizeof(int) * amax, s>>>(                       \
         A.row_ptr, A.col, A.val, out->agg, ptent, d, out->omega, P.row_ptr, P.col, P.val)
