@@ -118,3 +118,31 @@ def test_rejections():
     assert e.value.status == amg.AMG_ERR_STATE
     with pytest.raises(amg.AmgError):  # the batch takes SPAI0 or block Jacobi only
         amg.AMGBatch([args[:3]], [args[3]], [1], coarse_enough=100, smoother=amg.SMOOTH_ILU0)
+
+
+@pytest.mark.parametrize("variant", ["translations", "mis2"])
+def test_block_jacobi_with_translations_or_mis2(variant):
+    """Block Jacobi on the other hierarchies: the three translations as the
+    near-nullspace (3x3 blocks on every level) and MIS-2 aggregation; PCG
+    against the oracle's block Jacobi solve on the same hierarchy."""
+    p = q.make_problem((11, 10, 12), traction=(0, 0, -1), inclusion_frac=0.2)
+    if variant == "translations":
+        B = np.zeros((p.ndof, 3))
+        for c in range(3):
+            B[c::3, c] = 1.0
+        okw, gkw = {}, {}
+    else:
+        B = p.B
+        okw, gkw = {"aggregation": "mis2"}, {"aggregation": amg.AGG_MIS2}
+    H = o.Hierarchy(o.from_problem(p), 3, B, coarse_enough=200, smoother="bjacobi", **okw)
+    rp, cl, val, _ = dev_args(p, torch)
+    G = amg.AMG(rp, cl, val, torch.from_numpy(B).cuda(), coarse_enough=200,
+                smoother=amg.SMOOTH_BJACOBI, **gkw)
+    assert G.nlevels == H.nlevels >= 2
+    for l in range(H.nlevels - 1):
+        assert G.level_info(l)["bs"] == H.level(l)["b"]
+        assert rel(G.export(l)["Mb"], H.level(l)["Mb"]) <= 1e-12, l
+    uo, ito, _ = H.solve(p.f, tol=1e-8, maxiter=3000)
+    u, it, res, st = G.solve(torch.from_numpy(p.f).cuda(), tol=1e-8, maxiter=3000)
+    assert st == amg.AMG_OK and res <= 1e-8 and abs(it - ito) <= 1, (it, ito)
+    assert np.linalg.norm(u.cpu().numpy() - uo) <= 1e-7 * np.linalg.norm(uo)
