@@ -61,8 +61,9 @@ constexpr int SELL_THREADS = 128;
 
 // Register budget: the kernel is compiled for minb resident CTAs per SM
 // (65536 / (128 x minb) registers per thread): 12 (40 registers) for 3x3
-// blocks, 8 (64) for the others, whose paired FP64 loads hold 18-36 values
-// (at 10 CTAs the 6x3 restriction spilled and ran 7 % slower).  Grid: up to cap CTAs per SM,
+// blocks, 8 (64) for the others (6 for FP64 6x6, below), whose paired FP64
+// loads hold 18-36 values (at 10 CTAs the 6x3 restriction spilled and ran
+// 7 % slower).  Grid: up to cap CTAs per SM,
 // measured on the 80^3 hierarchy.  The fine-level shapes (3-row blocks, one
 // lane per row, uniform slices) run fastest oversubscribed, one slice group
 // per CTA with the hardware scheduler balancing; the 6x6 coarse operators
@@ -93,8 +94,24 @@ template <class VT> __host__ __device__ constexpr int sell_minb_dot(int br, int 
                : sell_minb_t<VT>(br, bc);
 }
 
+// A 6x6 FP64 block is 72 registers of values: those kernels are compiled
+// for 6 resident CTAs per SM (80 registers) rather than 8 (64), which took
+// level-1 A 113 -> 111 us, level-1 P 35 -> 33 us and the level-2 P and R
+// 17-18 -> 15-17 us at 80^3 (the rows' arithmetic unchanged).  Launches
+// whose rows span several warps, and the prolongations, size their grid to
+// that one resident wave; the other 6x6 launches keep 8 CTAs per SM, the
+// ones past the first wave taking the tail of the warp-strided loop.
+template <class VT> __host__ __device__ constexpr bool sell_roomy(int br, int bc)
+{
+    return std::is_same<VT, double>::value && br == 6 && bc == 6;
+}
+template <class VT> __host__ __device__ constexpr int sell_minb_k(int br, int bc, int dot)
+{
+    return sell_roomy<VT>(br, bc) ? 6 : sell_minb_dot<VT>(br, bc, dot);
+}
+
 template <int BR, int BC, class VT, class TV, int MODE, int DOT, bool WIDE>
-__global__ void __launch_bounds__(SELL_THREADS, sell_minb_dot<VT>(BR, BC, DOT)) sell_spmv_kernel(SellArgs<TV> a)
+__global__ void __launch_bounds__(SELL_THREADS, sell_minb_k<VT>(BR, BC, DOT)) sell_spmv_kernel(SellArgs<TV> a)
 {
     using Acc = TV;
     constexpr int BB = BR * BC;
@@ -365,7 +382,11 @@ int launch_sell(const Sell<VT> &A, int mode, int dot, SellArgs<TV> a, const Geom
     a.col = A.col;
     a.val = A.val;
     a.perm = A.perm;
-    int grid = sell_grid_cap(A.nslices, sell_cap_t<VT>(A.br, A.bc), g);
+    int grid = sell_grid_cap(A.nslices,
+                             sell_roomy<VT>(A.br, A.bc) && (A.G > 32 || mode == SPMV_AXPY)
+                                 ? 6
+                                 : sell_cap_t<VT>(A.br, A.bc),
+                             g);
     if (max_grid > 0 && grid > max_grid) grid = max_grid;
     if (((uintptr_t)a.x & (sizeof(TV) - 1)) != 0) {
         set_error("the sliced SpMV needs x aligned to its element size");
