@@ -97,17 +97,21 @@ template <class VT> __host__ __device__ constexpr int sell_minb_dot(int br, int 
 // A 6x6 FP64 block is 72 registers of values: those kernels are compiled
 // for 6 resident CTAs per SM (80 registers) rather than 8 (64), which took
 // level-1 A 113 -> 111 us, level-1 P 35 -> 33 us and the level-2 P and R
-// 17-18 -> 15-17 us at 80^3 (the rows' arithmetic unchanged).  Launches
-// whose rows span several warps, and the prolongations, size their grid to
-// that one resident wave; the other 6x6 launches keep 8 CTAs per SM, the
-// ones past the first wave taking the tail of the warp-strided loop.
+// 17-18 -> 15-17 us at 80^3 (the rows' arithmetic unchanged); 5 CTAs (96
+// registers) gained nothing more.  The FP64 6x3 restriction (36 registers
+// of values) likewise runs at 6: 112.7 -> 110.8 us.  Launches whose rows
+// span several warps, and the 6x6 prolongations, size their grid to that
+// one resident wave; the other launches keep their grid (8 or 16 CTAs per
+// SM), the CTAs past the first wave taking the tail of the work.
 template <class VT> __host__ __device__ constexpr bool sell_roomy(int br, int bc)
 {
     return std::is_same<VT, double>::value && br == 6 && bc == 6;
 }
 template <class VT> __host__ __device__ constexpr int sell_minb_k(int br, int bc, int dot)
 {
-    return sell_roomy<VT>(br, bc) ? 6 : sell_minb_dot<VT>(br, bc, dot);
+    return (sell_roomy<VT>(br, bc) || (std::is_same<VT, double>::value && br == 6 && bc == 3))
+               ? 6
+               : sell_minb_dot<VT>(br, bc, dot);
 }
 
 template <int BR, int BC, class VT, class TV, int MODE, int DOT, bool WIDE>
