@@ -5,7 +5,9 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstdio>
+#include <exception>
 #include <memory>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -17,6 +19,25 @@ namespace amg {
 void set_error(const char *fmt, ...);
 void clear_error();
 const char *last_error();
+
+// f() with any C++ exception (host memory exhausted in a std::vector, a
+// thread that cannot start) turned into an error status: nothing unwinds
+// through the C ABI or out of a worker thread.
+template <class F> int no_throw(F &&f)
+{
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        set_error("host memory exhausted");
+        return AMG_ERR_LIMIT;
+    } catch (const std::exception &e) {
+        set_error("%s", e.what());
+        return AMG_ERR_STATE;
+    } catch (...) {
+        set_error("unexpected exception");
+        return AMG_ERR_STATE;
+    }
+}
 
 // Kernel launch accounting: every launch site reports itself; launches
 // recorded into a graph under capture are counted per graph execution.

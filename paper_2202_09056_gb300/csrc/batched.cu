@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <system_error>
 #include <thread>
 
 #include "amg_internal.cuh"
@@ -1471,7 +1472,7 @@ static int setup_instances(amg_batch h, const amg_bsr *A, const double *const *B
             } else {
                 x->stream = ws;
                 x->mem.stream = ws;
-                st = setup_impl(x, &A[i], B[i]);
+                st = no_throw([&] { return setup_impl(x, &A[i], B[i]); });
                 cudaStreamSynchronize(ws);  // nothing of the instance stays queued on ws
                 x->stream = s;
                 x->mem.stream = s;
@@ -1485,7 +1486,14 @@ static int setup_instances(amg_batch h, const amg_bsr *A, const double *const *B
     };
     std::vector<std::thread> pool;
     pool.reserve(nw);
-    for (int w = 0; w < nw; ++w) pool.emplace_back(worker, w);
+    for (int w = 0; w < nw; ++w) {
+        try {
+            pool.emplace_back(worker, w);
+        } catch (const std::system_error &) {
+            break;  // fewer threads: those started take every instance
+        }
+    }
+    if (pool.empty()) worker(0);  // no thread could be started: this one does the work
     for (std::thread &t : pool) t.join();
     cudaEventDestroy(ready);
     for (int i = 0; i < ni; ++i)
@@ -1790,7 +1798,7 @@ int amg_batch_setup(int32_t ninst, const amg_bsr *A, const double *const *B, con
     h->stream = (cudaStream_t)stream;
     h->mem.stream = h->stream;
     h->ninst = ninst;
-    int st = bsetup_impl(h, A, B, nrhs);
+    int st = no_throw([&] { return bsetup_impl(h, A, B, nrhs); });
     if (st < 0) {
         std::string msg = amg::last_error();
         bdestroy(h);

@@ -1178,7 +1178,7 @@ int amg_setup(const amg_bsr *A, const double *B, int32_t nb_ns, const amg_params
     h->stream = (cudaStream_t)stream;
     h->mem.stream = h->stream;
     AllocScope scope(h->allocator());
-    int st = setup_impl(h, A, B);
+    int st = no_throw([&] { return setup_impl(h, A, B); });
     if (st < 0) {
         std::string msg = amg::last_error();
         destroy_handle(h);
