@@ -299,7 +299,7 @@ template <> VLevel<__nv_bfloat16, float> view<__nv_bfloat16, float>(Level &L)
 
 template <class TV>
 static int launch_vec_dot(amg_handle h, const TV *x, const TV *y, int64_t n, double *part,
-                          cudaStream_t s);
+                          cudaStream_t s, int *grid_out = nullptr);
 
 // Block ILU(0) smoothing step x = ILU_l^-1 r and y = a + b (FP64 V-cycle only).
 template <class TV> static int ilu_smooth(amg_handle h, int l, const TV *r, TV *x, cudaStream_t s);
@@ -328,7 +328,8 @@ template <> int vec_add<float>(const float *, const float *, float *, int64_t, c
 // in VT and vectors in TV.  Level 0's u must already hold the first
 // pre-smoothing sweep M_0 f0 (or zero without pre-smoothing).  With
 // rz_partials, the last level-0 kernel also leaves the per-CTA partial sums
-// of f0 . z0 (accumulated in FP64).
+// of f0 . z0 (accumulated in FP64), and *rz_np their number (the grid of
+// the kernel that wrote them).
 // The learned blocks in the V-cycle's vector precision.
 // The smoother blocks of level l, in the V-cycle vectors' precision, or null
 // when the level smooths with the SPAI0 diagonal: block damped Jacobi blocks
@@ -348,7 +349,8 @@ template <> const float *blocks_ptr<float>(const amg_handle h, size_t l)
 }
 
 template <class VT, class TV>
-static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials, cudaStream_t s)
+static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials, cudaStream_t s,
+                         int *rz_np = nullptr)
 {
     const int L = (int)h->lv.size() - 1;
     const int npre = h->prm.npre, npost = h->prm.npost;
@@ -416,7 +418,8 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
         const TV *fL = (L == 0) ? f0 : Cc.f;
         TV *zL = (L == 0) ? z0 : Cc.z;
         AMG_TRY(launch_coarse_gemv<TV>(h->Ainv, h->nc, fL, zL, g, s));
-        if (L == 0 && rz_partials) AMG_TRY(launch_vec_dot<TV>(h, f0, z0, h->nc, rz_partials, s));
+        if (L == 0 && rz_partials)
+            AMG_TRY(launch_vec_dot<TV>(h, f0, z0, h->nc, rz_partials, s, rz_np));
     }
     for (int l = L - 1; l >= 0; --l) {
         VLevel<VT, TV> &C = V[l];
@@ -442,7 +445,7 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
                 AMG_TRY(vec_add<TV>(u, t, sweep == npost - 1 ? zl : u, C.n, s));
             }
             if (npost > 0 && l == 0 && rz_partials)
-                AMG_TRY(launch_vec_dot<TV>(h, f0, z0, C.n, rz_partials, s));
+                AMG_TRY(launch_vec_dot<TV>(h, f0, z0, C.n, rz_partials, s, rz_np));
         }
         const TV *w = u;
         const TV *mb = blocks_ptr<TV>(h, l);
@@ -458,26 +461,18 @@ static int record_vcycle(amg_handle h, const TV *f0, TV *z0, double *rz_partials
             a.y = out;
             a.partials = rz_partials;
             const int dot = (l == 0 && last && rz_partials) ? DOT_FY : DOT_NONE;
-            AMG_TRY((launch_sell<VT, TV>(*C.A, blocks ? SPMV_SMOOTHB : SPMV_SMOOTH, dot, a, g, s)));
+            AMG_TRY((launch_sell<VT, TV>(*C.A, blocks ? SPMV_SMOOTHB : SPMV_SMOOTH, dot, a, g, s,
+                                         dot != DOT_NONE ? rz_np : nullptr)));
             w = out;
             t = (out == t) ? u : t;  // ping-pong between u and t
         }
         if (npost == 0) {
             AMG_TRY_CUDA(cudaMemcpyAsync(zl, u, sizeof(TV) * C.n, cudaMemcpyDeviceToDevice, s));
-            if (l == 0 && rz_partials) AMG_TRY(launch_vec_dot<TV>(h, f0, z0, C.n, rz_partials, s));
+            if (l == 0 && rz_partials)
+                AMG_TRY(launch_vec_dot<TV>(h, f0, z0, C.n, rz_partials, s, rz_np));
         }
     }
     return AMG_OK;
-}
-
-// Number of partial sums the level-0 fused r.z leaves (= the grid of the
-// kernel that computes it).
-static int rz_parts(amg_handle h)
-{
-    const Level &L0 = h->lv[0];
-    if (h->lv.size() == 1) return vgrid(h, h->nc);
-    if (h->prm.npost == 0 || h->ilu) return vgrid(h, L0.n());
-    return sell_grid(L0.sA.nslices, L0.sA.br, L0.sA.bc, h->geom);
 }
 
 // One CG iteration, as recorded into the body of the graph.  The outer
@@ -499,8 +494,13 @@ static int record_cg_iteration_t(amg_handle h, cudaStream_t s, cudaGraphConditio
     TV *z0 = f64 ? (TV *)h->z : (TV *)h->zv;
     TV *rv = f64 ? nullptr : (TV *)h->rv;
     // z = V(r), partial r.z
-    AMG_TRY((record_vcycle<VT, TV>(h, f0, z0, h->partials, s)));
-    cg_beta_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, rz_parts(h)); ::amg::count_launch(1);
+    int rz_np = 0;
+    AMG_TRY((record_vcycle<VT, TV>(h, f0, z0, h->partials, s, &rz_np)));
+    if (rz_np < 1) {
+        set_error("the V-cycle left no partial sums of r.z");
+        return AMG_ERR_STATE;
+    }
+    cg_beta_kernel<<<1, FIN_THREADS, 0, s>>>(h->st, h->partials, rz_np); ::amg::count_launch(1);
     cg_direction_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(z0, h->p, h->st, n); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
     int grid = 0;
@@ -557,10 +557,12 @@ static int record_cg_iteration(amg_handle h, cudaStream_t s, cudaGraphConditiona
 
 template <class TV>
 static int launch_vec_dot(amg_handle h, const TV *x, const TV *y, int64_t n, double *part,
-                          cudaStream_t s)
+                          cudaStream_t s, int *grid_out)
 {
-    vec_dot_kernel<TV><<<vgrid(h, n), 256, 0, s>>>(x, y, n, part); ::amg::count_launch(1);
+    const int grid = vgrid(h, n);
+    vec_dot_kernel<TV><<<grid, 256, 0, s>>>(x, y, n, part); ::amg::count_launch(1);
     AMG_TRY_CUDA(cudaGetLastError());
+    if (grid_out) *grid_out = grid;
     return AMG_OK;
 }
 
