@@ -259,28 +259,28 @@ __global__ void __launch_bounds__(BT_MAX) bspmm_kernel(BArgs a)
                         else if (a.y2) a.y2[i] = corr;
                     }
                 }
-                continue;
-            }
+            } else {
 #pragma unroll
-            for (int r = 0; r < BR; ++r)
+                for (int r = 0; r < BR; ++r)
 #pragma unroll
-                for (int t = 0; t < KT; ++t) {
-                    const int k = k0 + t;
-                    if (k >= K) continue;
-                    const int64_t i = yo + ((int64_t)row * BR + r) * K + k;
-                    double out;
-                    if (MODE == SPMV_PLAIN) out = acc[r][t];
-                    else if (MODE == SPMV_RESID) out = a.f[i] - acc[r][t];
-                    else if (MODE == SPMV_SMOOTH)
-                        out = a.x[i] + a.M[a.moff[inst] + (int64_t)row * BR + r] * (a.f[i] - acc[r][t]);
-                    else if (MODE == SPMV_AXPY) out = a.u[i] + acc[r][t];
-                    else out = acc[r][t];
-                    a.y[i] = out;
-                    if (MODE == SPMV_RESTRICT && a.y2) {
-                        const int64_t mo = a.moff[inst];
-                        a.y2[i] = (mo >= 0) ? a.M[mo + (int64_t)row * BR + r] * out : 0.0;
+                    for (int t = 0; t < KT; ++t) {
+                        const int k = k0 + t;
+                        if (k >= K) continue;
+                        const int64_t i = yo + ((int64_t)row * BR + r) * K + k;
+                        double out;
+                        if (MODE == SPMV_PLAIN) out = acc[r][t];
+                        else if (MODE == SPMV_RESID) out = a.f[i] - acc[r][t];
+                        else if (MODE == SPMV_SMOOTH)
+                            out = a.x[i] + a.M[a.moff[inst] + (int64_t)row * BR + r] * (a.f[i] - acc[r][t]);
+                        else if (MODE == SPMV_AXPY) out = a.u[i] + acc[r][t];
+                        else out = acc[r][t];
+                        a.y[i] = out;
+                        if (MODE == SPMV_RESTRICT && a.y2) {
+                            const int64_t mo = a.moff[inst];
+                            a.y2[i] = (mo >= 0) ? a.M[mo + (int64_t)row * BR + r] * out : 0.0;
+                        }
                     }
-                }
+            }
         }
     }
 }
